@@ -1,0 +1,102 @@
+"""Reference V-cycle (Alg. 1) on the assembled Galerkin hierarchy — oracle, test infra.
+
+The paper's Alg. 1 ("Standard GMG V-Cycle"), step by step, with the smoother replaced by
+damped block-Jacobi or Chebyshev (the smoother choice of this build; the paper's own
+update form u_i <- u_i + omega D_i^{-1} r_i is Sec. 4.6 "Parallel Smoothing", applied to
+all nodes at once instead of colour by colour):
+
+    for l = 1..L-1: pre-smooth; r^l = f^l - K^l u^l; f^{l+1} = R r^l; u^{l+1} = 0
+    coarsest solve
+    for l = L-1..1: u^l += P u^{l+1}; post-smooth
+
+D^l is the block diagonal of K^l (D x D node blocks). The coarsest solve (reading of
+Alg. 1's GS(K^L ...) step, replaced by an exact solve) is the solution of
+(K^L + rho J) u = f^L, J the per-component all-ones coupling and rho the mean diagonal of
+K^L: for right-hand sides orthogonal to translations this is the zero-mean solution of
+K^L u = f^L.
+
+Chebyshev: one polynomial of degree k = nu (the sweep count, so that both smoothers apply K
+the same number of times) on D^{-1}K over [a, b] = [lmax/ratio, upper*lmax]:
+theta = (b+a)/2, delta = (b-a)/2, sigma = theta/delta, rho_0 = 1/sigma; d = D^{-1} r/theta;
+then k times: u += d; if not last: r = f - K u, rho' = 1/(2 sigma - rho),
+d = rho' rho d + (2 rho'/delta) D^{-1} r, rho = rho'.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def block_diag_inverse(K, D: int):
+    """Inverse of the D x D node blocks on the diagonal of K, as a sparse matrix."""
+    n = K.shape[0] // D
+    Kd = K.tocsr()
+    blocks = np.zeros((n, D, D))
+    for i in range(D):
+        for j in range(D):
+            rows = np.arange(n) * D + i
+            cols = np.arange(n) * D + j
+            blocks[:, i, j] = np.asarray(Kd[rows, cols]).reshape(-1)
+    inv = np.linalg.inv(blocks)
+    r = (np.arange(n)[:, None, None] * D + np.arange(D)[None, :, None]).repeat(D, axis=2)
+    c = (np.arange(n)[:, None, None] * D + np.arange(D)[None, None, :]).repeat(D, axis=1)
+    return sp.csr_matrix((inv.reshape(-1), (r.reshape(-1), c.reshape(-1))), shape=K.shape)
+
+
+def coarsest_matrix(KL, D: int) -> np.ndarray:
+    A = KL.toarray()
+    n = A.shape[0] // D
+    rho = float(np.mean(np.diag(A)))
+    for c in range(D):
+        idx = np.arange(n) * D + c
+        A[np.ix_(idx, idx)] += rho
+    return A
+
+
+class VCycle:
+    def __init__(self, Ks, Ps, D: int, nu_pre=2, nu_post=2, omega=0.6, smoother="jacobi",
+                 cheb_lmax=None, cheb_ratio=30.0, cheb_upper=1.1):
+        self.Ks, self.Ps, self.D = Ks, Ps, D
+        self.nu_pre, self.nu_post, self.omega = nu_pre, nu_post, omega
+        self.smoother = smoother
+        self.Dinv = [block_diag_inverse(K, D) for K in Ks[:-1]]
+        self.Ainv = np.linalg.inv(coarsest_matrix(Ks[-1], D))
+        self.lmax = cheb_lmax
+        self.ratio, self.upper = cheb_ratio, cheb_upper
+
+    def smooth(self, l: int, u, f, sweeps: int):
+        K, Di = self.Ks[l], self.Dinv[l]
+        if self.smoother == "jacobi":
+            for _ in range(sweeps):
+                u = u + self.omega * (Di @ (f - K @ u))
+            return u
+        lmax = self.lmax[l]
+        b = self.upper * lmax
+        a = lmax / self.ratio
+        theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        d = (Di @ (f - K @ u)) / theta
+        for i in range(sweeps):
+            u = u + d
+            if i == sweeps - 1:
+                break
+            r = f - K @ u
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + (2.0 * rho_new / delta) * (Di @ r)
+            rho = rho_new
+        return u
+
+    def cycle(self, f, u=None, level: int = 0):
+        L = len(self.Ks)
+        if level == L - 1:
+            return self.Ainv @ f
+        if u is None:
+            u = np.zeros_like(f)
+        u = self.smooth(level, u, f, self.nu_pre)
+        r = f - self.Ks[level] @ u
+        fc = self.Ps[level].T @ r
+        uc = self.cycle(fc, None, level + 1)
+        u = u + self.Ps[level] @ uc
+        u = self.smooth(level, u, f, self.nu_post)
+        return u
