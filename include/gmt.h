@@ -1,0 +1,199 @@
+/*
+ * gmt.h — C ABI of the B300 periodic-homogenization library (libgmt.so).
+ *
+ * The library solves the periodic cell problems of a binary voxel cell with a matrix-free
+ * geometric-multigrid V-cycle on a sparse active-voxel hierarchy and returns the
+ * homogenized tensor. Problem statement: Sec. 3.1 of the paper (eq. generic_cell,
+ * linear_system; Example 1 linear elasticity with six unit macro-strain modes, Example 2
+ * steady heat conduction with three unit gradients) and App. F (element matrices, C^H and
+ * kappa^H energy averages). Hierarchy: Sec. 4.1 (sparse voxels, octant features,
+ * conservative coarsening, eq. gmgcoarsenode). Solver: Sec. 3.2 (Alg. 1, Galerkin
+ * operators), Sec. 4.6 (element-by-element operator, smoothing, local Galerkin
+ * projection), App. E (matrix-free trilinear transfers).
+ *
+ * Conventions shared by every call
+ *   - Voxels: N^3 uint8, index x + N*y + N^2*z (x fastest); nonzero = solid.
+ *   - Levels are numbered 0 (finest, the voxel grid) .. L-1 (coarsest); level l has
+ *     N_l = N / 2^l voxels per side.
+ *   - Node order ("canonical"): active nodes of a level sorted by x + N_l*y + N_l^2*z.
+ *   - Field layout: double[node][component][case], i.e. value (n, i, m) at
+ *     n*D*M + i*M + m, with D = 3, M = 6 (elasticity; cases in Voigt order
+ *     xx, yy, zz, yz, xz, xy, engineering shear) or D = 1, M = 3 (heat; cases x, y, z).
+ *   - Sign: fields u solve K u = +f with f = sum_e A_e^T K_e x0, so u = -chi and the total
+ *     field on an element is x0 - u_e (App. F.1).
+ *   - Pointers documented "device" must be CUDA device (or managed) memory on the
+ *     device that was current at gmt_build_hierarchy; "host" pointers are ordinary host
+ *     memory. The caller owns every pointer it passes; the library owns the hierarchy,
+ *     its operators and all scratch, and frees them in gmt_free_hierarchy.
+ *   - Every call returns a gmt_status and never aborts, traps or exits. On an error the
+ *     outputs are unspecified and gmt_last_error() describes the failure (thread-local).
+ *   - All work is issued on the stream given to gmt_build_hierarchy (or gmt_set_stream);
+ *     calls that return host values synchronize that stream.
+ *   - A hierarchy is not thread-safe: one host thread at a time per hierarchy.
+ */
+#ifndef GMT_H
+#define GMT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmt_hierarchy gmt_hierarchy;
+
+typedef enum { GMT_ELASTIC = 0, GMT_HEAT = 1 } gmt_physics;
+
+typedef enum {
+  GMT_OK = 0,
+  GMT_ERR_ARG = 1,          /* invalid argument (null pointer, bad level, bad option) */
+  GMT_ERR_RES = 2,          /* resolution not a multiple of 4 / not divisible by 2^(L-1) */
+  GMT_ERR_EMPTY = 3,        /* the cell has no solid voxel */
+  GMT_ERR_OOM = 4,          /* device allocation failed */
+  GMT_ERR_CUDA = 5,         /* a CUDA call failed */
+  GMT_NOT_CONVERGED = 6,    /* iteration caps reached; best field written, info filled */
+  GMT_DIVERGED = 7,         /* residual grew by > 1e4 or became NaN; best field written */
+  GMT_ERR_STATE = 8         /* call needs gmt_prepare / gmt_solve to have run first */
+} gmt_status;
+
+typedef enum { GMT_PREC_FP64 = 0, GMT_PREC_FP32 = 1, GMT_PREC_BF16 = 2 } gmt_precision;
+typedef enum { GMT_SMOOTH_JACOBI = 0, GMT_SMOOTH_CHEBYSHEV = 1 } gmt_smoother;
+
+/* Solver options. gmt_default_options fills the defaults given in brackets. */
+typedef struct {
+  int levels;          /* [0] number of levels L; 0 = smallest L with coarsest <= coarsest_max */
+  int coarsest_max;    /* [8] automatic level rule: coarsest grid side at most this */
+  int smoother;        /* [GMT_SMOOTH_JACOBI] damped block-Jacobi or Chebyshev */
+  int nu_pre;          /* [2] pre-smoothing sweeps (Chebyshev: polynomial degree) */
+  int nu_post;         /* [2] post-smoothing sweeps */
+  double omega;        /* [0.6] Jacobi damping */
+  double cheb_ratio;   /* [30] Chebyshev interval [lmax/cheb_ratio, cheb_upper*lmax] */
+  double cheb_upper;   /* [1.1] */
+  int precision;       /* [GMT_PREC_FP32] arithmetic of the inner V-cycle / Krylov loop;
+                          GMT_PREC_FP64 = plain all-FP64 solve */
+  int krylov;          /* [1] 1: conjugate gradients preconditioned by the V-cycle;
+                          0: stationary V-cycle iteration (the paper's GMG loop) */
+  double inner_tol;    /* [1e-3] inner relative reduction per outer refinement */
+  int max_inner;       /* [40] inner iterations (V-cycles) per refinement */
+  int max_outer;       /* [8] outer residual refinements (mixed precision) */
+} gmt_options;
+
+/* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,
+   computed by the library's outer residual (0 for a case whose load cancels exactly). */
+typedef struct {
+  int outer;             /* outer refinements performed */
+  int inner_total;       /* V-cycles applied in total */
+  int cases;             /* number of load cases (6 or 3) */
+  double rel_residual[6];
+  double t_setup_ms;     /* operator setup for this material (0 if cached) */
+  double t_solve_ms;     /* solve time (host wall clock around the device work) */
+} gmt_info;
+
+void gmt_default_options(gmt_options* opts);
+
+const char* gmt_status_string(gmt_status s);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* gmt_last_error(void);
+
+/* Build the sparse hierarchy (Sec. 4.1): active elements and nodes, octant masks,
+   canonical numbering, conservative coarsening, brick tables. Geometry only; operators
+   are built by gmt_prepare (or implicitly by gmt_solve).
+   voxels: N^3 bytes, host memory if voxels_on_device == 0, else device memory; read only
+   during the call. res: N, a positive multiple of 4 with N divisible by 2^(L-1).
+   opts: nullable (defaults). stream: a cudaStream_t (nullable = legacy default stream).
+   out: receives the new hierarchy (library-owned; release with gmt_free_hierarchy).
+   Errors: GMT_ERR_ARG, GMT_ERR_RES, GMT_ERR_EMPTY, GMT_ERR_OOM, GMT_ERR_CUDA. */
+gmt_status gmt_build_hierarchy(const uint8_t* voxels, int res, int voxels_on_device,
+                               const gmt_options* opts, void* stream, gmt_hierarchy** out);
+
+void gmt_free_hierarchy(gmt_hierarchy* h);
+
+gmt_status gmt_set_stream(gmt_hierarchy* h, void* stream);
+gmt_status gmt_set_options(gmt_hierarchy* h, const gmt_options* opts);  /* solver fields only */
+
+int gmt_num_levels(const gmt_hierarchy* h);
+int gmt_level_res(const gmt_hierarchy* h, int level);
+int64_t gmt_num_nodes(const gmt_hierarchy* h, int level);
+int64_t gmt_num_elements(const gmt_hierarchy* h, int level);
+int64_t gmt_num_bricks(const gmt_hierarchy* h, int level);   /* 4^3-node bricks (0 = dense) */
+int64_t gmt_device_bytes(const gmt_hierarchy* h);            /* library-owned device memory */
+
+/* Canonical node list of a level (Sec. 4.1): xyz_out device int32[n][3] (x, y, z);
+   mask_out device uint8[n] octant masks (bit o set when the element whose local vertex o
+   is this node is active), nullable. */
+gmt_status gmt_node_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out,
+                           uint8_t* mask_out);
+
+/* Active elements of a level, sorted by linear index: xyz_out device int32[ne][3];
+   child_mask_out device uint8[ne] (levels >= 1: bit c set when child 2X + c is active;
+   level 0: all ones), nullable. */
+gmt_status gmt_element_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out,
+                              uint8_t* child_mask_out);
+
+/* Transfer stencil tuples of App. E.2 between level and level+1: for every active node
+   of `level` (canonical order) the 8 coarse canonical indices and weights; zero-weight
+   slots hold index -1 and weight 0. idx_out device int32[n][8], w_out device double[n][8]. */
+gmt_status gmt_transfer_stencil(const gmt_hierarchy* h, int level, int32_t* idx_out,
+                                double* w_out);
+
+/* Build the operators for one material (App. F element matrices; Sec. 4.6 element-local
+   Galerkin coarse operators; coarsest dense generalized inverse; smoother data).
+   physics GMT_ELASTIC uses E > 0 and -1 < nu < 0.5; GMT_HEAT uses k > 0. Cached: a
+   repeat call with the same arguments does no work. */
+gmt_status gmt_prepare(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k);
+
+/* y = K_level u on canonical fields of `level` (device double[n][D][M]) for the prepared
+   material, computed in `precision` (FP64 or FP32 arithmetic). Level 0 is the
+   matrix-free operator of Sec. 4.6; levels >= 1 are the Galerkin operators. */
+gmt_status gmt_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);
+
+/* `sweeps` smoothing steps of the configured smoother on K_level u = f, in place on u
+   (device canonical fields). zero_init != 0 means u is taken as 0 on entry. */
+gmt_status gmt_smooth(gmt_hierarchy* h, int level, int precision, const double* f,
+                      double* u, int sweeps, int zero_init);
+
+/* f_coarse = P^T r_fine (restriction, App. E.2, gather form) from `level` to level+1. */
+gmt_status gmt_restrict(gmt_hierarchy* h, int level, int precision, const double* r_fine,
+                        double* f_coarse);
+
+/* u_fine += P u_coarse (prolongation and correction, App. E.2) from level+1 to `level`. */
+gmt_status gmt_prolong(gmt_hierarchy* h, int level, int precision, const double* u_coarse,
+                       double* u_fine);
+
+/* Coarsest-level solve: u = zero-mean solution of K_{L-1} u = f (device canonical). */
+gmt_status gmt_coarse_solve(gmt_hierarchy* h, const double* f, double* u);
+
+/* One V-cycle (Alg. 1) on K_0 u = f at `precision`; u holds the initial guess on entry
+   (zero_init != 0: taken as 0) and the result on exit. */
+gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u,
+                      int zero_init);
+
+/* Largest eigenvalue estimate of D^-1 K at `level` used by the Chebyshev smoother
+   (host double out). */
+gmt_status gmt_lambda_max(gmt_hierarchy* h, int level, double* out);
+
+/* Solve the cell problems to max_m r_m <= tol (Sec. 5 metric r, Sec. 3.1).
+   u0: device canonical initial guess, nullable (zero). u_out: device canonical field,
+   nullable (the library keeps its own copy for gmt_homogenize). info: host, nullable.
+   Returns GMT_OK, GMT_NOT_CONVERGED or GMT_DIVERGED (field and info still written) or
+   an error. Fields are gauge-fixed: zero mean over active nodes per component/case. */
+gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                     double tol, const double* u0, double* u_out, gmt_info* info);
+
+/* Homogenized tensor (App. F.1 C^H, App. F.2 kappa^H): CH_out host double[M][M]
+   row-major = 1/N^3 sum_e (x0^I - u_e^I)^T K_e (x0^J - u_e^J). u: device canonical field,
+   or NULL for the field of the last gmt_solve on this hierarchy. */
+gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
+                          double k, const double* u, double* CH_out);
+
+/* Relative residuals ||f_m - K u_m|| / ||f_m|| of a device canonical field u (host out[M]),
+   with the solver's outer residual (precision FP32: float-float difference form;
+   FP64: native FP64). */
+gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMT_H */

@@ -107,6 +107,31 @@ def cg(K, F: np.ndarray, tol: float = 1e-12, maxiter: int = 200000):
     return U, iters
 
 
+def apply_ebe(level: Level, Ke: np.ndarray, U: np.ndarray, D: int, chunk: int = 65536):
+    """K U = sum_e A_e^T K_e A_e U (Sec. 4.6 EBE form) without assembling K, in element
+    chunks; for cells too large for an assembled matrix."""
+    en = level.element_nodes()
+    out = np.zeros_like(U)
+    for s in range(0, en.shape[0], chunk):
+        nodes = en[s:s + chunk]
+        dofs = nodes if D == 1 else (nodes[:, :, None] * D + np.arange(D)).reshape(nodes.shape[0], -1)
+        Y = np.einsum("rc,ecm->erm", Ke, U[dofs])
+        np.add.at(out, dofs.reshape(-1), Y.reshape(-1, U.shape[1]))
+    return out
+
+
+def homogenize_chunked(level: Level, U, Ke, x0, D, chunk: int = 65536) -> np.ndarray:
+    """homogenize() evaluated in element chunks (same definition, bounded memory)."""
+    en = level.element_nodes()
+    C = np.zeros((x0.shape[1], x0.shape[1]))
+    for s in range(0, en.shape[0], chunk):
+        nodes = en[s:s + chunk]
+        dofs = nodes if D == 1 else (nodes[:, :, None] * D + np.arange(D)).reshape(nodes.shape[0], -1)
+        W = x0[None, :, :] - U[dofs]
+        C += np.einsum("eri,erj->ij", W, np.einsum("rc,ecm->erm", Ke, W))
+    return C / float(level.n ** 3)
+
+
 def relative_residual(K, F: np.ndarray, U: np.ndarray) -> np.ndarray:
     """r_m = ||f_m - K u_m|| / ||f_m|| per load case (0 where f_m = 0 and u_m solves)."""
     R = F - K @ U

@@ -1,0 +1,381 @@
+// extern "C" boundary of libgmt.so (declarations and contracts in include/gmt.h).
+// Every entry point validates its arguments, converts internal failures into a
+// gmt_status, and never lets an exception or a CUDA error escape.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace gmt {
+gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, gmt_info* info);
+void homogenize(gmt_hierarchy* h, const double* u, double* CH);
+void residual_of(gmt_hierarchy* h, int precision, const double* u, double* out);
+void estimate_lmax(gmt_hierarchy* h);
+void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);
+void step_smooth(gmt_hierarchy* h, int level, int precision, const double* f, double* u,
+                 int sweeps, bool zero);
+void step_restrict(gmt_hierarchy* h, int level, int precision, const double* rf, double* fc);
+void step_prolong(gmt_hierarchy* h, int level, int precision, const double* uc, double* uf);
+void step_coarse(gmt_hierarchy* h, const double* f, double* u);
+void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero);
+void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);
+void export_elems(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* c);
+void export_stencil(gmt_hierarchy* h, int l, int32_t* idx, double* w);
+}  // namespace gmt
+
+using gmt::Fail;
+
+#define GMT_API_BEGIN \
+  gmt::set_error("%s", ""); \
+  try {
+#define GMT_API_END                                           \
+  }                                                           \
+  catch (const Fail& f) {                                     \
+    return f.status;                                          \
+  }                                                           \
+  catch (...) {                                               \
+    gmt::set_error("unexpected host exception");              \
+    return GMT_ERR_ARG;                                       \
+  }
+
+static bool opts_valid(const gmt_options& o) {
+  return o.levels >= 0 && o.coarsest_max >= 4 && (o.smoother == 0 || o.smoother == 1) &&
+         o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post > 0 && o.omega > 0 &&
+         o.cheb_ratio > 1 && o.cheb_upper >= 1 && o.precision >= 0 && o.precision <= 2 &&
+         o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0;
+}
+
+static void ensure_device(gmt_hierarchy* h) { GMT_CUDA(cudaSetDevice(h->device)); }
+
+static void ensure_material(gmt_hierarchy* h, gmt_physics ph, double E, double nu, double k,
+                            double* setup_ms) {
+  GMT_REQUIRE(ph == GMT_ELASTIC || ph == GMT_HEAT, GMT_ERR_ARG, "unknown physics %d", (int)ph);
+  if (ph == GMT_ELASTIC)
+    GMT_REQUIRE(E > 0 && nu > -1.0 && nu < 0.5 && std::isfinite(E), GMT_ERR_ARG,
+                "elastic material needs E > 0 and -1 < nu < 0.5");
+  else
+    GMT_REQUIRE(k > 0 && std::isfinite(k), GMT_ERR_ARG, "heat conduction needs k > 0");
+  const gmt::Material& m = h->mat;
+  const bool same = h->prepared && m.physics == (int)ph &&
+                    (ph == GMT_ELASTIC ? (m.E == E && m.nu == nu) : m.k == k);
+  if (same) {
+    if (setup_ms) *setup_ms = 0.0;
+    return;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  gmt::free_workspace(h);
+  h->have_solution = false;
+  gmt::prepare_material(h, (int)ph, E, nu, k);
+  if (h->opts.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1) gmt::estimate_lmax(h);
+  if (setup_ms)
+    *setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+static void check_level(const gmt_hierarchy* h, int level) {
+  GMT_REQUIRE(h && level >= 0 && level < h->L, GMT_ERR_ARG, "level %d out of range", level);
+}
+
+extern "C" {
+
+void gmt_default_options(gmt_options* o) {
+  if (!o) return;
+  o->levels = 0;
+  o->coarsest_max = 8;
+  o->smoother = GMT_SMOOTH_JACOBI;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->omega = 0.6;
+  o->cheb_ratio = 30.0;
+  o->cheb_upper = 1.1;
+  o->precision = GMT_PREC_FP32;
+  o->krylov = 1;
+  o->inner_tol = 1e-3;
+  o->max_inner = 40;
+  o->max_outer = 8;
+}
+
+const char* gmt_status_string(gmt_status s) {
+  switch (s) {
+    case GMT_OK: return "ok";
+    case GMT_ERR_ARG: return "invalid argument";
+    case GMT_ERR_RES: return "unsupported resolution / level count";
+    case GMT_ERR_EMPTY: return "cell has no solid voxel";
+    case GMT_ERR_OOM: return "device out of memory";
+    case GMT_ERR_CUDA: return "CUDA error";
+    case GMT_NOT_CONVERGED: return "not converged";
+    case GMT_DIVERGED: return "diverged";
+    case GMT_ERR_STATE: return "operation needs a prepared material or a solution";
+  }
+  return "unknown status";
+}
+
+const char* gmt_last_error(void) { return gmt::last_error(); }
+
+gmt_status gmt_build_hierarchy(const uint8_t* voxels, int res, int voxels_on_device,
+                               const gmt_options* opts, void* stream, gmt_hierarchy** out) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(voxels && out, GMT_ERR_ARG, "null voxels or output pointer");
+  *out = nullptr;
+  gmt_options o;
+  gmt_default_options(&o);
+  if (opts) o = *opts;
+  GMT_REQUIRE(opts_valid(o), GMT_ERR_ARG, "invalid options");
+  GMT_REQUIRE(res >= 4 && res % 4 == 0 && res <= 2048, GMT_ERR_RES,
+              "resolution %d must be a multiple of 4 in [4, 2048]", res);
+  int L = o.levels > 0 ? o.levels : gmt::choose_levels(res, o.coarsest_max);
+  GMT_REQUIRE(L >= 1 && res % (1 << (L - 1)) == 0, GMT_ERR_RES,
+              "resolution %d not divisible by 2^(L-1) with L = %d", res, L);
+  for (int l = 0; l + 1 < L; ++l)
+    GMT_REQUIRE((res >> l) % 4 == 0, GMT_ERR_RES, "non-coarsest level %d side %d not a multiple of 4",
+                l, res >> l);
+  GMT_REQUIRE((res >> (L - 1)) >= 4, GMT_ERR_RES, "coarsest level must be at least 4 per side");
+  GMT_REQUIRE(((int64_t)(res >> (L - 1)) * (res >> (L - 1)) * (res >> (L - 1))) <= 4096,
+              GMT_ERR_RES, "coarsest level too large for the dense solve (use more levels)");
+  gmt_hierarchy* h = new gmt_hierarchy();
+  try {
+    GMT_CUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    h->opts = o;
+    h->N = res;
+    h->L = L;
+    gmt::build_hierarchy(h, voxels, voxels_on_device != 0);
+  } catch (...) {
+    gmt::free_workspace(h);
+    delete h;
+    throw;
+  }
+  *out = h;
+  return GMT_OK;
+  GMT_API_END
+}
+
+void gmt_free_hierarchy(gmt_hierarchy* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  gmt::free_workspace(h);
+  delete h;
+}
+
+gmt_status gmt_set_stream(gmt_hierarchy* h, void* stream) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  h->stream = (cudaStream_t)stream;
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_set_options(gmt_hierarchy* h, const gmt_options* opts) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h && opts && opts_valid(*opts), GMT_ERR_ARG, "invalid options");
+  gmt_options o = *opts;
+  o.levels = h->opts.levels;
+  o.coarsest_max = h->opts.coarsest_max;
+  const bool cheb_new = o.smoother == GMT_SMOOTH_CHEBYSHEV && h->opts.smoother != o.smoother;
+  h->opts = o;
+  if (cheb_new && h->prepared && h->L > 1) {
+    ensure_device(h);
+    gmt::estimate_lmax(h);
+  }
+  return GMT_OK;
+  GMT_API_END
+}
+
+int gmt_num_levels(const gmt_hierarchy* h) { return h ? h->L : 0; }
+int gmt_level_res(const gmt_hierarchy* h, int level) {
+  return (h && level >= 0 && level < h->L) ? h->lv[level].n : 0;
+}
+int64_t gmt_num_nodes(const gmt_hierarchy* h, int level) {
+  return (h && level >= 0 && level < h->L) ? h->lv[level].n_nodes : -1;
+}
+int64_t gmt_num_elements(const gmt_hierarchy* h, int level) {
+  return (h && level >= 0 && level < h->L) ? h->lv[level].n_elems : -1;
+}
+int64_t gmt_num_bricks(const gmt_hierarchy* h, int level) {
+  return (h && level >= 0 && level < h->L) ? (h->lv[level].dense ? 0 : h->lv[level].nb) : -1;
+}
+int64_t gmt_device_bytes(const gmt_hierarchy* h) {
+  return h ? (int64_t)(h->geo.bytes + h->op.bytes + h->work.bytes) : 0;
+}
+
+gmt_status gmt_node_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out, uint8_t* mask_out) {
+  GMT_API_BEGIN
+  check_level(h, level);
+  GMT_REQUIRE(xyz_out, GMT_ERR_ARG, "null output");
+  gmt_hierarchy* hh = const_cast<gmt_hierarchy*>(h);
+  ensure_device(hh);
+  gmt::export_nodes(hh, level, xyz_out, mask_out);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_element_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out,
+                              uint8_t* child_mask_out) {
+  GMT_API_BEGIN
+  check_level(h, level);
+  GMT_REQUIRE(xyz_out, GMT_ERR_ARG, "null output");
+  gmt_hierarchy* hh = const_cast<gmt_hierarchy*>(h);
+  ensure_device(hh);
+  gmt::export_elems(hh, level, xyz_out, child_mask_out);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_transfer_stencil(const gmt_hierarchy* h, int level, int32_t* idx_out, double* w_out) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h && level >= 0 && level + 1 < h->L, GMT_ERR_ARG, "no level below %d", level);
+  GMT_REQUIRE(idx_out && w_out, GMT_ERR_ARG, "null output");
+  gmt_hierarchy* hh = const_cast<gmt_hierarchy*>(h);
+  ensure_device(hh);
+  gmt::export_stencil(hh, level, idx_out, w_out);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_prepare(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  ensure_device(h);
+  ensure_material(h, physics, E, nu, k, nullptr);
+  return GMT_OK;
+  GMT_API_END
+}
+
+static void need_prepared(gmt_hierarchy* h) {
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  GMT_REQUIRE(h->prepared, GMT_ERR_STATE, "gmt_prepare has not run");
+}
+
+gmt_status gmt_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  check_level(h, level);
+  GMT_REQUIRE(u && y, GMT_ERR_ARG, "null field");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  GMT_REQUIRE(!h->lv[level].dense, GMT_ERR_ARG,
+              "level %d is the dense coarsest level (side not a multiple of 4)", level);
+  ensure_device(h);
+  gmt::step_apply(h, level, precision, u, y);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_smooth(gmt_hierarchy* h, int level, int precision, const double* f, double* u,
+                      int sweeps, int zero_init) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  check_level(h, level);
+  GMT_REQUIRE(f && u && sweeps >= 0, GMT_ERR_ARG, "bad arguments");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  GMT_REQUIRE(!h->lv[level].dense, GMT_ERR_ARG, "level %d is the dense coarsest level", level);
+  GMT_REQUIRE(!(h->opts.smoother == GMT_SMOOTH_CHEBYSHEV && level == h->L - 1), GMT_ERR_ARG,
+              "no Chebyshev bounds on the coarsest level");
+  ensure_device(h);
+  gmt::step_smooth(h, level, precision, f, u, sweeps, zero_init != 0);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_restrict(gmt_hierarchy* h, int level, int precision, const double* r_fine,
+                        double* f_coarse) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(level >= 0 && level + 1 < h->L, GMT_ERR_ARG, "no level below %d", level);
+  GMT_REQUIRE(r_fine && f_coarse, GMT_ERR_ARG, "null field");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  ensure_device(h);
+  gmt::step_restrict(h, level, precision, r_fine, f_coarse);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_prolong(gmt_hierarchy* h, int level, int precision, const double* u_coarse,
+                       double* u_fine) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(level >= 0 && level + 1 < h->L, GMT_ERR_ARG, "no level below %d", level);
+  GMT_REQUIRE(u_coarse && u_fine, GMT_ERR_ARG, "null field");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  ensure_device(h);
+  gmt::step_prolong(h, level, precision, u_coarse, u_fine);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_coarse_solve(gmt_hierarchy* h, const double* f, double* u) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(f && u, GMT_ERR_ARG, "null field");
+  ensure_device(h);
+  gmt::step_coarse(h, f, u);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, int zero_init) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(f && u, GMT_ERR_ARG, "null field");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  ensure_device(h);
+  gmt::step_vcycle(h, precision, f, u, zero_init != 0);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_lambda_max(gmt_hierarchy* h, int level, double* out) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(out && level >= 0 && level + 1 < h->L, GMT_ERR_ARG, "bad level");
+  ensure_device(h);
+  if (h->lv[level].lmax == 0.0) gmt::estimate_lmax(h);
+  *out = h->lv[level].lmax;
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                     double tol, const double* u0, double* u_out, gmt_info* info) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  GMT_REQUIRE(tol > 0 && tol < 1, GMT_ERR_ARG, "tol must be in (0, 1)");
+  ensure_device(h);
+  double setup = 0.0;
+  ensure_material(h, physics, E, nu, k, &setup);
+  gmt_status st = gmt::solve(h, tol, u0, u_out, info);
+  if (info) info->t_setup_ms = setup;
+  return st;
+  GMT_API_END
+}
+
+gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                          const double* u, double* CH_out) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h && CH_out, GMT_ERR_ARG, "null argument");
+  ensure_device(h);
+  const bool stored = u == nullptr;
+  if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "no stored solution");
+  ensure_material(h, physics, E, nu, k, nullptr);
+  if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "stored solution belongs to another material");
+  gmt::homogenize(h, u, CH_out);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double* out) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(u && out, GMT_ERR_ARG, "null argument");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  ensure_device(h);
+  gmt::residual_of(h, precision, u, out);
+  return GMT_OK;
+  GMT_API_END
+}
+
+}  // extern "C"

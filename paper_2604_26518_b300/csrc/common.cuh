@@ -1,0 +1,189 @@
+// Internal definitions shared by the library's translation units.
+//
+// Data layout (all non-coarsest levels): the N_l^3 node sites are cut into 4x4x4 bricks;
+// only bricks that hold at least one active node are stored. A "slot" is
+// brick * 64 + (x & 3) + 4 (y & 3) + 16 (z & 3). A field with C values per node
+// (C = D * M: components x load cases) is stored brick-major, value-major inside the
+// brick: value v of slot s lives at (s >> 6) * 64 * C + v * 64 + (s & 63), so a warp
+// reading one value of 32 consecutive slots touches 128 contiguous bytes. Inactive nodes
+// inside stored bricks hold 0. The coarsest level uses the same formula on a dense
+// N_L^3 slot range (slot = x + N y + N^2 z), padded to a multiple of 64.
+// Value index v = component * M + case, matching the canonical [node][comp][case] order.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gmt.h"
+
+namespace gmt {
+
+// ------------------------------------------------------------------ error handling
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+struct Fail {
+  gmt_status status;
+};
+
+#define GMT_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::gmt::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                       __LINE__);                                                         \
+      throw ::gmt::Fail{e_ == cudaErrorMemoryAllocation ? GMT_ERR_OOM : GMT_ERR_CUDA};   \
+    }                                                                                     \
+  } while (0)
+
+#define GMT_LAUNCH_CHECK() GMT_CUDA(cudaGetLastError())
+
+#define GMT_REQUIRE(cond, st, ...)        \
+  do {                                    \
+    if (!(cond)) {                        \
+      ::gmt::set_error(__VA_ARGS__);      \
+      throw ::gmt::Fail{st};              \
+    }                                     \
+  } while (0)
+
+// ------------------------------------------------------------------ layout helpers
+__host__ __device__ __forceinline__ int64_t vaddr(int64_t slot, int v, int C) {
+  return (slot >> 6) * (int64_t)(64 * C) + (int64_t)v * 64 + (slot & 63);
+}
+
+// slot of node site (x, y, z) of a level: dense levels index the site directly, bricked
+// levels go through the brick map (-1 when the brick is not stored)
+__device__ __forceinline__ int64_t site_slot(int x, int y, int z, int n, int nbx,
+                                             const int* bmap, bool dense) {
+  if (dense) return x + (int64_t)n * (y + (int64_t)n * z);
+  int b = bmap[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nbx * (z >> 2))];
+  if (b < 0) return -1;
+  return (int64_t)b * 64 + (x & 3) + 4 * (y & 3) + 16 * (z & 3);
+}
+
+__device__ __forceinline__ void slot_coords(int64_t s, int n, bool dense, const int* bxyz,
+                                            int& x, int& y, int& z) {
+  if (dense) {
+    x = (int)(s % n);
+    y = (int)((s / n) % n);
+    z = (int)(s / ((int64_t)n * n));
+  } else {
+    int64_t b = s >> 6;
+    int l = (int)(s & 63);
+    x = 4 * bxyz[3 * b] + (l & 3);
+    y = 4 * bxyz[3 * b + 1] + ((l >> 2) & 3);
+    z = 4 * bxyz[3 * b + 2] + (l >> 4);
+  }
+}
+
+static inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T> __device__ __forceinline__ float to_f(T x);
+template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+template <typename A, typename T> __device__ __forceinline__ A load_as(const T* p) {
+  return (A)(*p);
+}
+template <> __device__ __forceinline__ float load_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <typename T, typename A> __device__ __forceinline__ T store_as(A x) { return (T)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// ------------------------------------------------------------------ device arena
+// Every device allocation of a hierarchy goes through one Arena, which owns it until the
+// hierarchy is freed (or the material-dependent part is rebuilt).
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  void* raw(size_t n);
+  template <typename T> T* alloc(size_t count) { return (T*)raw(count * sizeof(T)); }
+  void release();
+  ~Arena() { release(); }
+};
+
+// ------------------------------------------------------------------ hierarchy
+struct Level {
+  int n = 0;             // N_l
+  int nbx = 0;           // n / 4 for bricked levels
+  bool dense = false;    // coarsest level stored as a dense slot range
+  int64_t nb = 0;        // stored bricks (dense: nslots / 64)
+  int64_t nslots = 0;    // nb * 64
+  int64_t n_nodes = 0, n_elems = 0;
+  // geometry (device)
+  uint8_t* eflag = nullptr;     // dense n^3 element flags (1 = active)
+  uint8_t* child = nullptr;     // dense n^3 child masks (levels >= 1)
+  int* brick_map = nullptr;     // nbx^3 -> brick or -1 (bricked)
+  int* brick_xyz = nullptr;     // nb x 3 (bricked)
+  int* brick_nbr = nullptr;     // nb x 27, index (dz+1)*9 + (dy+1)*3 + (dx+1) (bricked)
+  uint8_t* mask = nullptr;      // nslots octant masks (0 = inactive node)
+  int* slot_canon = nullptr;    // nslots -> canonical node or -1
+  int* canon_slot = nullptr;    // n_nodes -> slot
+  int* kidx = nullptr;          // nslots -> element-matrix index of the element with origin
+                                // at this slot (level 1: child mask; >= 2: element id), -1
+  int* elem_slot = nullptr;     // n_elems -> slot of the element's origin (canonical order)
+  // material-dependent operator data (device)
+  double* K64 = nullptr;        // level 1: [256][MM] table; level >= 2: [n_elems][MM]
+  float* K32 = nullptr;
+  double* dinv64 = nullptr;     // levels >= 1: nslots x D*D block-diagonal inverses
+  float* dinv32 = nullptr;
+  double lmax = 0.0;            // Chebyshev: estimate of lambda_max(D^-1 K)
+};
+
+struct Material {
+  int physics = -1;
+  double E = 0, nu = 0, k = 0;
+  int D = 0, M = 0, C = 0, MM = 0;   // dofs/node, cases, values/node, (8D)^2
+  double Ke[576];                    // element matrix, (8D) x (8D) row-major
+  double Fe[144];                    // K_e x0, (8D) x M
+  double X0[144];                    // x0, (8D) x M
+  double C0[36];                     // x0^T K_e x0 (base tensor)
+  double gross[6];                   // sqrt(n_e * ||K_e x0_m||^2) per case
+};
+
+struct Workspace;  // solver buffers (solver.cu)
+
+}  // namespace gmt
+
+struct gmt_hierarchy {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gmt_options opts;
+  int N = 0, L = 0;
+  std::vector<gmt::Level> lv;
+  gmt::Arena geo;         // geometry allocations
+  gmt::Arena op;          // material-dependent allocations
+  gmt::Arena work;        // solver work buffers
+  gmt::Material mat;
+  bool prepared = false;
+  double* Ke64 = nullptr;  // device copies of the level-0 element matrix
+  float* Ke32 = nullptr;
+  // coarsest dense generalized inverse (FP64), m = n_nodes(L-1) * D
+  int64_t m = 0;
+  double* Ainv = nullptr;
+  double* cb = nullptr;   // m x M gather buffer
+  double* cu = nullptr;   // m x M result buffer
+  gmt::Workspace* ws = nullptr;
+  bool have_solution = false;
+  int64_t ws_for_prec = -1;
+};
+
+namespace gmt {
+// hierarchy.cu
+void build_hierarchy(gmt_hierarchy* h, const uint8_t* vox, bool on_device);
+int choose_levels(int n, int coarsest_max);
+// operators.cu
+void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double k);
+// solver.cu
+void free_workspace(gmt_hierarchy* h);
+}  // namespace gmt

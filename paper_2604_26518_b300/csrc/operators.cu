@@ -1,0 +1,486 @@
+// Material-dependent operators, all built by kernels:
+//   * the hex8 element matrix K_e, the affine modes x0, the element load K_e x0 and the
+//     base tensor x0^T K_e x0 (App. F.1 / F.2; 2x2x2 Gauss-Legendre, exact here);
+//   * element-local Galerkin coarse matrices (Sec. 4.6 "Operator Consistency via Galerkin
+//     Projection": K_c = R_loc K_patch P_loc, written as the sum over the 8 children of
+//     P_c^T K_child P_c with the trilinear weights of App. E.1). Level 1 depends only on the
+//     8-bit child mask, so it is a 256-entry table; levels >= 2 are stored per element;
+//   * D x D block-diagonal inverses of the coarse operators (smoother, Sec. 4.6);
+//   * the coarsest level's dense generalized inverse of K_L + rho J (J couples equal
+//     components of all nodes, rho = mean diagonal), by in-place Gauss-Jordan with
+//     semidefinite pivot dropping. For right-hand sides orthogonal to translations this
+//     returns the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS
+//     is replaced by this exact solve.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace gmt {
+
+// ------------------------------------------------------------------ element matrices
+__device__ double gauss_x(int q) { return q ? 0.5 + 0.5 / sqrt(3.0) : 0.5 - 0.5 / sqrt(3.0); }
+
+__device__ double shape_grad(int a, int d, const double xi[3]) {
+  double v = ((a >> d) & 1) ? 1.0 : -1.0;
+  for (int e = 0; e < 3; ++e)
+    if (e != d) v *= ((a >> e) & 1) ? xi[e] : 1.0 - xi[e];
+  return v;
+}
+
+// Voigt (xx, yy, zz, yz, xz, xy) engineering strain of dof col = 3a + i
+__device__ double strain_B(int row, int col, const double xi[3]) {
+  int a = col / 3, i = col % 3;
+  double g[3] = {shape_grad(a, 0, xi), shape_grad(a, 1, xi), shape_grad(a, 2, xi)};
+  switch (row) {
+    case 0: return i == 0 ? g[0] : 0.0;
+    case 1: return i == 1 ? g[1] : 0.0;
+    case 2: return i == 2 ? g[2] : 0.0;
+    case 3: return i == 1 ? g[2] : (i == 2 ? g[1] : 0.0);
+    case 4: return i == 0 ? g[2] : (i == 2 ? g[0] : 0.0);
+    default: return i == 0 ? g[1] : (i == 1 ? g[0] : 0.0);
+  }
+}
+
+// out: Ke[(8D)^2], Fe[8D*M], X0[8D*M], C0[M*M]
+__global__ void k_element(int physics, double E, double nu, double kappa, double* out) {
+  const int D = physics == GMT_ELASTIC ? 3 : 1, M = physics == GMT_ELASTIC ? 6 : 3;
+  const int R = 8 * D, MM = R * R;
+  __shared__ double sK[576], sX[144], sF[144];
+  const int t = threadIdx.x;
+  if (t < MM) {
+    int r = t / R, c = t % R;
+    double acc = 0.0;
+    if (physics == GMT_ELASTIC) {
+      double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = E / (2.0 * (1.0 + nu));
+      for (int q = 0; q < 8; ++q) {
+        double xi[3] = {gauss_x(q & 1), gauss_x((q >> 1) & 1), gauss_x((q >> 2) & 1)};
+        double br[6], bc[6];
+        for (int i = 0; i < 6; ++i) {
+          br[i] = strain_B(i, r, xi);
+          bc[i] = strain_B(i, c, xi);
+        }
+        double s = 0.0;
+        for (int i = 0; i < 6; ++i) {
+          double ci = 0.0;  // (C0 bc)_i
+          if (i < 3) {
+            for (int j = 0; j < 3; ++j) ci += (i == j ? lam + 2.0 * mu : lam) * bc[j];
+          } else {
+            ci = mu * bc[i];
+          }
+          s += br[i] * ci;
+        }
+        acc += 0.125 * s;
+      }
+    } else {
+      for (int q = 0; q < 8; ++q) {
+        double xi[3] = {gauss_x(q & 1), gauss_x((q >> 1) & 1), gauss_x((q >> 2) & 1)};
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) s += shape_grad(r, d, xi) * shape_grad(c, d, xi);
+        acc += 0.125 * kappa * s;
+      }
+    }
+    sK[t] = acc;
+    out[t] = acc;
+  }
+  if (t < R * M) {
+    int r = t / M, m = t % M;
+    double v;
+    if (physics == GMT_ELASTIC) {
+      int a = r / 3, i = r % 3;
+      double x[3] = {(double)(a & 1), (double)((a >> 1) & 1), (double)((a >> 2) & 1)};
+      // symmetric strain tensor of Voigt mode m (engineering shear -> 1/2 entries)
+      double Em[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      if (m < 3) {
+        Em[m][m] = 1.0;
+      } else {
+        int p = m == 3 ? 1 : 0, q = m == 5 ? 1 : 2;
+        Em[p][q] = Em[q][p] = 0.5;
+      }
+      v = Em[i][0] * x[0] + Em[i][1] * x[1] + Em[i][2] * x[2];
+    } else {
+      v = (double)((r >> m) & 1);
+    }
+    sX[t] = v;
+  }
+  __syncthreads();
+  if (t < R * M) {
+    int r = t / M, m = t % M;
+    double s = 0.0;
+    for (int c = 0; c < R; ++c) s += sK[r * R + c] * sX[c * M + m];
+    sF[t] = s;
+    out[MM + t] = s;
+    out[MM + R * M + t] = sX[t];
+  }
+  __syncthreads();
+  if (t < M * M) {
+    int I = t / M, J = t % M;
+    double s = 0.0;
+    for (int r = 0; r < R; ++r) s += sX[r * M + I] * sF[r * M + J];
+    out[MM + 2 * R * M + t] = s;
+  }
+}
+
+// ------------------------------------------------------------------ Galerkin
+// weight of coarse-local vertex b at child c's local vertex a (App. E.1 trilinear weights)
+__device__ __forceinline__ double wchild(int c, int a, int b) {
+  double w = 1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double pos = 0.5 * (((c >> d) & 1) + ((a >> d) & 1));
+    w *= 1.0 - fabs(pos - (double)((b >> d) & 1));
+  }
+  return w;
+}
+
+// Q[c] = P_c^T K_e P_c (block c, one thread per entry)
+__global__ void k_child_products(const double* __restrict__ Ke, int D, double* __restrict__ Q) {
+  const int R = 8 * D, MM = R * R;
+  const int c = blockIdx.x, t = threadIdx.x;
+  if (t >= MM) return;
+  int r = t / R, s = t % R;
+  int b = r / D, i = r % D, bb = s / D, j = s % D;
+  double acc = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    double wa = wchild(c, a, b);
+    if (wa == 0.0) continue;
+    for (int aa = 0; aa < 8; ++aa) {
+      double wb = wchild(c, aa, bb);
+      if (wb == 0.0) continue;
+      acc += wa * wb * Ke[(a * D + i) * R + aa * D + j];
+    }
+  }
+  Q[(int64_t)c * MM + t] = acc;
+}
+
+// level-1 table: T[mask] = sum_{c in mask} Q[c]
+__global__ void k_mask_table(const double* __restrict__ Q, int MM, double* __restrict__ T64,
+                             float* __restrict__ T32) {
+  const int m = blockIdx.x;
+  for (int t = threadIdx.x; t < MM; t += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < 8; ++c)
+      if ((m >> c) & 1) acc += Q[(int64_t)c * MM + t];
+    T64[(int64_t)m * MM + t] = acc;
+    T32[(int64_t)m * MM + t] = (float)acc;
+  }
+}
+
+// levels >= 2: K(E) = sum over active children c of P_c^T K(child) P_c
+__global__ void k_galerkin_elem(int D, int nc, const int* __restrict__ elem_slot,
+                                const int* __restrict__ cbxyz, bool cdense,
+                                const uint8_t* __restrict__ cchild, int nf, int fnbx,
+                                const int* __restrict__ fbmap, bool fdense,
+                                const int* __restrict__ fkidx, const double* __restrict__ Kf,
+                                double* __restrict__ K64, float* __restrict__ K32) {
+  const int R = 8 * D, MM = R * R;
+  __shared__ double sK[576], sT[576];
+  const int64_t e = blockIdx.x;
+  const int t = threadIdx.x;
+  int X, Y, Z;
+  slot_coords(elem_slot[e], nc, cdense, cbxyz, X, Y, Z);
+  const unsigned cm = cchild[X + (int64_t)nc * (Y + (int64_t)nc * Z)];
+  const int r = t / R, s = t % R;
+  double acc = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    if (!((cm >> c) & 1)) continue;  // uniform across the block
+    int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + ((c >> 2) & 1);
+    int64_t fs = site_slot(fx, fy, fz, nf, fnbx, fbmap, fdense);
+    const double* Kc = Kf + (int64_t)fkidx[fs] * MM;
+    __syncthreads();
+    if (t < MM) sK[t] = Kc[t];
+    __syncthreads();
+    if (t < MM) {  // sT[(a i), (b' j)] = sum_a' K[(a i)(a' j)] w(c, a', b')
+      int bb = s / D, j = s % D;
+      double v = 0.0;
+      for (int aa = 0; aa < 8; ++aa) {
+        double w = wchild(c, aa, bb);
+        if (w != 0.0) v += sK[r * R + aa * D + j] * w;
+      }
+      sT[t] = v;
+    }
+    __syncthreads();
+    if (t < MM) {  // acc[(b i), (b' j)] += sum_a w(c, a, b) sT[(a i), (b' j)]
+      int b = r / D, i = r % D;
+      for (int a = 0; a < 8; ++a) {
+        double w = wchild(c, a, b);
+        if (w != 0.0) acc += w * sT[(a * D + i) * R + s];
+      }
+    }
+  }
+  if (t < MM) {
+    K64[e * MM + t] = acc;
+    K32[e * MM + t] = (float)acc;
+  }
+}
+
+// D x D block-diagonal inverse of a coarse operator at every active slot
+__global__ void k_diag_inv(int D, int n, int nbx, const int* __restrict__ bxyz,
+                           const int* __restrict__ bmap, bool dense, int64_t nslots,
+                           const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
+                           const double* __restrict__ K, double* __restrict__ d64,
+                           float* __restrict__ d32) {
+  const int R = 8 * D, MM = R * R;
+  int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslots) return;
+  unsigned m = mask[sl];
+  double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (m && (dense ? sl < (int64_t)n * n * n : true)) {
+    int x, y, z;
+    slot_coords(sl, n, dense, bxyz, x, y, z);
+    for (int a = 0; a < 8; ++a) {
+      if (!((m >> a) & 1)) continue;
+      int ex = (x - (a & 1) + n) % n, ey = (y - ((a >> 1) & 1) + n) % n,
+          ez = (z - ((a >> 2) & 1) + n) % n;
+      int64_t es = site_slot(ex, ey, ez, n, nbx, bmap, dense);
+      const double* Kc = K + (int64_t)kidx[es] * MM;
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) A[i * D + j] += Kc[(a * D + i) * R + a * D + j];
+    }
+  }
+  double Inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (m) {
+    if (D == 1) {
+      Inv[0] = 1.0 / A[0];
+    } else {
+      double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8],
+             c02 = A[3] * A[7] - A[4] * A[6];
+      double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+      double id = 1.0 / det;
+      Inv[0] = c00 * id;
+      Inv[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+      Inv[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+      Inv[3] = c01 * id;
+      Inv[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+      Inv[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+      Inv[6] = c02 * id;
+      Inv[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+      Inv[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    }
+  }
+  for (int q = 0; q < D * D; ++q) {
+    d64[sl * D * D + q] = Inv[q];
+    d32[sl * D * D + q] = (float)Inv[q];
+  }
+}
+
+// ------------------------------------------------------------------ coarsest dense solve
+// thread per (canonical node i, neighbour offset d): the D x D block K(i, i + d)
+__global__ void k_coarse_assemble(int D, int level, int n, int nbx, const int* __restrict__ bxyz,
+                                  const int* __restrict__ bmap, bool dense,
+                                  const uint8_t* __restrict__ eflag,
+                                  const int* __restrict__ canon_slot,
+                                  const int* __restrict__ slot_canon,
+                                  const int* __restrict__ kidx, const double* __restrict__ K,
+                                  const double* __restrict__ Ke, int64_t nn, int64_t m,
+                                  double* __restrict__ A) {
+  const int R = 8 * D, MM = R * R;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * 27) return;
+  int64_t i = g / 27;
+  int d = (int)(g % 27);
+  int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+  int x, y, z;
+  slot_coords(canon_slot[i], n, dense, bxyz, x, y, z);
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  bool any = false;
+  for (int a = 0; a < 8; ++a) {
+    int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+    int bx = ax + dx, by = ay + dy, bz = az + dz;
+    if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+    int b = bx + 2 * by + 4 * bz;
+    int ex = (x - ax + n) % n, ey = (y - ay + n) % n, ez = (z - az + n) % n;
+    if (!eflag[ex + (int64_t)n * (ey + (int64_t)n * ez)]) continue;
+    const double* Kc;
+    if (level == 0) {
+      Kc = Ke;
+    } else {
+      int64_t es = site_slot(ex, ey, ez, n, nbx, bmap, dense);
+      Kc = K + (int64_t)kidx[es] * MM;
+    }
+    for (int p = 0; p < D; ++p)
+      for (int q = 0; q < D; ++q) S[p * D + q] += Kc[(a * D + p) * R + b * D + q];
+    any = true;
+  }
+  if (!any) return;
+  int jx = (x + dx + n) % n, jy = (y + dy + n) % n, jz = (z + dz + n) % n;
+  int64_t js = site_slot(jx, jy, jz, n, nbx, bmap, dense);
+  int64_t j = slot_canon[js];
+  for (int p = 0; p < D; ++p)
+    for (int q = 0; q < D; ++q) A[(i * D + p) * m + j * D + q] = S[p * D + q];
+}
+
+__global__ void k_diag_sum(const double* __restrict__ A, int64_t m, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double s = 0.0, mx = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    s += A[i * m + i];
+    mx = fmax(mx, A[i * m + i]);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+  __syncthreads();
+  sh[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[1] = sh[0];
+}
+
+__global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, double rho) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * m) return;
+  int64_t r = g / m, c = g % m;
+  if (r % D == c % D) A[g] += rho;
+}
+
+// Gauss-Jordan step k: save row k, column k and the pivot decision
+__global__ void k_gj_save(const double* __restrict__ A, int64_t m, int64_t k, double tol,
+                          double* __restrict__ row, double* __restrict__ col,
+                          int* __restrict__ ok) {
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    row[j] = A[k * m + j];
+    col[j] = A[j * m + k];
+  }
+  if (threadIdx.x == 0) ok[0] = A[k * m + k] > tol;
+}
+
+__global__ void k_gj_update(double* __restrict__ A, int64_t m, int64_t k,
+                            const double* __restrict__ row, const double* __restrict__ col,
+                            const int* __restrict__ ok) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * m) return;
+  int64_t i = g / m, j = g % m;
+  if (!ok[0]) {  // semidefinite: drop the null pivot (row and column become zero)
+    if (i == k || j == k) A[g] = 0.0;
+    return;
+  }
+  double p = row[k];
+  if (i == k) {
+    A[g] = (j == k) ? 1.0 / p : row[j] / p;
+  } else if (j == k) {
+    A[g] = -col[i] / p;
+  } else {
+    A[g] -= col[i] * row[j] / p;
+  }
+}
+
+// ------------------------------------------------------------------ host driver
+void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double kappa) {
+  cudaStream_t s = h->stream;
+  h->op.release();
+  h->prepared = false;
+  Material& mt = h->mat;
+  mt = Material();
+  mt.physics = physics;
+  mt.E = E;
+  mt.nu = nu;
+  mt.k = kappa;
+  mt.D = physics == GMT_ELASTIC ? 3 : 1;
+  mt.M = physics == GMT_ELASTIC ? 6 : 3;
+  mt.C = mt.D * mt.M;
+  const int D = mt.D, M = mt.M, R = 8 * D, MM = R * R;
+  mt.MM = MM;
+  Arena tmp;
+  // element matrices
+  double* eout = tmp.alloc<double>(MM + 2 * R * M + M * M);
+  k_element<<<1, 576, 0, s>>>(physics, E, nu, kappa, eout);
+  GMT_LAUNCH_CHECK();
+  std::vector<double> host(MM + 2 * R * M + M * M);
+  GMT_CUDA(cudaMemcpyAsync(host.data(), eout, host.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  GMT_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(mt.Ke, host.data(), MM * sizeof(double));
+  std::memcpy(mt.Fe, host.data() + MM, R * M * sizeof(double));
+  std::memcpy(mt.X0, host.data() + MM + R * M, R * M * sizeof(double));
+  std::memcpy(mt.C0, host.data() + MM + 2 * R * M, M * M * sizeof(double));
+  for (int m = 0; m < M; ++m) {
+    double s2 = 0.0;
+    for (int r = 0; r < R; ++r) s2 += mt.Fe[r * M + m] * mt.Fe[r * M + m];
+    mt.gross[m] = std::sqrt((double)h->lv[0].n_elems * s2);
+  }
+  h->Ke64 = h->op.alloc<double>(MM);
+  h->Ke32 = h->op.alloc<float>(MM);
+  GMT_CUDA(cudaMemcpyAsync(h->Ke64, eout, MM * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  {
+    std::vector<float> k32(MM);
+    for (int i = 0; i < MM; ++i) k32[i] = (float)mt.Ke[i];
+    GMT_CUDA(cudaMemcpyAsync(h->Ke32, k32.data(), MM * sizeof(float), cudaMemcpyHostToDevice, s));
+    GMT_CUDA(cudaStreamSynchronize(s));
+  }
+  // Galerkin coarse operators
+  if (h->L >= 2) {
+    double* Q = tmp.alloc<double>(8 * MM);
+    k_child_products<<<8, MM, 0, s>>>(h->Ke64, D, Q);
+    GMT_LAUNCH_CHECK();
+    Level& l1 = h->lv[1];
+    l1.K64 = h->op.alloc<double>(256 * (size_t)MM);
+    l1.K32 = h->op.alloc<float>(256 * (size_t)MM);
+    k_mask_table<<<256, 256, 0, s>>>(Q, MM, l1.K64, l1.K32);
+    GMT_LAUNCH_CHECK();
+  }
+  for (int l = 2; l < h->L; ++l) {
+    Level& c = h->lv[l];
+    Level& f = h->lv[l - 1];
+    c.K64 = h->op.alloc<double>(c.n_elems * (size_t)MM);
+    c.K32 = h->op.alloc<float>(c.n_elems * (size_t)MM);
+    k_galerkin_elem<<<(unsigned)c.n_elems, MM, 0, s>>>(D, c.n, c.elem_slot, c.brick_xyz, c.dense,
+                                                       c.child, f.n, f.nbx, f.brick_map, f.dense,
+                                                       f.kidx, f.K64, c.K64, c.K32);
+    GMT_LAUNCH_CHECK();
+  }
+  for (int l = 1; l < h->L; ++l) {
+    Level& c = h->lv[l];
+    c.dinv64 = h->op.alloc<double>(c.nslots * D * D);
+    c.dinv32 = h->op.alloc<float>(c.nslots * D * D);
+    k_diag_inv<<<grid_for(c.nslots, 128), 128, 0, s>>>(D, c.n, c.nbx, c.brick_xyz, c.brick_map,
+                                                       c.dense, c.nslots, c.mask, c.kidx, c.K64,
+                                                       c.dinv64, c.dinv32);
+    GMT_LAUNCH_CHECK();
+  }
+  // coarsest generalized inverse
+  {
+    const int lc = h->L - 1;
+    Level& c = h->lv[lc];
+    const int64_t m = c.n_nodes * D;
+    h->m = m;
+    h->Ainv = h->op.alloc<double>(m * m);
+    h->cb = h->op.alloc<double>(m * M);
+    h->cu = h->op.alloc<double>(m * M);
+    GMT_CUDA(cudaMemsetAsync(h->Ainv, 0, m * m * sizeof(double), s));
+    k_coarse_assemble<<<grid_for(c.n_nodes * 27, 128), 128, 0, s>>>(
+        D, lc, c.n, c.nbx, c.brick_xyz, c.brick_map, c.dense, c.eflag, c.canon_slot, c.slot_canon,
+        c.kidx, c.K64, h->Ke64, c.n_nodes, m, h->Ainv);
+    GMT_LAUNCH_CHECK();
+    double* ds = tmp.alloc<double>(2);
+    k_diag_sum<<<1, 1024, 0, s>>>(h->Ainv, m, ds);
+    GMT_LAUNCH_CHECK();
+    double dh[2];
+    GMT_CUDA(cudaMemcpyAsync(dh, ds, sizeof(dh), cudaMemcpyDeviceToHost, s));
+    GMT_CUDA(cudaStreamSynchronize(s));
+    const double rho = dh[0] / (double)m;
+    k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->Ainv, m, D, rho);
+    GMT_LAUNCH_CHECK();
+    const double tol = 1e-12 * (dh[1] + rho * (double)c.n_nodes);
+    double* row = tmp.alloc<double>(m);
+    double* col = tmp.alloc<double>(m);
+    int* ok = tmp.alloc<int>(1);
+    for (int64_t k = 0; k < m; ++k) {
+      k_gj_save<<<1, 256, 0, s>>>(h->Ainv, m, k, tol, row, col, ok);
+      k_gj_update<<<grid_for(m * m, 256), 256, 0, s>>>(h->Ainv, m, k, row, col, ok);
+    }
+    GMT_LAUNCH_CHECK();
+  }
+  GMT_CUDA(cudaStreamSynchronize(s));
+  h->prepared = true;
+}
+
+}  // namespace gmt

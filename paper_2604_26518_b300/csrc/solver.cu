@@ -1,0 +1,609 @@
+// Solver orchestration: the V-cycle of Alg. 1 (smoother, residual, restriction, recursion,
+// coarsest solve, prolongation, smoother), used either as the preconditioner of a
+// conjugate-gradient loop or as a stationary iteration (the paper's GMG loop, Sec. 5
+// baselines), wrapped in outer residual refinement:
+//
+//   precision FP64:  u <- u + CG_V(f - K u) entirely in FP64;
+//   precision FP32:  u kept as a float-float pair (hi, lo); r = f - K u from the
+//                    difference-form level-0 residual (FP32 arithmetic, ~1e-7 accurate);
+//                    d = CG_V(r) in FP32; u += d; repeat until max_m r_m <= tol.
+//
+// Stopping rule (Sec. 5 metric r, reading: the maximum over load cases must meet tol).
+// Gauge (Sec. 3.1 zero-mean constraint): the mean over active nodes of every component
+// and case is removed from the final field. Load cases whose assembled load cancels
+// (||f_m|| <= 1e-12 of its gross element-load norm) have u_m = 0 and r_m = 0.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "stencil.cuh"
+
+namespace gmt {
+
+// deterministic pseudo-random fill (power iteration start vector)
+__global__ void k_hash_fill(float* __restrict__ x, const uint8_t* __restrict__ mask, int C,
+                            int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
+  uint32_t hsh = (uint32_t)(i * 2654435761ull) ^ 0x9e3779b9u;
+  hsh ^= hsh >> 16;
+  hsh *= 0x7feb352du;
+  hsh ^= hsh >> 15;
+  hsh *= 0x846ca68bu;
+  hsh ^= hsh >> 16;
+  x[i] = mask[slot] ? ((float)(hsh & 0xffffff) / 16777216.0f - 0.5f) : 0.0f;
+}
+
+// level-0 load f (from masks) and its per-case norms; f_n = sum_{a in mask} (K_e x0)[a]
+template <typename TS, typename A, int D, int M>
+__global__ void k_fine_load(const uint8_t* __restrict__ mask, TS* __restrict__ out,
+                            double* __restrict__ part, const __grid_constant__ Material mt) {
+  constexpr int C = D * M;
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  const unsigned mk = mask[b * 64 + t];
+  double nrm[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) nrm[m] = 0.0;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int i = v / M, m = v % M;
+    A f = A(0);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if ((mk >> a) & 1u) f += (A)mt.Fe[(a * D + i) * M + m];
+    out[b * 64 * C + v * 64 + t] = store_as<TS>(f);
+    nrm[m] += (double)f * (double)f;
+  }
+  // block reduce
+  __shared__ double red[2][6];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    double x = nrm[m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) red[t >> 5][m] = x;
+  }
+  __syncthreads();
+  if (t < M) part[b * M + t] = red[0][t] + red[1][t];
+}
+
+struct Workspace {
+  Prec prec = P32;       // inner storage precision
+  Prec arith = P32;      // CG vector precision (P64 for the FP64 solve, else P32)
+  std::vector<void*> ua, ub, f, r, dc;  // per level: ping-pong u, rhs, residual, Chebyshev d
+  void *x = nullptr, *rr = nullptr, *p = nullptr, *q = nullptr, *cvt = nullptr;
+  float *hi = nullptr, *lo = nullptr, *rout = nullptr;
+  double* u64 = nullptr;
+  double* f64 = nullptr;
+  double* part = nullptr;
+  int64_t part_rows = 0;
+  double* red = nullptr;     // reduction slots, 8 x 32 doubles
+  int* active = nullptr;     // per case flags (device)
+  double* ones = nullptr;    // per case 1.0 (device)
+};
+
+void free_workspace(gmt_hierarchy* h) {
+  h->work.release();
+  delete h->ws;
+  h->ws = nullptr;
+  h->ws_for_prec = -1;
+}
+
+static Workspace* workspace(gmt_hierarchy* h, Prec prec) {
+  if (h->ws && h->ws_for_prec == (int64_t)prec) return h->ws;
+  free_workspace(h);
+  Workspace* w = new Workspace();
+  h->ws = w;
+  h->ws_for_prec = prec;
+  w->prec = prec;
+  w->arith = prec == P64 ? P64 : P32;
+  const int C = h->mat.C;
+  const size_t sb = prec_bytes(prec), ab = prec_bytes(w->arith);
+  for (int l = 0; l < h->L; ++l) {
+    const int64_t nv = h->lv[l].nslots * C;
+    w->ua.push_back(h->work.raw(nv * sb));
+    w->ub.push_back(h->work.raw(nv * sb));
+    w->f.push_back(h->work.raw(nv * sb));
+    w->r.push_back(h->work.raw(nv * sb));
+    w->dc.push_back(h->work.raw(nv * sb));
+  }
+  const int64_t n0 = h->lv[0].nslots * C;
+  w->x = h->work.raw(n0 * ab);
+  w->rr = h->work.raw(n0 * ab);
+  w->p = h->work.raw(n0 * ab);
+  w->q = h->work.raw(n0 * ab);
+  w->cvt = h->work.raw(n0 * ab);
+  w->hi = h->work.alloc<float>(n0);
+  w->lo = h->work.alloc<float>(n0);
+  w->rout = h->work.alloc<float>(n0);
+  w->u64 = h->work.alloc<double>(n0);
+  w->f64 = h->work.alloc<double>(n0);
+  int64_t rows = 1;
+  for (int l = 0; l < h->L; ++l) rows = std::max<int64_t>(rows, h->lv[l].nb);
+  w->part_rows = rows;
+  w->part = h->work.alloc<double>(rows * 32);
+  w->red = h->work.alloc<double>(8 * 32);
+  w->active = h->work.alloc<int>(8);
+  w->ones = h->work.alloc<double>(8);
+  double ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  GMT_CUDA(cudaMemcpyAsync(w->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream));
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  return w;
+}
+
+// reduce the [nb][K] partials of `level` into red slot `slot` (device)
+static double* reduce_to(gmt_hierarchy* h, Workspace* w, int level, int K, int slot) {
+  double* out = w->red + slot * 32;
+  launch_reduce(h, w->part, h->lv[level].nb, K, out);
+  return out;
+}
+
+static void fetch(gmt_hierarchy* h, const double* dev, double* host, int n) {
+  GMT_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ------------------------------------------------------------------ smoother / V-cycle
+// smooth `sweeps` times on level l from *u (or zero); the result pointer is returned in *u
+// (it alternates between the level's two buffers)
+static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** u, void** other,
+                   int sweeps, bool zero) {
+  const gmt_options& o = h->opts;
+  const Prec pr = w->prec;
+  if (sweeps <= 0) {
+    if (zero) vec_zero(h, l, pr, *u);
+    return;
+  }
+  if (o.smoother == GMT_SMOOTH_JACOBI) {
+    int s0 = 0;
+    if (zero) {
+      launch_diag(h, l, pr, f, *u, nullptr, o.omega);
+      s0 = 1;
+    }
+    for (int s = s0; s < sweeps; ++s) {
+      VecArgs a;
+      a.u = *u;
+      a.f = f;
+      a.out = *other;
+      a.omega = o.omega;
+      launch_stencil(h, l, pr, ST_JACOBI, a);
+      std::swap(*u, *other);
+    }
+    return;
+  }
+  // Chebyshev polynomial of degree `sweeps` on D^-1 K over [lmax/ratio, upper*lmax]
+  const double lmax = h->lv[l].lmax;
+  const double bnd = o.cheb_upper * lmax, a0 = lmax / o.cheb_ratio;
+  const double theta = 0.5 * (bnd + a0), delta = 0.5 * (bnd - a0), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  void* d = w->dc[l];
+  int s0 = 0;
+  if (zero) {
+    launch_diag(h, l, pr, f, *u, d, 1.0 / theta);  // d0 = D^-1 f / theta, u1 = d0
+    s0 = 1;
+  } else {
+    VecArgs a;  // d0 = D^-1 (f - K u) / theta, u1 = u + d0
+    a.u = *u;
+    a.f = f;
+    a.dprev = d;
+    a.out = *other;
+    a.dout = d;
+    a.c1 = 0.0;
+    a.c2 = 1.0 / theta;
+    launch_stencil(h, l, pr, ST_CHEB, a);
+    std::swap(*u, *other);
+    s0 = 1;
+  }
+  for (int s = s0; s < sweeps; ++s) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    VecArgs a;
+    a.u = *u;
+    a.f = f;
+    a.dprev = d;
+    a.out = *other;
+    a.dout = (s + 1 < sweeps) ? d : nullptr;
+    a.c1 = rho_new * rho;
+    a.c2 = 2.0 * rho_new / delta;
+    launch_stencil(h, l, pr, ST_CHEB, a);
+    std::swap(*u, *other);
+    rho = rho_new;
+  }
+}
+
+// One V-cycle on level l for K_l u = f (u zero on entry when zero == true). Returns the
+// buffer that holds the result: one of the level's two ping-pong buffers (level 0: ua/ub).
+static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* u_init, bool zero) {
+  const Prec pr = w->prec;
+  if (l == h->L - 1) {
+    launch_coarse_solve(h, pr, f, w->ua[l]);
+    return w->ua[l];
+  }
+  void* u = zero ? w->ua[l] : u_init;
+  void* other = (u == w->ua[l]) ? w->ub[l] : w->ua[l];
+  smooth(h, w, l, f, &u, &other, h->opts.nu_pre, zero);
+  VecArgs a;
+  a.u = u;
+  a.f = f;
+  a.out = w->r[l];
+  launch_stencil(h, l, pr, ST_RESID, a);
+  launch_restrict(h, l, pr, w->r[l], w->f[l + 1]);
+  void* uc = vcycle(h, w, l + 1, w->f[l + 1], nullptr, true);
+  launch_prolong(h, l, pr, uc, u);
+  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false);
+  return u;
+}
+
+// ------------------------------------------------------------------ Chebyshev bounds
+void estimate_lmax(gmt_hierarchy* h) {
+  Workspace* w = workspace(h, P32);
+  const int C = h->mat.C, M = h->mat.M;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const int64_t n = h->lv[l].nslots * C;
+    float* x = (float*)w->ua[l];
+    float* y = (float*)w->ub[l];
+    k_hash_fill<<<grid_for(n, 256), 256, 0, h->stream>>>(x, h->lv[l].mask, C, n);
+    GMT_LAUNCH_CHECK();
+    double lam = 0.0;
+    for (int it = 0; it < 20; ++it) {
+      VecArgs a;
+      a.u = x;
+      a.out = y;
+      launch_stencil(h, l, P32, ST_APPLY, a);
+      launch_diag(h, l, P32, y, y, nullptr, 1.0);   // y = D^-1 K x (pointwise, in place)
+      vec_dot(h, l, P32, y, y, w->part);
+      double* yy = reduce_to(h, w, l, M, 0);
+      vec_dot(h, l, P32, x, y, w->part);
+      double* xy = reduce_to(h, w, l, M, 1);
+      vec_dot(h, l, P32, x, x, w->part);
+      double* xx = reduce_to(h, w, l, M, 2);
+      double hy[8], hxy[8], hx[8];
+      fetch(h, yy, hy, M);
+      fetch(h, xy, hxy, M);
+      fetch(h, xx, hx, M);
+      lam = 0.0;
+      double sc[8];
+      for (int m = 0; m < M; ++m) {
+        lam = std::max(lam, std::sqrt(hy[m] / std::max(hx[m], 1e-300)));
+        sc[m] = 1.0 / std::sqrt(std::max(hy[m], 1e-300));
+      }
+      GMT_CUDA(cudaMemcpyAsync(w->red + 3 * 32, sc, M * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream));
+      vec_scale_cases(h, l, P32, w->red + 3 * 32, y);
+      std::swap(x, y);
+    }
+    h->lv[l].lmax = lam;
+  }
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ------------------------------------------------------------------ inner iteration
+// Solve K x = b (b in w->rr on entry, arith precision) to a relative reduction inner_tol
+// per active case; x in w->x. Returns the number of V-cycles applied.
+static int inner_solve(gmt_hierarchy* h, Workspace* w, const bool* act_host, double inner_tol,
+                       int max_inner, double* final_rel) {
+  const int M = h->mat.M;
+  const Prec ar = w->arith;
+  const bool krylov = h->opts.krylov != 0;
+  int act[8] = {0};
+  for (int m = 0; m < M; ++m) act[m] = act_host[m];
+  GMT_CUDA(cudaMemcpyAsync(w->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
+  vec_zero(h, 0, ar, w->x);
+  vec_dot(h, 0, ar, w->rr, w->rr, w->part);
+  double r0h[8];
+  fetch(h, reduce_to(h, w, 0, M, 0), r0h, M);
+  for (int m = 0; m < M; ++m) {
+    r0h[m] = std::sqrt(r0h[m]);
+    if (r0h[m] == 0.0) act[m] = 0;
+  }
+  GMT_CUDA(cudaMemcpyAsync(w->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
+  // preconditioner application z = V(rr)
+  auto precond = [&]() -> void* {
+    const void* fin = w->rr;
+    if (w->prec != ar) {  // (bf16 inner storage) convert rr
+      GMT_REQUIRE(false, GMT_ERR_ARG, "mixed storage precision not supported");
+    }
+    return vcycle(h, w, 0, fin, nullptr, true);
+  };
+  int cycles = 0;
+  void* z = precond();
+  ++cycles;
+  double* rz = w->red + 4 * 32;  // device: r.z per case
+  double* pq = w->red + 5 * 32;
+  double* rz_new = w->red + 6 * 32;
+  if (krylov) {
+    vec_copy(h, 0, ar, z, w->p);
+    vec_dot(h, 0, ar, w->rr, z, w->part);
+    launch_reduce(h, w->part, h->lv[0].nb, M, rz);
+  }
+  double rel = 1.0;
+  for (int it = 0; it < max_inner; ++it) {
+    VecArgs a;
+    if (krylov) {
+      a.u = w->p;
+      a.out = w->q;
+      a.part = w->part;
+      launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K p, part = p.q
+      launch_reduce(h, w->part, h->lv[0].nb, M, pq);
+      vec_cg_update(h, ar, rz, pq, w->active, w->x, w->p, w->rr, w->q, w->part);
+    } else {
+      a.u = z;
+      a.out = w->q;
+      launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K z
+      vec_cg_update(h, ar, w->ones, w->ones, w->active, w->x, z, w->rr, w->q, w->part);
+    }
+    double rn[8];
+    fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+    rel = 0.0;
+    bool done = true;
+    for (int m = 0; m < M; ++m) {
+      if (!act[m]) continue;
+      const double rm = std::sqrt(rn[m]) / r0h[m];
+      if (!(rm <= inner_tol)) done = false;
+      if (std::isnan(rm)) {
+        rel = rm;
+        done = true;
+        break;
+      }
+      rel = std::max(rel, rm);
+    }
+    if (done || it + 1 == max_inner) break;
+    z = precond();
+    ++cycles;
+    if (krylov) {
+      vec_dot(h, 0, ar, w->rr, z, w->part);
+      launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
+      vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
+      GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+  }
+  if (final_rel) *final_rel = rel;
+  return cycles;
+}
+
+// ------------------------------------------------------------------ solve
+static Prec prec_of(int p) { return p == GMT_PREC_FP64 ? P64 : (p == GMT_PREC_BF16 ? PBF : P32); }
+
+gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, gmt_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const gmt_options& o = h->opts;
+  const Prec pr = prec_of(o.precision);
+  GMT_REQUIRE(pr != PBF, GMT_ERR_ARG, "BF16 inner precision is not available in this build");
+  if (o.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1 && h->lv[0].lmax == 0.0) estimate_lmax(h);
+  Workspace* w = workspace(h, pr);
+  const int M = h->mat.M;
+  const Material& mt = h->mat;
+  // ||f_m|| and the load-cancellation rule
+  const unsigned nb0 = (unsigned)h->lv[0].nb;
+  if (mt.D == 3)
+    k_fine_load<double, double, 3, 6><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
+  else
+    k_fine_load<double, double, 1, 3><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
+  GMT_LAUNCH_CHECK();
+  double fn[8];
+  fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
+  bool act[8] = {false};
+  for (int m = 0; m < M; ++m) {
+    fn[m] = std::sqrt(fn[m]);
+    act[m] = fn[m] > 1e-12 * mt.gross[m];
+  }
+  double rel[8] = {0};
+  int outer = 0, cycles = 0;
+  gmt_status st = GMT_NOT_CONVERGED;
+  double first_max = -1.0;
+  auto residual = [&](bool ff) {
+    double rn[8];
+    if (ff) {
+      launch_resid_ff(h, w->hi, w->lo, w->rout, w->part);
+    } else {
+      VecArgs a;
+      a.u = w->u64;
+      a.f = nullptr;
+      a.out = w->rr;
+      a.part = w->part;
+      launch_stencil(h, 0, P64, ST_RESID, a);
+    }
+    fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+    double mx = 0.0;
+    for (int m = 0; m < M; ++m) {
+      rel[m] = act[m] ? std::sqrt(rn[m]) / fn[m] : 0.0;
+      if (act[m]) mx = std::max(mx, rel[m]);
+    }
+    return mx;
+  };
+  if (pr == P64) {
+    if (u0) canon_to_slots(h, 0, P64, u0, w->u64);
+    else vec_zero(h, 0, P64, w->u64);
+  } else {
+    if (u0) canon_to_ff(h, u0, w->hi, w->lo);
+    else {
+      vec_zero(h, 0, P32, w->hi);
+      vec_zero(h, 0, P32, w->lo);
+    }
+  }
+  for (;;) {
+    const double mx = residual(pr != P64);
+    if (first_max < 0) first_max = mx;
+    if (std::isnan(mx) || mx > 1e4 * std::max(first_max, 1e-300)) {
+      st = GMT_DIVERGED;
+      break;
+    }
+    if (mx <= tol) {
+      st = GMT_OK;
+      break;
+    }
+    if (outer >= o.max_outer) break;
+    bool ia[8];
+    for (int m = 0; m < M; ++m) ia[m] = act[m] && rel[m] > tol;
+    if (pr == P64) {
+      // FP64: one inner CG to the full tolerance
+      double itol = tol / std::max(mx, 1e-300) * 0.5;
+      cycles += inner_solve(h, w, ia, std::min(itol, 0.5), o.max_inner, nullptr);
+      vec_add(h, 0, P64, w->x, w->u64);
+    } else {
+      vec_copy(h, 0, P32, w->rout, w->rr);
+      cycles += inner_solve(h, w, ia, o.inner_tol, o.max_inner, nullptr);
+      vec_ff_add(h, (const float*)w->x, w->hi, w->lo);
+    }
+    ++outer;
+  }
+  // gauge: remove the mean of every component and case over active nodes
+  {
+    const int C = mt.C;
+    if (pr == P64) vec_sum_values(h, 0, P64, w->u64, nullptr, w->part);
+    else vec_sum_values(h, 0, P32, w->hi, w->lo, w->part);
+    double* sums = reduce_to(h, w, 0, C, 1);
+    double hs[18];
+    fetch(h, sums, hs, C);
+    for (int v = 0; v < C; ++v) hs[v] /= (double)h->lv[0].n_nodes;
+    GMT_CUDA(cudaMemcpyAsync(w->red + 2 * 32, hs, C * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (pr == P64) vec_sub_mean64(h, 0, w->red + 2 * 32, w->u64);
+    else vec_ff_sub_mean(h, w->red + 2 * 32, w->hi, w->lo);
+  }
+  if (u_out) {
+    if (pr == P64) slots_to_canon(h, 0, P64, w->u64, u_out);
+    else ff_to_canon(h, w->hi, w->lo, u_out);
+  }
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  h->have_solution = true;
+  if (info) {
+    info->outer = outer;
+    info->inner_total = cycles;
+    info->cases = M;
+    for (int m = 0; m < 6; ++m) info->rel_residual[m] = m < M ? rel[m] : 0.0;
+    info->t_solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
+}
+
+// C^H from the stored solution (u == nullptr) or a canonical field
+void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
+  const Material& mt = h->mat;
+  const int M = mt.M, K = M * (M + 1) / 2;
+  Workspace* w = h->ws;
+  Prec pr = w ? w->prec : P32;
+  if (!w) w = workspace(h, P32);
+  if (u) {
+    // external field: float-float split of the FP64 input
+    canon_to_ff(h, u, w->hi, w->lo);
+    pr = P32;
+  }
+  if (pr == P64) launch_energy(h, P64, w->u64, nullptr, w->part);
+  else launch_energy(h, P32, w->hi, w->lo, w->part);
+  double e[21];
+  fetch(h, reduce_to(h, w, 0, K, 0), e, K);
+  const double vol = (double)h->N * h->N * h->N;
+  for (int I = 0; I < M; ++I)
+    for (int J = I; J < M; ++J) {
+      const double v = e[I * M - I * (I - 1) / 2 + (J - I)] / vol;
+      CH[I * M + J] = v;
+      CH[J * M + I] = v;
+    }
+}
+
+// relative residuals of a canonical field
+void residual_of(gmt_hierarchy* h, int precision, const double* u, double* out) {
+  const Material& mt = h->mat;
+  const int M = mt.M;
+  Workspace* w = workspace(h, h->ws ? (Prec)h->ws_for_prec : P32);
+  const unsigned nb0 = (unsigned)h->lv[0].nb;
+  if (mt.D == 3)
+    k_fine_load<double, double, 3, 6><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
+  else
+    k_fine_load<double, double, 1, 3><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
+  GMT_LAUNCH_CHECK();
+  double fn[8], rn[8];
+  fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
+  if (precision == GMT_PREC_FP64) {
+    canon_to_slots(h, 0, P64, u, w->u64);
+    VecArgs a;
+    a.u = w->u64;
+    a.out = w->f64;
+    a.part = w->part;
+    launch_stencil(h, 0, P64, ST_RESID, a);
+  } else {
+    float* hi = (float*)w->cvt;  // scratch of >= n0 floats
+    float* lo = w->rout;
+    canon_to_ff(h, u, hi, lo);
+    launch_resid_ff(h, hi, lo, (float*)w->q, w->part);
+  }
+  fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+  for (int m = 0; m < M; ++m) {
+    const double f = std::sqrt(fn[m]);
+    out[m] = f > 1e-12 * mt.gross[m] ? std::sqrt(rn[m]) / f : std::sqrt(rn[m]);
+  }
+}
+
+// ------------------------------------------------------------------ per-step entry points
+void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, level, pr, u, w->ua[level]);
+  VecArgs a;
+  a.u = w->ua[level];
+  a.out = w->ub[level];
+  launch_stencil(h, level, pr, ST_APPLY, a);
+  slots_to_canon(h, level, pr, w->ub[level], y);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void step_smooth(gmt_hierarchy* h, int level, int precision, const double* f, double* u,
+                 int sweeps, bool zero) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  if (h->opts.smoother == GMT_SMOOTH_CHEBYSHEV && h->lv[level].lmax == 0.0) estimate_lmax(h);
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, level, pr, f, w->f[level]);
+  void* cur = w->ua[level];
+  void* oth = w->ub[level];
+  if (!zero) canon_to_slots(h, level, pr, u, cur);
+  smooth(h, w, level, w->f[level], &cur, &oth, sweeps, zero);
+  slots_to_canon(h, level, pr, cur, u);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void step_restrict(gmt_hierarchy* h, int level, int precision, const double* rf, double* fc) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, level, pr, rf, w->r[level]);
+  launch_restrict(h, level, pr, w->r[level], w->f[level + 1]);
+  slots_to_canon(h, level + 1, pr, w->f[level + 1], fc);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void step_prolong(gmt_hierarchy* h, int level, int precision, const double* uc, double* uf) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, level + 1, pr, uc, w->ua[level + 1]);
+  canon_to_slots(h, level, pr, uf, w->ub[level]);
+  launch_prolong(h, level, pr, w->ua[level + 1], w->ub[level]);
+  slots_to_canon(h, level, pr, w->ub[level], uf);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void step_coarse(gmt_hierarchy* h, const double* f, double* u) {
+  Workspace* w = workspace(h, P64);
+  const int lc = h->L - 1;
+  canon_to_slots(h, lc, P64, f, w->f[lc]);
+  launch_coarse_solve(h, P64, w->f[lc], w->ua[lc]);
+  slots_to_canon(h, lc, P64, w->ua[lc], u);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  if (h->opts.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1 && h->lv[0].lmax == 0.0) estimate_lmax(h);
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, 0, pr, f, w->f[0]);
+  void* init = nullptr;
+  if (!zero) {
+    canon_to_slots(h, 0, pr, u, w->ua[0]);
+    init = w->ua[0];
+  }
+  void* res = vcycle(h, w, 0, w->f[0], init, zero);
+  slots_to_canon(h, 0, pr, res, u);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+}  // namespace gmt

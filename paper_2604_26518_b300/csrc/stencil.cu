@@ -1,0 +1,1204 @@
+// Hot-path kernels: the matrix-free element-by-element operator (Sec. 4.6
+// "Matrix-Free EBE Formulation": K u = sum_e A_e^T K_e A_e u_e), applied node by node, the
+// damped block-Jacobi / Chebyshev smoother (Sec. 4.6 "Parallel Smoothing" update form
+// u <- u + omega D^-1 r, all nodes at once), the trilinear transfers (App. E.2, restriction
+// written as a gather so every sum has a fixed order), the coarsest solve (Alg. 1), the
+// element-energy reduction for C^H (App. F.1/F.2) and the vector kernels of the solver.
+//
+// Node-centric operator. For node n with octant mask m(n),
+//     (K u)_n = sum_{d in {-1,0,1}^3} S_n(d) u_{n+d},
+//     S_n(d) = sum_{a in {0,1}^3, a+d in {0,1}^3} [element n-a active] K(n-a)[a, a+d],
+// i.e. the node's rows of every active incident element (a = local index of n in element
+// n - a). At level 0 every element carries the same K_e, which is passed in the kernel's
+// parameter (constant) bank, so the D x D blocks S_n(d) are formed in registers from the
+// mask bits and K_e operands; coarser levels read each incident element's Galerkin matrix.
+// One 64-thread block owns one 4^3 brick and stages the brick plus a one-node halo
+// (6^3 nodes x C values) in shared memory; every output sum runs in a fixed order.
+#include <cstring>
+
+#include "stencil.cuh"
+
+namespace gmt {
+
+// ------------------------------------------------------------------ parameters
+template <typename A, int D, int M>
+struct FineC {
+  A Ke[64 * D * D];  // (8D) x (8D)
+  A Fe[8 * D * M];   // K_e x0, (8D) x M
+};
+
+template <typename TS, typename A, int D, int M>
+struct StArgs {
+  const int* nbr;
+  const uint8_t* mask;
+  const int* kidx;
+  const A* kmat;
+  const A* dinv;
+  const TS* u;
+  const TS* f;
+  const TS* dprev;
+  TS* out;
+  TS* dout;
+  double* part;
+  A omega, c1, c2;
+  FineC<A, D, M> fc;
+};
+
+template <typename T> struct ArithOf { using type = float; };
+template <> struct ArithOf<double> { using type = double; };
+
+// ------------------------------------------------------------------ block reduction helper
+template <int K>
+__device__ __forceinline__ void block_partial_64(double (&v)[K], double* __restrict__ out) {
+  // 64-thread block: reduce K values per thread into out[K] (fixed order)
+  __shared__ double red[2][K > 0 ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[k] = x;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[w][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < K) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+}
+
+// symmetric-positive D x D inverse (D = 1 or 3)
+template <typename A, int D>
+__device__ __forceinline__ void inv_block(const A (&Bk)[D * D], A (&I)[D * D]) {
+  if constexpr (D == 1) {
+    I[0] = A(1) / Bk[0];
+  } else {
+    A c00 = Bk[4] * Bk[8] - Bk[5] * Bk[7], c01 = Bk[5] * Bk[6] - Bk[3] * Bk[8],
+      c02 = Bk[3] * Bk[7] - Bk[4] * Bk[6];
+    A id = A(1) / (Bk[0] * c00 + Bk[1] * c01 + Bk[2] * c02);
+    I[0] = c00 * id;
+    I[1] = (Bk[2] * Bk[7] - Bk[1] * Bk[8]) * id;
+    I[2] = (Bk[1] * Bk[5] - Bk[2] * Bk[4]) * id;
+    I[3] = c01 * id;
+    I[4] = (Bk[0] * Bk[8] - Bk[2] * Bk[6]) * id;
+    I[5] = (Bk[2] * Bk[3] - Bk[0] * Bk[5]) * id;
+    I[6] = c02 * id;
+    I[7] = (Bk[1] * Bk[6] - Bk[0] * Bk[7]) * id;
+    I[8] = (Bk[0] * Bk[4] - Bk[1] * Bk[3]) * id;
+  }
+}
+
+// level-0 diagonal block D_n = sum_{a in mask} K_e[a, a]
+template <typename A, int D, int M>
+__device__ __forceinline__ void fine_diag_inv(const FineC<A, D, M>& fc, unsigned mk,
+                                              A (&I)[D * D]) {
+  A Bk[D * D];
+#pragma unroll
+  for (int q = 0; q < D * D; ++q) Bk[q] = A(0);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const A bit = ((mk >> a) & 1u) ? A(1) : A(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Bk[i * D + j] += bit * fc.Ke[(a * D + i) * (8 * D) + a * D + j];
+  }
+  inv_block<A, D>(Bk, I);
+}
+
+// ------------------------------------------------------------------ the stencil kernel
+template <typename TS, typename A, int D, int M, int KIND, int MODE>
+__global__ void __launch_bounds__(64)
+    k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
+  constexpr int C = D * M, R = 8 * D, MM = R * R;
+  __shared__ A tile[C * 216];
+  __shared__ int nb[27];
+  __shared__ int eid[KIND == 0 ? 1 : 125];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (t < 27) nb[t] = p.nbr[b * 27 + t];
+  __syncthreads();
+  for (int i = t; i < C * 216; i += 64) {
+    const int v = i / 216, q = i - v * 216;
+    const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
+    const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
+    const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
+    const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
+    const int nbi = nb[bz * 9 + by * 3 + bx];
+    A val = A(0);
+    if (nbi >= 0)
+      val = load_as<A>(p.u + (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) +
+                       4 * ((ty + 3) & 3) + 16 * ((tz + 3) & 3));
+    tile[i] = val;
+  }
+  if constexpr (KIND != 0) {
+    for (int i = t; i < 125; i += 64) {
+      const int ex = i % 5, ey = (i / 5) % 5, ez = i / 25;
+      const int nbi = nb[(ez == 0 ? 0 : 1) * 9 + (ey == 0 ? 0 : 1) * 3 + (ex == 0 ? 0 : 1)];
+      eid[i] = nbi >= 0 ? p.kidx[(int64_t)nbi * 64 + ((ex + 3) & 3) + 4 * ((ey + 3) & 3) +
+                                 16 * ((ez + 3) & 3)]
+                        : -1;
+    }
+  }
+  __syncthreads();
+  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
+  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
+  const int64_t slot = b * 64 + t;
+  const unsigned mk = p.mask[slot];
+  A acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = A(0);
+  if (mk) {
+    A bf[8];
+    const A* Km[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if constexpr (KIND == 0) {
+        bf[a] = ((mk >> a) & 1u) ? A(1) : A(0);
+      } else {
+        const int e = eid[(lx + 1 - (a & 1)) + 5 * (ly + 1 - ((a >> 1) & 1)) +
+                          25 * (lz + 1 - (a >> 2))];
+        Km[a] = e >= 0 ? p.kmat + (int64_t)e * MM : nullptr;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      A S[D * D];
+#pragma unroll
+      for (int k = 0; k < D * D; ++k) S[k] = A(0);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+        const int bb = ex + 2 * ey + 4 * ez;
+        if constexpr (KIND == 0) {
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+              S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+        } else {
+          if (Km[a] != nullptr) {
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+              for (int j = 0; j < D; ++j) S[i * D + j] += Km[a][(a * D + i) * R + bb * D + j];
+          }
+        }
+      }
+      const int q = q0 + dx + 6 * dy + 36 * dz;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const A uv = tile[(j * M + m) * 216 + q];
+#pragma unroll
+          for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * uv;
+        }
+      }
+    }
+  }
+  const int64_t base = b * (64 * C) + t;
+  if constexpr (MODE == ST_APPLY) {
+    double dots[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) dots[m] = 0.0;
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+      p.out[base + v * 64] = store_as<TS>(mk ? acc[v] : A(0));
+      if (mk) dots[v % M] += (double)(tile[v * 216 + q0] * acc[v]);
+    }
+    if (p.part) block_partial_64<M>(dots, p.part + b * M);
+  } else if constexpr (MODE == ST_RESID) {
+    double nrm[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) nrm[m] = 0.0;
+#pragma unroll
+    for (int v = 0; v < C; ++v) {
+      A fv;
+      if constexpr (KIND == 0) {
+        if (p.f != nullptr) {
+          fv = load_as<A>(p.f + base + v * 64);
+        } else {  // level-0 load from the mask: f_n = sum_{a in mask} (K_e x0)[a]
+          fv = A(0);
+          const int i = v / M, m = v % M;
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+            fv += (((mk >> a) & 1u) ? A(1) : A(0)) * p.fc.Fe[(a * D + i) * M + m];
+        }
+      } else {
+        fv = load_as<A>(p.f + base + v * 64);
+      }
+      const A r = mk ? fv - acc[v] : A(0);
+      p.out[base + v * 64] = store_as<TS>(r);
+      nrm[v % M] += (double)r * (double)r;
+    }
+    if (p.part) block_partial_64<M>(nrm, p.part + b * M);
+  } else {
+    A Iv[D * D];
+    if (mk) {
+      if constexpr (KIND == 0) {
+        fine_diag_inv<A, D, M>(p.fc, mk, Iv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < D * D; ++k) Iv[k] = p.dinv[slot * D * D + k];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      A r[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) r[i] = load_as<A>(p.f + base + (i * M + m) * 64) - acc[i * M + m];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        A z = A(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) z += Iv[i * D + j] * r[j];
+        const int v = i * M + m;
+        const A self = tile[v * 216 + q0];
+        if constexpr (MODE == ST_JACOBI) {
+          p.out[base + v * 64] = store_as<TS>(mk ? self + p.omega * z : A(0));
+        } else {
+          const A dn = (p.c1 != A(0) ? p.c1 * load_as<A>(p.dprev + base + v * 64) : A(0)) + p.c2 * z;
+          p.out[base + v * 64] = store_as<TS>(mk ? self + dn : A(0));
+          if (p.dout) p.dout[base + v * 64] = store_as<TS>(mk ? dn : A(0));
+        }
+      }
+    }
+  }
+}
+
+// first smoothing step from a zero initial guess: out = scale * D^-1 f
+template <typename TS, typename A, int D, int M, int KIND>
+__global__ void k_diag(const __grid_constant__ StArgs<TS, A, D, M> p, int64_t nslots) {
+  constexpr int C = D * M;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslots) return;
+  const unsigned mk = p.mask[slot];
+  A Iv[D * D];
+  if (mk) {
+    if constexpr (KIND == 0) {
+      fine_diag_inv<A, D, M>(p.fc, mk, Iv);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D * D; ++k) Iv[k] = p.dinv[slot * D * D + k];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    A f[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) f[i] = load_as<A>(p.f + vaddr(slot, i * M + m, C));
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      A z = A(0);
+#pragma unroll
+      for (int j = 0; j < D; ++j) z += Iv[i * D + j] * f[j];
+      const A o = mk ? p.omega * z : A(0);
+      p.out[vaddr(slot, i * M + m, C)] = store_as<TS>(o);
+      if (p.dout) p.dout[vaddr(slot, i * M + m, C)] = store_as<TS>(o);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ float-float residual
+template <int D, int M>
+struct FFArgs {
+  const int* nbr;
+  const uint8_t* mask;
+  const float* hi;
+  const float* lo;
+  float* out;
+  double* part;
+  FineC<float, D, M> fc;
+};
+
+// r = f - K u at level 0 with u = hi + lo, in difference form
+//   (K u)_n = sum_{d != 0} S_n(d) (u_{n+d} - u_n)     (rows of K sum to zero),
+// each difference formed as (hi_{n+d} - hi_n) + (lo_{n+d} - lo_n) in FP32: the differences
+// of a smooth field are O(1) while u itself grows with N, so FP32 arithmetic on them keeps
+// the residual accurate to ~1e-7 of the load without FP64 instructions.
+template <int D, int M>
+__global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<D, M> p) {
+  constexpr int C = D * M, R = 8 * D;
+  __shared__ float th[C * 216];
+  __shared__ float tl[C * 216];
+  __shared__ int nb[27];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (t < 27) nb[t] = p.nbr[b * 27 + t];
+  __syncthreads();
+  for (int i = t; i < C * 216; i += 64) {
+    const int v = i / 216, q = i - v * 216;
+    const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
+    const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
+    const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
+    const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
+    const int nbi = nb[bz * 9 + by * 3 + bx];
+    float h = 0.f, l = 0.f;
+    if (nbi >= 0) {
+      const int64_t a = (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
+                        16 * ((tz + 3) & 3);
+      h = p.hi[a];
+      l = p.lo[a];
+    }
+    th[i] = h;
+    tl[i] = l;
+  }
+  __syncthreads();
+  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
+  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
+  const int64_t slot = b * 64 + t;
+  const unsigned mk = p.mask[slot];
+  float acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = 0.f;
+  if (mk) {
+    float bf[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) bf[a] = ((mk >> a) & 1u) ? 1.f : 0.f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13) continue;  // d = 0 carries no difference
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float S[D * D];
+#pragma unroll
+      for (int k = 0; k < D * D; ++k) S[k] = 0.f;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+        const int bb = ex + 2 * ey + 4 * ez;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+            S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+      }
+      const int q = q0 + dx + 6 * dy + 36 * dz;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int v = j * M + m;
+          const float du = (th[v * 216 + q] - th[v * 216 + q0]) + (tl[v * 216 + q] - tl[v * 216 + q0]);
+#pragma unroll
+          for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * du;
+        }
+      }
+    }
+  }
+  double nrm[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) nrm[m] = 0.0;
+  const int64_t base = b * (64 * C) + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int i = v / M, m = v % M;
+    float fv = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fv += (((mk >> a) & 1u) ? 1.f : 0.f) * p.fc.Fe[(a * D + i) * M + m];
+    const float r = mk ? fv - acc[v] : 0.f;
+    p.out[base + v * 64] = r;
+    nrm[m] += (double)r * (double)r;
+  }
+  if (p.part) block_partial_64<M>(nrm, p.part + b * M);
+}
+
+// ------------------------------------------------------------------ transfers
+struct LvView {
+  int n, nbx;
+  bool dense;
+  int64_t nslots;
+  const int* bmap;
+  const int* bxyz;
+  const uint8_t* mask;
+};
+
+static LvView view(const Level& l) {
+  return LvView{l.n, l.nbx, l.dense, l.nslots, l.brick_map, l.brick_xyz, l.mask};
+}
+
+// f_c(j) = sum_{d in {-1,0,1}^3} prod_k (1 - |d_k|/2) r_f(2j + d): the transpose of the
+// trilinear prolongation of App. E.2, gathered per coarse node
+template <typename TS, typename A, int C>
+__global__ void k_restrict(const TS* __restrict__ rf, TS* __restrict__ fc, LvView f, LvView c) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= c.nslots) return;
+  A acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = A(0);
+  if (c.mask[s]) {
+    int X, Y, Z;
+    slot_coords(s, c.n, c.dense, c.bxyz, X, Y, Z);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const A w = (dx ? A(0.5) : A(1)) * (dy ? A(0.5) : A(1)) * (dz ? A(0.5) : A(1));
+      const int fx = (2 * X + dx + f.n) % f.n, fy = (2 * Y + dy + f.n) % f.n,
+                fz = (2 * Z + dz + f.n) % f.n;
+      const int64_t fs = site_slot(fx, fy, fz, f.n, f.nbx, f.bmap, false);
+      if (fs < 0) continue;
+#pragma unroll
+      for (int v = 0; v < C; ++v) acc[v] += w * load_as<A>(rf + vaddr(fs, v, C));
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < C; ++v) fc[vaddr(s, v, C)] = store_as<TS>(acc[v]);
+}
+
+// u_f(i) += sum_k W_ik u_c(I_ik) (App. E.2 weighted gather)
+template <typename TS, typename A, int C>
+__global__ void k_prolong(const TS* __restrict__ uc, TS* __restrict__ uf, LvView f, LvView c) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= f.nslots || !f.mask[s]) return;
+  int x, y, z;
+  slot_coords(s, f.n, false, f.bxyz, x, y, z);
+  const int xs[3] = {x, y, z};
+  int j0[3], j1[3];
+  int cnt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    j0[k] = xs[k] >> 1;
+    cnt[k] = (xs[k] & 1) ? 2 : 1;
+    j1[k] = (j0[k] + 1) % c.n;
+  }
+  A acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = A(0);
+  for (int cz = 0; cz < cnt[2]; ++cz)
+    for (int cy = 0; cy < cnt[1]; ++cy)
+      for (int cx = 0; cx < cnt[0]; ++cx) {
+        const A w = (cnt[0] == 2 ? A(0.5) : A(1)) * (cnt[1] == 2 ? A(0.5) : A(1)) *
+                    (cnt[2] == 2 ? A(0.5) : A(1));
+        const int64_t cs = site_slot(cx ? j1[0] : j0[0], cy ? j1[1] : j0[1], cz ? j1[2] : j0[2],
+                                     c.n, c.nbx, c.bmap, c.dense);
+        if (cs < 0) continue;  // cannot happen: nonzero weights land on active coarse nodes
+#pragma unroll
+        for (int v = 0; v < C; ++v) acc[v] += w * load_as<A>(uc + vaddr(cs, v, C));
+      }
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int64_t a = vaddr(s, v, C);
+    uf[a] = store_as<TS>(load_as<A>(uf + a) + acc[v]);
+  }
+}
+
+// ------------------------------------------------------------------ coarsest solve
+template <typename TS, int D, int M>
+__global__ void k_coarse_gather(const TS* __restrict__ f, const int* __restrict__ canon_slot,
+                                int64_t nn, double* __restrict__ bvec) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * D * M) return;
+  const int64_t i = g / (D * M);
+  const int v = (int)(g % (D * M));
+  bvec[g] = (double)load_as<typename ArithOf<TS>::type>(f + vaddr(canon_slot[i], v, D * M));
+}
+
+// u[r][m] = sum_k Ainv[r][k] b[k][m]; one block per row r, fixed-order tree per row
+template <int M>
+__global__ void k_coarse_gemv(const double* __restrict__ Ainv, const double* __restrict__ bvec,
+                              int64_t mrows, double* __restrict__ uvec) {
+  const int64_t r = blockIdx.x;
+  double acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = 0.0;
+  for (int64_t k = threadIdx.x; k < mrows; k += blockDim.x) {
+    const double a = Ainv[r * mrows + k];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += a * bvec[k * M + m];
+  }
+  __shared__ double sh[M][128];
+#pragma unroll
+  for (int m = 0; m < M; ++m) sh[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) sh[m][threadIdx.x] += sh[m][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < M) uvec[r * M + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <typename TS, int D, int M>
+__global__ void k_coarse_scatter(const double* __restrict__ uvec, const int* __restrict__ canon_slot,
+                                 int64_t nn, TS* __restrict__ u) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * D * M) return;
+  const int64_t i = g / (D * M);
+  const int v = (int)(g % (D * M));
+  u[vaddr(canon_slot[i], v, D * M)] = store_as<TS>((typename ArithOf<TS>::type)uvec[g]);
+}
+
+// ------------------------------------------------------------------ element energies
+template <typename A, int D, int M>
+struct EnArgs {
+  const int* nbr;
+  const uint8_t* mask;
+  const void* hi;   // A-typed field, or float hi part (ff)
+  const float* lo;  // ff low part or nullptr
+  double* part;
+  A Ke[64 * D * D];
+  A X0[8 * D * M];
+};
+
+// per active element e (origin slot n): w^I = x0^I - (u_e^I - u_n^I) (a translation, which
+// K_e annihilates, removed so that FP32 sees O(1) values), E_IJ = w^I . K_e w^J, I <= J
+template <typename A, int D, int M, bool FF>
+__global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
+  constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
+  __shared__ A th[C * 216];
+  __shared__ A tl[FF ? C * 216 : 1];
+  __shared__ int nb[27];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (t < 27) nb[t] = p.nbr[b * 27 + t];
+  __syncthreads();
+  for (int i = t; i < C * 216; i += 64) {
+    const int v = i / 216, q = i - v * 216;
+    const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
+    const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
+    const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
+    const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
+    const int nbi = nb[bz * 9 + by * 3 + bx];
+    A h = A(0), l = A(0);
+    if (nbi >= 0) {
+      const int64_t a = (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
+                        16 * ((tz + 3) & 3);
+      h = ((const A*)p.hi)[a];
+      if constexpr (FF) l = (A)p.lo[a];
+    }
+    th[i] = h;
+    if constexpr (FF) tl[i] = l;
+  }
+  __syncthreads();
+  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
+  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
+  const unsigned mk = p.mask[b * 64 + t];
+  double e[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) e[k] = 0.0;
+  if (mk & 1u) {  // element with origin at this node is active
+    auto wval = [&](int r, int I) -> A {
+      const int bb = r / D, i = r % D;
+      const int q = q0 + (bb & 1) + 6 * ((bb >> 1) & 1) + 36 * (bb >> 2);
+      const int v = i * M + I;
+      A du = th[v * 216 + q] - th[v * 216 + q0];
+      if constexpr (FF) du += tl[v * 216 + q] - tl[v * 216 + q0];
+      return p.X0[r * M + I] - du;
+    };
+#pragma unroll 1
+    for (int J = 0; J < M; ++J) {
+      A w[R], z[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) w[r] = wval(r, J);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        A s = A(0);
+#pragma unroll
+        for (int c = 0; c < R; ++c) s += p.Ke[r * R + c] * w[c];
+        z[r] = s;
+      }
+#pragma unroll 1
+      for (int I = 0; I <= J; ++I) {
+        A s = A(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) s += wval(r, I) * z[r];
+        e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s;
+      }
+    }
+  }
+  block_partial_64<K>(e, p.part + b * K);
+}
+
+// deterministic reduction of [nblk][K] partials (Neumaier-compensated per thread,
+// fixed-order tree across threads)
+__global__ void k_reduce(const double* __restrict__ part, int64_t nblk, int K,
+                         double* __restrict__ out) {
+  __shared__ double ss[1024], sc[1024];
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0, c = 0.0;
+    for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) {
+      const double x = part[i * K + k];
+      const double tt = s + x;
+      c += fabs(s) >= fabs(x) ? (s - tt) + x : (x - tt) + s;
+      s = tt;
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const double a = ss[threadIdx.x], x = ss[threadIdx.x + o];
+        const double tt = a + x;
+        sc[threadIdx.x] += sc[threadIdx.x + o] + (fabs(a) >= fabs(x) ? (a - tt) + x : (x - tt) + a);
+        ss[threadIdx.x] = tt;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = ss[0] + sc[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ vector kernels
+template <typename TS>
+__global__ void k_vzero(TS* __restrict__ x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = store_as<TS>((typename ArithOf<TS>::type)0);
+}
+
+template <typename TS>
+__global__ void k_vcopy(const TS* __restrict__ a, TS* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+template <typename TS>
+__global__ void k_vadd(const TS* __restrict__ y, TS* __restrict__ x, int64_t n) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = store_as<TS>(load_as<A>(x + i) + load_as<A>(y + i));
+}
+
+// block of 64 slots (one brick) per block
+template <typename TS, int M, int C>
+__global__ void __launch_bounds__(64) k_vdot(const TS* __restrict__ x, const TS* __restrict__ y,
+                                             double* __restrict__ part) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
+  double d[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) d[m] = 0.0;
+#pragma unroll
+  for (int v = 0; v < C; ++v)
+    d[v % M] += (double)(load_as<A>(x + base + v * 64) * load_as<A>(y + base + v * 64));
+  block_partial_64<M>(d, part + (int64_t)blockIdx.x * M);
+}
+
+template <typename TS, int M, int C>
+__global__ void __launch_bounds__(64)
+    k_cg_update(const double* __restrict__ num, const double* __restrict__ den,
+                const int* __restrict__ active, TS* __restrict__ x, const TS* __restrict__ pp,
+                TS* __restrict__ r, const TS* __restrict__ q, double* __restrict__ part) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
+  double nr[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) nr[m] = 0.0;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int m = v % M;
+    const A al = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
+    const int64_t a = base + v * 64;
+    x[a] = store_as<TS>(load_as<A>(x + a) + al * load_as<A>(pp + a));
+    const A rn = load_as<A>(r + a) - al * load_as<A>(q + a);
+    r[a] = store_as<TS>(rn);
+    nr[m] += (double)rn * (double)rn;
+  }
+  block_partial_64<M>(nr, part + (int64_t)blockIdx.x * M);
+}
+
+template <typename TS, int M, int C>
+__global__ void k_cg_dir(const double* __restrict__ num, const double* __restrict__ den,
+                         const int* __restrict__ active, const TS* __restrict__ z,
+                         TS* __restrict__ pp, int64_t n) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = (int)((i >> 6) % C);
+  const int m = v % M;
+  const A be = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
+  pp[i] = store_as<TS>(load_as<A>(z + i) + be * load_as<A>(pp + i));
+}
+
+// float-float accumulate (hi, lo) += d with Knuth's TwoSum and a fast renormalisation
+__global__ void k_ff_add(const float* __restrict__ d, float* __restrict__ hi,
+                         float* __restrict__ lo, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float a = hi[i], b = d[i];
+  const float s = a + b;
+  const float bb = s - a;
+  const float err = (a - (s - bb)) + (b - bb);
+  const float l = lo[i] + err;
+  const float h2 = s + l;
+  hi[i] = h2;
+  lo[i] = l - (h2 - s);
+}
+
+// float-float minus a double mean, with the mean split into two floats
+template <int C>
+__global__ void k_ff_sub_mean(const double* __restrict__ mean, const uint8_t* __restrict__ mask,
+                              float* __restrict__ hi, float* __restrict__ lo, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
+  if (!mask[slot]) return;
+  const int v = (int)((i >> 6) % C);
+  const double mu = mean[v];
+  const float mh = (float)mu;
+  const float ml = (float)(mu - (double)mh);
+  const float a = hi[i], b = -mh;
+  const float s = a + b;
+  const float bb = s - a;
+  const float err = (a - (s - bb)) + (b - bb);
+  const float l = lo[i] - ml + err;
+  const float h2 = s + l;
+  hi[i] = h2;
+  lo[i] = l - (h2 - s);
+}
+
+template <typename TS, int C>
+__global__ void __launch_bounds__(64) k_sum_values(const TS* __restrict__ x,
+                                                   const float* __restrict__ lo,
+                                                   const uint8_t* __restrict__ mask,
+                                                   double* __restrict__ part) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
+  const bool act = mask[(int64_t)blockIdx.x * 64 + threadIdx.x] != 0;
+  double s[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    double val = act ? (double)load_as<A>(x + base + v * 64) : 0.0;
+    if (lo && act) val += (double)lo[base + v * 64];
+    s[v] = val;
+  }
+  block_partial_64<C>(s, part + (int64_t)blockIdx.x * C);
+}
+
+template <int C>
+__global__ void k_sub_mean64(const double* __restrict__ mean, const uint8_t* __restrict__ mask,
+                             double* __restrict__ x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
+  if (!mask[slot]) return;
+  x[i] -= mean[(i >> 6) % C];
+}
+
+template <typename TS, int M, int C>
+__global__ void k_scale_cases(const double* __restrict__ s, TS* __restrict__ x, int64_t n) {
+  using A = typename ArithOf<TS>::type;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = (int)((i >> 6) % C);
+  x[i] = store_as<TS>(load_as<A>(x + i) * (A)s[v % M]);
+}
+
+template <typename TS>
+__global__ void k_canon_to_slots(const double* __restrict__ src, const int* __restrict__ canon_slot,
+                                 int64_t nn, int C, TS* __restrict__ dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * C) return;
+  const int64_t i = g / C;
+  const int v = (int)(g % C);
+  dst[vaddr(canon_slot[i], v, C)] = store_as<TS>((typename ArithOf<TS>::type)src[g]);
+}
+
+template <typename TS>
+__global__ void k_slots_to_canon(const TS* __restrict__ src, const int* __restrict__ canon_slot,
+                                 int64_t nn, int C, double* __restrict__ dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * C) return;
+  const int64_t i = g / C;
+  const int v = (int)(g % C);
+  dst[g] = (double)load_as<typename ArithOf<TS>::type>(src + vaddr(canon_slot[i], v, C));
+}
+
+__global__ void k_canon_to_ff(const double* __restrict__ src, const int* __restrict__ canon_slot,
+                              int64_t nn, int C, float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * C) return;
+  const int64_t i = g / C;
+  const int v = (int)(g % C);
+  const double x = src[g];
+  const float h = (float)x;
+  const int64_t a = vaddr(canon_slot[i], v, C);
+  hi[a] = h;
+  lo[a] = (float)(x - (double)h);
+}
+
+__global__ void k_ff_to_canon(const float* __restrict__ hi, const float* __restrict__ lo,
+                              const int* __restrict__ canon_slot, int64_t nn, int C,
+                              double* __restrict__ dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nn * C) return;
+  const int64_t i = g / C;
+  const int v = (int)(g % C);
+  const int64_t a = vaddr(canon_slot[i], v, C);
+  dst[g] = (double)hi[a] + (double)lo[a];
+}
+
+__global__ void k_ff_to_f64(const float* __restrict__ hi, const float* __restrict__ lo,
+                            double* __restrict__ dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)hi[i] + (double)lo[i];
+}
+
+// ------------------------------------------------------------------ host launchers
+template <typename A, int D, int M>
+static void fill_fine(const Material& mt, FineC<A, D, M>& fc) {
+  for (int i = 0; i < 64 * D * D; ++i) fc.Ke[i] = (A)mt.Ke[i];
+  for (int i = 0; i < 8 * D * M; ++i) fc.Fe[i] = (A)mt.Fe[i];
+}
+
+template <typename TS, typename A, int D, int M>
+static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& va) {
+  const Level& lv = h->lv[level];
+  StArgs<TS, A, D, M> p;
+  std::memset(&p, 0, sizeof(p));
+  p.nbr = lv.brick_nbr;
+  p.mask = lv.mask;
+  p.kidx = lv.kidx;
+  if constexpr (sizeof(A) == 8) {
+    p.kmat = (const A*)lv.K64;
+    p.dinv = (const A*)lv.dinv64;
+  } else {
+    p.kmat = (const A*)lv.K32;
+    p.dinv = (const A*)lv.dinv32;
+  }
+  p.u = (const TS*)va.u;
+  p.f = (const TS*)va.f;
+  p.dprev = (const TS*)va.dprev;
+  p.out = (TS*)va.out;
+  p.dout = (TS*)va.dout;
+  p.part = va.part;
+  p.omega = (A)va.omega;
+  p.c1 = (A)va.c1;
+  p.c2 = (A)va.c2;
+  const bool fine = level == 0;
+  if (fine) fill_fine<A, D, M>(h->mat, p.fc);
+  const unsigned g = (unsigned)lv.nb;
+  cudaStream_t s = h->stream;
+#define GMT_ST(KIND, MODE) k_stencil<TS, A, D, M, KIND, MODE><<<g, 64, 0, s>>>(p)
+  switch (mode) {
+    case ST_APPLY: if (fine) GMT_ST(0, ST_APPLY); else GMT_ST(1, ST_APPLY); break;
+    case ST_RESID: if (fine) GMT_ST(0, ST_RESID); else GMT_ST(1, ST_RESID); break;
+    case ST_JACOBI: if (fine) GMT_ST(0, ST_JACOBI); else GMT_ST(1, ST_JACOBI); break;
+    case ST_CHEB: if (fine) GMT_ST(0, ST_CHEB); else GMT_ST(1, ST_CHEB); break;
+  }
+#undef GMT_ST
+  GMT_LAUNCH_CHECK();
+}
+
+#define GMT_DISPATCH_PREC(prec, FN, ...)                                  \
+  do {                                                                    \
+    if (h->mat.D == 3) {                                                  \
+      if (prec == P64) FN<double, double, 3, 6>(__VA_ARGS__);             \
+      else if (prec == P32) FN<float, float, 3, 6>(__VA_ARGS__);          \
+      else FN<__nv_bfloat16, float, 3, 6>(__VA_ARGS__);                   \
+    } else {                                                              \
+      if (prec == P64) FN<double, double, 1, 3>(__VA_ARGS__);             \
+      else if (prec == P32) FN<float, float, 1, 3>(__VA_ARGS__);          \
+      else FN<__nv_bfloat16, float, 1, 3>(__VA_ARGS__);                   \
+    }                                                                     \
+  } while (0)
+
+void launch_stencil(gmt_hierarchy* h, int level, Prec prec, StencilMode mode, const VecArgs& a) {
+  GMT_DISPATCH_PREC(prec, stencil_t, h, level, mode, a);
+}
+
+template <typename TS, typename A, int D, int M>
+static void diag_t(gmt_hierarchy* h, int level, const void* f, void* out, void* dout, double scale) {
+  const Level& lv = h->lv[level];
+  StArgs<TS, A, D, M> p;
+  std::memset(&p, 0, sizeof(p));
+  p.mask = lv.mask;
+  p.dinv = sizeof(A) == 8 ? (const A*)lv.dinv64 : (const A*)lv.dinv32;
+  p.f = (const TS*)f;
+  p.out = (TS*)out;
+  p.dout = (TS*)dout;
+  p.omega = (A)scale;
+  const unsigned g = grid_for(lv.nslots, 128);
+  if (level == 0) {
+    fill_fine<A, D, M>(h->mat, p.fc);
+    k_diag<TS, A, D, M, 0><<<g, 128, 0, h->stream>>>(p, lv.nslots);
+  } else {
+    k_diag<TS, A, D, M, 1><<<g, 128, 0, h->stream>>>(p, lv.nslots);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+void launch_diag(gmt_hierarchy* h, int level, Prec prec, const void* f, void* out, void* dout,
+                 double scale) {
+  GMT_DISPATCH_PREC(prec, diag_t, h, level, f, out, dout, scale);
+}
+
+template <int D, int M>
+static void resid_ff_t(gmt_hierarchy* h, const float* hi, const float* lo, float* r, double* part) {
+  const Level& lv = h->lv[0];
+  FFArgs<D, M> p;
+  std::memset(&p, 0, sizeof(p));
+  p.nbr = lv.brick_nbr;
+  p.mask = lv.mask;
+  p.hi = hi;
+  p.lo = lo;
+  p.out = r;
+  p.part = part;
+  fill_fine<float, D, M>(h->mat, p.fc);
+  k_resid_ff<D, M><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  GMT_LAUNCH_CHECK();
+}
+
+void launch_resid_ff(gmt_hierarchy* h, const float* hi, const float* lo, float* r, double* part) {
+  if (h->mat.D == 3) resid_ff_t<3, 6>(h, hi, lo, r, part);
+  else resid_ff_t<1, 3>(h, hi, lo, r, part);
+}
+
+template <typename TS, typename A, int D, int M>
+static void restrict_t(gmt_hierarchy* h, int level, const void* rf, void* fc) {
+  const Level& c = h->lv[level + 1];
+  k_restrict<TS, A, D * M><<<grid_for(c.nslots, 64), 64, 0, h->stream>>>(
+      (const TS*)rf, (TS*)fc, view(h->lv[level]), view(c));
+  GMT_LAUNCH_CHECK();
+}
+void launch_restrict(gmt_hierarchy* h, int level, Prec prec, const void* rf, void* fc) {
+  GMT_DISPATCH_PREC(prec, restrict_t, h, level, rf, fc);
+}
+
+template <typename TS, typename A, int D, int M>
+static void prolong_t(gmt_hierarchy* h, int level, const void* uc, void* uf) {
+  const Level& f = h->lv[level];
+  k_prolong<TS, A, D * M><<<grid_for(f.nslots, 64), 64, 0, h->stream>>>(
+      (const TS*)uc, (TS*)uf, view(f), view(h->lv[level + 1]));
+  GMT_LAUNCH_CHECK();
+}
+void launch_prolong(gmt_hierarchy* h, int level, Prec prec, const void* uc, void* uf) {
+  GMT_DISPATCH_PREC(prec, prolong_t, h, level, uc, uf);
+}
+
+template <typename TS, typename A, int D, int M>
+static void coarse_t(gmt_hierarchy* h, const void* f, void* u) {
+  const Level& c = h->lv[h->L - 1];
+  const int64_t cnt = c.n_nodes * D * M;
+  k_coarse_gather<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const TS*)f, c.canon_slot,
+                                                                       c.n_nodes, h->cb);
+  GMT_LAUNCH_CHECK();
+  k_coarse_gemv<M><<<(unsigned)h->m, 128, 0, h->stream>>>(h->Ainv, h->cb, h->m, h->cu);
+  GMT_LAUNCH_CHECK();
+  vec_zero(h, h->L - 1, sizeof(TS) == 8 ? P64 : (sizeof(TS) == 4 ? P32 : PBF), u);
+  k_coarse_scatter<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>(h->cu, c.canon_slot,
+                                                                        c.n_nodes, (TS*)u);
+  GMT_LAUNCH_CHECK();
+}
+void launch_coarse_solve(gmt_hierarchy* h, Prec prec, const void* f, void* u) {
+  GMT_DISPATCH_PREC(prec, coarse_t, h, f, u);
+}
+
+template <typename A, int D, int M, bool FF>
+static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* part) {
+  const Level& lv = h->lv[0];
+  EnArgs<A, D, M> p;
+  std::memset(&p, 0, sizeof(p));
+  p.nbr = lv.brick_nbr;
+  p.mask = lv.mask;
+  p.hi = hi;
+  p.lo = lo;
+  p.part = part;
+  for (int i = 0; i < 64 * D * D; ++i) p.Ke[i] = (A)h->mat.Ke[i];
+  for (int i = 0; i < 8 * D * M; ++i) p.X0[i] = (A)h->mat.X0[i];
+  k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  GMT_LAUNCH_CHECK();
+}
+
+void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u_lo,
+                   double* part) {
+  const bool d3 = h->mat.D == 3;
+  if (prec == P64) {
+    if (d3) energy_t<double, 3, 6, false>(h, u_hi, nullptr, part);
+    else energy_t<double, 1, 3, false>(h, u_hi, nullptr, part);
+  } else {
+    if (d3) energy_t<float, 3, 6, true>(h, u_hi, u_lo, part);
+    else energy_t<float, 1, 3, true>(h, u_hi, u_lo, part);
+  }
+}
+
+void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out) {
+  k_reduce<<<1, 1024, 0, h->stream>>>(part, nblk, K, out);
+  GMT_LAUNCH_CHECK();
+}
+
+static int64_t nvals(gmt_hierarchy* h, int level) { return h->lv[level].nslots * h->mat.C; }
+
+void vec_zero(gmt_hierarchy* h, int level, Prec prec, void* x) {
+  const int64_t n = nvals(h, level);
+  if (prec == P64) k_vzero<double><<<grid_for(n, 256), 256, 0, h->stream>>>((double*)x, n);
+  else if (prec == P32) k_vzero<float><<<grid_for(n, 256), 256, 0, h->stream>>>((float*)x, n);
+  else k_vzero<__nv_bfloat16><<<grid_for(n, 256), 256, 0, h->stream>>>((__nv_bfloat16*)x, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_copy(gmt_hierarchy* h, int level, Prec prec, const void* a, void* b) {
+  GMT_CUDA(cudaMemcpyAsync(b, a, nvals(h, level) * prec_bytes(prec), cudaMemcpyDeviceToDevice,
+                           h->stream));
+}
+
+void vec_add(gmt_hierarchy* h, int level, Prec prec, const void* y, void* x) {
+  const int64_t n = nvals(h, level);
+  if (prec == P64) k_vadd<double><<<grid_for(n, 256), 256, 0, h->stream>>>((const double*)y, (double*)x, n);
+  else if (prec == P32) k_vadd<float><<<grid_for(n, 256), 256, 0, h->stream>>>((const float*)y, (float*)x, n);
+  else k_vadd<__nv_bfloat16><<<grid_for(n, 256), 256, 0, h->stream>>>((const __nv_bfloat16*)y, (__nv_bfloat16*)x, n);
+  GMT_LAUNCH_CHECK();
+}
+
+
+template <typename TS, int M, int C>
+static void vdot_dispatch(const void* x, const void* y, double* part, unsigned g, cudaStream_t s) {
+  k_vdot<TS, M, C><<<g, 64, 0, s>>>((const TS*)x, (const TS*)y, part);
+}
+
+void vec_dot(gmt_hierarchy* h, int level, Prec prec, const void* x, const void* y, double* part) {
+  const unsigned g = (unsigned)h->lv[level].nb;
+  if (h->mat.D == 3) {
+    if (prec == P64) vdot_dispatch<double, 6, 18>(x, y, part, g, h->stream);
+    else if (prec == P32) vdot_dispatch<float, 6, 18>(x, y, part, g, h->stream);
+    else vdot_dispatch<__nv_bfloat16, 6, 18>(x, y, part, g, h->stream);
+  } else {
+    if (prec == P64) vdot_dispatch<double, 3, 3>(x, y, part, g, h->stream);
+    else if (prec == P32) vdot_dispatch<float, 3, 3>(x, y, part, g, h->stream);
+    else vdot_dispatch<__nv_bfloat16, 3, 3>(x, y, part, g, h->stream);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+template <typename TS, int M, int C>
+static void cgu(const double* num, const double* den, const int* act, void* x, const void* p,
+                void* r, const void* q, double* part, unsigned g, cudaStream_t s) {
+  k_cg_update<TS, M, C><<<g, 64, 0, s>>>(num, den, act, (TS*)x, (const TS*)p, (TS*)r,
+                                         (const TS*)q, part);
+}
+
+void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
+                   const int* active, void* x, const void* p, void* r, const void* q,
+                   double* part) {
+  const unsigned g = (unsigned)h->lv[0].nb;
+  if (h->mat.D == 3) {
+    if (prec == P64) cgu<double, 6, 18>(num, den, active, x, p, r, q, part, g, h->stream);
+    else cgu<float, 6, 18>(num, den, active, x, p, r, q, part, g, h->stream);
+  } else {
+    if (prec == P64) cgu<double, 3, 3>(num, den, active, x, p, r, q, part, g, h->stream);
+    else cgu<float, 3, 3>(num, den, active, x, p, r, q, part, g, h->stream);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+template <typename TS, int M, int C>
+static void cgd(const double* num, const double* den, const int* act, const void* z, void* p,
+                int64_t n, cudaStream_t s) {
+  k_cg_dir<TS, M, C><<<grid_for(n, 256), 256, 0, s>>>(num, den, act, (const TS*)z, (TS*)p, n);
+}
+
+void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
+                const int* active, const void* z, void* p) {
+  const int64_t n = nvals(h, 0);
+  if (h->mat.D == 3) {
+    if (prec == P64) cgd<double, 6, 18>(num, den, active, z, p, n, h->stream);
+    else cgd<float, 6, 18>(num, den, active, z, p, n, h->stream);
+  } else {
+    if (prec == P64) cgd<double, 3, 3>(num, den, active, z, p, n, h->stream);
+    else cgd<float, 3, 3>(num, den, active, z, p, n, h->stream);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_ff_add(gmt_hierarchy* h, const float* d, float* hi, float* lo) {
+  const int64_t n = nvals(h, 0);
+  k_ff_add<<<grid_for(n, 256), 256, 0, h->stream>>>(d, hi, lo, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_ff_sub_mean(gmt_hierarchy* h, const double* mean, float* hi, float* lo) {
+  const int64_t n = nvals(h, 0);
+  if (h->mat.C == 18) k_ff_sub_mean<18><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo, n);
+  else k_ff_sub_mean<3><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_sum_values(gmt_hierarchy* h, int level, Prec prec, const void* x, const float* lo,
+                    double* part) {
+  const unsigned g = (unsigned)h->lv[level].nb;
+  const uint8_t* mk = h->lv[level].mask;
+  if (h->mat.C == 18) {
+    if (prec == P64) k_sum_values<double, 18><<<g, 64, 0, h->stream>>>((const double*)x, lo, mk, part);
+    else k_sum_values<float, 18><<<g, 64, 0, h->stream>>>((const float*)x, lo, mk, part);
+  } else {
+    if (prec == P64) k_sum_values<double, 3><<<g, 64, 0, h->stream>>>((const double*)x, lo, mk, part);
+    else k_sum_values<float, 3><<<g, 64, 0, h->stream>>>((const float*)x, lo, mk, part);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_sub_mean64(gmt_hierarchy* h, int level, const double* mean, double* x) {
+  const int64_t n = nvals(h, level);
+  if (h->mat.C == 18) k_sub_mean64<18><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[level].mask, x, n);
+  else k_sub_mean64<3><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[level].mask, x, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_scale_cases(gmt_hierarchy* h, int level, Prec prec, const double* s, void* x) {
+  const int64_t n = nvals(h, level);
+  const unsigned g = grid_for(n, 256);
+  cudaStream_t st = h->stream;
+  if (h->mat.D == 3) {
+    if (prec == P64) k_scale_cases<double, 6, 18><<<g, 256, 0, st>>>(s, (double*)x, n);
+    else if (prec == P32) k_scale_cases<float, 6, 18><<<g, 256, 0, st>>>(s, (float*)x, n);
+    else k_scale_cases<__nv_bfloat16, 6, 18><<<g, 256, 0, st>>>(s, (__nv_bfloat16*)x, n);
+  } else {
+    if (prec == P64) k_scale_cases<double, 3, 3><<<g, 256, 0, st>>>(s, (double*)x, n);
+    else if (prec == P32) k_scale_cases<float, 3, 3><<<g, 256, 0, st>>>(s, (float*)x, n);
+    else k_scale_cases<__nv_bfloat16, 3, 3><<<g, 256, 0, st>>>(s, (__nv_bfloat16*)x, n);
+  }
+  GMT_LAUNCH_CHECK();
+}
+
+void canon_to_slots(gmt_hierarchy* h, int level, Prec prec, const double* src, void* dst) {
+  const Level& lv = h->lv[level];
+  const int C = h->mat.C;
+  const int64_t cnt = lv.n_nodes * C;
+  vec_zero(h, level, prec, dst);
+  if (prec == P64) k_canon_to_slots<double><<<grid_for(cnt, 256), 256, 0, h->stream>>>(src, lv.canon_slot, lv.n_nodes, C, (double*)dst);
+  else if (prec == P32) k_canon_to_slots<float><<<grid_for(cnt, 256), 256, 0, h->stream>>>(src, lv.canon_slot, lv.n_nodes, C, (float*)dst);
+  else k_canon_to_slots<__nv_bfloat16><<<grid_for(cnt, 256), 256, 0, h->stream>>>(src, lv.canon_slot, lv.n_nodes, C, (__nv_bfloat16*)dst);
+  GMT_LAUNCH_CHECK();
+}
+
+void slots_to_canon(gmt_hierarchy* h, int level, Prec prec, const void* src, double* dst) {
+  const Level& lv = h->lv[level];
+  const int C = h->mat.C;
+  const int64_t cnt = lv.n_nodes * C;
+  if (prec == P64) k_slots_to_canon<double><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const double*)src, lv.canon_slot, lv.n_nodes, C, dst);
+  else if (prec == P32) k_slots_to_canon<float><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const float*)src, lv.canon_slot, lv.n_nodes, C, dst);
+  else k_slots_to_canon<__nv_bfloat16><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const __nv_bfloat16*)src, lv.canon_slot, lv.n_nodes, C, dst);
+  GMT_LAUNCH_CHECK();
+}
+
+void canon_to_ff(gmt_hierarchy* h, const double* src, float* hi, float* lo) {
+  const Level& lv = h->lv[0];
+  const int C = h->mat.C;
+  vec_zero(h, 0, P32, hi);
+  vec_zero(h, 0, P32, lo);
+  k_canon_to_ff<<<grid_for(lv.n_nodes * C, 256), 256, 0, h->stream>>>(src, lv.canon_slot, lv.n_nodes, C, hi, lo);
+  GMT_LAUNCH_CHECK();
+}
+
+void ff_to_canon(gmt_hierarchy* h, const float* hi, const float* lo, double* dst) {
+  const Level& lv = h->lv[0];
+  const int C = h->mat.C;
+  k_ff_to_canon<<<grid_for(lv.n_nodes * C, 256), 256, 0, h->stream>>>(hi, lo, lv.canon_slot, lv.n_nodes, C, dst);
+  GMT_LAUNCH_CHECK();
+}
+
+void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst) {
+  const int64_t n = nvals(h, 0);
+  k_ff_to_f64<<<grid_for(n, 256), 256, 0, h->stream>>>(hi, lo, dst, n);
+  GMT_LAUNCH_CHECK();
+}
+
+}  // namespace gmt

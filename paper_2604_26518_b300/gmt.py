@@ -1,0 +1,336 @@
+"""Python binding of libgmt.so (C ABI in include/gmt.h).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels. Device
+buffers are torch CUDA tensors (torch supplies device memory and the current stream); the
+library receives raw pointers and sizes. There is no CPU fallback: if the library or a CUDA
+device is missing, every call raises.
+
+Field layout (canonical): float64 tensor of shape (nodes, D, M), D = 3 components and
+M = 6 Voigt load cases for elasticity, D = 1 and M = 3 for heat conduction; node order is
+increasing x + N*y + N^2*z over active nodes of the level.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgmt.so")
+
+ELASTIC, HEAT = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
+JACOBI, CHEBYSHEV = 0, 1
+
+OK, ERR_ARG, ERR_RES, ERR_EMPTY, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, ERR_STATE = range(9)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("coarsest_max", ctypes.c_int),
+        ("smoother", ctypes.c_int),
+        ("nu_pre", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("cheb_ratio", ctypes.c_double),
+        ("cheb_upper", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("krylov", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("max_inner", ctypes.c_int),
+        ("max_outer", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("outer", ctypes.c_int),
+        ("inner_total", ctypes.c_int),
+        ("cases", ctypes.c_int),
+        ("rel_residual", ctypes.c_double * 6),
+        ("t_setup_ms", ctypes.c_double),
+        ("t_solve_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {"outer": self.outer, "cycles": self.inner_total,
+                "rel_residual": list(self.rel_residual)[: self.cases],
+                "t_setup_ms": self.t_setup_ms, "t_solve_ms": self.t_solve_ms}
+
+
+class GmtError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status} ({message})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_L = ctypes.c_int64
+
+_SIGS = {
+    "gmt_default_options": (None, [ctypes.POINTER(Options)]),
+    "gmt_status_string": (ctypes.c_char_p, [_I]),
+    "gmt_last_error": (ctypes.c_char_p, []),
+    "gmt_build_hierarchy": (_I, [_P, _I, _I, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
+    "gmt_free_hierarchy": (None, [_P]),
+    "gmt_set_stream": (_I, [_P, _P]),
+    "gmt_set_options": (_I, [_P, ctypes.POINTER(Options)]),
+    "gmt_num_levels": (_I, [_P]),
+    "gmt_level_res": (_I, [_P, _I]),
+    "gmt_num_nodes": (_L, [_P, _I]),
+    "gmt_num_elements": (_L, [_P, _I]),
+    "gmt_num_bricks": (_L, [_P, _I]),
+    "gmt_device_bytes": (_L, [_P]),
+    "gmt_node_coords": (_I, [_P, _I, _P, _P]),
+    "gmt_element_coords": (_I, [_P, _I, _P, _P]),
+    "gmt_transfer_stencil": (_I, [_P, _I, _P, _P]),
+    "gmt_prepare": (_I, [_P, _I, _D, _D, _D]),
+    "gmt_apply": (_I, [_P, _I, _I, _P, _P]),
+    "gmt_smooth": (_I, [_P, _I, _I, _P, _P, _I, _I]),
+    "gmt_restrict": (_I, [_P, _I, _I, _P, _P]),
+    "gmt_prolong": (_I, [_P, _I, _I, _P, _P]),
+    "gmt_coarse_solve": (_I, [_P, _P, _P]),
+    "gmt_vcycle": (_I, [_P, _I, _P, _P, _I]),
+    "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
+    "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
+    "gmt_residual": (_I, [_P, _I, _P, _P]),
+}
+
+
+def lib():
+    """Load libgmt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2604_26518_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().gmt_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _check(st: int, where: str, allow=(OK,)):
+    if st not in allow:
+        msg = lib().gmt_last_error().decode() or lib().gmt_status_string(st).decode()
+        raise GmtError(st, where, msg)
+    return st
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libgmt needs a CUDA device; none is available")
+    return torch
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Hierarchy:
+    """Sparse periodic GMG hierarchy of one voxel cell (gmt_build_hierarchy)."""
+
+    def __init__(self, voxels, options: Options | None = None, stream=None):
+        torch = _torch()
+        self._h = _P()
+        L = lib()
+        if isinstance(voxels, np.ndarray):
+            vox = np.ascontiguousarray(voxels, dtype=np.uint8)
+            n = vox.shape[0]
+            assert vox.shape == (n, n, n)
+            src, on_dev, self._keep = vox.ctypes.data, 0, vox
+        else:
+            vox = voxels.contiguous()
+            assert vox.dtype == torch.uint8 and vox.is_cuda
+            n = vox.shape[0]
+            src, on_dev, self._keep = vox.data_ptr(), 1, vox
+        self.n = int(n)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opts = options if options is not None else default_options()
+        st = L.gmt_build_hierarchy(src, self.n, on_dev, ctypes.byref(opts),
+                                   self.stream.cuda_stream, ctypes.byref(self._h))
+        _check(st, "gmt_build_hierarchy")
+        self._keep = None
+        self.physics = None
+
+    # ---------------------------------------------------------------- lifetime
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gmt_free_hierarchy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- sizes
+    @property
+    def levels(self) -> int:
+        return lib().gmt_num_levels(self._h)
+
+    def level_res(self, l: int) -> int:
+        return lib().gmt_level_res(self._h, l)
+
+    def num_nodes(self, l: int = 0) -> int:
+        return int(lib().gmt_num_nodes(self._h, l))
+
+    def num_elements(self, l: int = 0) -> int:
+        return int(lib().gmt_num_elements(self._h, l))
+
+    def num_bricks(self, l: int = 0) -> int:
+        return int(lib().gmt_num_bricks(self._h, l))
+
+    def device_bytes(self) -> int:
+        return int(lib().gmt_device_bytes(self._h))
+
+    def set_options(self, options: Options):
+        _check(lib().gmt_set_options(self._h, ctypes.byref(options)), "gmt_set_options")
+
+    # ---------------------------------------------------------------- geometry export
+    def node_coords(self, l: int = 0):
+        torch = _torch()
+        n = self.num_nodes(l)
+        xyz = torch.empty((n, 3), dtype=torch.int32, device="cuda")
+        m = torch.empty((n,), dtype=torch.uint8, device="cuda")
+        _check(lib().gmt_node_coords(self._h, l, _ptr(xyz), _ptr(m)), "gmt_node_coords")
+        return xyz, m
+
+    def element_coords(self, l: int = 0):
+        torch = _torch()
+        n = self.num_elements(l)
+        xyz = torch.empty((n, 3), dtype=torch.int32, device="cuda")
+        c = torch.empty((n,), dtype=torch.uint8, device="cuda")
+        _check(lib().gmt_element_coords(self._h, l, _ptr(xyz), _ptr(c)), "gmt_element_coords")
+        return xyz, c
+
+    def transfer_stencil(self, l: int = 0):
+        torch = _torch()
+        n = self.num_nodes(l)
+        idx = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+        w = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+        _check(lib().gmt_transfer_stencil(self._h, l, _ptr(idx), _ptr(w)), "gmt_transfer_stencil")
+        return idx, w
+
+    # ---------------------------------------------------------------- operators
+    def prepare(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0):
+        _check(lib().gmt_prepare(self._h, physics, E, nu, k), "gmt_prepare")
+        self.physics = physics
+
+    def _dm(self):
+        return (3, 6) if self.physics == ELASTIC else (1, 3)
+
+    def _field(self, l, x):
+        torch = _torch()
+        D, M = self._dm()
+        n = self.num_nodes(l)
+        if x is None:
+            return torch.zeros((n, D, M), dtype=torch.float64, device="cuda")
+        x = torch.as_tensor(x, dtype=torch.float64, device="cuda").contiguous()
+        assert x.numel() == n * D * M, (x.shape, n, D, M)
+        return x.view(n, D, M)
+
+    def apply(self, level, u, precision=FP64):
+        u = self._field(level, u)
+        y = self._field(level, None)
+        _check(lib().gmt_apply(self._h, level, precision, _ptr(u), _ptr(y)), "gmt_apply")
+        return y
+
+    def smooth(self, level, f, u=None, sweeps=1, precision=FP64):
+        f = self._field(level, f)
+        zero = u is None
+        u = self._field(level, u).clone()
+        _check(lib().gmt_smooth(self._h, level, precision, _ptr(f), _ptr(u), sweeps, int(zero)),
+               "gmt_smooth")
+        return u
+
+    def restrict(self, level, r, precision=FP64):
+        r = self._field(level, r)
+        fc = self._field(level + 1, None)
+        _check(lib().gmt_restrict(self._h, level, precision, _ptr(r), _ptr(fc)), "gmt_restrict")
+        return fc
+
+    def prolong(self, level, uc, uf=None, precision=FP64):
+        uc = self._field(level + 1, uc)
+        uf = self._field(level, uf).clone()
+        _check(lib().gmt_prolong(self._h, level, precision, _ptr(uc), _ptr(uf)), "gmt_prolong")
+        return uf
+
+    def coarse_solve(self, f):
+        f = self._field(self.levels - 1, f)
+        u = self._field(self.levels - 1, None)
+        _check(lib().gmt_coarse_solve(self._h, _ptr(f), _ptr(u)), "gmt_coarse_solve")
+        return u
+
+    def vcycle(self, f, u=None, precision=FP64):
+        f = self._field(0, f)
+        zero = u is None
+        u = self._field(0, u).clone()
+        _check(lib().gmt_vcycle(self._h, precision, _ptr(f), _ptr(u), int(zero)), "gmt_vcycle")
+        return u
+
+    def lambda_max(self, level):
+        out = ctypes.c_double()
+        _check(lib().gmt_lambda_max(self._h, level, ctypes.byref(out)), "gmt_lambda_max")
+        return out.value
+
+    # ---------------------------------------------------------------- solve
+    def solve(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, tol=1e-5, u0=None, want_field=True,
+              allow_not_converged=False):
+        self.physics = physics
+        u0t = None if u0 is None else self._field(0, u0)
+        out = self._field(0, None) if want_field else None
+        info = Info()
+        allow = (OK, NOT_CONVERGED, DIVERGED) if allow_not_converged else (OK,)
+        st = lib().gmt_solve(self._h, physics, E, nu, k, tol, _ptr(u0t), _ptr(out),
+                             ctypes.byref(info))
+        _check(st, "gmt_solve", allow)
+        return st, out, info
+
+    def homogenize(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, u=None):
+        self.physics = physics
+        D, M = self._dm()
+        CH = np.zeros((M, M), dtype=np.float64)
+        ut = None if u is None else self._field(0, u)
+        _check(lib().gmt_homogenize(self._h, physics, E, nu, k, _ptr(ut),
+                                    CH.ctypes.data_as(ctypes.c_void_p)), "gmt_homogenize")
+        return CH
+
+    def residual(self, u, precision=FP32):
+        D, M = self._dm()
+        u = self._field(0, u)
+        out = np.zeros(M, dtype=np.float64)
+        _check(lib().gmt_residual(self._h, precision, _ptr(u), out.ctypes.data_as(ctypes.c_void_p)),
+               "gmt_residual")
+        return out
+
+
+def declared_symbols(header: str | None = None):
+    """Function names declared in include/gmt.h."""
+    import re
+    if header is None:
+        header = os.path.join(os.path.dirname(_HERE), "include", "gmt.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gmt_[a-z_0-9]+)\s*\(", text)))

@@ -1,0 +1,31 @@
+"""The C-ABI library builds, loads and exports every symbol include/gmt.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+
+from paper_2604_26518_b300 import build, gmt
+
+
+def test_library_builds_and_exports_declared_symbols():
+    build.build()
+    L = ctypes.CDLL(gmt.LIB_PATH)
+    names = gmt.declared_symbols()
+    assert len(names) >= 25
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares a signature for every exported entry point
+    assert set(names) == set(gmt._SIGS), set(names) ^ set(gmt._SIGS)
+
+
+def test_host_only_calls():
+    L = gmt.lib()
+    o = gmt.default_options()
+    assert o.levels == 0 and o.coarsest_max == 8 and o.nu_pre == 2 and o.precision == gmt.FP32
+    assert L.gmt_status_string(gmt.ERR_RES).decode().startswith("unsupported")
+    # argument errors are reported as statuses, not crashes (checked before any CUDA call)
+    h = ctypes.c_void_p()
+    st = L.gmt_build_hierarchy(None, 32, 0, None, None, ctypes.byref(h))
+    assert st == gmt.ERR_ARG
+    buf = (ctypes.c_uint8 * 8)()
+    st = L.gmt_build_hierarchy(buf, 30, 0, None, None, ctypes.byref(h))
+    assert st == gmt.ERR_RES and b"multiple of 4" in L.gmt_last_error()
+    assert L.gmt_num_levels(None) == 0

@@ -1,0 +1,156 @@
+"""End-to-end parity of gmt_solve + gmt_homogenize against the FP64 oracle: C^H within
+1e-4 (normalised by the largest entry) at relative residual 1e-5, fields in the energy norm,
+closed forms, edge cases, determinism, and a full-size 128^3 cell checked through
+properties the oracle evaluates on the library's field."""
+import numpy as np
+import pytest
+
+from oracle import fe, grid, solve
+from paper_2604_26518_b300 import lattices as L
+from helpers import rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gyroid32():
+    vox = L.tpms_network("gyroid", 32, 0.30)
+    return vox, solve.solve_cell(vox, "elastic"), solve.solve_cell(vox, "heat")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("krylov", [1, 0])
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+def test_config1_gyroid32(gmt_lib, gyroid32, precision, krylov, kind):
+    gmt = gmt_lib
+    vox, el, th = gyroid32
+    ref = el if kind == "elastic" else th
+    prec = gmt.FP64 if precision == "fp64" else gmt.FP32
+    opts = gmt.default_options(precision=prec, krylov=krylov, max_inner=200)
+    h = gmt.Hierarchy(vox, opts)
+    assert h.levels == 3
+    ph = gmt.ELASTIC if kind == "elastic" else gmt.HEAT
+    st, u, info = h.solve(ph, tol=TOL)
+    D, M = ref["D"], ref["NC"]
+    U = to_np(u, D, M)
+    res = solve.relative_residual(ref["K"], ref["F"], U)      # oracle's own SpMV
+    assert res.max() <= TOL * 1.02, (res, info.as_dict())
+    np.testing.assert_allclose(np.array(info.as_dict()["rel_residual"]), res, rtol=0.05, atol=1e-9)
+    CH = h.homogenize(ph)
+    err = np.abs(CH - ref["CH"]).max() / np.abs(ref["CH"]).max()
+    assert err <= 1e-4, err
+    # the library's C^H of its own field equals the oracle's energy average of that field
+    C_orc_of_gpu = solve.homogenize(ref["level"], U, ref["Ke"], ref["x0"], D)
+    assert np.abs(CH - C_orc_of_gpu).max() <= 1e-9 * np.abs(ref["CH"]).max()
+    en = solve.energy_norm_error(ref["K"], U, ref["U"], ref["Ke"], ref["x0"], ref["level"], D)
+    assert en.max() <= 1e-4, en
+    # gauge: zero mean per component and case
+    assert np.abs(U.reshape(-1, D, M).mean(axis=0)).max() < 1e-9 * max(np.abs(U).max(), 1)
+
+
+def test_solid_cell_and_laminates_closed_forms(gmt_lib):
+    gmt = gmt_lib
+    E, nu = 1.0, 0.3
+    h = gmt.Hierarchy(np.ones((16, 16, 16), dtype=np.uint8))
+    st, u, info = h.solve(gmt.ELASTIC, E=E, nu=nu, tol=TOL)
+    assert float(u.abs().max()) == 0.0
+    np.testing.assert_allclose(h.homogenize(gmt.ELASTIC, E=E, nu=nu), fe.elastic_C0(E, nu), atol=1e-12)
+    vox = L.laminate_z(16, [0, 1, 2, 3, 8, 9])
+    phi = 6 / 16
+    h = gmt.Hierarchy(vox)
+    h.solve(gmt.ELASTIC, tol=1e-8)
+    C = h.homogenize(gmt.ELASTIC)
+    expect = np.zeros((6, 6))
+    expect[0, 0] = expect[1, 1] = phi * E / (1 - nu ** 2)
+    expect[0, 1] = expect[1, 0] = phi * E * nu / (1 - nu ** 2)
+    expect[5, 5] = phi * E / (2 * (1 + nu))
+    assert np.abs(C - expect).max() < 1e-6
+    h.solve(gmt.HEAT, tol=1e-8)
+    np.testing.assert_allclose(h.homogenize(gmt.HEAT), np.diag([phi, phi, 0.0]), atol=1e-6)
+    vox = L.rods_x(16, 4, 2, 2)
+    h = gmt.Hierarchy(vox)
+    h.solve(gmt.ELASTIC, tol=1e-8)
+    C = h.homogenize(gmt.ELASTIC)
+    expect = np.zeros((6, 6))
+    expect[0, 0] = vox.mean() * E
+    assert np.abs(C - expect).max() < 1e-6
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_single_level_direct_solve_brute_force(gmt_lib, n):
+    gmt = gmt_lib
+    vox = L.largest_component(L.random_binary(n, 0.6, np.random.default_rng(n)))
+    h = gmt.Hierarchy(vox)
+    assert h.levels == 1
+    st, u, info = h.solve(gmt.ELASTIC, tol=1e-9)
+    Ub, Cb = solve.brute_force(vox, "elastic")
+    assert np.abs(h.homogenize(gmt.ELASTIC) - Cb).max() <= 1e-8 * np.abs(Cb).max()
+
+
+def test_edge_cases_report_status(gmt_lib):
+    gmt = gmt_lib
+    with pytest.raises(gmt.GmtError) as e:
+        gmt.Hierarchy(np.zeros((16, 16, 16), dtype=np.uint8))
+    assert e.value.status == gmt.ERR_EMPTY
+    with pytest.raises(gmt.GmtError) as e:
+        gmt.Hierarchy(np.ones((18, 18, 18), dtype=np.uint8))
+    assert e.value.status == gmt.ERR_RES
+    with pytest.raises(gmt.GmtError) as e:
+        gmt.Hierarchy(np.ones((16, 16, 16), dtype=np.uint8), gmt.default_options(levels=4))
+    assert e.value.status == gmt.ERR_RES
+    h = gmt.Hierarchy(L.tpms_network("gyroid", 16, 0.3))
+    with pytest.raises(gmt.GmtError) as e:
+        h.solve(gmt.ELASTIC, nu=0.5)
+    assert e.value.status == gmt.ERR_ARG
+    with pytest.raises(gmt.GmtError) as e:
+        h.homogenize(gmt.ELASTIC)                   # nothing solved yet
+    assert e.value.status == gmt.ERR_STATE
+    # an iteration cap the solve cannot meet returns NOT_CONVERGED with the best field
+    h.set_options(gmt.default_options(max_outer=1, max_inner=1))
+    st, u, info = h.solve(gmt.ELASTIC, tol=1e-12, allow_not_converged=True)
+    assert st == gmt.NOT_CONVERGED and max(info.as_dict()["rel_residual"]) > 1e-12
+
+
+def test_repeat_runs_bitwise_identical(gmt_lib):
+    gmt = gmt_lib
+    vox = L.tpms_plate("diamond", 32, 0.25)
+    out = []
+    for _ in range(2):
+        h = gmt.Hierarchy(vox)
+        st, u, info = h.solve(gmt.ELASTIC, tol=TOL)
+        out.append((u.cpu().numpy().copy(), h.homogenize(gmt.ELASTIC)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_warm_start_resumes(gmt_lib):
+    gmt = gmt_lib
+    vox = L.largest_component(L.truss("bcc", 32, 0.09))
+    h = gmt.Hierarchy(vox)
+    st, u, info = h.solve(gmt.ELASTIC, tol=TOL)
+    st2, u2, info2 = h.solve(gmt.ELASTIC, tol=TOL, u0=u)
+    assert info2.outer == 0 and info2.inner_total == 0
+
+
+@pytest.mark.slow
+def test_full_size_128_properties(gmt_lib):
+    """A 128^3 cell of the mixed workload at the launch configuration the benchmark times:
+    the oracle evaluates the residual and the energy average on the library's field (matrix-
+    free, chunked) instead of solving the 2M-dof system itself."""
+    gmt = gmt_lib
+    vox, desc = L.mixed_cell(2002, 128)
+    h = gmt.Hierarchy(vox)
+    st, u, info = h.solve(gmt.ELASTIC, tol=TOL)
+    lev = grid.Level(vox)
+    Ke, x0, D, M, C0 = fe.physics("elastic")
+    U = to_np(u, D, M)
+    F = solve.load(lev, Ke, x0, D)
+    R = F - solve.apply_ebe(lev, Ke, U, D)
+    res = np.linalg.norm(R, axis=0) / np.linalg.norm(F, axis=0)
+    assert res.max() <= TOL * 1.02, res
+    CH = h.homogenize(gmt.ELASTIC)
+    Co = solve.homogenize_chunked(lev, U, Ke, x0, D)
+    assert np.abs(CH - Co).max() <= 1e-9 * np.abs(Co).max()
+    phi = vox.mean()
+    assert np.linalg.eigvalsh(phi * C0 - CH).min() > -1e-9       # Voigt bound
+    assert np.linalg.eigvalsh(CH).min() > -1e-9 and np.abs(CH - CH.T).max() < 1e-12

@@ -139,3 +139,13 @@ def test_rotation_permutes_tensor(gyroid16):
     C2 = solve.solve_cell(sw, "elastic", E, NU)["CH"]
     perm = [1, 0, 2, 4, 3, 5]                      # xx<->yy, yz<->xz, xy fixed
     assert np.abs(C2 - el["CH"][np.ix_(perm, perm)]).max() < 1e-10
+
+
+def test_ebe_apply_and_chunked_energy_match_assembled(gyroid16):
+    vox, el, _ = gyroid16
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal(el["F"].shape)
+    np.testing.assert_allclose(solve.apply_ebe(el["level"], el["Ke"], U, 3, chunk=257),
+                               el["K"] @ U, atol=1e-12)
+    C = solve.homogenize_chunked(el["level"], el["U"], el["Ke"], el["x0"], 3, chunk=300)
+    np.testing.assert_allclose(C, el["CH"], atol=1e-14)
