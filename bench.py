@@ -1,0 +1,341 @@
+"""Benchmark: C^H solves/s at relative residual 1e-5 on 128^3 lattice cells.
+
+One step = the whole hot path over one batch: for each of 16 seeded 128^3 cells (TPMS
+network and plate lattices, BCC / octet trusses, volume fractions 0.1-0.4), build the sparse
+hierarchy, build the Galerkin operators and the coarsest inverse for E = 1, nu = 0.3, solve
+the six elasticity cell problems to max_m r_m <= 1e-5 (mixed-precision V-cycle CG) and
+reduce C^H. `value` = cells / second with the voxels already on the device; `e2e` repeats
+the step through the same public API from pinned host voxels (host->device copy inside the
+timed region) and reads each C^H back to the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmt|reference]
+                    [--workload c128|c32|c512] [--physics elastic|heat] [--precision fp32|fp64]
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own 16 cells (weak scaling,
+no data-path collective); the timing is the max over ranks. `--impl reference` times the CPU
+FP64 oracle (assembled FE system, Jacobi-preconditioned CG, energy-average C^H) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_26518_b300 import lattices  # noqa: E402
+
+C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_p",
+               "plate_diamond", "bcc", "octet")
+METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
+TOL = 1e-5
+# ncu DRAM bytes (read + write) per active node of one level-0 smoother sweep, from the
+# capture summarised in profiles/ (None until a capture of the current kernel exists)
+NCU_DRAM_BYTES_PER_NODE = None
+
+
+def workload(name: str, rank: int):
+    if name == "c128":
+        cells = [lattices.mixed_cell(2000 + 16 * rank + i, 128, families=C2_FAMILIES)
+                 for i in range(16)]
+        desc = "16 seeded 128^3 cells: TPMS network/plate (gyroid, Schwarz-P, diamond), " \
+               "BCC/octet trusses, phi 0.1-0.4"
+    elif name == "c32":
+        cells = [(lattices.tpms_network("gyroid", 32, 0.30), {"family": "gyroid", "n": 32})]
+        desc = "gyroid 32^3, phi 0.30"
+    elif name == "c512":
+        cells = [(lattices.tpms_network("gyroid", 512, 0.20), {"family": "gyroid", "n": 512})]
+        desc = "gyroid 512^3, phi 0.20"
+    else:
+        raise ValueError(name)
+    return cells, desc
+
+
+# ---------------------------------------------------------------- clocks sampling
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def cpu_sample(n_cells: int = 1, timeout: float = 600.0):
+    """Time the oracle on a bounded sample: the batch's first cells regenerated at 32^3
+    (same generator and seeds), full solve to r <= 1e-5 and C^H, single thread."""
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "from paper_2604_26518_b300 import lattices\n"
+        "from oracle import solve\n"
+        "fams = %r\n"
+        "cells = [lattices.mixed_cell(2000 + i, 32, families=fams)[0] for i in range(%d)]\n"
+        "t = time.perf_counter()\n"
+        "for v in cells: solve.solve_cell(v, 'elastic', 1.0, 0.3, tol=%g)\n"
+        "print(json.dumps({'seconds': time.perf_counter() - t, 'cells': len(cells)}))\n"
+    ) % (ROOT, C2_FAMILIES, n_cells, TOL)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       timeout=timeout, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["cells"] / out["seconds"], out
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample(1)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, _ = cpu_sample(1)
+        rates.append(rate)
+    elapsed = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    sample = ("per step: the batch's first cell (seed 2000) regenerated at 32^3 by the same "
+              "generator, CPU FP64 oracle: assembled K, Jacobi-PCG to max_m r_m <= 1e-5, "
+              "energy-average C^H (the 128^3 cells exceed the oracle's assembled-matrix memory)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "C^H solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c128 batch, bounded 32^3 sample (see cpu_baseline.sample)",
+                   "physics": "elastic", "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "C^H solves/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "C^H solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gmt(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_26518_b300 import gmt
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    gmt.lib()
+    cells, desc = workload(args.workload, rank)
+    ph = gmt.ELASTIC if args.physics == "elastic" else gmt.HEAT
+    prec = gmt.FP32 if args.precision == "fp32" else gmt.FP64
+    opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
+    if args.cells:
+        cells = cells[:args.cells]
+    vox_dev = [torch.from_numpy(v).to(dev) for v, _ in cells]
+    vox_host = [torch.from_numpy(v).pin_memory() for v, _ in cells]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def one_step(src, trace):
+        tot = {}
+        CH = []
+        for v in src:
+            h = gmt.Hierarchy(v, opts, stream)
+            if trace:
+                h.trace(True)
+            st, _, info = h.solve(ph, E=1.0, nu=0.3, k=1.0, tol=TOL, want_field=False,
+                                  allow_not_converged=True)
+            if st != gmt.OK:
+                raise RuntimeError(f"solve status {st}: {info.as_dict()}")
+            CH.append(h.homogenize(ph, E=1.0, nu=0.3, k=1.0))
+            if trace:
+                for k, (n, ms, b) in h.trace_totals().items():
+                    a = tot.setdefault(k, [0, 0.0, 0.0])
+                    a[0] += n
+                    a[1] += ms
+                    a[2] += b
+            h.free()
+        return tot, CH
+
+    for _ in range(args.warmup):
+        one_step(vox_dev, False)
+    # ---- device-resident timed region
+    flush.zero_()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    launches0 = gmt.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    totals = {}
+    step_ms = []
+    for s in range(args.steps):
+        flush.zero_()                       # L2 flush between timed iterations (not timed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        tot, CH = one_step(vox_dev, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, a in tot.items():
+            t = totals.setdefault(k, [0, 0.0, 0.0])
+            for i in range(3):
+                t[i] += a[i]
+    launches = gmt.launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    barrier()
+    elapsed_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    cells_total = len(cells) * world * args.steps
+    value = cells_total / (elapsed_ms / 1000.0)
+    # ---- e2e through the public API from pinned host voxels
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        one_step(vox_host, False)
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = cells_total / (e2e_ms / 1000.0)
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel: the level-0 smoother sweep
+    n_sm, ms_sm, b_sm = totals.get("smooth_l0", [0, 0.0, 0.0])
+    peak, peak_src = measured_peak_gbs()
+    achieved = (b_sm / (ms_sm / 1000.0)) / 1e9 if ms_sm > 0 else None
+    avg_nodes = b_sm / max(n_sm, 1) / (3 * 18 * (4 if prec == gmt.FP32 else 8))
+    traffic = (NCU_DRAM_BYTES_PER_NODE * avg_nodes) if NCU_DRAM_BYTES_PER_NODE else None
+    total_dev_ms = sum(v[1] for v in totals.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "C^H solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == gmt.FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "cells_per_step_per_gpu": len(cells),
+                   "n": cells[0][1]["n"], "physics": args.physics, "tol": TOL,
+                   "precision": ("fp32 V-cycle CG, float-float outer residual, fp64 coarsest "
+                                 "solve and C^H accumulation") if prec == gmt.FP32 else "fp64",
+                   "step": "hierarchy + operators + solve + C^H per cell",
+                   "coarsest_max": args.coarsest,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "C^H solves/s",
+                "h2d_bytes_per_step": int(sum(v.numel() for v in vox_host)),
+                "d2h_bytes_per_step": int(len(cells) * (36 if ph == gmt.ELASTIC else 9) * 8)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "level-0 smoother sweep (k_stencil JACOBI)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes": "3 vectors x 18 values x 4 B per active node",
+                     "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
+        "phases_ms_per_step": {k: v[1] / args.steps for k, v in sorted(totals.items())},
+        "traced_device_ms_per_step": total_dev_ms / args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu:
+        try:
+            rate, out = cpu_sample(1)
+            line["cpu_baseline"] = {
+                "value": rate, "unit": "C^H solves/s", "cores": 1, "kind": "oracle",
+                "sample": "first cell of the batch (seed 2000) regenerated at 32^3 by the same "
+                          "generator; CPU FP64 oracle to r <= 1e-5 + C^H; %.1f s" % out["seconds"]}
+        except Exception as exc:  # noqa: BLE001
+            line["cpu_baseline"] = {"value": None, "error": str(exc)[-300:]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gmt", choices=["gmt", "reference"])
+    ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c512"])
+    ap.add_argument("--physics", default="elastic", choices=["elastic", "heat"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--coarsest", type=int, default=8, help="coarsest grid side bound")
+    ap.add_argument("--cells", type=int, default=0, help="use only the first K cells (profiling)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (torch.cuda.is_available() and args.impl == "gmt") else "gloo"
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gmt(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

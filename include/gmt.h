@@ -127,7 +127,7 @@ gmt_status gmt_node_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out,
 
 /* Active elements of a level, sorted by linear index: xyz_out device int32[ne][3];
    child_mask_out device uint8[ne] (levels >= 1: bit c set when child 2X + c is active;
-   level 0: all ones), nullable. */
+   level 0: 0), nullable. */
 gmt_status gmt_element_coords(const gmt_hierarchy* h, int level, int32_t* xyz_out,
                               uint8_t* child_mask_out);
 
@@ -191,6 +191,24 @@ gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, doubl
    with the solver's outer residual (precision FP32: float-float difference form;
    FP64: native FP64). */
 gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double* out);
+
+/* ---- tracing (measurement support; not part of the method) -----------------------------
+   When enabled, the library records a CUDA event pair on its stream around every launch of
+   the kernels below and accumulates, per category, the launch count, the summed device time
+   and the algorithmic bytes (the bytes the operation must move per active node, times the
+   active nodes: vectors read + written, counted once; no halo re-reads).
+   Categories: 0 level-0 smoother sweep (Jacobi / Chebyshev stencil), 1 level-0 residual in the
+   V-cycle, 2 level-0 operator apply (CG), 3 outer residual (float-float or FP64), 4 level-0
+   first smoothing step (diagonal), 5 coarse-level stencils, 6 restriction, 7 prolongation,
+   8 coarsest solve, 9 C^H energy reduction, 10 vector / reduction kernels, 11 setup. */
+#define GMT_TRACE_CATEGORIES 12
+gmt_status gmt_trace_enable(gmt_hierarchy* h, int on);   /* on != 0 enables; resets totals */
+/* Totals since enabling (synchronizes the stream): launches, device milliseconds, bytes. */
+gmt_status gmt_trace_query(gmt_hierarchy* h, int category, int64_t* launches, double* ms,
+                           double* bytes);
+const char* gmt_trace_name(int category);
+/* Kernels launched by this process through the library so far (all hierarchies). */
+int64_t gmt_launch_count(void);
 
 #ifdef __cplusplus
 }

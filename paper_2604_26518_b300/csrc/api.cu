@@ -22,6 +22,7 @@ void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bo
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);
 void export_elems(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* c);
 void export_stencil(gmt_hierarchy* h, int l, int32_t* idx, double* w);
+int64_t launch_count();
 }  // namespace gmt
 
 using gmt::Fail;
@@ -155,6 +156,7 @@ void gmt_free_hierarchy(gmt_hierarchy* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  h->tracer.destroy();
   gmt::free_workspace(h);
   delete h;
 }
@@ -377,5 +379,39 @@ gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double
   return GMT_OK;
   GMT_API_END
 }
+
+gmt_status gmt_trace_enable(gmt_hierarchy* h, int on) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  ensure_device(h);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  h->tracer.reset();
+  h->tracer.on = on != 0;
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_trace_query(gmt_hierarchy* h, int category, int64_t* launches, double* ms,
+                           double* bytes) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h && category >= 0 && category < gmt::TR_NCAT, GMT_ERR_ARG, "bad category");
+  ensure_device(h);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+  h->tracer.flush();
+  if (launches) *launches = h->tracer.launches[category];
+  if (ms) *ms = h->tracer.ms[category];
+  if (bytes) *bytes = h->tracer.bytes[category];
+  return GMT_OK;
+  GMT_API_END
+}
+
+const char* gmt_trace_name(int c) {
+  static const char* names[gmt::TR_NCAT] = {
+      "smooth_l0", "resid_l0", "apply_l0", "outer_resid", "diag_l0", "stencil_coarse",
+      "restrict", "prolong", "coarse_solve", "energy", "vector", "setup"};
+  return (c >= 0 && c < gmt::TR_NCAT) ? names[c] : "";
+}
+
+int64_t gmt_launch_count(void) { return gmt::launch_count(); }
 
 }  // extern "C"

@@ -41,7 +41,13 @@ struct Fail {
     }                                                                                     \
   } while (0)
 
-#define GMT_LAUNCH_CHECK() GMT_CUDA(cudaGetLastError())
+// every kernel launch site ends with GMT_LAUNCH_CHECK(), which also counts the launch
+void count_launch(int64_t n = 1);
+#define GMT_LAUNCH_CHECK()              \
+  do {                                  \
+    ::gmt::count_launch();              \
+    GMT_CUDA(cudaGetLastError());       \
+  } while (0)
 
 #define GMT_REQUIRE(cond, st, ...)        \
   do {                                    \
@@ -153,6 +159,41 @@ struct Material {
 
 struct Workspace;  // solver buffers (solver.cu)
 
+// Per-hierarchy event tracing of kernel launches (see gmt_trace_* in gmt.h)
+enum TraceCat {
+  TR_SMOOTH0 = 0, TR_RESID0 = 1, TR_APPLY0 = 2, TR_OUTER = 3, TR_DIAG0 = 4, TR_COARSE_ST = 5,
+  TR_RESTRICT = 6, TR_PROLONG = 7, TR_CSOLVE = 8, TR_ENERGY = 9, TR_VEC = 10, TR_SETUP = 11,
+  TR_NCAT = 12
+};
+struct Tracer {
+  bool on = false;
+  struct Rec {
+    int cat;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> recs;
+  int64_t launches[TR_NCAT] = {0};
+  double ms[TR_NCAT] = {0};
+  double bytes[TR_NCAT] = {0};
+  cudaEvent_t get();
+  void flush();      // harvest completed records (synchronize first)
+  void reset();
+  void destroy();
+};
+
+// RAII scope recording an event pair around the launches it encloses
+struct TraceScope {
+  Tracer* t;
+  cudaStream_t s;
+  int cat;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  TraceScope(Tracer* tr, cudaStream_t st, int c, double b);
+  ~TraceScope();
+};
+
 }  // namespace gmt
 
 struct gmt_hierarchy {
@@ -174,6 +215,7 @@ struct gmt_hierarchy {
   double* cb = nullptr;   // m x M gather buffer
   double* cu = nullptr;   // m x M result buffer
   gmt::Workspace* ws = nullptr;
+  gmt::Tracer tracer;
   bool have_solution = false;
   int64_t ws_for_prec = -1;
 };

@@ -8,6 +8,7 @@
 //
 // Everything is computed by kernels on dense N_l^3 flag grids, then compacted into 4^3
 // bricks with exclusive scans. Counts are read back once per level to size allocations.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 
@@ -44,6 +45,70 @@ void Arena::release() {
   for (void* p : ptrs) cudaFree(p);
   ptrs.clear();
   bytes = 0;
+}
+
+// ------------------------------------------------------------------ launch counting, tracing
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(); }
+
+cudaEvent_t Tracer::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  GMT_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void Tracer::flush() {
+  for (Rec& r : recs) {
+    float t = 0.f;
+    GMT_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    launches[r.cat] += 1;
+    ms[r.cat] += t;
+    bytes[r.cat] += r.bytes;
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  recs.clear();
+}
+
+void Tracer::reset() {
+  for (Rec& r : recs) {
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  recs.clear();
+  for (int c = 0; c < TR_NCAT; ++c) {
+    launches[c] = 0;
+    ms[c] = 0;
+    bytes[c] = 0;
+  }
+}
+
+void Tracer::destroy() {
+  reset();
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+
+TraceScope::TraceScope(Tracer* tr, cudaStream_t st, int c, double b)
+    : t(tr), s(st), cat(c), bytes(b) {
+  if (t && t->on) {
+    a = t->get();
+    GMT_CUDA(cudaEventRecord(a, s));
+  }
+}
+
+TraceScope::~TraceScope() {
+  if (a) {
+    cudaEvent_t b = t->get();
+    cudaEventRecord(b, s);
+    t->recs.push_back(Tracer::Rec{cat, bytes, a, b});
+  }
 }
 
 // ------------------------------------------------------------------ exclusive scan
@@ -263,6 +328,7 @@ int choose_levels(int n, int coarsest_max) {
 
 void build_hierarchy(gmt_hierarchy* h, const uint8_t* vox, bool on_device) {
   cudaStream_t s = h->stream;
+  TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
   const int N = h->N;
   const int64_t n3 = (int64_t)N * N * N;
   Arena tmp;

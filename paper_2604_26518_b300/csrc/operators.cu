@@ -7,7 +7,7 @@
 //     8-bit child mask, so it is a 256-entry table; levels >= 2 are stored per element;
 //   * D x D block-diagonal inverses of the coarse operators (smoother, Sec. 4.6);
 //   * the coarsest level's dense generalized inverse of K_L + rho J (J couples equal
-//     components of all nodes, rho = mean diagonal), by in-place Gauss-Jordan with
+//     components of all nodes, rho = mean diagonal), by blocked in-place Gauss-Jordan with
 //     semidefinite pivot dropping. For right-hand sides orthogonal to translations this
 //     returns the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS
 //     is replaced by this exact solve.
@@ -342,40 +342,107 @@ __global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, double rho) 
   if (r % D == c % D) A[g] += rho;
 }
 
-// Gauss-Jordan step k: save row k, column k and the pivot decision
-__global__ void k_gj_save(const double* __restrict__ A, int64_t m, int64_t k, double tol,
-                          double* __restrict__ row, double* __restrict__ col,
-                          int* __restrict__ ok) {
-  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
-    row[j] = A[k * m + j];
-    col[j] = A[j * m + k];
+// Blocked in-place Gauss-Jordan inversion with 32-wide pivot panels. For the panel
+// rows/columns P and the rest Q of the current matrix:
+//   A_PP <- A_PP^+ (small GJ in shared memory, null pivots dropped: semidefinite case)
+//   A_PQ <- A_PP^+ A_PQ,   A_QP <- -A_QP A_PP^+,   A_QQ <- A_QQ - A_QP A_PP^+ A_PQ
+// After all panels the matrix holds the (generalized) inverse.
+constexpr int GJB = 32;
+
+// one block: invert the bb x bb diagonal panel block (pivots <= tol are dropped)
+__global__ void __launch_bounds__(1024) k_gj_panel(const double* __restrict__ A, int64_t m,
+                                                   int64_t k0, int bb, double tol,
+                                                   double* __restrict__ inv) {
+  __shared__ double P[GJB][GJB + 1];
+  __shared__ double rowk[GJB], colk[GJB];
+  __shared__ int ok;
+  const int t = threadIdx.x, i = t / GJB, j = t % GJB;
+  if (i < bb && j < bb) P[i][j] = A[(k0 + i) * m + k0 + j];
+  __syncthreads();
+  for (int k = 0; k < bb; ++k) {
+    if (t < bb) {
+      rowk[t] = P[k][t];
+      colk[t] = P[t][k];
+    }
+    if (t == 0) ok = P[k][k] > tol;
+    __syncthreads();
+    if (i < bb && j < bb) {
+      if (!ok) {
+        if (i == k || j == k) P[i][j] = 0.0;
+      } else {
+        const double p = rowk[k];
+        if (i == k) P[i][j] = (j == k) ? 1.0 / p : rowk[j] / p;
+        else if (j == k) P[i][j] = -colk[i] / p;
+        else P[i][j] -= colk[i] * rowk[j] / p;
+      }
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) ok[0] = A[k * m + k] > tol;
+  if (i < bb && j < bb) inv[i * GJB + j] = P[i][j];
 }
 
-__global__ void k_gj_update(double* __restrict__ A, int64_t m, int64_t k,
-                            const double* __restrict__ row, const double* __restrict__ col,
-                            const int* __restrict__ ok) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= m * m) return;
-  int64_t i = g / m, j = g % m;
-  if (!ok[0]) {  // semidefinite: drop the null pivot (row and column become zero)
-    if (i == k || j == k) A[g] = 0.0;
-    return;
+// T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns)
+__global__ void k_gj_rows(const double* __restrict__ A, int64_t m, int64_t k0, int bb,
+                          const double* __restrict__ inv, double* __restrict__ T,
+                          double* __restrict__ O) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double col[GJB];
+  for (int r = 0; r < bb; ++r) col[r] = A[(k0 + r) * m + j];
+  for (int c = 0; c < bb; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < bb; ++r) s += inv[c * GJB + r] * col[r];
+    T[c * m + j] = s;
   }
-  double p = row[k];
-  if (i == k) {
-    A[g] = (j == k) ? 1.0 / p : row[j] / p;
-  } else if (j == k) {
-    A[g] = -col[i] / p;
-  } else {
-    A[g] -= col[i] * row[j] / p;
+  for (int c = 0; c < bb; ++c) O[j * GJB + c] = A[j * m + k0 + c];
+}
+
+// the rank-bb update of everything, tiled 32 x 32 per block
+__global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ A, int64_t m, int64_t k0,
+                                                   int bb, const double* __restrict__ inv,
+                                                   const double* __restrict__ T,
+                                                   const double* __restrict__ O) {
+  __shared__ double sO[32][GJB + 1];   // O rows of this tile: O[i][r]
+  __shared__ double sT[GJB][32 + 1];   // T columns of this tile: T[r][j]
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int q = threadIdx.x; q < 32 * GJB; q += 256) {
+    const int a = q / GJB, r = q % GJB;
+    sO[a][r] = (i0 + a < m && r < bb) ? O[(i0 + a) * GJB + r] : 0.0;
+    const int rr = q / 32, b = q % 32;
+    sT[rr][b] = (rr < bb && j0 + b < m) ? T[rr * m + j0 + b] : 0.0;
+  }
+  __syncthreads();
+  const int64_t j = j0 + tx;
+  if (j >= m) return;
+  const bool jp = j >= k0 && j < k0 + bb;
+  for (int a = ty; a < 32; a += 8) {
+    const int64_t i = i0 + a;
+    if (i >= m) break;
+    const bool ip = i >= k0 && i < k0 + bb;
+    double v;
+    if (ip && jp) {
+      v = inv[(i - k0) * GJB + (j - k0)];
+    } else if (ip) {
+      v = sT[i - k0][tx];
+    } else if (jp) {
+      double s = 0.0;
+      for (int r = 0; r < bb; ++r) s += sO[a][r] * inv[r * GJB + (j - k0)];
+      v = -s;
+    } else {
+      double s = 0.0;
+#pragma unroll 8
+      for (int r = 0; r < GJB; ++r) s += sO[a][r] * sT[r][tx];
+      v = A[i * m + j] - s;
+    }
+    A[i * m + j] = v;
   }
 }
 
 // ------------------------------------------------------------------ host driver
 void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double kappa) {
   cudaStream_t s = h->stream;
+  TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
   h->op.release();
   h->prepared = false;
   Material& mt = h->mat;
@@ -470,14 +537,19 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->Ainv, m, D, rho);
     GMT_LAUNCH_CHECK();
     const double tol = 1e-12 * (dh[1] + rho * (double)c.n_nodes);
-    double* row = tmp.alloc<double>(m);
-    double* col = tmp.alloc<double>(m);
-    int* ok = tmp.alloc<int>(1);
-    for (int64_t k = 0; k < m; ++k) {
-      k_gj_save<<<1, 256, 0, s>>>(h->Ainv, m, k, tol, row, col, ok);
-      k_gj_update<<<grid_for(m * m, 256), 256, 0, s>>>(h->Ainv, m, k, row, col, ok);
+    double* inv = tmp.alloc<double>(GJB * GJB);
+    double* T = tmp.alloc<double>(GJB * m);
+    double* O = tmp.alloc<double>(GJB * m);
+    const dim3 ug((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+    for (int64_t k0 = 0; k0 < m; k0 += GJB) {
+      const int bb = (int)std::min<int64_t>(GJB, m - k0);
+      k_gj_panel<<<1, 1024, 0, s>>>(h->Ainv, m, k0, bb, tol, inv);
+      GMT_LAUNCH_CHECK();
+      k_gj_rows<<<grid_for(m, 128), 128, 0, s>>>(h->Ainv, m, k0, bb, inv, T, O);
+      GMT_LAUNCH_CHECK();
+      k_gj_update<<<ug, 256, 0, s>>>(h->Ainv, m, k0, bb, inv, T, O);
+      GMT_LAUNCH_CHECK();
     }
-    GMT_LAUNCH_CHECK();
   }
   GMT_CUDA(cudaStreamSynchronize(s));
   h->prepared = true;

@@ -8,6 +8,7 @@
 //                    difference-form level-0 residual (FP32 arithmetic, ~1e-7 accurate);
 //                    d = CG_V(r) in FP32; u += d; repeat until max_m r_m <= tol.
 //
+// Tolerances below 2e-6 evaluate the outer residual in native FP64 instead.
 // Stopping rule (Sec. 5 metric r, reading: the maximum over load cases must meet tol).
 // Gauge (Sec. 3.1 zero-mean constraint): the mean over active nodes of every component
 // and case is removed from the final field. Load cases whose assembled load cancels
@@ -392,10 +393,22 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   int outer = 0, cycles = 0;
   gmt_status st = GMT_NOT_CONVERGED;
   double first_max = -1.0;
-  auto residual = [&](bool ff) {
+  // The float-float residual is accurate to ~1e-7 of ||f||; tolerances below 2e-6 switch
+  // the mixed-precision outer residual to native FP64 on u = hi + lo.
+  const bool ff_outer = pr != P64 && tol >= 2e-6;
+  auto residual = [&](bool mixed) {
     double rn[8];
-    if (ff) {
+    if (mixed && ff_outer) {
       launch_resid_ff(h, w->hi, w->lo, w->rout, w->part);
+    } else if (mixed) {
+      ff_to_f64(h, w->hi, w->lo, w->u64);
+      VecArgs a;
+      a.u = w->u64;
+      a.f = nullptr;
+      a.out = w->f64;
+      a.part = w->part;
+      launch_stencil(h, 0, P64, ST_RESID, a);
+      f64_to_f32(h, w->f64, w->rout);
     } else {
       VecArgs a;
       a.u = w->u64;

@@ -842,6 +842,11 @@ __global__ void k_ff_to_f64(const float* __restrict__ hi, const float* __restric
   if (i < n) dst[i] = (double)hi[i] + (double)lo[i];
 }
 
+__global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
 // ------------------------------------------------------------------ host launchers
 template <typename A, int D, int M>
 static void fill_fine(const Material& mt, FineC<A, D, M>& fc) {
@@ -877,6 +882,14 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   if (fine) fill_fine<A, D, M>(h->mat, p.fc);
   const unsigned g = (unsigned)lv.nb;
   cudaStream_t s = h->stream;
+  int nvec = 2, cat = TR_COARSE_ST;
+  if (mode == ST_RESID) nvec = va.f ? 3 : 2;
+  if (mode == ST_JACOBI) nvec = 3;
+  if (mode == ST_CHEB) nvec = 3 + (va.c1 != 0.0) + (va.dout != nullptr);
+  if (fine) {
+    cat = mode == ST_APPLY ? TR_APPLY0 : (mode == ST_RESID ? (va.f ? TR_RESID0 : TR_OUTER) : TR_SMOOTH0);
+  }
+  TraceScope ts(&h->tracer, s, cat, (double)lv.n_nodes * nvec * D * M * sizeof(TS));
 #define GMT_ST(KIND, MODE) k_stencil<TS, A, D, M, KIND, MODE><<<g, 64, 0, s>>>(p)
   switch (mode) {
     case ST_APPLY: if (fine) GMT_ST(0, ST_APPLY); else GMT_ST(1, ST_APPLY); break;
@@ -917,6 +930,8 @@ static void diag_t(gmt_hierarchy* h, int level, const void* f, void* out, void* 
   p.dout = (TS*)dout;
   p.omega = (A)scale;
   const unsigned g = grid_for(lv.nslots, 128);
+  TraceScope ts(&h->tracer, h->stream, level == 0 ? TR_DIAG0 : TR_COARSE_ST,
+                (double)lv.n_nodes * (dout ? 3 : 2) * D * M * sizeof(TS));
   if (level == 0) {
     fill_fine<A, D, M>(h->mat, p.fc);
     k_diag<TS, A, D, M, 0><<<g, 128, 0, h->stream>>>(p, lv.nslots);
@@ -943,6 +958,7 @@ static void resid_ff_t(gmt_hierarchy* h, const float* hi, const float* lo, float
   p.out = r;
   p.part = part;
   fill_fine<float, D, M>(h->mat, p.fc);
+  TraceScope ts(&h->tracer, h->stream, TR_OUTER, (double)lv.n_nodes * 3 * D * M * sizeof(float));
   k_resid_ff<D, M><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
   GMT_LAUNCH_CHECK();
 }
@@ -955,6 +971,8 @@ void launch_resid_ff(gmt_hierarchy* h, const float* hi, const float* lo, float* 
 template <typename TS, typename A, int D, int M>
 static void restrict_t(gmt_hierarchy* h, int level, const void* rf, void* fc) {
   const Level& c = h->lv[level + 1];
+  TraceScope ts(&h->tracer, h->stream, TR_RESTRICT,
+                (double)(h->lv[level].n_nodes + c.n_nodes) * D * M * sizeof(TS));
   k_restrict<TS, A, D * M><<<grid_for(c.nslots, 64), 64, 0, h->stream>>>(
       (const TS*)rf, (TS*)fc, view(h->lv[level]), view(c));
   GMT_LAUNCH_CHECK();
@@ -966,6 +984,8 @@ void launch_restrict(gmt_hierarchy* h, int level, Prec prec, const void* rf, voi
 template <typename TS, typename A, int D, int M>
 static void prolong_t(gmt_hierarchy* h, int level, const void* uc, void* uf) {
   const Level& f = h->lv[level];
+  TraceScope ts(&h->tracer, h->stream, TR_PROLONG,
+                (double)(2 * f.n_nodes + h->lv[level + 1].n_nodes) * D * M * sizeof(TS));
   k_prolong<TS, A, D * M><<<grid_for(f.nslots, 64), 64, 0, h->stream>>>(
       (const TS*)uc, (TS*)uf, view(f), view(h->lv[level + 1]));
   GMT_LAUNCH_CHECK();
@@ -978,6 +998,7 @@ template <typename TS, typename A, int D, int M>
 static void coarse_t(gmt_hierarchy* h, const void* f, void* u) {
   const Level& c = h->lv[h->L - 1];
   const int64_t cnt = c.n_nodes * D * M;
+  TraceScope ts(&h->tracer, h->stream, TR_CSOLVE, (double)h->m * h->m * 8.0);
   k_coarse_gather<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const TS*)f, c.canon_slot,
                                                                        c.n_nodes, h->cb);
   GMT_LAUNCH_CHECK();
@@ -1004,6 +1025,7 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
   p.part = part;
   for (int i = 0; i < 64 * D * D; ++i) p.Ke[i] = (A)h->mat.Ke[i];
   for (int i = 0; i < 8 * D * M; ++i) p.X0[i] = (A)h->mat.X0[i];
+  TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
   k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
   GMT_LAUNCH_CHECK();
 }
@@ -1198,6 +1220,12 @@ void ff_to_canon(gmt_hierarchy* h, const float* hi, const float* lo, double* dst
 void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst) {
   const int64_t n = nvals(h, 0);
   k_ff_to_f64<<<grid_for(n, 256), 256, 0, h->stream>>>(hi, lo, dst, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst) {
+  const int64_t n = nvals(h, 0);
+  k_f64_to_f32<<<grid_for(n, 256), 256, 0, h->stream>>>(src, dst, n);
   GMT_LAUNCH_CHECK();
 }
 

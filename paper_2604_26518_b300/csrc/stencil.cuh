@@ -72,6 +72,8 @@ void slots_to_canon(gmt_hierarchy* h, int level, Prec prec, const void* src, dou
 void canon_to_ff(gmt_hierarchy* h, const double* src, float* hi, float* lo);
 void ff_to_canon(gmt_hierarchy* h, const float* hi, const float* lo, double* dst);
 void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst);
+// level-0 slot field FP64 -> FP32
+void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst);
 
 inline int64_t blocks_of(const Level& lv) { return lv.nb; }
 inline size_t prec_bytes(Prec p) { return p == P64 ? 8 : (p == P32 ? 4 : 2); }

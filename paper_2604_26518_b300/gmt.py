@@ -100,7 +100,18 @@ _SIGS = {
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
     "gmt_residual": (_I, [_P, _I, _P, _P]),
+    "gmt_trace_enable": (_I, [_P, _I]),
+    "gmt_trace_query": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "gmt_trace_name": (ctypes.c_char_p, [_I]),
+    "gmt_launch_count": (_L, []),
 }
+
+TRACE_CATEGORIES = 12
+
+
+def launch_count() -> int:
+    """Kernels launched through the library by this process so far."""
+    return int(lib().gmt_launch_count())
 
 
 def lib():
@@ -316,6 +327,20 @@ class Hierarchy:
         _check(lib().gmt_homogenize(self._h, physics, E, nu, k, _ptr(ut),
                                     CH.ctypes.data_as(ctypes.c_void_p)), "gmt_homogenize")
         return CH
+
+    # ---------------------------------------------------------------- tracing
+    def trace(self, on=True):
+        _check(lib().gmt_trace_enable(self._h, int(on)), "gmt_trace_enable")
+
+    def trace_totals(self):
+        """{category: (launches, device ms, algorithmic bytes)} since trace(True)."""
+        out = {}
+        for c in range(TRACE_CATEGORIES):
+            n, ms, b = _L(), _D(), _D()
+            _check(lib().gmt_trace_query(self._h, c, ctypes.byref(n), ctypes.byref(ms),
+                                         ctypes.byref(b)), "gmt_trace_query")
+            out[lib().gmt_trace_name(c).decode()] = (n.value, ms.value, b.value)
+        return out
 
     def residual(self, u, precision=FP32):
         D, M = self._dm()

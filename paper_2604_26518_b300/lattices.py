@@ -103,22 +103,33 @@ def _segments(kind: str) -> np.ndarray:
 
 def truss(kind: str, n: int, radius: float) -> np.ndarray:
     """Strut lattice: solid where the periodic distance from the voxel centre to any strut
-    axis is at most `radius` (in units of the cell size)."""
+    axis is at most `radius` (in units of the cell size). Each periodic image of a strut is
+    only evaluated on the voxels inside its bounding box grown by the radius (the only
+    voxels it can reach)."""
     c = (np.arange(n, dtype=np.float64) + 0.5) / n
-    z, y, x = np.meshgrid(c, c, c, indexing="ij")
-    p = np.stack([x, y, z], axis=-1).reshape(-1, 3)
-    best = np.full(p.shape[0], np.inf)
+    best = np.full((n, n, n), np.inf)
     for a, b in _segments(kind):
         ab = b - a
         l2 = float(ab @ ab)
         for sx in (-1, 0, 1):
             for sy in (-1, 0, 1):
                 for sz in (-1, 0, 1):
-                    q = p + np.array([sx, sy, sz], dtype=np.float64) - a
+                    s = np.array([sx, sy, sz], dtype=np.float64)
+                    lo = np.minimum(a, b) + s - radius
+                    hi = np.maximum(a, b) + s + radius
+                    i0 = np.maximum(np.ceil(lo * n - 0.5), 0).astype(int)
+                    i1 = np.minimum(np.floor(hi * n - 0.5), n - 1).astype(int)
+                    if (i1 < i0).any():
+                        continue
+                    zc, yc, xc = (c[i0[2]:i1[2] + 1], c[i0[1]:i1[1] + 1], c[i0[0]:i1[0] + 1])
+                    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+                    q = np.stack([X, Y, Z], axis=-1) - (a + s)
                     t = np.clip(q @ ab / l2, 0.0, 1.0)
-                    d = q - t[:, None] * ab[None, :]
-                    np.minimum(best, np.einsum("ij,ij->i", d, d), out=best)
-    return (best <= radius * radius).astype(np.uint8).reshape(n, n, n)
+                    d = q - t[..., None] * ab
+                    d2 = np.einsum("...i,...i->...", d, d)
+                    sub = best[i0[2]:i1[2] + 1, i0[1]:i1[1] + 1, i0[0]:i1[0] + 1]
+                    np.minimum(sub, d2, out=sub)
+    return (best <= radius * radius).astype(np.uint8)
 
 
 def spinodal(n: int, phi: float, wavenumber: int, rng: np.random.Generator,

