@@ -508,9 +508,10 @@ void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
   double e[21];
   fetch(h, reduce_to(h, w, 0, K, 0), e, K);
   const double vol = (double)h->N * h->N * h->N;
+  const double ne = pr == P64 ? 0.0 : (double)h->lv[0].n_elems;  // ff path: + n_e C0
   for (int I = 0; I < M; ++I)
     for (int J = I; J < M; ++J) {
-      const double v = e[I * M - I * (I - 1) / 2 + (J - I)] / vol;
+      const double v = (e[I * M - I * (I - 1) / 2 + (J - I)] + ne * mt.C0[I * M + J]) / vol;
       CH[I * M + J] = v;
       CH[J * M + I] = v;
     }

@@ -544,12 +544,21 @@ struct EnArgs {
   const void* hi;   // A-typed field, or float hi part (ff)
   const float* lo;  // ff low part or nullptr
   double* part;
-  A Ke[64 * D * D];
-  A X0[8 * D * M];
+  A Ke[64 * D * D];       // FP64 path: K_e; ff path: K_e rounded to FP32 (hi part)
+  A Kl[64 * D * D];       // ff path: K_e - hi (lo part)
+  A X0[8 * D * M];        // FP64 path: x0
+  A Fh[8 * D * M];        // ff path: f_e = K_e x0, hi and lo parts
+  A Fl[8 * D * M];
 };
 
-// per active element e (origin slot n): w^I = x0^I - (u_e^I - u_n^I) (a translation, which
-// K_e annihilates, removed so that FP32 sees O(1) values), E_IJ = w^I . K_e w^J, I <= J
+// Per active element e (origin slot n) and load cases I <= J, the energy
+// (x0^I - u_e^I)^T K_e (x0^J - u_e^J). The element displacement enters through
+// d = u_e - u_n (a translation, which K_e annihilates, removed so that FP32 sees O(1)
+// values). FP64 path: w = x0 - d, E_IJ = w^I . K_e w^J. Float-float path, expanded so that
+// no FP32 rounding is common to every element:
+//     E_IJ - C0_IJ = d^I . K_e d^J - f^I . d^J - d^I . f^J,      f = K_e x0,
+// with K_e and f split into FP32 hi + lo parts; C0_IJ (exact) is added once per element in
+// FP64 on the host side (n_e C0).
 template <typename A, int D, int M, bool FF>
 __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
   constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
@@ -585,32 +594,59 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
 #pragma unroll
   for (int k = 0; k < K; ++k) e[k] = 0.0;
   if (mk & 1u) {  // element with origin at this node is active
-    auto wval = [&](int r, int I) -> A {
+    auto dval = [&](int r, int I) -> A {  // d^I at element dof r = (node bb, component i)
       const int bb = r / D, i = r % D;
       const int q = q0 + (bb & 1) + 6 * ((bb >> 1) & 1) + 36 * (bb >> 2);
       const int v = i * M + I;
       A du = th[v * 216 + q] - th[v * 216 + q0];
       if constexpr (FF) du += tl[v * 216 + q] - tl[v * 216 + q0];
-      return p.X0[r * M + I] - du;
+      return du;
     };
 #pragma unroll 1
     for (int J = 0; J < M; ++J) {
       A w[R], z[R];
+      if constexpr (FF) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) w[r] = wval(r, J);
+        for (int r = 0; r < R; ++r) w[r] = dval(r, J);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        A s = A(0);
+        for (int r = 0; r < R; ++r) {
+          A sh = A(0), sl = A(0);
 #pragma unroll
-        for (int c = 0; c < R; ++c) s += p.Ke[r * R + c] * w[c];
-        z[r] = s;
+          for (int c = 0; c < R; ++c) {
+            sh += p.Ke[r * R + c] * w[c];
+            sl += p.Kl[r * R + c] * w[c];
+          }
+          z[r] = sh + sl;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = p.X0[r * M + J] - dval(r, J);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          A s = A(0);
+#pragma unroll
+          for (int c = 0; c < R; ++c) s += p.Ke[r * R + c] * w[c];
+          z[r] = s;
+        }
       }
 #pragma unroll 1
       for (int I = 0; I <= J; ++I) {
         A s = A(0);
+        if constexpr (FF) {
+          A fd = A(0), df = A(0);   // f^I . d^J and d^I . f^J
 #pragma unroll
-        for (int r = 0; r < R; ++r) s += wval(r, I) * z[r];
-        e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s;
+          for (int r = 0; r < R; ++r) {
+            const A dI = dval(r, I);
+            s += dI * z[r];
+            fd += (p.Fh[r * M + I] + p.Fl[r * M + I]) * w[r];
+            df += dI * (p.Fh[r * M + J] + p.Fl[r * M + J]);
+          }
+          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s - (double)fd - (double)df;
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) s += (p.X0[r * M + I] - dval(r, I)) * z[r];
+          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s;
+        }
       }
     }
   }
@@ -1023,8 +1059,15 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
   p.hi = hi;
   p.lo = lo;
   p.part = part;
-  for (int i = 0; i < 64 * D * D; ++i) p.Ke[i] = (A)h->mat.Ke[i];
-  for (int i = 0; i < 8 * D * M; ++i) p.X0[i] = (A)h->mat.X0[i];
+  for (int i = 0; i < 64 * D * D; ++i) {
+    p.Ke[i] = (A)h->mat.Ke[i];
+    p.Kl[i] = (A)(h->mat.Ke[i] - (double)p.Ke[i]);
+  }
+  for (int i = 0; i < 8 * D * M; ++i) {
+    p.X0[i] = (A)h->mat.X0[i];
+    p.Fh[i] = (A)h->mat.Fe[i];
+    p.Fl[i] = (A)(h->mat.Fe[i] - (double)p.Fh[i]);
+  }
   TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
   k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
   GMT_LAUNCH_CHECK();

@@ -172,9 +172,9 @@ class Hierarchy:
             src, on_dev, self._keep = vox.ctypes.data, 0, vox
         else:
             vox = voxels.contiguous()
-            assert vox.dtype == torch.uint8 and vox.is_cuda
+            assert vox.dtype == torch.uint8 and vox.dim() == 3
             n = vox.shape[0]
-            src, on_dev, self._keep = vox.data_ptr(), 1, vox
+            src, on_dev, self._keep = vox.data_ptr(), int(vox.is_cuda), vox
         self.n = int(n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opts = options if options is not None else default_options()
