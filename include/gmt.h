@@ -73,9 +73,10 @@ typedef struct {
                           GMT_PREC_FP64 = plain all-FP64 solve */
   int krylov;          /* [1] 1: conjugate gradients preconditioned by the V-cycle;
                           0: stationary V-cycle iteration (the paper's GMG loop) */
-  double inner_tol;    /* [1e-3] inner relative reduction per outer refinement */
-  int max_inner;       /* [40] inner iterations (V-cycles) per refinement */
-  int max_outer;       /* [8] outer residual refinements (mixed precision) */
+  double inner_tol;    /* [0.1] mixed precision: the true residual is recomputed (and replaces the
+                          iterated one) whenever the iterated residual fell by this factor */
+  int max_inner;       /* [40] with max_outer: at most max_inner * max(1, max_outer) V-cycles */
+  int max_outer;       /* [8] */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,

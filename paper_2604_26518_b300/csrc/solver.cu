@@ -1,14 +1,9 @@
 // Solver orchestration: the V-cycle of Alg. 1 (smoother, residual, restriction, recursion,
 // coarsest solve, prolongation, smoother), used either as the preconditioner of a
 // conjugate-gradient loop or as a stationary iteration (the paper's GMG loop, Sec. 5
-// baselines), wrapped in outer residual refinement:
-//
-//   precision FP64:  u <- u + CG_V(f - K u) entirely in FP64;
-//   precision FP32:  u kept as a float-float pair (hi, lo); r = f - K u from the
-//                    difference-form level-0 residual (FP32 arithmetic, ~1e-7 accurate);
-//                    d = CG_V(r) in FP32; u += d; repeat until max_m r_m <= tol.
-//
-// Tolerances below 2e-6 evaluate the outer residual in native FP64 instead.
+// baselines), with the solution kept in FP64 (precision FP64) or as a float-float pair
+// refined by reliable residual replacement (precision FP32; see solve()).
+// Tolerances below 2e-6 evaluate the mixed-precision true residual in native FP64.
 // Stopping rule (Sec. 5 metric r, reading: the maximum over load cases must meet tol).
 // Gauge (Sec. 3.1 zero-mean constraint): the mean over active nodes of every component
 // and case is removed from the final field. Load cases whose assembled load cancels
@@ -279,93 +274,20 @@ void estimate_lmax(gmt_hierarchy* h) {
   GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
 
-// ------------------------------------------------------------------ inner iteration
-// Solve K x = b (b in w->rr on entry, arith precision) to a relative reduction inner_tol
-// per active case; x in w->x. Returns the number of V-cycles applied.
-static int inner_solve(gmt_hierarchy* h, Workspace* w, const bool* act_host, double inner_tol,
-                       int max_inner, double* final_rel) {
-  const int M = h->mat.M;
-  const Prec ar = w->arith;
-  const bool krylov = h->opts.krylov != 0;
-  int act[8] = {0};
-  for (int m = 0; m < M; ++m) act[m] = act_host[m];
-  GMT_CUDA(cudaMemcpyAsync(w->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
-  vec_zero(h, 0, ar, w->x);
-  vec_dot(h, 0, ar, w->rr, w->rr, w->part);
-  double r0h[8];
-  fetch(h, reduce_to(h, w, 0, M, 0), r0h, M);
-  for (int m = 0; m < M; ++m) {
-    r0h[m] = std::sqrt(r0h[m]);
-    if (r0h[m] == 0.0) act[m] = 0;
-  }
-  GMT_CUDA(cudaMemcpyAsync(w->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
-  // preconditioner application z = V(rr)
-  auto precond = [&]() -> void* {
-    const void* fin = w->rr;
-    if (w->prec != ar) {  // (bf16 inner storage) convert rr
-      GMT_REQUIRE(false, GMT_ERR_ARG, "mixed storage precision not supported");
-    }
-    return vcycle(h, w, 0, fin, nullptr, true);
-  };
-  int cycles = 0;
-  void* z = precond();
-  ++cycles;
-  double* rz = w->red + 4 * 32;  // device: r.z per case
-  double* pq = w->red + 5 * 32;
-  double* rz_new = w->red + 6 * 32;
-  if (krylov) {
-    vec_copy(h, 0, ar, z, w->p);
-    vec_dot(h, 0, ar, w->rr, z, w->part);
-    launch_reduce(h, w->part, h->lv[0].nb, M, rz);
-  }
-  double rel = 1.0;
-  for (int it = 0; it < max_inner; ++it) {
-    VecArgs a;
-    if (krylov) {
-      a.u = w->p;
-      a.out = w->q;
-      a.part = w->part;
-      launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K p, part = p.q
-      launch_reduce(h, w->part, h->lv[0].nb, M, pq);
-      vec_cg_update(h, ar, rz, pq, w->active, w->x, w->p, w->rr, w->q, w->part);
-    } else {
-      a.u = z;
-      a.out = w->q;
-      launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K z
-      vec_cg_update(h, ar, w->ones, w->ones, w->active, w->x, z, w->rr, w->q, w->part);
-    }
-    double rn[8];
-    fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
-    rel = 0.0;
-    bool done = true;
-    for (int m = 0; m < M; ++m) {
-      if (!act[m]) continue;
-      const double rm = std::sqrt(rn[m]) / r0h[m];
-      if (!(rm <= inner_tol)) done = false;
-      if (std::isnan(rm)) {
-        rel = rm;
-        done = true;
-        break;
-      }
-      rel = std::max(rel, rm);
-    }
-    if (done || it + 1 == max_inner) break;
-    z = precond();
-    ++cycles;
-    if (krylov) {
-      vec_dot(h, 0, ar, w->rr, z, w->part);
-      launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
-      vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
-      GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    }
-  }
-  if (final_rel) *final_rel = rel;
-  return cycles;
-}
-
 // ------------------------------------------------------------------ solve
 static Prec prec_of(int p) { return p == GMT_PREC_FP64 ? P64 : (p == GMT_PREC_BF16 ? PBF : P32); }
 
+// Preconditioned iteration on K u = f with the V-cycle as preconditioner.
+//   krylov = 1: conjugate gradients; krylov = 0: stationary V-cycle iteration u += V(f - K u).
+// FP64: all vectors FP64; the recursively updated residual is trusted until it reaches
+//   tol / 2, then the true residual decides.
+// FP32 (mixed precision with reliable updates): the iteration vectors are FP32 and the
+//   correction accumulates in an FP32 vector x; whenever the iterated residual has dropped
+//   by `inner_tol` relative to the last true residual (or looks converged), x is added to
+//   the float-float solution (hi, lo), the true residual f - K u is recomputed with the
+//   float-float difference-form kernel and replaces the iterated one. The Krylov recurrence
+//   (p, r.z) continues across these replacements instead of restarting, so the iteration
+//   count stays that of FP64 CG while every vector operation runs in FP32.
 gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, gmt_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   const gmt_options& o = h->opts;
@@ -375,6 +297,8 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   Workspace* w = workspace(h, pr);
   const int M = h->mat.M;
   const Material& mt = h->mat;
+  const bool mixed = pr != P64;
+  const bool krylov = o.krylov != 0;
   // ||f_m|| and the load-cancellation rule
   const unsigned nb0 = (unsigned)h->lv[0].nb;
   if (mt.D == 3)
@@ -384,38 +308,33 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   GMT_LAUNCH_CHECK();
   double fn[8];
   fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
-  bool act[8] = {false};
+  int act[8] = {0};
   for (int m = 0; m < M; ++m) {
     fn[m] = std::sqrt(fn[m]);
     act[m] = fn[m] > 1e-12 * mt.gross[m];
   }
+  // the float-float residual is accurate to ~1e-7 of ||f||; tighter tolerances use FP64
+  const bool ff_outer = mixed && tol >= 2e-6;
   double rel[8] = {0};
-  int outer = 0, cycles = 0;
-  gmt_status st = GMT_NOT_CONVERGED;
-  double first_max = -1.0;
-  // The float-float residual is accurate to ~1e-7 of ||f||; tolerances below 2e-6 switch
-  // the mixed-precision outer residual to native FP64 on u = hi + lo.
-  const bool ff_outer = pr != P64 && tol >= 2e-6;
-  auto residual = [&](bool mixed) {
+  // true residual of the current solution into w->rr (arith precision), norms into rel[]
+  auto true_residual = [&]() -> double {
     double rn[8];
-    if (mixed && ff_outer) {
-      launch_resid_ff(h, w->hi, w->lo, w->rout, w->part);
-    } else if (mixed) {
-      ff_to_f64(h, w->hi, w->lo, w->u64);
+    if (!mixed) {
       VecArgs a;
       a.u = w->u64;
-      a.f = nullptr;
-      a.out = w->f64;
-      a.part = w->part;
-      launch_stencil(h, 0, P64, ST_RESID, a);
-      f64_to_f32(h, w->f64, w->rout);
-    } else {
-      VecArgs a;
-      a.u = w->u64;
-      a.f = nullptr;
       a.out = w->rr;
       a.part = w->part;
       launch_stencil(h, 0, P64, ST_RESID, a);
+    } else if (ff_outer) {
+      launch_resid_ff(h, w->hi, w->lo, (float*)w->rr, w->part);
+    } else {
+      ff_to_f64(h, w->hi, w->lo, w->u64);
+      VecArgs a;
+      a.u = w->u64;
+      a.out = w->f64;
+      a.part = w->part;
+      launch_stencil(h, 0, P64, ST_RESID, a);
+      f64_to_f32(h, w->f64, (float*)w->rr);
     }
     fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
     double mx = 0.0;
@@ -425,7 +344,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     }
     return mx;
   };
-  if (pr == P64) {
+  if (!mixed) {
     if (u0) canon_to_slots(h, 0, P64, u0, w->u64);
     else vec_zero(h, 0, P64, w->u64);
   } else {
@@ -435,53 +354,113 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       vec_zero(h, 0, P32, w->lo);
     }
   }
-  for (;;) {
-    const double mx = residual(pr != P64);
-    if (first_max < 0) first_max = mx;
-    if (std::isnan(mx) || mx > 1e4 * std::max(first_max, 1e-300)) {
-      st = GMT_DIVERGED;
-      break;
+  const Prec ar = w->arith;
+  int cycles = 0, updates = 0;
+  gmt_status st = GMT_NOT_CONVERGED;
+  double mx = true_residual();
+  const double first = mx;
+  double ref[8];   // true residual norms at the last replacement
+  for (int m = 0; m < M; ++m) ref[m] = rel[m];
+  auto push_active = [&]() {
+    GMT_CUDA(cudaMemcpyAsync(w->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
+  };
+  auto deactivate_converged = [&]() {
+    for (int m = 0; m < M; ++m)
+      if (act[m] && rel[m] <= tol) act[m] = 0;
+  };
+  int live[8];
+  for (int m = 0; m < M; ++m) live[m] = act[m];
+  const int max_cycles = o.max_inner * std::max(1, o.max_outer);
+  if (mx <= tol) {
+    st = GMT_OK;
+  } else {
+    for (int m = 0; m < M; ++m) act[m] = live[m] && rel[m] > tol;
+    push_active();
+    vec_zero(h, 0, ar, w->x);
+    double* rz = w->red + 4 * 32;
+    double* pq = w->red + 5 * 32;
+    double* rz_new = w->red + 6 * 32;
+    void* z = vcycle(h, w, 0, w->rr, nullptr, true);
+    ++cycles;
+    if (krylov) {
+      vec_copy(h, 0, ar, z, w->p);
+      vec_dot(h, 0, ar, w->rr, z, w->part);
+      launch_reduce(h, w->part, h->lv[0].nb, M, rz);
     }
-    if (mx <= tol) {
-      st = GMT_OK;
-      break;
+    for (;;) {
+      VecArgs a;
+      a.u = krylov ? w->p : z;
+      a.out = w->q;
+      a.part = krylov ? w->part : nullptr;
+      launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K p (and p.q)
+      if (krylov) {
+        launch_reduce(h, w->part, h->lv[0].nb, M, pq);
+        vec_cg_update(h, ar, rz, pq, w->active, w->x, w->p, w->rr, w->q, w->part);
+      } else {
+        vec_cg_update(h, ar, w->ones, w->ones, w->active, w->x, z, w->rr, w->q, w->part);
+      }
+      double rn[8];
+      fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+      bool replace = false, nan = false;
+      for (int m = 0; m < M; ++m) {
+        if (!act[m]) continue;
+        const double r = std::sqrt(rn[m]) / fn[m];
+        if (std::isnan(r)) nan = true;
+        if (r <= 0.5 * tol || (mixed && r <= o.inner_tol * ref[m])) replace = true;
+      }
+      const bool last = cycles >= max_cycles;
+      if (replace || nan || last) {
+        // fold the correction into the solution and take the true residual
+        if (mixed) vec_ff_add(h, (const float*)w->x, w->hi, w->lo);
+        else vec_add(h, 0, P64, w->x, w->u64);
+        vec_zero(h, 0, ar, w->x);
+        mx = true_residual();
+        ++updates;
+        if (mx <= tol) {
+          st = GMT_OK;
+          break;
+        }
+        if (std::isnan(mx) || mx > 1e4 * std::max(first, 1e-300)) {
+          st = GMT_DIVERGED;
+          break;
+        }
+        if (last) break;
+        for (int m = 0; m < M; ++m) ref[m] = rel[m];
+        deactivate_converged();
+        push_active();
+      }
+      z = vcycle(h, w, 0, w->rr, nullptr, true);
+      ++cycles;
+      if (krylov) {
+        vec_dot(h, 0, ar, w->rr, z, w->part);
+        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
+        vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
+        GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 h->stream));
+      }
     }
-    if (outer >= o.max_outer) break;
-    bool ia[8];
-    for (int m = 0; m < M; ++m) ia[m] = act[m] && rel[m] > tol;
-    if (pr == P64) {
-      // FP64: one inner CG to the full tolerance
-      double itol = tol / std::max(mx, 1e-300) * 0.5;
-      cycles += inner_solve(h, w, ia, std::min(itol, 0.5), o.max_inner, nullptr);
-      vec_add(h, 0, P64, w->x, w->u64);
-    } else {
-      vec_copy(h, 0, P32, w->rout, w->rr);
-      cycles += inner_solve(h, w, ia, o.inner_tol, o.max_inner, nullptr);
-      vec_ff_add(h, (const float*)w->x, w->hi, w->lo);
-    }
-    ++outer;
   }
   // gauge: remove the mean of every component and case over active nodes
   {
     const int C = mt.C;
-    if (pr == P64) vec_sum_values(h, 0, P64, w->u64, nullptr, w->part);
+    if (!mixed) vec_sum_values(h, 0, P64, w->u64, nullptr, w->part);
     else vec_sum_values(h, 0, P32, w->hi, w->lo, w->part);
     double* sums = reduce_to(h, w, 0, C, 1);
     double hs[18];
     fetch(h, sums, hs, C);
     for (int v = 0; v < C; ++v) hs[v] /= (double)h->lv[0].n_nodes;
     GMT_CUDA(cudaMemcpyAsync(w->red + 2 * 32, hs, C * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (pr == P64) vec_sub_mean64(h, 0, w->red + 2 * 32, w->u64);
+    if (!mixed) vec_sub_mean64(h, 0, w->red + 2 * 32, w->u64);
     else vec_ff_sub_mean(h, w->red + 2 * 32, w->hi, w->lo);
   }
   if (u_out) {
-    if (pr == P64) slots_to_canon(h, 0, P64, w->u64, u_out);
+    if (!mixed) slots_to_canon(h, 0, P64, w->u64, u_out);
     else ff_to_canon(h, w->hi, w->lo, u_out);
   }
   GMT_CUDA(cudaStreamSynchronize(h->stream));
   h->have_solution = true;
   if (info) {
-    info->outer = outer;
+    info->outer = updates;
     info->inner_total = cycles;
     info->cases = M;
     for (int m = 0; m < 6; ++m) info->rel_residual[m] = m < M ? rel[m] : 0.0;
