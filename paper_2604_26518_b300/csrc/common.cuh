@@ -141,6 +141,8 @@ struct Level {
   // material-dependent operator data (device)
   double* K64 = nullptr;        // level 1: [256][MM] table; level >= 2: [n_elems][MM]
   float* K32 = nullptr;
+  double* S64 = nullptr;        // levels >= 1: per-node stencils [brick][27 D D][64] (lazy)
+  float* S32 = nullptr;
   double* dinv64 = nullptr;     // levels >= 1: nslots x D*D block-diagonal inverses
   float* dinv32 = nullptr;
   double lmax = 0.0;            // Chebyshev: estimate of lambda_max(D^-1 K)

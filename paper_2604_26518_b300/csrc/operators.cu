@@ -19,6 +19,8 @@
 
 namespace gmt {
 
+void build_node_stencils(gmt_hierarchy* h, int level, bool fp64);
+
 // ------------------------------------------------------------------ element matrices
 __device__ double gauss_x(int q) { return q ? 0.5 + 0.5 / sqrt(3.0) : 0.5 - 0.5 / sqrt(3.0); }
 
@@ -444,6 +446,11 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   cudaStream_t s = h->stream;
   TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
   h->op.release();
+  for (Level& l : h->lv) {
+    l.K64 = l.S64 = l.dinv64 = nullptr;
+    l.K32 = l.S32 = l.dinv32 = nullptr;
+    l.lmax = 0.0;
+  }
   h->prepared = false;
   Material& mt = h->mat;
   mt = Material();
@@ -513,6 +520,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
                                                        c.dinv64, c.dinv32);
     GMT_LAUNCH_CHECK();
   }
+  for (int l = 1; l + 1 < h->L; ++l) build_node_stencils(h, l, false);
   // coarsest generalized inverse
   {
     const int lc = h->L - 1;

@@ -308,10 +308,10 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   GMT_LAUNCH_CHECK();
   double fn[8];
   fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
-  int act[8] = {0};
+  int act[8] = {0}, live[8] = {0};   // live: the case has a load; act: still iterating
   for (int m = 0; m < M; ++m) {
     fn[m] = std::sqrt(fn[m]);
-    act[m] = fn[m] > 1e-12 * mt.gross[m];
+    live[m] = act[m] = fn[m] > 1e-12 * mt.gross[m];
   }
   // the float-float residual is accurate to ~1e-7 of ||f||; tighter tolerances use FP64
   const bool ff_outer = mixed && tol >= 2e-6;
@@ -339,8 +339,8 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
     double mx = 0.0;
     for (int m = 0; m < M; ++m) {
-      rel[m] = act[m] ? std::sqrt(rn[m]) / fn[m] : 0.0;
-      if (act[m]) mx = std::max(mx, rel[m]);
+      rel[m] = live[m] ? std::sqrt(rn[m]) / fn[m] : 0.0;
+      if (live[m]) mx = std::max(mx, rel[m]);
     }
     return mx;
   };
@@ -368,8 +368,6 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     for (int m = 0; m < M; ++m)
       if (act[m] && rel[m] <= tol) act[m] = 0;
   };
-  int live[8];
-  for (int m = 0; m < M; ++m) live[m] = act[m];
   const int max_cycles = o.max_inner * std::max(1, o.max_outer);
   if (mx <= tol) {
     st = GMT_OK;

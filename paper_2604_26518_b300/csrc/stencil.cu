@@ -107,43 +107,59 @@ __device__ __forceinline__ void fine_diag_inv(const FineC<A, D, M>& fc, unsigned
   inv_block<A, D>(Bk, I);
 }
 
-// ------------------------------------------------------------------ the stencil kernel
-template <typename TS, typename A, int D, int M, int KIND, int MODE>
-__global__ void __launch_bounds__(64)
-    k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
-  constexpr int C = D * M, R = 8 * D, MM = R * R;
-  __shared__ A tile[C * 216];
-  __shared__ int nb[27];
-  __shared__ int eid[KIND == 0 ? 1 : 125];
-  const int t = threadIdx.x;
-  const int64_t b = blockIdx.x;
-  if (t < 27) nb[t] = p.nbr[b * 27 + t];
-  __syncthreads();
-  for (int i = t; i < C * 216; i += 64) {
-    const int v = i / 216, q = i - v * 216;
+// ------------------------------------------------------------------ tile staging
+// Stage the brick (own node of every thread, coalesced, kept in registers) plus its
+// one-node halo (152 of the 216 tile positions, gathered from the 26 neighbour bricks) in
+// shared memory. Index arithmetic is done once per tile position, not per value.
+template <typename TS, typename A, int C>
+__device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, int t,
+                                           const int* nb, A* tile, A (&self)[C]) {
+  const int q0 = ((t & 3) + 1) + 6 * (((t >> 2) & 3) + 1) + 36 * ((t >> 4) + 1);
+  const TS* own = u + b * (64 * C) + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) self[v] = load_as<A>(own + v * 64);
+#pragma unroll
+  for (int v = 0; v < C; ++v) tile[v * 216 + q0] = self[v];
+  for (int q = t; q < 216; q += 64) {
     const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
+    if (tx >= 1 && tx <= 4 && ty >= 1 && ty <= 4 && tz >= 1 && tz <= 4) continue;
     const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
     const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
     const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
     const int nbi = nb[bz * 9 + by * 3 + bx];
-    A val = A(0);
-    if (nbi >= 0)
-      val = load_as<A>(p.u + (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) +
-                       4 * ((ty + 3) & 3) + 16 * ((tz + 3) & 3));
-    tile[i] = val;
-  }
-  if constexpr (KIND != 0) {
-    for (int i = t; i < 125; i += 64) {
-      const int ex = i % 5, ey = (i / 5) % 5, ez = i / 25;
-      const int nbi = nb[(ez == 0 ? 0 : 1) * 9 + (ey == 0 ? 0 : 1) * 3 + (ex == 0 ? 0 : 1)];
-      eid[i] = nbi >= 0 ? p.kidx[(int64_t)nbi * 64 + ((ex + 3) & 3) + 4 * ((ey + 3) & 3) +
-                                 16 * ((ez + 3) & 3)]
-                        : -1;
+    if (nbi >= 0) {
+      const TS* src = u + (int64_t)nbi * (64 * C) + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
+                      16 * ((tz + 3) & 3);
+      A vals[C];
+#pragma unroll
+      for (int v = 0; v < C; ++v) vals[v] = load_as<A>(src + v * 64);
+#pragma unroll
+      for (int v = 0; v < C; ++v) tile[v * 216 + q] = vals[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < C; ++v) tile[v * 216 + q] = A(0);
     }
   }
+}
+
+// ------------------------------------------------------------------ the stencil kernel
+// KIND 0: level 0, S_n(d) formed from the octant mask and K_e (parameter bank).
+// KIND 1: coarse levels, S_n(d) read from the per-node assembled stencil, stored
+//         brick-major as [brick][27 * D * D][64] so each coefficient load is coalesced.
+template <typename TS, typename A, int D, int M, int KIND, int MODE>
+__global__ void __launch_bounds__(64)
+    k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
+  constexpr int C = D * M, R = 8 * D, DD = D * D;
+  __shared__ A tile[C * 216];
+  __shared__ int nb[27];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (t < 27) nb[t] = p.nbr[b * 27 + t];
   __syncthreads();
-  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
-  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
+  A self[C];
+  stage_tile<TS, A, C>(p.u, b, t, nb, tile, self);
+  __syncthreads();
+  const int q0 = ((t & 3) + 1) + 6 * (((t >> 2) & 3) + 1) + 36 * ((t >> 4) + 1);
   const int64_t slot = b * 64 + t;
   const unsigned mk = p.mask[slot];
   A acc[C];
@@ -151,50 +167,38 @@ __global__ void __launch_bounds__(64)
   for (int v = 0; v < C; ++v) acc[v] = A(0);
   if (mk) {
     A bf[8];
-    const A* Km[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      if constexpr (KIND == 0) {
-        bf[a] = ((mk >> a) & 1u) ? A(1) : A(0);
-      } else {
-        const int e = eid[(lx + 1 - (a & 1)) + 5 * (ly + 1 - ((a >> 1) & 1)) +
-                          25 * (lz + 1 - (a >> 2))];
-        Km[a] = e >= 0 ? p.kmat + (int64_t)e * MM : nullptr;
-      }
-    }
+    for (int a = 0; a < 8; ++a) bf[a] = ((mk >> a) & 1u) ? A(1) : A(0);
+    const A* sten = p.kmat + b * (64 * 27 * DD) + t;
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      A S[D * D];
+      A S[DD];
+      if constexpr (KIND == 0) {
 #pragma unroll
-      for (int k = 0; k < D * D; ++k) S[k] = A(0);
+        for (int k = 0; k < DD; ++k) S[k] = A(0);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
-        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
-        const int bb = ex + 2 * ey + 4 * ez;
-        if constexpr (KIND == 0) {
+        for (int a = 0; a < 8; ++a) {
+          const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+          const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+          if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+          const int bb = ex + 2 * ey + 4 * ez;
 #pragma unroll
           for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j)
               S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
-        } else {
-          if (Km[a] != nullptr) {
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-              for (int j = 0; j < D; ++j) S[i * D + j] += Km[a][(a * D + i) * R + bb * D + j];
-          }
         }
+      } else {
+#pragma unroll
+        for (int k = 0; k < DD; ++k) S[k] = sten[(d * DD + k) * 64];
       }
       const int q = q0 + dx + 6 * dy + 36 * dz;
 #pragma unroll
       for (int j = 0; j < D; ++j) {
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const A uv = tile[(j * M + m) * 216 + q];
+          const A uv = (d == 13) ? self[j * M + m] : tile[(j * M + m) * 216 + q];
 #pragma unroll
           for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * uv;
         }
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(64)
 #pragma unroll
     for (int v = 0; v < C; ++v) {
       p.out[base + v * 64] = store_as<TS>(mk ? acc[v] : A(0));
-      if (mk) dots[v % M] += (double)(tile[v * 216 + q0] * acc[v]);
+      if (mk) dots[v % M] += (double)(self[v] * acc[v]);
     }
     if (p.part) block_partial_64<M>(dots, p.part + b * M);
   } else if constexpr (MODE == ST_RESID) {
@@ -238,13 +242,13 @@ __global__ void __launch_bounds__(64)
     }
     if (p.part) block_partial_64<M>(nrm, p.part + b * M);
   } else {
-    A Iv[D * D];
+    A Iv[DD];
     if (mk) {
       if constexpr (KIND == 0) {
         fine_diag_inv<A, D, M>(p.fc, mk, Iv);
       } else {
 #pragma unroll
-        for (int k = 0; k < D * D; ++k) Iv[k] = p.dinv[slot * D * D + k];
+        for (int k = 0; k < DD; ++k) Iv[k] = p.dinv[slot * DD + k];
       }
     }
 #pragma unroll
@@ -258,17 +262,73 @@ __global__ void __launch_bounds__(64)
 #pragma unroll
         for (int j = 0; j < D; ++j) z += Iv[i * D + j] * r[j];
         const int v = i * M + m;
-        const A self = tile[v * 216 + q0];
         if constexpr (MODE == ST_JACOBI) {
-          p.out[base + v * 64] = store_as<TS>(mk ? self + p.omega * z : A(0));
+          p.out[base + v * 64] = store_as<TS>(mk ? self[v] + p.omega * z : A(0));
         } else {
           const A dn = (p.c1 != A(0) ? p.c1 * load_as<A>(p.dprev + base + v * 64) : A(0)) + p.c2 * z;
-          p.out[base + v * 64] = store_as<TS>(mk ? self + dn : A(0));
+          p.out[base + v * 64] = store_as<TS>(mk ? self[v] + dn : A(0));
           if (p.dout) p.dout[base + v * 64] = store_as<TS>(mk ? dn : A(0));
         }
       }
     }
   }
+}
+
+// per-node assembled stencil of a coarse level: S_n(d) = sum over active elements e = n - a
+// with a + d in {0,1}^3 of K(e)[a, a + d], written as [brick][27 * D * D][64]
+__global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bxyz,
+                               const int* __restrict__ bmap, bool dense, int64_t nslots,
+                               const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
+                               const double* __restrict__ K, double* __restrict__ S64,
+                               float* __restrict__ S32) {
+  const int R = 8 * D, MM = R * R, DD = D * D;
+  const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslots) return;
+  const unsigned mk = mask[sl];
+  int x = 0, y = 0, z = 0;
+  if (mk) slot_coords(sl, n, dense, bxyz, x, y, z);
+  const int64_t base = (sl >> 6) * (64 * 27 * DD) + (sl & 63);
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (mk) {
+      for (int a = 0; a < 8; ++a) {
+        if (!((mk >> a) & 1u)) continue;
+        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+        const int bb = ex + 2 * ey + 4 * ez;
+        const int64_t es = site_slot((x - ax + n) % n, (y - ay + n) % n, (z - az + n) % n, n, nbx,
+                                     bmap, dense);
+        const double* Ke = K + (int64_t)kidx[es] * MM;
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j) S[i * D + j] += Ke[(a * D + i) * R + bb * D + j];
+      }
+    }
+    for (int k = 0; k < DD; ++k) {
+      if (S64) S64[base + (int64_t)(d * DD + k) * 64] = S[k];
+      if (S32) S32[base + (int64_t)(d * DD + k) * 64] = (float)S[k];
+    }
+  }
+}
+
+void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
+  Level& lv = h->lv[level];
+  const int D = h->mat.D;
+  const size_t cnt = (size_t)lv.nslots * 27 * D * D;
+  double* s64 = nullptr;
+  float* s32 = nullptr;
+  if (fp64) {
+    if (lv.S64) return;
+    s64 = lv.S64 = h->op.alloc<double>(cnt);
+  } else {
+    if (lv.S32) return;
+    s32 = lv.S32 = h->op.alloc<float>(cnt);
+  }
+  k_node_stencil<<<grid_for(lv.nslots, 128), 128, 0, h->stream>>>(
+      D, lv.n, lv.nbx, lv.brick_xyz, lv.brick_map, lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K64,
+      s64, s32);
+  GMT_LAUNCH_CHECK();
 }
 
 // first smoothing step from a zero initial guess: out = scale * D^-1 f
@@ -331,23 +391,9 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   const int64_t b = blockIdx.x;
   if (t < 27) nb[t] = p.nbr[b * 27 + t];
   __syncthreads();
-  for (int i = t; i < C * 216; i += 64) {
-    const int v = i / 216, q = i - v * 216;
-    const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
-    const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
-    const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
-    const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
-    const int nbi = nb[bz * 9 + by * 3 + bx];
-    float h = 0.f, l = 0.f;
-    if (nbi >= 0) {
-      const int64_t a = (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
-                        16 * ((tz + 3) & 3);
-      h = p.hi[a];
-      l = p.lo[a];
-    }
-    th[i] = h;
-    tl[i] = l;
-  }
+  float sh[C], sl[C];
+  stage_tile<float, float, C>(p.hi, b, t, nb, th, sh);
+  stage_tile<float, float, C>(p.lo, b, t, nb, tl, sl);
   __syncthreads();
   const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
   const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
@@ -385,7 +431,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           const int v = j * M + m;
-          const float du = (th[v * 216 + q] - th[v * 216 + q0]) + (tl[v * 216 + q] - tl[v * 216 + q0]);
+          const float du = (th[v * 216 + q] - sh[v]) + (tl[v * 216 + q] - sl[v]);
 #pragma unroll
           for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * du;
         }
@@ -569,22 +615,10 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
   const int64_t b = blockIdx.x;
   if (t < 27) nb[t] = p.nbr[b * 27 + t];
   __syncthreads();
-  for (int i = t; i < C * 216; i += 64) {
-    const int v = i / 216, q = i - v * 216;
-    const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
-    const int bx = tx == 0 ? 0 : (tx == 5 ? 2 : 1);
-    const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
-    const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
-    const int nbi = nb[bz * 9 + by * 3 + bx];
-    A h = A(0), l = A(0);
-    if (nbi >= 0) {
-      const int64_t a = (int64_t)nbi * (64 * C) + v * 64 + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
-                        16 * ((tz + 3) & 3);
-      h = ((const A*)p.hi)[a];
-      if constexpr (FF) l = (A)p.lo[a];
-    }
-    th[i] = h;
-    if constexpr (FF) tl[i] = l;
+  {
+    A own[C];
+    stage_tile<A, A, C>((const A*)p.hi, b, t, nb, th, own);
+    if constexpr (FF) stage_tile<float, A, C>(p.lo, b, t, nb, tl, own);
   }
   __syncthreads();
   const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
@@ -653,34 +687,32 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
   block_partial_64<K>(e, p.part + b * K);
 }
 
-// deterministic reduction of [nblk][K] partials (Neumaier-compensated per thread,
-// fixed-order tree across threads)
-__global__ void k_reduce(const double* __restrict__ part, int64_t nblk, int K,
-                         double* __restrict__ out) {
-  __shared__ double ss[1024], sc[1024];
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0, c = 0.0;
-    for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) {
-      const double x = part[i * K + k];
-      const double tt = s + x;
-      c += fabs(s) >= fabs(x) ? (s - tt) + x : (x - tt) + s;
-      s = tt;
+// deterministic reduction of [nblk][K] partials: block k reduces column k
+// (Neumaier-compensated per thread over a fixed stride, fixed-order tree across threads)
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part, int64_t nblk,
+                                                int K, double* __restrict__ out) {
+  __shared__ double ss[256], sc[256];
+  const int k = blockIdx.x;
+  double s = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < nblk; i += 256) {
+    const double x = part[i * K + k];
+    const double tt = s + x;
+    c += fabs(s) >= fabs(x) ? (s - tt) + x : (x - tt) + s;
+    s = tt;
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = ss[threadIdx.x], x = ss[threadIdx.x + o];
+      const double tt = a + x;
+      sc[threadIdx.x] += sc[threadIdx.x + o] + (fabs(a) >= fabs(x) ? (a - tt) + x : (x - tt) + a);
+      ss[threadIdx.x] = tt;
     }
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        const double a = ss[threadIdx.x], x = ss[threadIdx.x + o];
-        const double tt = a + x;
-        sc[threadIdx.x] += sc[threadIdx.x + o] + (fabs(a) >= fabs(x) ? (a - tt) + x : (x - tt) + a);
-        ss[threadIdx.x] = tt;
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = ss[0] + sc[0];
     __syncthreads();
   }
+  if (threadIdx.x == 0) out[k] = ss[0] + sc[0];
 }
 
 // ------------------------------------------------------------------ vector kernels
@@ -898,11 +930,12 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   p.nbr = lv.brick_nbr;
   p.mask = lv.mask;
   p.kidx = lv.kidx;
+  if (level > 0) build_node_stencils(h, level, sizeof(A) == 8);
   if constexpr (sizeof(A) == 8) {
-    p.kmat = (const A*)lv.K64;
+    p.kmat = (const A*)lv.S64;
     p.dinv = (const A*)lv.dinv64;
   } else {
-    p.kmat = (const A*)lv.K32;
+    p.kmat = (const A*)lv.S32;
     p.dinv = (const A*)lv.dinv32;
   }
   p.u = (const TS*)va.u;
@@ -1086,7 +1119,7 @@ void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u
 }
 
 void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out) {
-  k_reduce<<<1, 1024, 0, h->stream>>>(part, nblk, K, out);
+  k_reduce<<<K, 256, 0, h->stream>>>(part, nblk, K, out);
   GMT_LAUNCH_CHECK();
 }
 

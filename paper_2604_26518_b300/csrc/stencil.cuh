@@ -20,6 +20,8 @@ struct VecArgs {
   double omega = 0, c1 = 0, c2 = 0;
 };
 
+// per-node assembled stencils of a coarse level (FP32 or FP64 copy; built once)
+void build_node_stencils(gmt_hierarchy* h, int level, bool fp64);
 // y/r/u' on one level (bricked levels only)
 void launch_stencil(gmt_hierarchy* h, int level, Prec prec, StencilMode mode, const VecArgs& a);
 // first smoothing step from a zero guess: out = scale * D^-1 f (and dout = out if non-null)
