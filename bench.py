@@ -190,6 +190,8 @@ def run_gmt(args, rank: int, world: int):
         if world > 1:
             dist.barrier()
 
+    cycles_seen = []
+
     def one_step(src, trace):
         tot = {}
         CH = []
@@ -202,6 +204,7 @@ def run_gmt(args, rank: int, world: int):
             if st != gmt.OK:
                 raise RuntimeError(f"solve status {st}: {info.as_dict()}")
             CH.append(h.homogenize(ph, E=1.0, nu=0.3, k=1.0))
+            cycles_seen.append(info.inner_total)
             if trace:
                 for k, (n, ms, b) in h.trace_totals().items():
                     a = tot.setdefault(k, [0, 0.0, 0.0])
@@ -292,6 +295,7 @@ def run_gmt(args, rank: int, world: int):
                      "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
         "phases_ms_per_step": {k: v[1] / args.steps for k, v in sorted(totals.items())},
         "traced_device_ms_per_step": total_dev_ms / args.steps,
+        "vcycles_per_cell": cycles_seen[-len(cells):],
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu:

@@ -355,7 +355,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     }
   }
   const Prec ar = w->arith;
-  int cycles = 0, updates = 0;
+  int cycles = 0, updates = 0, restarts = 0;
   gmt_status st = GMT_NOT_CONVERGED;
   double mx = true_residual();
   const double first = mx;
@@ -407,6 +407,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         if (r <= 0.5 * tol || (mixed && r <= o.inner_tol * ref[m])) replace = true;
       }
       const bool last = cycles >= max_cycles;
+      bool restart = false;
       if (replace || nan || last) {
         // fold the correction into the solution and take the true residual
         if (mixed) vec_ff_add(h, (const float*)w->x, w->hi, w->lo);
@@ -423,6 +424,10 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
           break;
         }
         if (last) break;
+        // stagnation guard: a replacement that gained less than 2x means the FP32
+        // recurrence drifted from the true residual; restart it from the true residual
+        for (int m = 0; m < M; ++m)
+          if (act[m] && rel[m] > 0.5 * ref[m]) restart = true;
         for (int m = 0; m < M; ++m) ref[m] = rel[m];
         deactivate_converged();
         push_active();
@@ -432,7 +437,12 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       if (krylov) {
         vec_dot(h, 0, ar, w->rr, z, w->part);
         launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
-        vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
+        if (restart) {
+          vec_copy(h, 0, ar, z, w->p);
+          ++restarts;
+        } else {
+          vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
+        }
         GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice,
                                  h->stream));
       }

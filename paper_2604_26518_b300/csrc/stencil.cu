@@ -25,6 +25,7 @@ template <typename A, int D, int M>
 struct FineC {
   A Ke[64 * D * D];  // (8D) x (8D)
   A Fe[8 * D * M];   // K_e x0, (8D) x M
+  A Sf[27 * D * D];  // S_n(d) of a node whose 8 incident elements are all active
 };
 
 template <typename TS, typename A, int D, int M>
@@ -108,18 +109,56 @@ __device__ __forceinline__ void fine_diag_inv(const FineC<A, D, M>& fc, unsigned
 }
 
 // ------------------------------------------------------------------ tile staging
-// Stage the brick (own node of every thread, coalesced, kept in registers) plus its
-// one-node halo (152 of the 216 tile positions, gathered from the 26 neighbour bricks) in
-// shared memory. Index arithmetic is done once per tile position, not per value.
+// Thread t of a 64-thread block owns brick node (lx, ly, lz) = (t & 3, t >> 4, (t >> 2) & 3):
+// the 8 lanes of a quarter-warp then cover (lx, lz) in 4 x 2, whose 16-byte tile entries
+// fall in distinct shared-memory banks.
+__device__ __forceinline__ int own_local(int t) { return (t & 3) + 4 * (t >> 4) + 16 * ((t >> 2) & 3); }
+__device__ __forceinline__ int own_q0(int t) {
+  return ((t & 3) + 1) + 6 * ((t >> 4) + 1) + 36 * (((t >> 2) & 3) + 1);
+}
+
+// 16-byte shared-memory vector of the arithmetic type
+template <typename A> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename A>
+__device__ __forceinline__ void vec_put(typename Vec16<A>::type& w, int k, A x) {
+  if constexpr (Vec16<A>::n == 4) {
+    if (k == 0) w.x = x; else if (k == 1) w.y = x; else if (k == 2) w.z = x; else w.w = x;
+  } else {
+    if (k == 0) w.x = x; else w.y = x;
+  }
+}
+template <typename A>
+__device__ __forceinline__ A vec_get(const typename Vec16<A>::type& w, int k) {
+  if constexpr (Vec16<A>::n == 4) {
+    return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+  } else {
+    return k == 0 ? w.x : w.y;
+  }
+}
+
+// Stage the brick (own node of every thread, kept in registers) plus its one-node halo
+// (152 of the 216 tile positions, gathered from the 26 neighbour bricks) in shared memory
+// as tile[g][q] = 16-byte groups of values; index arithmetic once per tile position.
 template <typename TS, typename A, int C>
 __device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, int t,
-                                           const int* nb, A* tile, A (&self)[C]) {
-  const int q0 = ((t & 3) + 1) + 6 * (((t >> 2) & 3) + 1) + 36 * ((t >> 4) + 1);
-  const TS* own = u + b * (64 * C) + t;
+                                           const int* nb, typename Vec16<A>::type* tile,
+                                           A (&self)[C]) {
+  using V = typename Vec16<A>::type;
+  constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  const int q0 = own_q0(t);
+  const TS* own = u + b * (64 * C) + own_local(t);
 #pragma unroll
   for (int v = 0; v < C; ++v) self[v] = load_as<A>(own + v * 64);
 #pragma unroll
-  for (int v = 0; v < C; ++v) tile[v * 216 + q0] = self[v];
+  for (int g = 0; g < G; ++g) {
+    V w;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vec_put<A>(w, k, g * NV + k < C ? self[g * NV + k] : A(0));
+    tile[g * 216 + q0] = w;
+  }
   for (int q = t; q < 216; q += 64) {
     const int tx = q % 6, ty = (q / 6) % 6, tz = q / 36;
     if (tx >= 1 && tx <= 4 && ty >= 1 && ty <= 4 && tz >= 1 && tz <= 4) continue;
@@ -127,30 +166,42 @@ __device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, 
     const int by = ty == 0 ? 0 : (ty == 5 ? 2 : 1);
     const int bz = tz == 0 ? 0 : (tz == 5 ? 2 : 1);
     const int nbi = nb[bz * 9 + by * 3 + bx];
+    A vals[C];
     if (nbi >= 0) {
       const TS* src = u + (int64_t)nbi * (64 * C) + ((tx + 3) & 3) + 4 * ((ty + 3) & 3) +
                       16 * ((tz + 3) & 3);
-      A vals[C];
 #pragma unroll
       for (int v = 0; v < C; ++v) vals[v] = load_as<A>(src + v * 64);
-#pragma unroll
-      for (int v = 0; v < C; ++v) tile[v * 216 + q] = vals[v];
     } else {
 #pragma unroll
-      for (int v = 0; v < C; ++v) tile[v * 216 + q] = A(0);
+      for (int v = 0; v < C; ++v) vals[v] = A(0);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      V w;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) vec_put<A>(w, k, g * NV + k < C ? vals[g * NV + k] : A(0));
+      tile[g * 216 + q] = w;
     }
   }
 }
 
 // ------------------------------------------------------------------ the stencil kernel
-// KIND 0: level 0, S_n(d) formed from the octant mask and K_e (parameter bank).
+// KIND 0: level 0, S_n(d) formed from the octant mask and K_e (parameter bank); warps whose
+//         32 nodes all have full masks use the precomputed full stencil instead.
 // KIND 1: coarse levels, S_n(d) read from the per-node assembled stencil, stored
 //         brick-major as [brick][27 * D * D][64] so each coefficient load is coalesced.
+// ST_APPLY uses the difference form sum_{d != 0} S_n(d) (u_{n+d} - u_n) (rows of K sum to
+// zero): the differences of a smooth field are small, which keeps FP32 products of the
+// Krylov search directions accurate.
 template <typename TS, typename A, int D, int M, int KIND, int MODE>
 __global__ void __launch_bounds__(64)
     k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
+  using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, DD = D * D;
-  __shared__ A tile[C * 216];
+  constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  constexpr bool DIFF = MODE == ST_APPLY;
+  __shared__ V tile[G * 216];
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
@@ -159,53 +210,93 @@ __global__ void __launch_bounds__(64)
   A self[C];
   stage_tile<TS, A, C>(p.u, b, t, nb, tile, self);
   __syncthreads();
-  const int q0 = ((t & 3) + 1) + 6 * (((t >> 2) & 3) + 1) + 36 * ((t >> 4) + 1);
-  const int64_t slot = b * 64 + t;
+  const int q0 = own_q0(t);
+  const int loc = own_local(t);
+  const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
   A acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = A(0);
+  // neighbour d's contribution with the D x D block S
+  auto contribute = [&](int d, const A (&S)[DD]) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const int q = q0 + dx + 6 * dy + 36 * dz;
+    A uv[G * NV];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const V w = tile[g * 216 + q];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) uv[g * NV + k] = vec_get<A>(w, k);
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        A x = uv[j * M + m];
+        if constexpr (DIFF) x -= self[j * M + m];
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * x;
+      }
+    }
+  };
   if (mk) {
-    A bf[8];
+    if constexpr (KIND == 0) {
+      if (__all_sync(0xffffffffu, mk == 0xffu)) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) bf[a] = ((mk >> a) & 1u) ? A(1) : A(0);
-    const A* sten = p.kmat + b * (64 * 27 * DD) + t;
+        for (int d = 0; d < 27; ++d) {
+          if (DIFF && d == 13) continue;
+          A S[DD];
 #pragma unroll
-    for (int d = 0; d < 27; ++d) {
-      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      A S[DD];
-      if constexpr (KIND == 0) {
-#pragma unroll
-        for (int k = 0; k < DD; ++k) S[k] = A(0);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-          const int ex = ax + dx, ey = ay + dy, ez = az + dz;
-          if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
-          const int bb = ex + 2 * ey + 4 * ez;
-#pragma unroll
-          for (int i = 0; i < D; ++i)
+          for (int k = 0; k < DD; ++k) S[k] = p.fc.Sf[d * DD + k];
+          if (d == 13) {  // own node: no shared-memory round trip
 #pragma unroll
             for (int j = 0; j < D; ++j)
-              S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+#pragma unroll
+              for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * self[j * M + m];
+          } else {
+            contribute(d, S);
+          }
         }
       } else {
+        A bf[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) bf[a] = ((mk >> a) & 1u) ? A(1) : A(0);
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+          if (DIFF && d == 13) continue;
+          const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+          A S[DD];
+#pragma unroll
+          for (int k = 0; k < DD; ++k) S[k] = A(0);
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            const int ex = (a & 1) + dx, ey = ((a >> 1) & 1) + dy, ez = (a >> 2) + dz;
+            if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+            const int bb = ex + 2 * ey + 4 * ez;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+              for (int j = 0; j < D; ++j)
+                S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+          }
+          contribute(d, S);
+        }
+      }
+    } else {
+      const A* sten = p.kmat + b * (64 * 27 * DD) + loc;
+#pragma unroll
+      for (int d = 0; d < 27; ++d) {
+        if (DIFF && d == 13) continue;
+        A S[DD];
 #pragma unroll
         for (int k = 0; k < DD; ++k) S[k] = sten[(d * DD + k) * 64];
-      }
-      const int q = q0 + dx + 6 * dy + 36 * dz;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const A uv = (d == 13) ? self[j * M + m] : tile[(j * M + m) * 216 + q];
-#pragma unroll
-          for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * uv;
-        }
+        contribute(d, S);
       }
     }
   }
-  const int64_t base = b * (64 * C) + t;
+  const int64_t base = b * (64 * C) + loc;
   if constexpr (MODE == ST_APPLY) {
     double dots[M];
 #pragma unroll
@@ -383,9 +474,10 @@ struct FFArgs {
 // the residual accurate to ~1e-7 of the load without FP64 instructions.
 template <int D, int M>
 __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<D, M> p) {
-  constexpr int C = D * M, R = 8 * D;
-  __shared__ float th[C * 216];
-  __shared__ float tl[C * 216];
+  using V = float4;
+  constexpr int C = D * M, R = 8 * D, G = (C + 3) / 4;
+  __shared__ V th[G * 216];
+  __shared__ V tl[G * 216];
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
@@ -395,9 +487,8 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   stage_tile<float, float, C>(p.hi, b, t, nb, th, sh);
   stage_tile<float, float, C>(p.lo, b, t, nb, tl, sl);
   __syncthreads();
-  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
-  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
-  const int64_t slot = b * 64 + t;
+  const int q0 = own_q0(t), loc = own_local(t);
+  const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
   float acc[C];
 #pragma unroll
@@ -415,8 +506,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
       for (int k = 0; k < D * D; ++k) S[k] = 0.f;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+        const int ex = (a & 1) + dx, ey = ((a >> 1) & 1) + dy, ez = (a >> 2) + dz;
         if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
         const int bb = ex + 2 * ey + 4 * ez;
 #pragma unroll
@@ -426,12 +516,19 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
             S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
       }
       const int q = q0 + dx + 6 * dy + 36 * dz;
+      float uh[G * 4], ul[G * 4];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const V wh = th[g * 216 + q], wl = tl[g * 216 + q];
+        uh[4 * g] = wh.x; uh[4 * g + 1] = wh.y; uh[4 * g + 2] = wh.z; uh[4 * g + 3] = wh.w;
+        ul[4 * g] = wl.x; ul[4 * g + 1] = wl.y; ul[4 * g + 2] = wl.z; ul[4 * g + 3] = wl.w;
+      }
 #pragma unroll
       for (int j = 0; j < D; ++j) {
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           const int v = j * M + m;
-          const float du = (th[v * 216 + q] - sh[v]) + (tl[v * 216 + q] - sl[v]);
+          const float du = (uh[v] - sh[v]) + (ul[v] - sl[v]);
 #pragma unroll
           for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * du;
         }
@@ -441,7 +538,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   double nrm[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) nrm[m] = 0.0;
-  const int64_t base = b * (64 * C) + t;
+  const int64_t base = b * (64 * C) + loc;
 #pragma unroll
   for (int v = 0; v < C; ++v) {
     const int i = v / M, m = v % M;
@@ -607,9 +704,11 @@ struct EnArgs {
 // FP64 on the host side (n_e C0).
 template <typename A, int D, int M, bool FF>
 __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
+  using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
-  __shared__ A th[C * 216];
-  __shared__ A tl[FF ? C * 216 : 1];
+  constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  __shared__ V th[G * 216];
+  __shared__ V tl[FF ? G * 216 : 1];
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
@@ -621,19 +720,21 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
     if constexpr (FF) stage_tile<float, A, C>(p.lo, b, t, nb, tl, own);
   }
   __syncthreads();
-  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
-  const int q0 = (lx + 1) + 6 * (ly + 1) + 36 * (lz + 1);
-  const unsigned mk = p.mask[b * 64 + t];
+  const int q0 = own_q0(t), loc = own_local(t);
+  const unsigned mk = p.mask[b * 64 + loc];
   double e[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) e[k] = 0.0;
   if (mk & 1u) {  // element with origin at this node is active
+    auto tv = [&](const V* tile, int v, int q) -> A {
+      return vec_get<A>(tile[(v / NV) * 216 + q], v % NV);
+    };
     auto dval = [&](int r, int I) -> A {  // d^I at element dof r = (node bb, component i)
       const int bb = r / D, i = r % D;
       const int q = q0 + (bb & 1) + 6 * ((bb >> 1) & 1) + 36 * (bb >> 2);
       const int v = i * M + I;
-      A du = th[v * 216 + q] - th[v * 216 + q0];
-      if constexpr (FF) du += tl[v * 216 + q] - tl[v * 216 + q0];
+      A du = tv(th, v, q) - tv(th, v, q0);
+      if constexpr (FF) du += tv(tl, v, q) - tv(tl, v, q0);
       return du;
     };
 #pragma unroll 1
@@ -644,42 +745,42 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
         for (int r = 0; r < R; ++r) w[r] = dval(r, J);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          A sh = A(0), sl = A(0);
+          A shi = A(0), slo = A(0);
 #pragma unroll
           for (int c = 0; c < R; ++c) {
-            sh += p.Ke[r * R + c] * w[c];
-            sl += p.Kl[r * R + c] * w[c];
+            shi += p.Ke[r * R + c] * w[c];
+            slo += p.Kl[r * R + c] * w[c];
           }
-          z[r] = sh + sl;
+          z[r] = shi + slo;
         }
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) w[r] = p.X0[r * M + J] - dval(r, J);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          A s = A(0);
+          A sacc = A(0);
 #pragma unroll
-          for (int c = 0; c < R; ++c) s += p.Ke[r * R + c] * w[c];
-          z[r] = s;
+          for (int c = 0; c < R; ++c) sacc += p.Ke[r * R + c] * w[c];
+          z[r] = sacc;
         }
       }
 #pragma unroll 1
       for (int I = 0; I <= J; ++I) {
-        A s = A(0);
+        A sacc = A(0);
         if constexpr (FF) {
           A fd = A(0), df = A(0);   // f^I . d^J and d^I . f^J
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const A dI = dval(r, I);
-            s += dI * z[r];
+            sacc += dI * z[r];
             fd += (p.Fh[r * M + I] + p.Fl[r * M + I]) * w[r];
             df += dI * (p.Fh[r * M + J] + p.Fl[r * M + J]);
           }
-          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s - (double)fd - (double)df;
+          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)sacc - (double)fd - (double)df;
         } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) s += (p.X0[r * M + I] - dval(r, I)) * z[r];
-          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)s;
+          for (int r = 0; r < R; ++r) sacc += (p.X0[r * M + I] - dval(r, I)) * z[r];
+          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)sacc;
         }
       }
     }
@@ -920,6 +1021,20 @@ template <typename A, int D, int M>
 static void fill_fine(const Material& mt, FineC<A, D, M>& fc) {
   for (int i = 0; i < 64 * D * D; ++i) fc.Ke[i] = (A)mt.Ke[i];
   for (int i = 0; i < 8 * D * M; ++i) fc.Fe[i] = (A)mt.Fe[i];
+  const int R = 8 * D;
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    for (int k = 0; k < D * D; ++k) {
+      double acc = 0.0;
+      for (int a = 0; a < 8; ++a) {
+        const int ex = (a & 1) + dx, ey = ((a >> 1) & 1) + dy, ez = (a >> 2) + dz;
+        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+        const int bb = ex + 2 * ey + 4 * ez;
+        acc += mt.Ke[(a * D + k / D) * R + bb * D + k % D];
+      }
+      fc.Sf[d * D * D + k] = (A)acc;
+    }
+  }
 }
 
 template <typename TS, typename A, int D, int M>
