@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(64)
   const int loc = own_local(t);
   const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
+  // warp vote taken by every lane (before any divergence): all 32 nodes have full masks
+  const bool warp_full = __all_sync(0xffffffffu, mk == 0xffu);
   A acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = A(0);
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(64)
   };
   if (mk) {
     if constexpr (KIND == 0) {
-      if (__all_sync(0xffffffffu, mk == 0xffu)) {
+      if (warp_full) {
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
           if (DIFF && d == 13) continue;
