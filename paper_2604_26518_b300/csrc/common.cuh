@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gmt.h"
+#include "gmt.h"
 
 namespace gmt {
 

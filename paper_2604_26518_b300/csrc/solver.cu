@@ -9,6 +9,8 @@
 // and case is removed from the final field. Load cases whose assembled load cancels
 // (||f_m|| <= 1e-12 of its gross element-load norm) have u_m = 0 and r_m = 0.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 
@@ -356,6 +358,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   }
   const Prec ar = w->arith;
   int cycles = 0, updates = 0, restarts = 0;
+  static const bool verbose = std::getenv("GMT_VERBOSE") != nullptr;
   gmt_status st = GMT_NOT_CONVERGED;
   double mx = true_residual();
   const double first = mx;
@@ -399,6 +402,11 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       }
       double rn[8];
       fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+      if (verbose) {
+        std::fprintf(stderr, "gmt: cycle %d iterated r/|f|:", cycles);
+        for (int m = 0; m < M; ++m) std::fprintf(stderr, " %.3e", std::sqrt(rn[m]) / fn[m]);
+        std::fprintf(stderr, "\n");
+      }
       bool replace = false, nan = false;
       for (int m = 0; m < M; ++m) {
         if (!act[m]) continue;
@@ -415,6 +423,11 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         vec_zero(h, 0, ar, w->x);
         mx = true_residual();
         ++updates;
+        if (verbose) {
+          std::fprintf(stderr, "gmt: update %d true r/|f|:", updates);
+          for (int m = 0; m < M; ++m) std::fprintf(stderr, " %.3e", rel[m]);
+          std::fprintf(stderr, "\n");
+        }
         if (mx <= tol) {
           st = GMT_OK;
           break;
@@ -424,10 +437,10 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
           break;
         }
         if (last) break;
-        // stagnation guard: a replacement that gained less than 2x means the FP32
-        // recurrence drifted from the true residual; restart it from the true residual
-        for (int m = 0; m < M; ++m)
-          if (act[m] && rel[m] > 0.5 * ref[m]) restart = true;
+        // the Krylov recurrence restarts from every true residual: each FP32 CG run then
+        // only has to gain the factor inner_tol, well inside FP32 accuracy even for thin,
+        // badly conditioned cells
+        restart = true;
         for (int m = 0; m < M; ++m) ref[m] = rel[m];
         deactivate_converged();
         push_active();
