@@ -193,6 +193,28 @@ gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, doubl
    FP64: native FP64). */
 gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double* out);
 
+/* ---- allocation-free homogenization --------------------------------------------------
+   The paper has no counterpart to this call. It serves callers that cannot allocate device
+   memory (an application whose memory manager owns the device and forbids side
+   allocations, a fixed-budget embedded or sandboxed process, a latency-bound loop that
+   cannot pay for an allocation's implicit device synchronisation). It computes the same
+   energy average as gmt_homogenize (App. F), in FP64, for a nodal field the caller
+   already holds, without a hierarchy and without any allocation: the working memory is a
+   352 KB array inside the library that each GPU using the library keeps until the process
+   exits.
+   voxels: device uint8[N^3] (x fastest). u_dense: device double[N^3][D][M], the field at
+   every node site x + N*y + N^2*z (values at sites without an active element are
+   ignored). CH: device double[M][M] written row-major. res: N, at most 512 (larger values
+   are rejected with GMT_ERR_ARG). stream: cudaStream_t (nullable); the call is
+   asynchronous on it and does not synchronise.
+   The first call on a device looks up the array's device address (once per device, with
+   that device current); make that first call before any stream capture. All calls share
+   the array: calls that overlap on the GPU (other streams or host threads) race with each
+   other and must be serialised by the caller. */
+gmt_status gmt_homogenize_dense_noalloc(const uint8_t* voxels, int res, gmt_physics physics,
+                                        double E, double nu, double k, const double* u_dense,
+                                        double* CH, void* stream);
+
 /* ---- tracing (measurement support; not part of the method) -----------------------------
    When enabled, the library records a CUDA event pair on its stream around every launch of
    the kernels below and accumulates, per category, the launch count, the summed device time

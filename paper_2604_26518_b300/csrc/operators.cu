@@ -124,6 +124,14 @@ __global__ void k_element(int physics, double E, double nu, double kappa, double
   }
 }
 
+// launch wrapper for other translation units: element data of one material into `out`
+// (layout as k_element)
+void launch_element_matrices(cudaStream_t s, int physics, double E, double nu, double kappa,
+                             double* out) {
+  k_element<<<1, 576, 0, s>>>(physics, E, nu, kappa, out);
+  GMT_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------ Galerkin
 // weight of coarse-local vertex b at child c's local vertex a (App. E.1 trilinear weights)
 __device__ __forceinline__ double wchild(int c, int a, int b) {

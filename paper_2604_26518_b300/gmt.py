@@ -104,6 +104,7 @@ _SIGS = {
     "gmt_trace_query": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gmt_trace_name": (ctypes.c_char_p, [_I]),
     "gmt_launch_count": (_L, []),
+    "gmt_homogenize_dense_noalloc": (_I, [_P, _I, _I, _D, _D, _D, _P, _P, _P]),
 }
 
 TRACE_CATEGORIES = 12
@@ -349,6 +350,23 @@ class Hierarchy:
         _check(lib().gmt_residual(self._h, precision, _ptr(u), out.ctypes.data_as(ctypes.c_void_p)),
                "gmt_residual")
         return out
+
+
+def homogenize_dense_noalloc(voxels, res: int, physics=ELASTIC, E=1.0, nu=0.3, k=1.0,
+                             u_dense=None, out=None, stream=None):
+    """C^H of a nodal field on the dense periodic node grid without any device allocation
+    in the library (gmt_homogenize_dense_noalloc). voxels: CUDA uint8 tensor (N,N,N);
+    u_dense: CUDA float64 tensor with N^3 * D * M values (node site major); out: CUDA
+    float64 (M, M) tensor, created if omitted (by torch, outside the library)."""
+    torch = _torch()
+    M = 6 if physics == ELASTIC else 3
+    if out is None:
+        out = torch.empty((M, M), dtype=torch.float64, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().gmt_homogenize_dense_noalloc(_ptr(voxels), res, physics, E, nu, k, _ptr(u_dense),
+                                            _ptr(out), s.cuda_stream)
+    _check(st, "gmt_homogenize_dense_noalloc")
+    return out
 
 
 def declared_symbols(header: str | None = None):
