@@ -233,6 +233,15 @@ const char* gmt_trace_name(int category);
 /* Kernels launched by this process through the library so far (all hierarchies). */
 int64_t gmt_launch_count(void);
 
+/* ---- device memory pool -----------------------------------------------------------------
+   Device memory of hierarchies, operators and solver buffers comes from a process-wide
+   caching pool: gmt_free_hierarchy returns it to the pool instead of the driver, so that
+   the next cell reuses it without cudaMalloc / cudaFree. gmt_release_cached_memory hands
+   every cached (unused) block back to the driver; a failed allocation does so first and
+   retries. gmt_cached_bytes reports the bytes held unused by the pool. Thread-safe. */
+void gmt_release_cached_memory(void);
+int64_t gmt_cached_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -414,4 +414,8 @@ const char* gmt_trace_name(int c) {
 
 int64_t gmt_launch_count(void) { return gmt::launch_count(); }
 
+void gmt_release_cached_memory(void) { gmt::pool_trim(); }
+
+int64_t gmt_cached_bytes(void) { return (int64_t)gmt::pool_cached_bytes(); }
+
 }  // extern "C"

@@ -109,6 +109,12 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, flo
 // ------------------------------------------------------------------ device arena
 // Every device allocation of a hierarchy goes through one Arena, which owns it until the
 // hierarchy is freed (or the material-dependent part is rebuilt).
+// process-wide caching device allocator (hierarchy.cu)
+void* pool_alloc(size_t n);
+void pool_free(void* p);
+void pool_trim();
+size_t pool_cached_bytes();
+
 struct Arena {
   std::vector<void*> ptrs;
   size_t bytes = 0;

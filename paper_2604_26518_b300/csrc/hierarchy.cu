@@ -9,6 +9,9 @@
 // Everything is computed by kernels on dense N_l^3 flag grids, then compacted into 4^3
 // bricks with exclusive scans. Counts are read back once per level to size allocations.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <unordered_map>
 #include <cstdarg>
 #include <cstring>
 
@@ -27,22 +30,106 @@ void set_error(const char* fmt, ...) {
 }
 const char* last_error() { return g_err; }
 
-void* Arena::raw(size_t n) {
-  void* p = nullptr;
-  size_t sz = n ? ((n + 255) & ~(size_t)255) : 256;
-  cudaError_t e = cudaMalloc(&p, sz);
+// ------------------------------------------------------------------ caching allocator
+// Process-wide pool of device blocks keyed by (device, size bucket). cudaMalloc and
+// cudaFree synchronise the device and cost tens to hundreds of microseconds each; a solve
+// per cell would otherwise pay dozens of them. Buckets: powers of two up to 1 MB, then
+// multiples of 1 MB. Released blocks return to the pool; gmt_release_cached_memory() (or
+// a failed cudaMalloc) hands the cached blocks back to the driver.
+namespace {
+struct Pool {
+  std::mutex mu;
+  std::map<std::pair<int, size_t>, std::vector<void*>> free_blocks;
+  std::unordered_map<void*, std::pair<int, size_t>> owner;
+  size_t cached = 0;
+};
+Pool& pool() {
+  static Pool* p = new Pool();   // never destroyed: blocks may outlive static destructors
+  return *p;
+}
+size_t bucket(size_t n) {
+  if (n <= 256) return 256;
+  if (n <= (1u << 20)) {
+    size_t b = 256;
+    while (b < n) b <<= 1;
+    return b;
+  }
+  return (n + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+}
+void trim_locked(Pool& P) {
+  for (auto& kv : P.free_blocks)
+    for (void* q : kv.second) {
+      cudaFree(q);
+      P.owner.erase(q);
+    }
+  P.free_blocks.clear();
+  P.cached = 0;
+}
+}  // namespace
+
+void* pool_alloc(size_t n) {
+  int dev = 0;
+  GMT_CUDA(cudaGetDevice(&dev));
+  const size_t sz = bucket(n);
+  Pool& P = pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  auto it = P.free_blocks.find({dev, sz});
+  if (it != P.free_blocks.end() && !it->second.empty()) {
+    void* q = it->second.back();
+    it->second.pop_back();
+    P.cached -= sz;
+    return q;
+  }
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sz);
+  if (e != cudaSuccess) {  // give the cache back to the driver and retry once
+    cudaGetLastError();
+    trim_locked(P);
+    e = cudaMalloc(&q, sz);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc(%zu bytes) failed: %s", sz, cudaGetErrorString(e));
     throw Fail{GMT_ERR_OOM};
   }
+  P.owner[q] = {dev, sz};
+  return q;
+}
+
+void pool_free(void* q) {
+  if (!q) return;
+  Pool& P = pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  auto it = P.owner.find(q);
+  if (it == P.owner.end()) return;
+  P.free_blocks[it->second].push_back(q);
+  P.cached += it->second.second;
+}
+
+void pool_trim() {
+  Pool& P = pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  trim_locked(P);
+}
+
+size_t pool_cached_bytes() {
+  Pool& P = pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  return P.cached;
+}
+
+void* Arena::raw(size_t n) {
+  void* p = pool_alloc(n);
   ptrs.push_back(p);
-  bytes += sz;
+  bytes += bucket(n);
   return p;
 }
 
 void Arena::release() {
-  for (void* p : ptrs) cudaFree(p);
+  // like cudaFree, wait for device work that may still use the blocks (any stream) before
+  // they can be handed to another allocation
+  if (!ptrs.empty()) cudaDeviceSynchronize();
+  for (void* p : ptrs) pool_free(p);
   ptrs.clear();
   bytes = 0;
 }

@@ -105,9 +105,20 @@ _SIGS = {
     "gmt_trace_name": (ctypes.c_char_p, [_I]),
     "gmt_launch_count": (_L, []),
     "gmt_homogenize_dense_noalloc": (_I, [_P, _I, _I, _D, _D, _D, _P, _P, _P]),
+    "gmt_release_cached_memory": (None, []),
+    "gmt_cached_bytes": (_L, []),
 }
 
 TRACE_CATEGORIES = 12
+
+
+def release_cached_memory():
+    """Return the library's cached, unused device blocks to the driver."""
+    lib().gmt_release_cached_memory()
+
+
+def cached_bytes() -> int:
+    return int(lib().gmt_cached_bytes())
 
 
 def launch_count() -> int:
