@@ -217,11 +217,16 @@ struct gmt_hierarchy {
   bool prepared = false;
   double* Ke64 = nullptr;  // device copies of the level-0 element matrix
   float* Ke32 = nullptr;
-  // coarsest dense generalized inverse (FP64), m = n_nodes(L-1) * D
+  // coarsest level, m = n_nodes(L-1) * D: regularized dense matrix (FP64), its FP32
+  // generalized inverse, and the exact FP64 inverse (built on first FP64 use)
   int64_t m = 0;
+  double* A64 = nullptr;
+  float* X32 = nullptr;
   double* Ainv = nullptr;
+  double ctol = 0.0;
   double* cb = nullptr;   // m x M gather buffer
   double* cu = nullptr;   // m x M result buffer
+  double* cr = nullptr;   // m x M refinement residual
   gmt::Workspace* ws = nullptr;
   gmt::Tracer tracer;
   bool have_solution = false;
@@ -234,6 +239,7 @@ void build_hierarchy(gmt_hierarchy* h, const uint8_t* vox, bool on_device);
 int choose_levels(int n, int coarsest_max);
 // operators.cu
 void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double k);
+void build_coarse_inverse64(gmt_hierarchy* h);
 // solver.cu
 void free_workspace(gmt_hierarchy* h);
 }  // namespace gmt

@@ -6,9 +6,11 @@
 //     P_c^T K_child P_c with the trilinear weights of App. E.1). Level 1 depends only on the
 //     8-bit child mask, so it is a 256-entry table; levels >= 2 are stored per element;
 //   * D x D block-diagonal inverses of the coarse operators (smoother, Sec. 4.6);
-//   * the coarsest level's dense generalized inverse of K_L + rho J (J couples equal
-//     components of all nodes, rho = mean diagonal), by blocked in-place Gauss-Jordan with
-//     semidefinite pivot dropping. For right-hand sides orthogonal to translations this
+//   * the coarsest level's dense matrix K_L + rho J (J couples equal components of all
+//     nodes, rho = mean diagonal) kept in FP64, and its generalized inverse by blocked
+//     in-place Gauss-Jordan with semidefinite pivot dropping: in FP32 for the
+//     mixed-precision solves (each use is refined once against the FP64 matrix), and in
+//     FP64 (built on first use) for the all-FP64 path. For right-hand sides orthogonal to translations this
 //     returns the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS
 //     is replaced by this exact solve.
 #include <algorithm>
@@ -360,11 +362,12 @@ __global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, double rho) 
 constexpr int GJB = 32;
 
 // one block: invert the bb x bb diagonal panel block (pivots <= tol are dropped)
-__global__ void __launch_bounds__(1024) k_gj_panel(const double* __restrict__ A, int64_t m,
-                                                   int64_t k0, int bb, double tol,
-                                                   double* __restrict__ inv) {
-  __shared__ double P[GJB][GJB + 1];
-  __shared__ double rowk[GJB], colk[GJB];
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_panel(const T* __restrict__ A, int64_t m,
+                                                   int64_t k0, int bb, T tol,
+                                                   T* __restrict__ inv) {
+  __shared__ T P[GJB][GJB + 1];
+  __shared__ T rowk[GJB], colk[GJB];
   __shared__ int ok;
   const int t = threadIdx.x, i = t / GJB, j = t % GJB;
   if (i < bb && j < bb) P[i][j] = A[(k0 + i) * m + k0 + j];
@@ -378,10 +381,10 @@ __global__ void __launch_bounds__(1024) k_gj_panel(const double* __restrict__ A,
     __syncthreads();
     if (i < bb && j < bb) {
       if (!ok) {
-        if (i == k || j == k) P[i][j] = 0.0;
+        if (i == k || j == k) P[i][j] = T(0);
       } else {
-        const double p = rowk[k];
-        if (i == k) P[i][j] = (j == k) ? 1.0 / p : rowk[j] / p;
+        const T p = rowk[k];
+        if (i == k) P[i][j] = (j == k) ? T(1) / p : rowk[j] / p;
         else if (j == k) P[i][j] = -colk[i] / p;
         else P[i][j] -= colk[i] * rowk[j] / p;
       }
@@ -392,35 +395,36 @@ __global__ void __launch_bounds__(1024) k_gj_panel(const double* __restrict__ A,
 }
 
 // T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns)
-__global__ void k_gj_rows(const double* __restrict__ A, int64_t m, int64_t k0, int bb,
-                          const double* __restrict__ inv, double* __restrict__ T,
-                          double* __restrict__ O) {
+template <typename T>
+__global__ void k_gj_rows(const T* __restrict__ A, int64_t m, int64_t k0, int bb,
+                          const T* __restrict__ inv, T* __restrict__ Tp, T* __restrict__ O) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  double col[GJB];
+  T col[GJB];
   for (int r = 0; r < bb; ++r) col[r] = A[(k0 + r) * m + j];
   for (int c = 0; c < bb; ++c) {
-    double s = 0.0;
-    for (int r = 0; r < bb; ++r) s += inv[c * GJB + r] * col[r];
-    T[c * m + j] = s;
+    T acc = T(0);
+    for (int r = 0; r < bb; ++r) acc += inv[c * GJB + r] * col[r];
+    Tp[c * m + j] = acc;
   }
   for (int c = 0; c < bb; ++c) O[j * GJB + c] = A[j * m + k0 + c];
 }
 
 // the rank-bb update of everything, tiled 32 x 32 per block
-__global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ A, int64_t m, int64_t k0,
-                                                   int bb, const double* __restrict__ inv,
-                                                   const double* __restrict__ T,
-                                                   const double* __restrict__ O) {
-  __shared__ double sO[32][GJB + 1];   // O rows of this tile: O[i][r]
-  __shared__ double sT[GJB][32 + 1];   // T columns of this tile: T[r][j]
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update(T* __restrict__ A, int64_t m, int64_t k0,
+                                                   int bb, const T* __restrict__ inv,
+                                                   const T* __restrict__ Tp,
+                                                   const T* __restrict__ O) {
+  __shared__ T sO[32][GJB + 1];   // O rows of this tile: O[i][r]
+  __shared__ T sT[GJB][32 + 1];   // T columns of this tile: T[r][j]
   const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int q = threadIdx.x; q < 32 * GJB; q += 256) {
     const int a = q / GJB, r = q % GJB;
-    sO[a][r] = (i0 + a < m && r < bb) ? O[(i0 + a) * GJB + r] : 0.0;
+    sO[a][r] = (i0 + a < m && r < bb) ? O[(i0 + a) * GJB + r] : T(0);
     const int rr = q / 32, b = q % 32;
-    sT[rr][b] = (rr < bb && j0 + b < m) ? T[rr * m + j0 + b] : 0.0;
+    sT[rr][b] = (rr < bb && j0 + b < m) ? Tp[rr * m + j0 + b] : T(0);
   }
   __syncthreads();
   const int64_t j = j0 + tx;
@@ -430,23 +434,59 @@ __global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ A, int64
     const int64_t i = i0 + a;
     if (i >= m) break;
     const bool ip = i >= k0 && i < k0 + bb;
-    double v;
+    T v;
     if (ip && jp) {
       v = inv[(i - k0) * GJB + (j - k0)];
     } else if (ip) {
       v = sT[i - k0][tx];
     } else if (jp) {
-      double s = 0.0;
-      for (int r = 0; r < bb; ++r) s += sO[a][r] * inv[r * GJB + (j - k0)];
-      v = -s;
+      T acc = T(0);
+      for (int r = 0; r < bb; ++r) acc += sO[a][r] * inv[r * GJB + (j - k0)];
+      v = -acc;
     } else {
-      double s = 0.0;
+      T acc = T(0);
 #pragma unroll 8
-      for (int r = 0; r < GJB; ++r) s += sO[a][r] * sT[r][tx];
-      v = A[i * m + j] - s;
+      for (int r = 0; r < GJB; ++r) acc += sO[a][r] * sT[r][tx];
+      v = A[i * m + j] - acc;
     }
     A[i * m + j] = v;
   }
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// in-place blocked Gauss-Jordan of an m x m matrix (generalized inverse, pivots <= tol dropped)
+template <typename T>
+static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, T tol, Arena& tmp) {
+  cudaStream_t s = h->stream;
+  T* inv = tmp.alloc<T>(GJB * GJB);
+  T* Tp = tmp.alloc<T>(GJB * m);
+  T* O = tmp.alloc<T>(GJB * m);
+  const dim3 ug((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+  for (int64_t k0 = 0; k0 < m; k0 += GJB) {
+    const int bb = (int)std::min<int64_t>(GJB, m - k0);
+    k_gj_panel<T><<<1, 1024, 0, s>>>(A, m, k0, bb, tol, inv);
+    GMT_LAUNCH_CHECK();
+    k_gj_rows<T><<<grid_for(m, 128), 128, 0, s>>>(A, m, k0, bb, inv, Tp, O);
+    GMT_LAUNCH_CHECK();
+    k_gj_update<T><<<ug, 256, 0, s>>>(A, m, k0, bb, inv, Tp, O);
+    GMT_LAUNCH_CHECK();
+  }
+}
+
+// exact FP64 generalized inverse of the regularized coarsest matrix (FP64 solve path; lazy)
+void build_coarse_inverse64(gmt_hierarchy* h) {
+  if (h->Ainv) return;
+  const int64_t m = h->m;
+  h->Ainv = h->op.alloc<double>(m * m);
+  GMT_CUDA(cudaMemcpyAsync(h->Ainv, h->A64, m * m * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->stream));
+  Arena tmp;
+  gauss_jordan<double>(h, h->Ainv, m, h->ctol, tmp);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
 
 // ------------------------------------------------------------------ host driver
@@ -454,6 +494,9 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   cudaStream_t s = h->stream;
   TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
   h->op.release();
+  h->A64 = nullptr;
+  h->X32 = nullptr;
+  h->Ainv = nullptr;
   for (Level& l : h->lv) {
     l.K64 = l.S64 = l.dinv64 = nullptr;
     l.K32 = l.S32 = l.dinv32 = nullptr;
@@ -535,37 +578,30 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     Level& c = h->lv[lc];
     const int64_t m = c.n_nodes * D;
     h->m = m;
-    h->Ainv = h->op.alloc<double>(m * m);
+    h->A64 = h->op.alloc<double>(m * m);
     h->cb = h->op.alloc<double>(m * M);
     h->cu = h->op.alloc<double>(m * M);
-    GMT_CUDA(cudaMemsetAsync(h->Ainv, 0, m * m * sizeof(double), s));
+    h->cr = h->op.alloc<double>(m * M);
+    GMT_CUDA(cudaMemsetAsync(h->A64, 0, m * m * sizeof(double), s));
     k_coarse_assemble<<<grid_for(c.n_nodes * 27, 128), 128, 0, s>>>(
         D, lc, c.n, c.nbx, c.brick_xyz, c.brick_map, c.dense, c.eflag, c.canon_slot, c.slot_canon,
-        c.kidx, c.K64, h->Ke64, c.n_nodes, m, h->Ainv);
+        c.kidx, c.K64, h->Ke64, c.n_nodes, m, h->A64);
     GMT_LAUNCH_CHECK();
     double* ds = tmp.alloc<double>(2);
-    k_diag_sum<<<1, 1024, 0, s>>>(h->Ainv, m, ds);
+    k_diag_sum<<<1, 1024, 0, s>>>(h->A64, m, ds);
     GMT_LAUNCH_CHECK();
     double dh[2];
     GMT_CUDA(cudaMemcpyAsync(dh, ds, sizeof(dh), cudaMemcpyDeviceToHost, s));
     GMT_CUDA(cudaStreamSynchronize(s));
     const double rho = dh[0] / (double)m;
-    k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->Ainv, m, D, rho);
+    k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, m, D, rho);
     GMT_LAUNCH_CHECK();
-    const double tol = 1e-12 * (dh[1] + rho * (double)c.n_nodes);
-    double* inv = tmp.alloc<double>(GJB * GJB);
-    double* T = tmp.alloc<double>(GJB * m);
-    double* O = tmp.alloc<double>(GJB * m);
-    const dim3 ug((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
-    for (int64_t k0 = 0; k0 < m; k0 += GJB) {
-      const int bb = (int)std::min<int64_t>(GJB, m - k0);
-      k_gj_panel<<<1, 1024, 0, s>>>(h->Ainv, m, k0, bb, tol, inv);
-      GMT_LAUNCH_CHECK();
-      k_gj_rows<<<grid_for(m, 128), 128, 0, s>>>(h->Ainv, m, k0, bb, inv, T, O);
-      GMT_LAUNCH_CHECK();
-      k_gj_update<<<ug, 256, 0, s>>>(h->Ainv, m, k0, bb, inv, T, O);
-      GMT_LAUNCH_CHECK();
-    }
+    h->ctol = 1e-12 * (dh[1] + rho * (double)c.n_nodes);
+    // FP32 generalized inverse for the mixed-precision solves (refined against A64 per use)
+    h->X32 = h->op.alloc<float>(m * m);
+    k_to_f32<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, h->X32, m * m);
+    GMT_LAUNCH_CHECK();
+    gauss_jordan<float>(h, h->X32, m, (float)(1e-6 * (dh[1] + rho * (double)c.n_nodes)), tmp);
   }
   GMT_CUDA(cudaStreamSynchronize(s));
   h->prepared = true;

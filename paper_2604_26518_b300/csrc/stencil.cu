@@ -641,16 +641,18 @@ __global__ void k_coarse_gather(const TS* __restrict__ f, const int* __restrict_
   bvec[g] = (double)load_as<typename ArithOf<TS>::type>(f + vaddr(canon_slot[i], v, D * M));
 }
 
-// u[r][m] = sum_k Ainv[r][k] b[k][m]; one block per row r, fixed-order tree per row
-template <int M>
-__global__ void k_coarse_gemv(const double* __restrict__ Ainv, const double* __restrict__ bvec,
-                              int64_t mrows, double* __restrict__ uvec) {
+// u[r][m] = sum_k X[r][k] b[k][m] (+ u0[r][m]); one block per row r, fixed-order tree per
+// row. With `A` given: res[r][m] = b[r][m] - sum_k A[r][k] u[k][m] instead (a residual).
+template <typename TX, int M>
+__global__ void k_coarse_gemv(const TX* __restrict__ X, const double* __restrict__ bvec,
+                              int64_t mrows, const double* __restrict__ add,
+                              double* __restrict__ uvec) {
   const int64_t r = blockIdx.x;
   double acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = 0.0;
   for (int64_t k = threadIdx.x; k < mrows; k += blockDim.x) {
-    const double a = Ainv[r * mrows + k];
+    const double a = (double)X[r * mrows + k];
 #pragma unroll
     for (int m = 0; m < M; ++m) acc[m] += a * bvec[k * M + m];
   }
@@ -665,7 +667,38 @@ __global__ void k_coarse_gemv(const double* __restrict__ Ainv, const double* __r
     }
     __syncthreads();
   }
-  if (threadIdx.x < M) uvec[r * M + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < M) {
+    const double v = sh[threadIdx.x][0];
+    uvec[r * M + threadIdx.x] = add ? add[r * M + threadIdx.x] + v : v;
+  }
+}
+
+// res = b - A u (FP64), same row-block structure
+template <int M>
+__global__ void k_coarse_resid(const double* __restrict__ A, const double* __restrict__ uvec,
+                               const double* __restrict__ bvec, int64_t mrows,
+                               double* __restrict__ res) {
+  const int64_t r = blockIdx.x;
+  double acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = 0.0;
+  for (int64_t k = threadIdx.x; k < mrows; k += blockDim.x) {
+    const double a = A[r * mrows + k];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += a * uvec[k * M + m];
+  }
+  __shared__ double sh[M][128];
+#pragma unroll
+  for (int m = 0; m < M; ++m) sh[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) sh[m][threadIdx.x] += sh[m][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < M) res[r * M + threadIdx.x] = bvec[r * M + threadIdx.x] - sh[threadIdx.x][0];
 }
 
 template <typename TS, int D, int M>
@@ -1181,12 +1214,25 @@ template <typename TS, typename A, int D, int M>
 static void coarse_t(gmt_hierarchy* h, const void* f, void* u) {
   const Level& c = h->lv[h->L - 1];
   const int64_t cnt = c.n_nodes * D * M;
+  const unsigned rows = (unsigned)h->m;
+  if constexpr (sizeof(TS) == 8) build_coarse_inverse64(h);
   TraceScope ts(&h->tracer, h->stream, TR_CSOLVE, (double)h->m * h->m * 8.0);
   k_coarse_gather<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const TS*)f, c.canon_slot,
                                                                        c.n_nodes, h->cb);
   GMT_LAUNCH_CHECK();
-  k_coarse_gemv<M><<<(unsigned)h->m, 128, 0, h->stream>>>(h->Ainv, h->cb, h->m, h->cu);
-  GMT_LAUNCH_CHECK();
+  if constexpr (sizeof(TS) == 8) {
+    // all-FP64 path: exact inverse
+    k_coarse_gemv<double, M><<<rows, 128, 0, h->stream>>>(h->Ainv, h->cb, h->m, nullptr, h->cu);
+    GMT_LAUNCH_CHECK();
+  } else {
+    // u = X f, then one FP64 refinement u += X (f - A u) against the FP64 matrix
+    k_coarse_gemv<float, M><<<rows, 128, 0, h->stream>>>(h->X32, h->cb, h->m, nullptr, h->cu);
+    GMT_LAUNCH_CHECK();
+    k_coarse_resid<M><<<rows, 128, 0, h->stream>>>(h->A64, h->cu, h->cb, h->m, h->cr);
+    GMT_LAUNCH_CHECK();
+    k_coarse_gemv<float, M><<<rows, 128, 0, h->stream>>>(h->X32, h->cr, h->m, h->cu, h->cu);
+    GMT_LAUNCH_CHECK();
+  }
   vec_zero(h, h->L - 1, sizeof(TS) == 8 ? P64 : (sizeof(TS) == 4 ? P32 : PBF), u);
   k_coarse_scatter<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>(h->cu, c.canon_slot,
                                                                         c.n_nodes, (TS*)u);
