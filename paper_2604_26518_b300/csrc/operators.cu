@@ -7,7 +7,7 @@
 //     8-bit child mask, so it is a 256-entry table; levels >= 2 are stored per element;
 //   * D x D block-diagonal inverses of the coarse operators (smoother, Sec. 4.6);
 //   * the coarsest level's dense matrix K_L + rho J (J couples equal components of all
-//     nodes, rho = mean diagonal) kept in FP64, and its generalized inverse by blocked
+//     nodes, rho = mean diagonal / number of coarse nodes) kept in FP64, and its generalized inverse by blocked
 //     in-place Gauss-Jordan with semidefinite pivot dropping: in FP32 for the
 //     mixed-precision solves (each use is refined once against the FP64 matrix), and in
 //     FP64 (built on first use) for the all-FP64 path. For right-hand sides orthogonal to translations this
@@ -179,7 +179,38 @@ __global__ void k_mask_table(const double* __restrict__ Q, int MM, double* __res
   }
 }
 
-// levels >= 2: K(E) = sum over active children c of P_c^T K(child) P_c
+// Nonzero trilinear weights per (child c, coarse-local vertex b): the child-local vertices
+// a with W[c][a][b] != 0 and the weights (exact binary fractions). 1, 2, 4 or 8 per (c, b).
+struct ChildWeights {
+  unsigned char cnt[8][8];
+  unsigned char a[8][8][8];
+  double w[8][8][8];
+};
+__constant__ ChildWeights c_cw;
+
+static ChildWeights make_child_weights() {
+  ChildWeights cw;
+  std::memset(&cw, 0, sizeof(cw));
+  for (int c = 0; c < 8; ++c)
+    for (int b = 0; b < 8; ++b)
+      for (int a = 0; a < 8; ++a) {
+        double w = 1.0;
+        for (int d = 0; d < 3; ++d) {
+          const double pos = 0.5 * (((c >> d) & 1) + ((a >> d) & 1));
+          w *= 1.0 - std::fabs(pos - (double)((b >> d) & 1));
+        }
+        if (w != 0.0) {
+          const int k = cw.cnt[c][b]++;
+          cw.a[c][b][k] = (unsigned char)a;
+          cw.w[c][b][k] = w;
+        }
+      }
+  return cw;
+}
+
+// levels >= 2: K(E) = sum over active children c of P_c^T K(child) P_c, using only the
+// nonzero weights: T[(a i), (b' j)] = sum_{a'} K[(a i)(a' j)] W[c][a'][b'], then
+// K(E)[(b i), (b' j)] += sum_a W[c][a][b] T[(a i), (b' j)]
 __global__ void k_galerkin_elem(int D, int nc, const int* __restrict__ elem_slot,
                                 const int* __restrict__ cbxyz, bool cdense,
                                 const uint8_t* __restrict__ cchild, int nf, int fnbx,
@@ -194,31 +225,26 @@ __global__ void k_galerkin_elem(int D, int nc, const int* __restrict__ elem_slot
   slot_coords(elem_slot[e], nc, cdense, cbxyz, X, Y, Z);
   const unsigned cm = cchild[X + (int64_t)nc * (Y + (int64_t)nc * Z)];
   const int r = t / R, s = t % R;
+  const int rb = r / D, ri = r % D, sb = s / D, sj = s % D;
   double acc = 0.0;
   for (int c = 0; c < 8; ++c) {
     if (!((cm >> c) & 1)) continue;  // uniform across the block
-    int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + ((c >> 2) & 1);
-    int64_t fs = site_slot(fx, fy, fz, nf, fnbx, fbmap, fdense);
+    const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + ((c >> 2) & 1);
+    const int64_t fs = site_slot(fx, fy, fz, nf, fnbx, fbmap, fdense);
     const double* Kc = Kf + (int64_t)fkidx[fs] * MM;
     __syncthreads();
     if (t < MM) sK[t] = Kc[t];
     __syncthreads();
-    if (t < MM) {  // sT[(a i), (b' j)] = sum_a' K[(a i)(a' j)] w(c, a', b')
-      int bb = s / D, j = s % D;
+    if (t < MM) {
       double v = 0.0;
-      for (int aa = 0; aa < 8; ++aa) {
-        double w = wchild(c, aa, bb);
-        if (w != 0.0) v += sK[r * R + aa * D + j] * w;
-      }
+      const int n = c_cw.cnt[c][sb];
+      for (int k = 0; k < n; ++k) v += sK[r * R + c_cw.a[c][sb][k] * D + sj] * c_cw.w[c][sb][k];
       sT[t] = v;
     }
     __syncthreads();
-    if (t < MM) {  // acc[(b i), (b' j)] += sum_a w(c, a, b) sT[(a i), (b' j)]
-      int b = r / D, i = r % D;
-      for (int a = 0; a < 8; ++a) {
-        double w = wchild(c, a, b);
-        if (w != 0.0) acc += w * sT[(a * D + i) * R + s];
-      }
+    if (t < MM) {
+      const int n = c_cw.cnt[c][rb];
+      for (int k = 0; k < n; ++k) acc += c_cw.w[c][rb][k] * sT[(c_cw.a[c][rb][k] * D + ri) * R + s];
     }
   }
   if (t < MM) {
@@ -394,20 +420,21 @@ __global__ void __launch_bounds__(1024) k_gj_panel(const T* __restrict__ A, int6
   if (i < bb && j < bb) inv[i * GJB + j] = P[i][j];
 }
 
-// T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns)
+// T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns);
+// one thread per (panel row c, column j)
 template <typename T>
 __global__ void k_gj_rows(const T* __restrict__ A, int64_t m, int64_t k0, int bb,
                           const T* __restrict__ inv, T* __restrict__ Tp, T* __restrict__ O) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  T col[GJB];
-  for (int r = 0; r < bb; ++r) col[r] = A[(k0 + r) * m + j];
-  for (int c = 0; c < bb; ++c) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)GJB * m) return;
+  const int c = (int)(g / m);
+  const int64_t j = g % m;
+  if (c < bb) {
     T acc = T(0);
-    for (int r = 0; r < bb; ++r) acc += inv[c * GJB + r] * col[r];
+    for (int r = 0; r < bb; ++r) acc += inv[c * GJB + r] * A[(k0 + r) * m + j];
     Tp[c * m + j] = acc;
+    O[j * GJB + c] = A[j * m + k0 + c];
   }
-  for (int c = 0; c < bb; ++c) O[j * GJB + c] = A[j * m + k0 + c];
 }
 
 // the rank-bb update of everything, tiled 32 x 32 per block
@@ -470,7 +497,7 @@ static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, T tol, Arena& tmp) {
     const int bb = (int)std::min<int64_t>(GJB, m - k0);
     k_gj_panel<T><<<1, 1024, 0, s>>>(A, m, k0, bb, tol, inv);
     GMT_LAUNCH_CHECK();
-    k_gj_rows<T><<<grid_for(m, 128), 128, 0, s>>>(A, m, k0, bb, inv, Tp, O);
+    k_gj_rows<T><<<grid_for(GJB * m, 256), 256, 0, s>>>(A, m, k0, bb, inv, Tp, O);
     GMT_LAUNCH_CHECK();
     k_gj_update<T><<<ug, 256, 0, s>>>(A, m, k0, bb, inv, Tp, O);
     GMT_LAUNCH_CHECK();
@@ -542,6 +569,10 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     GMT_CUDA(cudaStreamSynchronize(s));
   }
   // Galerkin coarse operators
+  {
+    static const ChildWeights cw = make_child_weights();
+    GMT_CUDA(cudaMemcpyToSymbolAsync(c_cw, &cw, sizeof(cw), 0, cudaMemcpyHostToDevice, s));
+  }
   if (h->L >= 2) {
     double* Q = tmp.alloc<double>(8 * MM);
     k_child_products<<<8, MM, 0, s>>>(h->Ke64, D, Q);
@@ -593,15 +624,20 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     double dh[2];
     GMT_CUDA(cudaMemcpyAsync(dh, ds, sizeof(dh), cudaMemcpyDeviceToHost, s));
     GMT_CUDA(cudaStreamSynchronize(s));
-    const double rho = dh[0] / (double)m;
+    // rho J adds rho * n to the eigenvalue of each translation; rho = mean diagonal / n puts
+    // it at the mean diagonal, inside the spectrum of K_L, so the regularized matrix is as
+    // well conditioned as K_L on the complement of the translations (for right-hand sides
+    // orthogonal to translations the solution does not depend on rho > 0)
+    const double rho = dh[0] / (double)m / (double)c.n_nodes;
     k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, m, D, rho);
     GMT_LAUNCH_CHECK();
-    h->ctol = 1e-12 * (dh[1] + rho * (double)c.n_nodes);
+    const double dmax = dh[1] + rho * (double)c.n_nodes;
+    h->ctol = 1e-12 * dmax;
     // FP32 generalized inverse for the mixed-precision solves (refined against A64 per use)
     h->X32 = h->op.alloc<float>(m * m);
     k_to_f32<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, h->X32, m * m);
     GMT_LAUNCH_CHECK();
-    gauss_jordan<float>(h, h->X32, m, (float)(1e-6 * (dh[1] + rho * (double)c.n_nodes)), tmp);
+    gauss_jordan<float>(h, h->X32, m, (float)(1e-6 * dmax), tmp);
   }
   GMT_CUDA(cudaStreamSynchronize(s));
   h->prepared = true;
