@@ -1279,6 +1279,7 @@ void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u
 }
 
 void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out) {
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)nblk * K * 8.0);
   k_reduce<<<K, 256, 0, h->stream>>>(part, nblk, K, out);
   GMT_LAUNCH_CHECK();
 }
@@ -1313,6 +1314,7 @@ static void vdot_dispatch(const void* x, const void* y, double* part, unsigned g
 }
 
 void vec_dot(gmt_hierarchy* h, int level, Prec prec, const void* x, const void* y, double* part) {
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[level].n_nodes * h->mat.C * 2 * prec_bytes(prec));
   const unsigned g = (unsigned)h->lv[level].nb;
   if (h->mat.D == 3) {
     if (prec == P64) vdot_dispatch<double, 6, 18>(x, y, part, g, h->stream);
@@ -1336,6 +1338,7 @@ static void cgu(const double* num, const double* den, const int* act, void* x, c
 void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
                    const int* active, void* x, const void* p, void* r, const void* q,
                    double* part) {
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 6 * prec_bytes(prec));
   const unsigned g = (unsigned)h->lv[0].nb;
   if (h->mat.D == 3) {
     if (prec == P64) cgu<double, 6, 18>(num, den, active, x, p, r, q, part, g, h->stream);
@@ -1355,6 +1358,7 @@ static void cgd(const double* num, const double* den, const int* act, const void
 
 void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
                 const int* active, const void* z, void* p) {
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 3 * prec_bytes(prec));
   const int64_t n = nvals(h, 0);
   if (h->mat.D == 3) {
     if (prec == P64) cgd<double, 6, 18>(num, den, active, z, p, n, h->stream);
@@ -1367,6 +1371,7 @@ void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* de
 }
 
 void vec_ff_add(gmt_hierarchy* h, const float* d, float* hi, float* lo) {
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 5 * prec_bytes(P32));
   const int64_t n = nvals(h, 0);
   k_ff_add<<<grid_for(n, 256), 256, 0, h->stream>>>(d, hi, lo, n);
   GMT_LAUNCH_CHECK();
