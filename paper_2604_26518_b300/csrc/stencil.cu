@@ -49,13 +49,15 @@ template <typename T> struct ArithOf { using type = float; };
 template <> struct ArithOf<double> { using type = double; };
 
 // ------------------------------------------------------------------ block reduction helper
-template <int K>
-__device__ __forceinline__ void block_partial_64(double (&v)[K], double* __restrict__ out) {
-  // 64-thread block: reduce K values per thread into out[K] (fixed order)
+// 64-thread block: reduce K values per thread into out[K] (fixed order). Lanes and warps
+// reduce in the values' own type T (FP32 kernels keep FP64 off the per-element path, where
+// B300's FP64 rate is 1/64 of FP32); the two warp sums are combined in FP64.
+template <int K, typename T>
+__device__ __forceinline__ void block_partial_64(T (&v)[K], double* __restrict__ out) {
   __shared__ double red[2][K > 0 ? K : 1];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double x = v[k];
+    T x = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     v[k] = x;
@@ -63,7 +65,7 @@ __device__ __forceinline__ void block_partial_64(double (&v)[K], double* __restr
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[w][k] = v[k];
+    for (int k = 0; k < K; ++k) red[w][k] = (double)v[k];
   }
   __syncthreads();
   if (threadIdx.x < K) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
@@ -297,19 +299,19 @@ __global__ void __launch_bounds__(64)
   }
   const int64_t base = b * (64 * C) + loc;
   if constexpr (MODE == ST_APPLY) {
-    double dots[M];
+    A dots[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) dots[m] = 0.0;
+    for (int m = 0; m < M; ++m) dots[m] = A(0);
 #pragma unroll
     for (int v = 0; v < C; ++v) {
       p.out[base + v * 64] = store_as<TS>(mk ? acc[v] : A(0));
-      if (mk) dots[v % M] += (double)(self[v] * acc[v]);
+      if (mk) dots[v % M] += self[v] * acc[v];
     }
-    if (p.part) block_partial_64<M>(dots, p.part + b * M);
+    if (p.part) block_partial_64<M, A>(dots, p.part + b * M);
   } else if constexpr (MODE == ST_RESID) {
-    double nrm[M];
+    A nrm[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) nrm[m] = 0.0;
+    for (int m = 0; m < M; ++m) nrm[m] = A(0);
 #pragma unroll
     for (int v = 0; v < C; ++v) {
       A fv;
@@ -328,9 +330,9 @@ __global__ void __launch_bounds__(64)
       }
       const A r = mk ? fv - acc[v] : A(0);
       p.out[base + v * 64] = store_as<TS>(r);
-      nrm[v % M] += (double)r * (double)r;
+      nrm[v % M] += r * r;
     }
-    if (p.part) block_partial_64<M>(nrm, p.part + b * M);
+    if (p.part) block_partial_64<M, A>(nrm, p.part + b * M);
   } else {
     A Iv[DD];
     if (mk) {
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   const int q0 = own_q0(t), loc = own_local(t);
   const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
+  const bool warp_full = __all_sync(0xffffffffu, mk == 0xffu);  // every lane votes
   float acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = 0.f;
@@ -501,18 +504,23 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
       if (d == 13) continue;  // d = 0 carries no difference
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
       float S[D * D];
+      if (warp_full) {
 #pragma unroll
-      for (int k = 0; k < D * D; ++k) S[k] = 0.f;
+        for (int k = 0; k < D * D; ++k) S[k] = p.fc.Sf[d * D * D + k];
+      } else {
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int ex = (a & 1) + dx, ey = ((a >> 1) & 1) + dy, ez = (a >> 2) + dz;
-        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
-        const int bb = ex + 2 * ey + 4 * ez;
+        for (int k = 0; k < D * D; ++k) S[k] = 0.f;
 #pragma unroll
-        for (int i = 0; i < D; ++i)
+        for (int a = 0; a < 8; ++a) {
+          const int ex = (a & 1) + dx, ey = ((a >> 1) & 1) + dy, ez = (a >> 2) + dz;
+          if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+          const int bb = ex + 2 * ey + 4 * ez;
 #pragma unroll
-          for (int j = 0; j < D; ++j)
-            S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+              S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
+        }
       }
       const int q = q0 + dx + 6 * dy + 36 * dz;
       float uh[G * 4], ul[G * 4];
@@ -534,9 +542,9 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
       }
     }
   }
-  double nrm[M];
+  float nrm[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) nrm[m] = 0.0;
+  for (int m = 0; m < M; ++m) nrm[m] = 0.f;
   const int64_t base = b * (64 * C) + loc;
 #pragma unroll
   for (int v = 0; v < C; ++v) {
@@ -546,9 +554,9 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
     for (int a = 0; a < 8; ++a) fv += (((mk >> a) & 1u) ? 1.f : 0.f) * p.fc.Fe[(a * D + i) * M + m];
     const float r = mk ? fv - acc[v] : 0.f;
     p.out[base + v * 64] = r;
-    nrm[m] += (double)r * (double)r;
+    nrm[m] += r * r;
   }
-  if (p.part) block_partial_64<M>(nrm, p.part + b * M);
+  if (p.part) block_partial_64<M, float>(nrm, p.part + b * M);
 }
 
 // ------------------------------------------------------------------ transfers
@@ -817,7 +825,7 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
       }
     }
   }
-  block_partial_64<K>(e, p.part + b * K);
+  block_partial_64<K, double>(e, p.part + b * K);
 }
 
 // deterministic reduction of [nblk][K] partials: block k reduces column k
@@ -874,13 +882,23 @@ __global__ void __launch_bounds__(64) k_vdot(const TS* __restrict__ x, const TS*
                                              double* __restrict__ part) {
   using A = typename ArithOf<TS>::type;
   const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
-  double d[M];
+  A d[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) d[m] = 0.0;
+  for (int m = 0; m < M; ++m) d[m] = A(0);
 #pragma unroll
-  for (int v = 0; v < C; ++v)
-    d[v % M] += (double)(load_as<A>(x + base + v * 64) * load_as<A>(y + base + v * 64));
-  block_partial_64<M>(d, part + (int64_t)blockIdx.x * M);
+  for (int v = 0; v < C; ++v) d[v % M] += load_as<A>(x + base + v * 64) * load_as<A>(y + base + v * 64);
+  block_partial_64<M, A>(d, part + (int64_t)blockIdx.x * M);
+}
+
+// per-case step ratio num/den (0 for inactive cases), computed once per block
+template <typename A, int M>
+__device__ __forceinline__ void block_ratios(const double* num, const double* den,
+                                             const int* active, A* out) {
+  if (threadIdx.x < M) {
+    const int m = threadIdx.x;
+    out[m] = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
+  }
+  __syncthreads();
 }
 
 template <typename TS, int M, int C>
@@ -889,34 +907,37 @@ __global__ void __launch_bounds__(64)
                 const int* __restrict__ active, TS* __restrict__ x, const TS* __restrict__ pp,
                 TS* __restrict__ r, const TS* __restrict__ q, double* __restrict__ part) {
   using A = typename ArithOf<TS>::type;
+  __shared__ A alpha[M];
+  block_ratios<A, M>(num, den, active, alpha);
   const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
-  double nr[M];
+  A nr[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) nr[m] = 0.0;
+  for (int m = 0; m < M; ++m) nr[m] = A(0);
 #pragma unroll
   for (int v = 0; v < C; ++v) {
-    const int m = v % M;
-    const A al = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
+    const A al = alpha[v % M];
     const int64_t a = base + v * 64;
     x[a] = store_as<TS>(load_as<A>(x + a) + al * load_as<A>(pp + a));
     const A rn = load_as<A>(r + a) - al * load_as<A>(q + a);
     r[a] = store_as<TS>(rn);
-    nr[m] += (double)rn * (double)rn;
+    nr[v % M] += rn * rn;
   }
-  block_partial_64<M>(nr, part + (int64_t)blockIdx.x * M);
+  block_partial_64<M, A>(nr, part + (int64_t)blockIdx.x * M);
 }
 
 template <typename TS, int M, int C>
-__global__ void k_cg_dir(const double* __restrict__ num, const double* __restrict__ den,
-                         const int* __restrict__ active, const TS* __restrict__ z,
-                         TS* __restrict__ pp, int64_t n) {
+__global__ void __launch_bounds__(256) k_cg_dir(const double* __restrict__ num,
+                                                const double* __restrict__ den,
+                                                const int* __restrict__ active,
+                                                const TS* __restrict__ z, TS* __restrict__ pp,
+                                                int64_t n) {
   using A = typename ArithOf<TS>::type;
+  __shared__ A beta[M];
+  block_ratios<A, M>(num, den, active, beta);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int v = (int)((i >> 6) % C);
-  const int m = v % M;
-  const A be = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
-  pp[i] = store_as<TS>(load_as<A>(z + i) + be * load_as<A>(pp + i));
+  pp[i] = store_as<TS>(load_as<A>(z + i) + beta[v % M] * load_as<A>(pp + i));
 }
 
 // float-float accumulate (hi, lo) += d with Knuth's TwoSum and a fast renormalisation
@@ -971,7 +992,7 @@ __global__ void __launch_bounds__(64) k_sum_values(const TS* __restrict__ x,
     if (lo && act) val += (double)lo[base + v * 64];
     s[v] = val;
   }
-  block_partial_64<C>(s, part + (int64_t)blockIdx.x * C);
+  block_partial_64<C, double>(s, part + (int64_t)blockIdx.x * C);
 }
 
 template <int C>
