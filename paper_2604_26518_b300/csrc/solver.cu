@@ -357,6 +357,18 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     }
   }
   const Prec ar = w->arith;
+  // Mixed precision: the difference-form FP32 operator annihilates translations exactly,
+  // while FP32 rounding leaves the iterated residual, and the V-cycle output, with small
+  // translation components that no step can reduce; left alone they grow through the
+  // recurrence and corrupt r.z versus p.Kp. Both vectors are therefore projected onto the
+  // zero-mean (per component and case) subspace, where the periodic problem lives.
+  auto project = [&](void* vec) {
+    if (!mixed) return;
+    double* sums = w->part + h->lv[0].nb * M;   // rows beyond the per-case partials
+    vec_sum_values(h, 0, P32, vec, nullptr, sums);
+    launch_reduce(h, sums, h->lv[0].nb, h->mat.C, w->red + 7 * 32 + 8);
+    vec_sub_mean32(h, w->red + 7 * 32 + 8, (float*)vec);
+  };
   int cycles = 0, updates = 0, restarts = 0;
   static const bool verbose = std::getenv("GMT_VERBOSE") != nullptr;
   gmt_status st = GMT_NOT_CONVERGED;
@@ -381,7 +393,9 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     double* rz = w->red + 4 * 32;
     double* pq = w->red + 5 * 32;
     double* rz_new = w->red + 6 * 32;
+    project(w->rr);
     void* z = vcycle(h, w, 0, w->rr, nullptr, true);
+    project(z);
     ++cycles;
     if (krylov) {
       vec_copy(h, 0, ar, z, w->p);
@@ -400,6 +414,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       } else {
         vec_cg_update(h, ar, w->ones, w->ones, w->active, w->x, z, w->rr, w->q, w->part);
       }
+      project(w->rr);
       double rn[8];
       fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
       if (verbose) {
@@ -437,15 +452,17 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
           break;
         }
         if (last) break;
-        // the Krylov recurrence restarts from every true residual: each FP32 CG run then
-        // only has to gain the factor inner_tol, well inside FP32 accuracy even for thin,
-        // badly conditioned cells
-        restart = true;
+        // stagnation guard: a replacement that gained less than 10 % restarts the Krylov
+        // recurrence from the true residual
+        for (int m = 0; m < M; ++m)
+          if (act[m] && rel[m] > 0.9 * ref[m]) restart = true;
         for (int m = 0; m < M; ++m) ref[m] = rel[m];
         deactivate_converged();
         push_active();
       }
+      project(w->rr);
       z = vcycle(h, w, 0, w->rr, nullptr, true);
+      project(z);
       ++cycles;
       if (krylov) {
         vec_dot(h, 0, ar, w->rr, z, w->part);

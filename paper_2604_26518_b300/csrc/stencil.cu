@@ -193,13 +193,18 @@ __device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, 
 //         32 nodes all have full masks use the precomputed full stencil instead.
 // KIND 1: coarse levels, S_n(d) read from the per-node assembled stencil, stored
 //         brick-major as [brick][27 * D * D][64] so each coefficient load is coalesced.
+// ST_APPLY uses the difference form sum_{d != 0} S_n(d) (u_{n+d} - u_n) (rows of K sum to
+// zero): the differences of a smooth Krylov direction are small, which keeps the FP32
+// product accurate (about 20x closer to the FP64 product than the direct form on V-cycle
+// output). It annihilates translations exactly, so the mixed-precision solver keeps its
+// residual and preconditioned directions free of translations (see solver.cu).
 template <typename TS, typename A, int D, int M, int KIND, int MODE>
 __global__ void __launch_bounds__(64)
     k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, DD = D * D;
   constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
-  constexpr bool DIFF = false;   // direct form sum_d S_n(d) u_{n+d} in every mode
+  constexpr bool DIFF = MODE == ST_APPLY;
   __shared__ V tile[G * 216];
   __shared__ int nb[27];
   const int t = threadIdx.x;
@@ -995,6 +1000,17 @@ __global__ void __launch_bounds__(64) k_sum_values(const TS* __restrict__ x,
   block_partial_64<C, double>(s, part + (int64_t)blockIdx.x * C);
 }
 
+// x -= sums[v] / n over active slots (FP32 field; sums on the device)
+template <int C>
+__global__ void k_sub_mean32(const double* __restrict__ sums, double inv_n,
+                             const uint8_t* __restrict__ mask, float* __restrict__ x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
+  if (!mask[slot]) return;
+  x[i] -= (float)(sums[(i >> 6) % C] * inv_n);
+}
+
 template <int C>
 __global__ void k_sub_mean64(const double* __restrict__ mean, const uint8_t* __restrict__ mask,
                              double* __restrict__ x, int64_t n) {
@@ -1416,6 +1432,17 @@ void vec_sum_values(gmt_hierarchy* h, int level, Prec prec, const void* x, const
     if (prec == P64) k_sum_values<double, 3><<<g, 64, 0, h->stream>>>((const double*)x, lo, mk, part);
     else k_sum_values<float, 3><<<g, 64, 0, h->stream>>>((const float*)x, lo, mk, part);
   }
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_sub_mean32(gmt_hierarchy* h, const double* sums, float* x) {
+  const int64_t n = nvals(h, 0);
+  const double inv = 1.0 / (double)h->lv[0].n_nodes;
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 8.0);
+  if (h->mat.C == 18)
+    k_sub_mean32<18><<<grid_for(n, 256), 256, 0, h->stream>>>(sums, inv, h->lv[0].mask, x, n);
+  else
+    k_sub_mean32<3><<<grid_for(n, 256), 256, 0, h->stream>>>(sums, inv, h->lv[0].mask, x, n);
   GMT_LAUNCH_CHECK();
 }
 

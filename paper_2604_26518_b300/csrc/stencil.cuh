@@ -63,6 +63,8 @@ void vec_ff_sub_mean(gmt_hierarchy* h, const double* mean, float* hi, float* lo)
 // per-block sums of each value over active slots: part[b][C]; ff adds hi + lo
 void vec_sum_values(gmt_hierarchy* h, int level, Prec prec, const void* x, const float* lo,
                     double* part);
+// x -= sums[v] / n_active (level-0 FP32 field; sums on the device)
+void vec_sub_mean32(gmt_hierarchy* h, const double* sums, float* x);
 // x -= mean[v] (FP64 field)
 void vec_sub_mean64(gmt_hierarchy* h, int level, const double* mean, double* x);
 // scale case m of x by s[m] (device doubles)
