@@ -362,12 +362,16 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   // translation components that no step can reduce; left alone they grow through the
   // recurrence and corrupt r.z versus p.Kp. Both vectors are therefore projected onto the
   // zero-mean (per component and case) subspace, where the periodic problem lives.
+  double* vsums = w->red + 7 * 32 + 8;          // device sums per value (C <= 18)
+  auto sum_values = [&](const void* vec) {
+    double* part = w->part + h->lv[0].nb * M;    // rows beyond the per-case partials
+    vec_sum_values32(h, (const float*)vec, part);
+    launch_reduce(h, part, h->lv[0].nb, h->mat.C, vsums);
+  };
   auto project = [&](void* vec) {
     if (!mixed) return;
-    double* sums = w->part + h->lv[0].nb * M;   // rows beyond the per-case partials
-    vec_sum_values(h, 0, P32, vec, nullptr, sums);
-    launch_reduce(h, sums, h->lv[0].nb, h->mat.C, w->red + 7 * 32 + 8);
-    vec_sub_mean32(h, w->red + 7 * 32 + 8, (float*)vec);
+    sum_values(vec);
+    vec_sub_mean32(h, vsums, (float*)vec);
   };
   int cycles = 0, updates = 0, restarts = 0;
   static const bool verbose = std::getenv("GMT_VERBOSE") != nullptr;
@@ -403,6 +407,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       launch_reduce(h, w->part, h->lv[0].nb, M, rz);
     }
     for (;;) {
+      if (!krylov) project(z);
       VecArgs a;
       a.u = krylov ? w->p : z;
       a.out = w->q;
@@ -447,6 +452,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
           st = GMT_OK;
           break;
         }
+        project(w->rr);
         if (std::isnan(mx) || mx > 1e4 * std::max(first, 1e-300)) {
           st = GMT_DIVERGED;
           break;
@@ -460,18 +466,20 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         deactivate_converged();
         push_active();
       }
-      project(w->rr);
       z = vcycle(h, w, 0, w->rr, nullptr, true);
-      project(z);
       ++cycles;
       if (krylov) {
+        // rr is mean-free, so r.z needs no correction for the mean of z; the mean of z is
+        // removed while forming the new direction
+        if (mixed) sum_values(z);
         vec_dot(h, 0, ar, w->rr, z, w->part);
         launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
         if (restart) {
+          if (mixed) vec_sub_mean32(h, vsums, (float*)z);
           vec_copy(h, 0, ar, z, w->p);
           ++restarts;
         } else {
-          vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p);
+          vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p, mixed ? vsums : nullptr);
         }
         GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice,
                                  h->stream));

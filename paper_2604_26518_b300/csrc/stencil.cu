@@ -935,14 +935,22 @@ __global__ void __launch_bounds__(256) k_cg_dir(const double* __restrict__ num,
                                                 const double* __restrict__ den,
                                                 const int* __restrict__ active,
                                                 const TS* __restrict__ z, TS* __restrict__ pp,
-                                                int64_t n) {
+                                                int64_t n, const double* __restrict__ zsum,
+                                                double inv_n, const uint8_t* __restrict__ mask) {
   using A = typename ArithOf<TS>::type;
   __shared__ A beta[M];
+  __shared__ A zmean[C];
   block_ratios<A, M>(num, den, active, beta);
+  if (zsum != nullptr) {
+    if (threadIdx.x < C) zmean[threadIdx.x] = (A)(zsum[threadIdx.x] * inv_n);
+    __syncthreads();
+  }
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int v = (int)((i >> 6) % C);
-  pp[i] = store_as<TS>(load_as<A>(z + i) + beta[v % M] * load_as<A>(pp + i));
+  A zv = load_as<A>(z + i);
+  if (zsum != nullptr && mask[((i >> 6) / C) * 64 + (i & 63)]) zv -= zmean[v];
+  pp[i] = store_as<TS>(zv + beta[v % M] * load_as<A>(pp + i));
 }
 
 // float-float accumulate (hi, lo) += d with Knuth's TwoSum and a fast renormalisation
@@ -1001,6 +1009,19 @@ __global__ void __launch_bounds__(64) k_sum_values(const TS* __restrict__ x,
 }
 
 // x -= sums[v] / n over active slots (FP32 field; sums on the device)
+// per-block sums of each value over active slots, FP32 per lane and warp (projections)
+template <int C>
+__global__ void __launch_bounds__(64) k_sum_values32(const float* __restrict__ x,
+                                                     const uint8_t* __restrict__ mask,
+                                                     double* __restrict__ part) {
+  const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
+  const bool act = mask[(int64_t)blockIdx.x * 64 + threadIdx.x] != 0;
+  float s[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) s[v] = act ? x[base + v * 64] : 0.f;
+  block_partial_64<C, float>(s, part + (int64_t)blockIdx.x * C);
+}
+
 template <int C>
 __global__ void k_sub_mean32(const double* __restrict__ sums, double inv_n,
                              const uint8_t* __restrict__ mask, float* __restrict__ x, int64_t n) {
@@ -1389,20 +1410,23 @@ void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double*
 
 template <typename TS, int M, int C>
 static void cgd(const double* num, const double* den, const int* act, const void* z, void* p,
-                int64_t n, cudaStream_t s) {
-  k_cg_dir<TS, M, C><<<grid_for(n, 256), 256, 0, s>>>(num, den, act, (const TS*)z, (TS*)p, n);
+                int64_t n, cudaStream_t s, const double* zsum, double inv_n, const uint8_t* mask) {
+  k_cg_dir<TS, M, C><<<grid_for(n, 256), 256, 0, s>>>(num, den, act, (const TS*)z, (TS*)p, n,
+                                                      zsum, inv_n, mask);
 }
 
 void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                const int* active, const void* z, void* p) {
+                const int* active, const void* z, void* p, const double* zsum) {
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 3 * prec_bytes(prec));
   const int64_t n = nvals(h, 0);
+  const double inv = 1.0 / (double)h->lv[0].n_nodes;
+  const uint8_t* mk = h->lv[0].mask;
   if (h->mat.D == 3) {
-    if (prec == P64) cgd<double, 6, 18>(num, den, active, z, p, n, h->stream);
-    else cgd<float, 6, 18>(num, den, active, z, p, n, h->stream);
+    if (prec == P64) cgd<double, 6, 18>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
+    else cgd<float, 6, 18>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
   } else {
-    if (prec == P64) cgd<double, 3, 3>(num, den, active, z, p, n, h->stream);
-    else cgd<float, 3, 3>(num, den, active, z, p, n, h->stream);
+    if (prec == P64) cgd<double, 3, 3>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
+    else cgd<float, 3, 3>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
   }
   GMT_LAUNCH_CHECK();
 }
@@ -1432,6 +1456,14 @@ void vec_sum_values(gmt_hierarchy* h, int level, Prec prec, const void* x, const
     if (prec == P64) k_sum_values<double, 3><<<g, 64, 0, h->stream>>>((const double*)x, lo, mk, part);
     else k_sum_values<float, 3><<<g, 64, 0, h->stream>>>((const float*)x, lo, mk, part);
   }
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_sum_values32(gmt_hierarchy* h, const float* x, double* part) {
+  const unsigned g = (unsigned)h->lv[0].nb;
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 4.0);
+  if (h->mat.C == 18) k_sum_values32<18><<<g, 64, 0, h->stream>>>(x, h->lv[0].mask, part);
+  else k_sum_values32<3><<<g, 64, 0, h->stream>>>(x, h->lv[0].mask, part);
   GMT_LAUNCH_CHECK();
 }
 

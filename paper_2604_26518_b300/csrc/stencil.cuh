@@ -51,9 +51,12 @@ void vec_dot(gmt_hierarchy* h, int level, Prec prec, const void* x, const void* 
 void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
                    const int* active, void* x, const void* p, void* r, const void* q,
                    double* part);
-// CG: beta_m = num[m] / den[m]; p = z + beta p
+// CG: beta_m = num[m] / den[m]; p = z + beta p; with zsum (device sums of z per value over
+// active nodes) the mean of z is removed on the fly: p = (z - zsum / n) + beta p
 void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                const int* active, const void* z, void* p);
+                const int* active, const void* z, void* p, const double* zsum = nullptr);
+// per-block FP32 sums of each value of a level-0 FP32 field over active slots
+void vec_sum_values32(gmt_hierarchy* h, const float* x, double* part);
 // x += y (same precision)
 void vec_add(gmt_hierarchy* h, int level, Prec prec, const void* y, void* x);
 // float-float: (hi, lo) += d
