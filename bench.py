@@ -179,6 +179,10 @@ def run_gmt(args, rank: int, world: int):
     ph = gmt.ELASTIC if args.physics == "elastic" else gmt.HEAT
     prec = gmt.FP32 if args.precision == "fp32" else gmt.FP64
     opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
+    if args.nu:
+        opts.nu_pre = opts.nu_post = args.nu
+    if args.smoother:
+        opts.smoother = gmt.JACOBI if args.smoother == "jacobi" else gmt.CHEBYSHEV
     if args.cells:
         cells = cells[:args.cells]
     vox_dev = [torch.from_numpy(v).to(dev) for v, _ in cells]
@@ -281,6 +285,8 @@ def run_gmt(args, rank: int, world: int):
                                  "solve and C^H accumulation") if prec == gmt.FP32 else "fp64",
                    "step": "hierarchy + operators + solve + C^H per cell",
                    "coarsest_max": args.coarsest,
+                   "smoother": "%s, nu_pre = nu_post = %d" % (
+                       "jacobi" if opts.smoother == gmt.JACOBI else "chebyshev", opts.nu_pre),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "C^H solves/s",
@@ -321,6 +327,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--coarsest", type=int, default=8, help="coarsest grid side bound")
+    ap.add_argument("--nu", type=int, default=0, help="pre/post smoothing sweeps (0: default)")
+    ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev"])
     ap.add_argument("--cells", type=int, default=0, help="use only the first K cells (profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -227,10 +227,18 @@ struct gmt_hierarchy {
   double* cb = nullptr;   // m x M gather buffer
   double* cu = nullptr;   // m x M result buffer
   double* cr = nullptr;   // m x M refinement residual
+  float* cb32 = nullptr;  // m x M FP32 copy of the right-hand side / refinement residual
   gmt::Workspace* ws = nullptr;
   gmt::Tracer tracer;
   bool have_solution = false;
   int64_t ws_for_prec = -1;
+  // histogram of the level-0 octant masks over active nodes (the load f_n depends on the
+  // mask alone); filled on first use
+  long long mask_hist[256] = {};
+  bool have_hist = false;
+  // split-column reductions: per-block (sum, compensation) pairs and arrival tickets
+  double* red_scratch = nullptr;
+  unsigned* red_ticket = nullptr;
 };
 
 namespace gmt {

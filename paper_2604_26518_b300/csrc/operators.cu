@@ -146,10 +146,12 @@ __device__ __forceinline__ double wchild(int c, int a, int b) {
   return w;
 }
 
-// Q[c] = P_c^T K_e P_c (block c, one thread per entry)
-__global__ void k_child_products(const double* __restrict__ Ke, int D, double* __restrict__ Q) {
+// Q[c][y] = P_c^T K[y] P_c for the gridDim.y input matrices K[y] (block (c, y), one thread
+// per entry)
+__global__ void k_child_products(const double* __restrict__ Kin, int D, double* __restrict__ Q) {
   const int R = 8 * D, MM = R * R;
-  const int c = blockIdx.x, t = threadIdx.x;
+  const int c = blockIdx.x, y = blockIdx.y, t = threadIdx.x;
+  const double* Ke = Kin + (int64_t)y * MM;
   if (t >= MM) return;
   int r = t / R, s = t % R;
   int b = r / D, i = r % D, bb = s / D, j = s % D;
@@ -163,20 +165,57 @@ __global__ void k_child_products(const double* __restrict__ Ke, int D, double* _
       acc += wa * wb * Ke[(a * D + i) * R + aa * D + j];
     }
   }
-  Q[(int64_t)c * MM + t] = acc;
+  Q[((int64_t)c * gridDim.y + y) * MM + t] = acc;
 }
 
-// level-1 table: T[mask] = sum_{c in mask} Q[c]
+// mask tables: T[y][mask] = sum_{c in mask} Q[y][c] for gridDim.y groups of 8 matrices
+// (level 1: one group, Q[c] = P_c^T K_e P_c; level 2: group c holds P_c^T Q[c'] P_c)
 __global__ void k_mask_table(const double* __restrict__ Q, int MM, double* __restrict__ T64,
                              float* __restrict__ T32) {
   const int m = blockIdx.x;
+  const int64_t y = blockIdx.y;
+  const double* Qy = Q + y * 8 * MM;
   for (int t = threadIdx.x; t < MM; t += blockDim.x) {
     double acc = 0.0;
     for (int c = 0; c < 8; ++c)
-      if ((m >> c) & 1) acc += Q[(int64_t)c * MM + t];
-    T64[(int64_t)m * MM + t] = acc;
-    T32[(int64_t)m * MM + t] = (float)acc;
+      if ((m >> c) & 1) acc += Qy[(int64_t)c * MM + t];
+    T64[(y * 256 + m) * MM + t] = acc;
+    if (T32) T32[(y * 256 + m) * MM + t] = (float)acc;
   }
+}
+
+// level 2: K(E) = sum over active children c of T2[c][mask(c)], where mask(c) is the
+// level-1 child's own child mask (its index into the level-1 table) and
+// T2[c][m] = sum_{c' in m} P_c^T Q[c'] P_c = P_c^T K1[m] P_c (Galerkin products are linear)
+__global__ void k_galerkin_l2(int D, int nc, const int* __restrict__ elem_slot,
+                              const int* __restrict__ cbxyz, bool cdense,
+                              const uint8_t* __restrict__ cchild, int nf, int fnbx,
+                              const int* __restrict__ fbmap, bool fdense,
+                              const int* __restrict__ fkidx, const double* __restrict__ T2,
+                              double* __restrict__ K64, float* __restrict__ K32) {
+  const int MM = 64 * D * D;
+  const int64_t e = blockIdx.x;
+  const int t = threadIdx.x;
+  __shared__ int sidx[8];
+  int X, Y, Z;
+  slot_coords(elem_slot[e], nc, cdense, cbxyz, X, Y, Z);
+  const unsigned cm = cchild[X + (int64_t)nc * (Y + (int64_t)nc * Z)];
+  if (t < 8) {
+    int id = -1;
+    if ((cm >> t) & 1) {
+      const int fx = 2 * X + (t & 1), fy = 2 * Y + ((t >> 1) & 1), fz = 2 * Z + ((t >> 2) & 1);
+      id = t * 256 + fkidx[site_slot(fx, fy, fz, nf, fnbx, fbmap, fdense)];
+    }
+    sidx[t] = id;
+  }
+  __syncthreads();
+  if (t >= MM) return;
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (sidx[c] >= 0) acc += T2[(int64_t)sidx[c] * MM + t];
+  K64[e * MM + t] = acc;
+  K32[e * MM + t] = (float)acc;
 }
 
 // Nonzero trilinear weights per (child c, coarse-local vertex b): the child-local vertices
@@ -573,14 +612,15 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     static const ChildWeights cw = make_child_weights();
     GMT_CUDA(cudaMemcpyToSymbolAsync(c_cw, &cw, sizeof(cw), 0, cudaMemcpyHostToDevice, s));
   }
+  double* Q = nullptr;
   if (h->L >= 2) {
-    double* Q = tmp.alloc<double>(8 * MM);
-    k_child_products<<<8, MM, 0, s>>>(h->Ke64, D, Q);
+    Q = tmp.alloc<double>(8 * MM);
+    k_child_products<<<dim3(8, 1), MM, 0, s>>>(h->Ke64, D, Q);
     GMT_LAUNCH_CHECK();
     Level& l1 = h->lv[1];
     l1.K64 = h->op.alloc<double>(256 * (size_t)MM);
     l1.K32 = h->op.alloc<float>(256 * (size_t)MM);
-    k_mask_table<<<256, 256, 0, s>>>(Q, MM, l1.K64, l1.K32);
+    k_mask_table<<<dim3(256, 1), 256, 0, s>>>(Q, MM, l1.K64, l1.K32);
     GMT_LAUNCH_CHECK();
   }
   for (int l = 2; l < h->L; ++l) {
@@ -588,9 +628,23 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     Level& f = h->lv[l - 1];
     c.K64 = h->op.alloc<double>(c.n_elems * (size_t)MM);
     c.K32 = h->op.alloc<float>(c.n_elems * (size_t)MM);
-    k_galerkin_elem<<<(unsigned)c.n_elems, MM, 0, s>>>(D, c.n, c.elem_slot, c.brick_xyz, c.dense,
+    if (l == 2) {
+      // 8 x 8 products P_c^T Q[c'] P_c, then the 8 x 256 table T2[c][m]
+      double* Q2 = tmp.alloc<double>(64 * (size_t)MM);
+      k_child_products<<<dim3(8, 8), MM, 0, s>>>(Q, D, Q2);
+      GMT_LAUNCH_CHECK();
+      double* T2 = tmp.alloc<double>(8 * 256 * (size_t)MM);
+      k_mask_table<<<dim3(256, 8), 256, 0, s>>>(Q2, MM, T2, nullptr);
+      GMT_LAUNCH_CHECK();
+      k_galerkin_l2<<<(unsigned)c.n_elems, MM, 0, s>>>(D, c.n, c.elem_slot, c.brick_xyz, c.dense,
                                                        c.child, f.n, f.nbx, f.brick_map, f.dense,
-                                                       f.kidx, f.K64, c.K64, c.K32);
+                                                       f.kidx, T2, c.K64, c.K32);
+    } else {
+      k_galerkin_elem<<<(unsigned)c.n_elems, MM, 0, s>>>(D, c.n, c.elem_slot, c.brick_xyz,
+                                                         c.dense, c.child, f.n, f.nbx,
+                                                         f.brick_map, f.dense, f.kidx, f.K64,
+                                                         c.K64, c.K32);
+    }
     GMT_LAUNCH_CHECK();
   }
   for (int l = 1; l < h->L; ++l) {
@@ -613,6 +667,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     h->cb = h->op.alloc<double>(m * M);
     h->cu = h->op.alloc<double>(m * M);
     h->cr = h->op.alloc<double>(m * M);
+    h->cb32 = h->op.alloc<float>(m * M);
     GMT_CUDA(cudaMemsetAsync(h->A64, 0, m * m * sizeof(double), s));
     k_coarse_assemble<<<grid_for(c.n_nodes * 27, 128), 128, 0, s>>>(
         D, lc, c.n, c.nbx, c.brick_xyz, c.brick_map, c.dense, c.eflag, c.canon_slot, c.slot_canon,

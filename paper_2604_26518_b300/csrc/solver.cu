@@ -33,38 +33,53 @@ __global__ void k_hash_fill(float* __restrict__ x, const uint8_t* __restrict__ m
   x[i] = mask[slot] ? ((float)(hsh & 0xffffff) / 16777216.0f - 0.5f) : 0.0f;
 }
 
-// level-0 load f (from masks) and its per-case norms; f_n = sum_{a in mask} (K_e x0)[a]
-template <typename TS, typename A, int D, int M>
-__global__ void k_fine_load(const uint8_t* __restrict__ mask, TS* __restrict__ out,
-                            double* __restrict__ part, const __grid_constant__ Material mt) {
-  constexpr int C = D * M;
-  const int64_t b = blockIdx.x;
-  const int t = threadIdx.x;
-  const unsigned mk = mask[b * 64 + t];
-  double nrm[M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) nrm[m] = 0.0;
-#pragma unroll
-  for (int v = 0; v < C; ++v) {
-    const int i = v / M, m = v % M;
-    A f = A(0);
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if ((mk >> a) & 1u) f += (A)mt.Fe[(a * D + i) * M + m];
-    out[b * 64 * C + v * 64 + t] = store_as<TS>(f);
-    nrm[m] += (double)f * (double)f;
-  }
-  // block reduce
-  __shared__ double red[2][6];
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    double x = nrm[m];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((t & 31) == 0) red[t >> 5][m] = x;
+// histogram of the octant masks of the active level-0 slots (integer atomics: exact)
+__global__ void k_mask_hist(const uint8_t* __restrict__ mask, int64_t n,
+                            unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int sh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned m = mask[i];
+    if (m) atomicAdd(&sh[m], 1u);
   }
   __syncthreads();
-  if (t < M) part[b * M + t] = red[0][t] + red[1][t];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+}
+
+// ||f_m||^2 of the level-0 load, f_n = sum_{a in mask} (K_e x0)[a]: the load of a node
+// depends on its octant mask alone, so the norm is the mask histogram times per-mask norms
+// (FP64 on the host, masks in increasing order)
+static void load_norms2(gmt_hierarchy* h, double* fn2) {
+  if (!h->have_hist) {
+    const Level& l0 = h->lv[0];
+    Arena tmp;
+    unsigned long long* d = tmp.alloc<unsigned long long>(256);
+    GMT_CUDA(cudaMemsetAsync(d, 0, 256 * sizeof(unsigned long long), h->stream));
+    const unsigned g = std::min<unsigned>(grid_for(l0.nslots, 256), 148u * 8u);
+    k_mask_hist<<<g, 256, 0, h->stream>>>(l0.mask, l0.nslots, d);
+    GMT_LAUNCH_CHECK();
+    unsigned long long hh[256];
+    GMT_CUDA(cudaMemcpyAsync(hh, d, sizeof(hh), cudaMemcpyDeviceToHost, h->stream));
+    GMT_CUDA(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 256; ++k) h->mask_hist[k] = (long long)hh[k];
+    h->have_hist = true;
+  }
+  const Material& mt = h->mat;
+  const int D = mt.D, M = mt.M;
+  for (int m = 0; m < M; ++m) fn2[m] = 0.0;
+  for (int k = 1; k < 256; ++k) {
+    if (h->mask_hist[k] == 0) continue;
+    for (int i = 0; i < D; ++i)
+      for (int m = 0; m < M; ++m) {
+        double f = 0.0;
+        for (int a = 0; a < 8; ++a)
+          if ((k >> a) & 1) f += mt.Fe[(a * D + i) * M + m];
+        fn2[m] += (double)h->mask_hist[k] * f * f;
+      }
+  }
 }
 
 struct Workspace {
@@ -77,7 +92,7 @@ struct Workspace {
   double* f64 = nullptr;
   double* part = nullptr;
   int64_t part_rows = 0;
-  double* red = nullptr;     // reduction slots, 8 x 32 doubles
+  double* red = nullptr;     // reduction slots, 12 x 32 doubles
   int* active = nullptr;     // per case flags (device)
   double* ones = nullptr;    // per case 1.0 (device)
 };
@@ -122,7 +137,7 @@ static Workspace* workspace(gmt_hierarchy* h, Prec prec) {
   for (int l = 0; l < h->L; ++l) rows = std::max<int64_t>(rows, h->lv[l].nb);
   w->part_rows = rows;
   w->part = h->work.alloc<double>(rows * 32);
-  w->red = h->work.alloc<double>(8 * 32);
+  w->red = h->work.alloc<double>(12 * 32);
   w->active = h->work.alloc<int>(8);
   w->ones = h->work.alloc<double>(8);
   double ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
@@ -145,9 +160,10 @@ static void fetch(gmt_hierarchy* h, const double* dev, double* host, int n) {
 
 // ------------------------------------------------------------------ smoother / V-cycle
 // smooth `sweeps` times on level l from *u (or zero); the result pointer is returned in *u
-// (it alternates between the level's two buffers)
+// (it alternates between the level's two buffers). part (level 0, zero == false): the last
+// sweep also writes [blocks][M + C] partials of f . u and the sums of u (fused).
 static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** u, void** other,
-                   int sweeps, bool zero) {
+                   int sweeps, bool zero, double* part = nullptr) {
   const gmt_options& o = h->opts;
   const Prec pr = w->prec;
   if (sweeps <= 0) {
@@ -166,6 +182,7 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
       a.f = f;
       a.out = *other;
       a.omega = o.omega;
+      if (s + 1 == sweeps) a.part = part;
       launch_stencil(h, l, pr, ST_JACOBI, a);
       std::swap(*u, *other);
     }
@@ -190,6 +207,7 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
     a.dout = d;
     a.c1 = 0.0;
     a.c2 = 1.0 / theta;
+    if (sweeps == 1) a.part = part;
     launch_stencil(h, l, pr, ST_CHEB, a);
     std::swap(*u, *other);
     s0 = 1;
@@ -204,6 +222,7 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
     a.dout = (s + 1 < sweeps) ? d : nullptr;
     a.c1 = rho_new * rho;
     a.c2 = 2.0 * rho_new / delta;
+    if (s + 1 == sweeps) a.part = part;
     launch_stencil(h, l, pr, ST_CHEB, a);
     std::swap(*u, *other);
     rho = rho_new;
@@ -212,7 +231,10 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
 
 // One V-cycle on level l for K_l u = f (u zero on entry when zero == true). Returns the
 // buffer that holds the result: one of the level's two ping-pong buffers (level 0: ua/ub).
-static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* u_init, bool zero) {
+// part (level 0, nu_post >= 1): the last post-smoothing sweep writes [blocks][M + C]
+// partials of f . u and the sums of u (see smooth()).
+static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* u_init, bool zero,
+                    double* part = nullptr) {
   const Prec pr = w->prec;
   if (l == h->L - 1) {
     launch_coarse_solve(h, pr, f, w->ua[l]);
@@ -229,7 +251,7 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
   launch_restrict(h, l, pr, w->r[l], w->f[l + 1]);
   void* uc = vcycle(h, w, l + 1, w->f[l + 1], nullptr, true);
   launch_prolong(h, l, pr, uc, u);
-  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false);
+  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false, part);
   return u;
 }
 
@@ -243,34 +265,33 @@ void estimate_lmax(gmt_hierarchy* h) {
     float* y = (float*)w->ub[l];
     k_hash_fill<<<grid_for(n, 256), 256, 0, h->stream>>>(x, h->lv[l].mask, C, n);
     GMT_LAUNCH_CHECK();
-    double lam = 0.0;
-    for (int it = 0; it < 20; ++it) {
+    // 20 power iterations on D^-1 K, each case normalised on the device (the scale
+    // 1 / ||y|| comes from the reduction's epilogue); only the last iteration is read back
+    constexpr int kIters = 20;
+    double hy[8], hx[8];
+    for (int it = 0; it < kIters; ++it) {
       VecArgs a;
       a.u = x;
       a.out = y;
       launch_stencil(h, l, P32, ST_APPLY, a);
       launch_diag(h, l, P32, y, y, nullptr, 1.0);   // y = D^-1 K x (pointwise, in place)
       vec_dot(h, l, P32, y, y, w->part);
-      double* yy = reduce_to(h, w, l, M, 0);
-      vec_dot(h, l, P32, x, y, w->part);
-      double* xy = reduce_to(h, w, l, M, 1);
-      vec_dot(h, l, P32, x, x, w->part);
-      double* xx = reduce_to(h, w, l, M, 2);
-      double hy[8], hxy[8], hx[8];
-      fetch(h, yy, hy, M);
-      fetch(h, xy, hxy, M);
-      fetch(h, xx, hx, M);
-      lam = 0.0;
-      double sc[8];
-      for (int m = 0; m < M; ++m) {
-        lam = std::max(lam, std::sqrt(hy[m] / std::max(hx[m], 1e-300)));
-        sc[m] = 1.0 / std::sqrt(std::max(hy[m], 1e-300));
+      RedEpi e;
+      e.mode = 5;
+      e.ratio = w->red + 3 * 32;
+      launch_reduce(h, w->part, h->lv[l].nb, M, w->red, e);
+      if (it + 1 == kIters) {
+        vec_dot(h, l, P32, x, x, w->part);
+        launch_reduce(h, w->part, h->lv[l].nb, M, w->red + 2 * 32);
+        fetch(h, w->red, hy, M);
+        fetch(h, w->red + 2 * 32, hx, M);
+        break;
       }
-      GMT_CUDA(cudaMemcpyAsync(w->red + 3 * 32, sc, M * sizeof(double), cudaMemcpyHostToDevice,
-                               h->stream));
       vec_scale_cases(h, l, P32, w->red + 3 * 32, y);
       std::swap(x, y);
     }
+    double lam = 0.0;
+    for (int m = 0; m < M; ++m) lam = std::max(lam, std::sqrt(hy[m] / std::max(hx[m], 1e-300)));
     h->lv[l].lmax = lam;
   }
   GMT_CUDA(cudaStreamSynchronize(h->stream));
@@ -297,19 +318,13 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   GMT_REQUIRE(pr != PBF, GMT_ERR_ARG, "BF16 inner precision is not available in this build");
   if (o.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1 && h->lv[0].lmax == 0.0) estimate_lmax(h);
   Workspace* w = workspace(h, pr);
-  const int M = h->mat.M;
+  const int M = h->mat.M, C = h->mat.C;
   const Material& mt = h->mat;
   const bool mixed = pr != P64;
   const bool krylov = o.krylov != 0;
   // ||f_m|| and the load-cancellation rule
-  const unsigned nb0 = (unsigned)h->lv[0].nb;
-  if (mt.D == 3)
-    k_fine_load<double, double, 3, 6><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
-  else
-    k_fine_load<double, double, 1, 3><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
-  GMT_LAUNCH_CHECK();
   double fn[8];
-  fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
+  load_norms2(h, fn);
   int act[8] = {0}, live[8] = {0};   // live: the case has a load; act: still iterating
   for (int m = 0; m < M; ++m) {
     fn[m] = std::sqrt(fn[m]);
@@ -319,9 +334,13 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   const bool ff_outer = mixed && tol >= 2e-6;
   double rel[8] = {0};
   // true residual of the current solution into w->rr (arith precision), norms into rel[]
+  bool zero_guess = u0 == nullptr;   // the first residual of a zero start is the load
   auto true_residual = [&]() -> double {
     double rn[8];
-    if (!mixed) {
+    if (ff_outer && zero_guess) {
+      launch_resid_ff(h, nullptr, nullptr, (float*)w->rr, w->part);
+      zero_guess = false;
+    } else if (!mixed) {
       VecArgs a;
       a.u = w->u64;
       a.out = w->rr;
@@ -363,15 +382,22 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   // recurrence and corrupt r.z versus p.Kp. Both vectors are therefore projected onto the
   // zero-mean (per component and case) subspace, where the periodic problem lives.
   double* vsums = w->red + 7 * 32 + 8;          // device sums per value (C <= 18)
+  double* alpha = w->red + 8 * 32;              // device step ratios per case
+  double* beta = w->red + 9 * 32;
+  float* vmean = (float*)(w->red + 10 * 32);    // device means per value (FP32)
   auto sum_values = [&](const void* vec) {
     double* part = w->part + h->lv[0].nb * M;    // rows beyond the per-case partials
     vec_sum_values32(h, (const float*)vec, part);
-    launch_reduce(h, part, h->lv[0].nb, h->mat.C, vsums);
+    RedEpi e;
+    e.mode = 3;
+    e.out32 = vmean;
+    e.scale = 1.0 / (double)h->lv[0].n_nodes;
+    launch_reduce(h, part, h->lv[0].nb, h->mat.C, vsums, e);
   };
   auto project = [&](void* vec) {
     if (!mixed) return;
     sum_values(vec);
-    vec_sub_mean32(h, vsums, (float*)vec);
+    vec_sub_mean32(h, vmean, (float*)vec);
   };
   int cycles = 0, updates = 0, restarts = 0;
   static const bool verbose = std::getenv("GMT_VERBOSE") != nullptr;
@@ -414,14 +440,31 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       a.part = krylov ? w->part : nullptr;
       launch_stencil(h, 0, ar, ST_APPLY, a);  // q = K p (and p.q)
       if (krylov) {
-        launch_reduce(h, w->part, h->lv[0].nb, M, pq);
-        vec_cg_update(h, ar, rz, pq, w->active, w->x, w->p, w->rr, w->q, w->part);
+        RedEpi e;
+        e.mode = 1;   // alpha = rz / pq
+        e.other = rz;
+        e.active = w->active;
+        e.ratio = alpha;
+        launch_reduce(h, w->part, h->lv[0].nb, M, pq, e);
+        vec_cg_update(h, ar, alpha, w->active, w->x, w->p, w->rr, w->q, w->part, mixed);
       } else {
-        vec_cg_update(h, ar, w->ones, w->ones, w->active, w->x, z, w->rr, w->q, w->part);
+        vec_cg_update(h, ar, w->ones, w->active, w->x, z, w->rr, w->q, w->part, mixed);
       }
-      project(w->rr);
+      double* rn_dev = w->red;
+      if (mixed) {
+        // ||r||^2 and the sums of r from the update's partials, then r loses its mean
+        launch_reduce(h, w->part, h->lv[0].nb, M, rn_dev, RedEpi(), M + C);
+        RedEpi em;
+        em.mode = 3;
+        em.out32 = vmean;
+        em.scale = 1.0 / (double)h->lv[0].n_nodes;
+        launch_reduce(h, w->part + M, h->lv[0].nb, C, vsums, em, M + C);
+        vec_sub_mean32(h, vmean, (float*)w->rr);
+      } else {
+        rn_dev = reduce_to(h, w, 0, M, 0);
+      }
       double rn[8];
-      fetch(h, reduce_to(h, w, 0, M, 0), rn, M);
+      fetch(h, rn_dev, rn, M);
       if (verbose) {
         std::fprintf(stderr, "gmt: cycle %d iterated r/|f|:", cycles);
         for (int m = 0; m < M; ++m) std::fprintf(stderr, " %.3e", std::sqrt(rn[m]) / fn[m]);
@@ -466,20 +509,38 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         deactivate_converged();
         push_active();
       }
-      z = vcycle(h, w, 0, w->rr, nullptr, true);
+      // the last post-smoothing sweep writes the partials of r.z and of the sums of z
+      const bool fused = krylov && h->L > 1 && o.nu_post >= 1;
+      z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr);
       ++cycles;
       if (krylov) {
         // rr is mean-free, so r.z needs no correction for the mean of z; the mean of z is
         // removed while forming the new direction
-        if (mixed) sum_values(z);
-        vec_dot(h, 0, ar, w->rr, z, w->part);
-        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
+        const int ld = fused ? M + C : M;
+        if (fused) {
+          if (mixed) {
+            RedEpi em;
+            em.mode = 3;
+            em.out32 = vmean;
+            em.scale = 1.0 / (double)h->lv[0].n_nodes;
+            launch_reduce(h, w->part + M, h->lv[0].nb, C, vsums, em, ld);
+          }
+        } else {
+          if (mixed) sum_values(z);
+          vec_dot(h, 0, ar, w->rr, z, w->part);
+        }
+        RedEpi e;
+        e.mode = 2;   // beta = rz_new / rz
+        e.other = rz;
+        e.active = w->active;
+        e.ratio = beta;
+        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new, e, ld);
         if (restart) {
-          if (mixed) vec_sub_mean32(h, vsums, (float*)z);
+          if (mixed) vec_sub_mean32(h, vmean, (float*)z);
           vec_copy(h, 0, ar, z, w->p);
           ++restarts;
         } else {
-          vec_cg_dir(h, ar, rz_new, rz, w->active, z, w->p, mixed ? vsums : nullptr);
+          vec_cg_dir(h, ar, beta, z, w->p, mixed ? vmean : nullptr);
         }
         GMT_CUDA(cudaMemcpyAsync(rz, rz_new, M * sizeof(double), cudaMemcpyDeviceToDevice,
                                  h->stream));
@@ -489,15 +550,26 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   // gauge: remove the mean of every component and case over active nodes
   {
     const int C = mt.C;
-    if (!mixed) vec_sum_values(h, 0, P64, w->u64, nullptr, w->part);
-    else vec_sum_values(h, 0, P32, w->hi, w->lo, w->part);
-    double* sums = reduce_to(h, w, 0, C, 1);
-    double hs[18];
-    fetch(h, sums, hs, C);
-    for (int v = 0; v < C; ++v) hs[v] /= (double)h->lv[0].n_nodes;
-    GMT_CUDA(cudaMemcpyAsync(w->red + 2 * 32, hs, C * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (!mixed) vec_sub_mean64(h, 0, w->red + 2 * 32, w->u64);
-    else vec_ff_sub_mean(h, w->red + 2 * 32, w->hi, w->lo);
+    if (!mixed) {
+      vec_sum_values(h, 0, P64, w->u64, nullptr, w->part);
+      double* sums = reduce_to(h, w, 0, C, 1);
+      double hs[18];
+      fetch(h, sums, hs, C);
+      for (int v = 0; v < C; ++v) hs[v] /= (double)h->lv[0].n_nodes;
+      GMT_CUDA(cudaMemcpyAsync(w->red + 2 * 32, hs, C * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream));
+      vec_sub_mean64(h, 0, w->red + 2 * 32, w->u64);
+    } else {
+      // float-float sums and means formed on the device (no host round trip)
+      vec_sum_ff(h, w->hi, w->lo, w->part);
+      RedEpi e;
+      e.mode = 4;
+      e.out32 = (float*)(w->red + 11 * 32);
+      e.scale = 1.0 / (double)h->lv[0].n_nodes;
+      e.count = C;
+      launch_reduce(h, w->part, h->lv[0].nb, C, w->red + 32, e);
+      vec_ff_sub_mean(h, (const float*)(w->red + 11 * 32), w->hi, w->lo);
+    }
   }
   if (u_out) {
     if (!mixed) slots_to_canon(h, 0, P64, w->u64, u_out);
@@ -547,14 +619,8 @@ void residual_of(gmt_hierarchy* h, int precision, const double* u, double* out) 
   const Material& mt = h->mat;
   const int M = mt.M;
   Workspace* w = workspace(h, h->ws ? (Prec)h->ws_for_prec : P32);
-  const unsigned nb0 = (unsigned)h->lv[0].nb;
-  if (mt.D == 3)
-    k_fine_load<double, double, 3, 6><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
-  else
-    k_fine_load<double, double, 1, 3><<<nb0, 64, 0, h->stream>>>(h->lv[0].mask, w->f64, w->part, mt);
-  GMT_LAUNCH_CHECK();
   double fn[8], rn[8];
-  fetch(h, reduce_to(h, w, 0, M, 7), fn, M);
+  load_norms2(h, fn);
   if (precision == GMT_PREC_FP64) {
     canon_to_slots(h, 0, P64, u, w->u64);
     VecArgs a;

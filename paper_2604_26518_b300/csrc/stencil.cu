@@ -49,24 +49,40 @@ template <typename T> struct ArithOf { using type = float; };
 template <> struct ArithOf<double> { using type = double; };
 
 // ------------------------------------------------------------------ block reduction helper
-// 64-thread block: reduce K values per thread into out[K] (fixed order). Lanes and warps
-// reduce in the values' own type T (FP32 kernels keep FP64 off the per-element path, where
-// B300's FP64 rate is 1/64 of FP32); the two warp sums are combined in FP64.
+// 64-thread block: reduce K <= 32 values per thread into out[K] (fixed order). Each warp
+// reduces all K values at once by a transposing butterfly: with the values padded to
+// P = 2^p >= K, the step at lane offset o halves the values a lane holds (it keeps one half
+// and adds its partner's copy of that half, received for the other), so after p steps each
+// lane holds one column summed over P lanes; plain xor steps finish the sum over the warp.
+// That is P - 1 + (5 - p) shuffles instead of 5 K. Lanes and warps add in the values' own
+// type T (FP32 kernels keep FP64 off the per-element path, where B300's FP64 rate is 1/64
+// of FP32); the two warp sums are combined in FP64.
 template <int K, typename T>
 __device__ __forceinline__ void block_partial_64(T (&v)[K], double* __restrict__ out) {
-  __shared__ double red[2][K > 0 ? K : 1];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    v[k] = x;
-  }
+  static_assert(K >= 1 && K <= 32, "at most 32 values per thread");
+  constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  constexpr int LP = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;
+  __shared__ double red[2][P];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
+  T x[P];
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[w][k] = (double)v[k];
+  for (int i = 0; i < P; ++i) x[i] = i < K ? v[i] : T(0);
+  int col = 0;
+#pragma unroll
+  for (int s = 0; s < LP; ++s) {
+    const int h = P >> (s + 1), o = 16 >> s;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? x[i] : x[i + h];
+      const T keep = up ? x[i + h] : x[i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (up) col += h;
   }
+#pragma unroll
+  for (int o = 16 >> LP; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+  if ((lane & ((32 >> LP) - 1)) == 0) red[w][col] = (double)x[0];
   __syncthreads();
   if (threadIdx.x < K) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
 }
@@ -198,7 +214,10 @@ __device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, 
 // product accurate (about 20x closer to the FP64 product than the direct form on V-cycle
 // output). It annihilates translations exactly, so the mixed-precision solver keeps its
 // residual and preconditioned directions free of translations (see solver.cu).
-template <typename TS, typename A, int D, int M, int KIND, int MODE>
+// SUMS (smoother modes): also write per-block partials [M + C] of f . out per case and of
+// out per value over active nodes (the V-cycle's last sweep: r.z and the mean of z for the
+// Krylov step, without another pass over the vectors).
+template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS = false>
 __global__ void __launch_bounds__(64)
     k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
   using V = typename Vec16<A>::type;
@@ -348,26 +367,43 @@ __global__ void __launch_bounds__(64)
         for (int k = 0; k < DD; ++k) Iv[k] = p.dinv[slot * DD + k];
       }
     }
+    A sums[SUMS ? M + C : 1];
+    if constexpr (SUMS) {
+#pragma unroll
+      for (int k = 0; k < M + C; ++k) sums[k] = A(0);
+    }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      A r[D];
+      A fv[D], r[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) r[i] = load_as<A>(p.f + base + (i * M + m) * 64) - acc[i * M + m];
+      for (int i = 0; i < D; ++i) {
+        fv[i] = load_as<A>(p.f + base + (i * M + m) * 64);
+        r[i] = fv[i] - acc[i * M + m];
+      }
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         A z = A(0);
 #pragma unroll
         for (int j = 0; j < D; ++j) z += Iv[i * D + j] * r[j];
         const int v = i * M + m;
+        A o;
         if constexpr (MODE == ST_JACOBI) {
-          p.out[base + v * 64] = store_as<TS>(mk ? self[v] + p.omega * z : A(0));
+          o = mk ? self[v] + p.omega * z : A(0);
         } else {
           const A dn = (p.c1 != A(0) ? p.c1 * load_as<A>(p.dprev + base + v * 64) : A(0)) + p.c2 * z;
-          p.out[base + v * 64] = store_as<TS>(mk ? self[v] + dn : A(0));
+          o = mk ? self[v] + dn : A(0);
           if (p.dout) p.dout[base + v * 64] = store_as<TS>(mk ? dn : A(0));
+        }
+        const TS os = store_as<TS>(o);
+        p.out[base + v * 64] = os;
+        if constexpr (SUMS) {
+          const A ov = load_as<A>(&os);   // the stored value
+          sums[m] += mk ? fv[i] * ov : A(0);
+          sums[M + v] += ov;
         }
       }
     }
+    if constexpr (SUMS) block_partial_64<M + C, A>(sums, p.part + b * (M + C));
   }
 }
 
@@ -478,21 +514,24 @@ struct FFArgs {
 // each difference formed as (hi_{n+d} - hi_n) + (lo_{n+d} - lo_n) in FP32: the differences
 // of a smooth field are O(1) while u itself grows with N, so FP32 arithmetic on them keeps
 // the residual accurate to ~1e-7 of the load without FP64 instructions.
-template <int D, int M>
+// ZERO: u = 0 (a zero start), r = f without staging or the stencil.
+template <int D, int M, bool ZERO>
 __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<D, M> p) {
   using V = float4;
   constexpr int C = D * M, R = 8 * D, G = (C + 3) / 4;
-  __shared__ V th[G * 216];
-  __shared__ V tl[G * 216];
+  __shared__ V th[ZERO ? 1 : G * 216];
+  __shared__ V tl[ZERO ? 1 : G * 216];
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
-  if (t < 27) nb[t] = p.nbr[b * 27 + t];
-  __syncthreads();
   float sh[C], sl[C];
-  stage_tile<float, float, C>(p.hi, b, t, nb, th, sh);
-  stage_tile<float, float, C>(p.lo, b, t, nb, tl, sl);
-  __syncthreads();
+  if constexpr (!ZERO) {
+    if (t < 27) nb[t] = p.nbr[b * 27 + t];
+    __syncthreads();
+    stage_tile<float, float, C>(p.hi, b, t, nb, th, sh);
+    stage_tile<float, float, C>(p.lo, b, t, nb, tl, sl);
+    __syncthreads();
+  }
   const int q0 = own_q0(t), loc = own_local(t);
   const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
@@ -500,7 +539,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   float acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = 0.f;
-  if (mk) {
+  if (!ZERO && mk) {
     float bf[8];
 #pragma unroll
     for (int a = 0; a < 8; ++a) bf[a] = ((mk >> a) & 1u) ? 1.f : 0.f;
@@ -646,12 +685,48 @@ __global__ void k_prolong(const TS* __restrict__ uc, TS* __restrict__ uf, LvView
 // ------------------------------------------------------------------ coarsest solve
 template <typename TS, int D, int M>
 __global__ void k_coarse_gather(const TS* __restrict__ f, const int* __restrict__ canon_slot,
-                                int64_t nn, double* __restrict__ bvec) {
+                                int64_t nn, double* __restrict__ bvec, float* __restrict__ b32) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nn * D * M) return;
   const int64_t i = g / (D * M);
   const int v = (int)(g % (D * M));
-  bvec[g] = (double)load_as<typename ArithOf<TS>::type>(f + vaddr(canon_slot[i], v, D * M));
+  const auto x = load_as<typename ArithOf<TS>::type>(f + vaddr(canon_slot[i], v, D * M));
+  bvec[g] = (double)x;
+  if (b32) b32[g] = (float)x;
+}
+
+// FP32 product with the FP32 generalized inverse: u[r][m] = sum_k X[r][k] b[k][m]
+// (+ add[r][m]); one warp per row, lanes over k in a fixed stride, fixed shuffle tree
+template <int M>
+__global__ void __launch_bounds__(256) k_coarse_gemv32(const float* __restrict__ X,
+                                                       const float* __restrict__ b32,
+                                                       int64_t mrows,
+                                                       const double* __restrict__ add,
+                                                       double* __restrict__ uvec) {
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= mrows) return;   // whole warp
+  float acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = 0.f;
+  const float* xr = X + r * mrows;
+#pragma unroll 4
+  for (int64_t k = lane; k < mrows; k += 32) {
+    const float a = xr[k];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += a * b32[k * M + m];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    float x = acc[m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    acc[m] = x;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) uvec[r * M + m] = (add ? add[r * M + m] : 0.0) + (double)acc[m];
+  }
 }
 
 // u[r][m] = sum_k X[r][k] b[k][m] (+ u0[r][m]); one block per row r, fixed-order tree per
@@ -690,7 +765,7 @@ __global__ void k_coarse_gemv(const TX* __restrict__ X, const double* __restrict
 template <int M>
 __global__ void k_coarse_resid(const double* __restrict__ A, const double* __restrict__ uvec,
                                const double* __restrict__ bvec, int64_t mrows,
-                               double* __restrict__ res) {
+                               double* __restrict__ res, float* __restrict__ res32) {
   const int64_t r = blockIdx.x;
   double acc[M];
 #pragma unroll
@@ -711,7 +786,11 @@ __global__ void k_coarse_resid(const double* __restrict__ A, const double* __res
     }
     __syncthreads();
   }
-  if (threadIdx.x < M) res[r * M + threadIdx.x] = bvec[r * M + threadIdx.x] - sh[threadIdx.x][0];
+  if (threadIdx.x < M) {
+    const double v = bvec[r * M + threadIdx.x] - sh[threadIdx.x][0];
+    res[r * M + threadIdx.x] = v;
+    if (res32) res32[r * M + threadIdx.x] = (float)v;
+  }
 }
 
 template <typename TS, int D, int M>
@@ -747,13 +826,28 @@ struct EnArgs {
 //     E_IJ - C0_IJ = d^I . K_e d^J - f^I . d^J - d^I . f^J,      f = K_e x0,
 // with K_e and f split into FP32 hi + lo parts; C0_IJ (exact) is added once per element in
 // FP64 on the host side (n_e C0).
+// One thread per element: its d (or w) for every case goes to a thread-private column of
+// shared memory, then each case J forms z = K_e d^J once and dots it with d^I for I <= J.
+// The per-pair sums live in shared memory (runtime J, no local-memory arrays); they reuse
+// the space of the staged tiles once d is formed.
+template <typename A, int D, int M, bool FF>
+constexpr size_t energy_smem_bytes() {
+  constexpr int C = D * M, NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  return (size_t)(FF ? 2 : 1) * G * 216 * 16 + (size_t)8 * D * M * 64 * sizeof(A);
+}
+
 template <typename A, int D, int M, bool FF>
 __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
   constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
-  __shared__ V th[G * 216];
-  __shared__ V tl[FF ? G * 216 : 1];
+  static_assert((size_t)K * 64 * 8 <= (size_t)(FF ? 2 : 1) * G * 216 * 16,
+                "pair sums must fit in the tile space");
+  extern __shared__ __align__(16) unsigned char en_smem[];
+  V* th = reinterpret_cast<V*>(en_smem);
+  V* tl = th + G * 216;                                              // FF only
+  A* ws = reinterpret_cast<A*>(en_smem + (size_t)(FF ? 2 : 1) * G * 216 * 16);  // [R*M][64]
+  double* es = reinterpret_cast<double*>(en_smem);                   // [K][64], after phase 1
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
@@ -766,99 +860,184 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
   }
   __syncthreads();
   const int q0 = own_q0(t), loc = own_local(t);
-  const unsigned mk = p.mask[b * 64 + loc];
-  double e[K];
+  const bool act = (p.mask[b * 64 + loc] & 1u) != 0;  // element with origin at this node
+  // phase 1: d (FF) or w = x0 - d (FP64) of this element, every dof r and case m
+  if (act) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) e[k] = 0.0;
-  if (mk & 1u) {  // element with origin at this node is active
-    auto tv = [&](const V* tile, int v, int q) -> A {
-      return vec_get<A>(tile[(v / NV) * 216 + q], v % NV);
-    };
-    auto dval = [&](int r, int I) -> A {  // d^I at element dof r = (node bb, component i)
-      const int bb = r / D, i = r % D;
+    for (int bb = 0; bb < 8; ++bb) {
       const int q = q0 + (bb & 1) + 6 * ((bb >> 1) & 1) + 36 * (bb >> 2);
-      const int v = i * M + I;
-      A du = tv(th, v, q) - tv(th, v, q0);
-      if constexpr (FF) du += tv(tl, v, q) - tv(tl, v, q0);
-      return du;
-    };
-#pragma unroll 1
-    for (int J = 0; J < M; ++J) {
-      A w[R], z[R];
-      if constexpr (FF) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = dval(r, J);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          A shi = A(0), slo = A(0);
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            shi += p.Ke[r * R + c] * w[c];
-            slo += p.Kl[r * R + c] * w[c];
-          }
-          z[r] = shi + slo;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = p.X0[r * M + J] - dval(r, J);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          A sacc = A(0);
-#pragma unroll
-          for (int c = 0; c < R; ++c) sacc += p.Ke[r * R + c] * w[c];
-          z[r] = sacc;
-        }
-      }
-#pragma unroll 1
-      for (int I = 0; I <= J; ++I) {
-        A sacc = A(0);
+      for (int g = 0; g < G; ++g) {
+        const V a = th[g * 216 + q], a0 = th[g * 216 + q0];
+        V l = a, l0 = a0;
         if constexpr (FF) {
-          A fd = A(0), df = A(0);   // f^I . d^J and d^I . f^J
+          l = tl[g * 216 + q];
+          l0 = tl[g * 216 + q0];
+        }
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const A dI = dval(r, I);
-            sacc += dI * z[r];
-            fd += (p.Fh[r * M + I] + p.Fl[r * M + I]) * w[r];
-            df += dI * (p.Fh[r * M + J] + p.Fl[r * M + J]);
+        for (int k = 0; k < NV; ++k) {
+          const int v = g * NV + k;
+          if (v < C) {
+            const int r = (v / M) + D * bb, m = v % M;
+            A du = vec_get<A>(a, k) - vec_get<A>(a0, k);
+            if constexpr (FF) {
+              du += vec_get<A>(l, k) - vec_get<A>(l0, k);
+              ws[(r * M + m) * 64 + t] = du;
+            } else {
+              ws[(r * M + m) * 64 + t] = p.X0[r * M + m] - du;
+            }
           }
-          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)sacc - (double)fd - (double)df;
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) sacc += (p.X0[r * M + I] - dval(r, I)) * z[r];
-          e[I * M - I * (I - 1) / 2 + (J - I)] += (double)sacc;
         }
       }
     }
   }
+  __syncthreads();  // tiles dead: es takes their space
+  if (act) {
+    // phase 2 (FF): the load terms f^I . d^J + f^J . d^I, kept as the pair's start value
+    if constexpr (FF) {
+      A phi[M][M];
+#pragma unroll
+      for (int J = 0; J < M; ++J) {
+        A d[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r] = ws[(r * M + J) * 64 + t];
+#pragma unroll
+        for (int I = 0; I < M; ++I) {
+          A sh = A(0), sl = A(0);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            sh += p.Fh[r * M + I] * d[r];
+            sl += p.Fl[r * M + I] * d[r];
+          }
+          phi[I][J] = sh + sl;
+        }
+      }
+#pragma unroll
+      for (int I = 0; I < M; ++I)
+#pragma unroll
+        for (int J = I; J < M; ++J)
+          es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t] = (double)phi[I][J] + (double)phi[J][I];
+    }
+    // phase 3: z = K_e d^J (hi + lo in FF), pair sums d^I . z for I <= J
+#pragma unroll 1
+    for (int J = 0; J < M; ++J) {
+      A w[R], z[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) w[r] = ws[(r * M + J) * 64 + t];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        A shi = A(0), slo = A(0);
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          shi += p.Ke[r * R + c] * w[c];
+          if constexpr (FF) slo += p.Kl[r * R + c] * w[c];
+        }
+        z[r] = shi + slo;
+      }
+#pragma unroll
+      for (int I = 0; I < M; ++I) {
+        if (I <= J) {
+          A sacc = A(0);
+#pragma unroll
+          for (int r = 0; r < R; ++r) sacc += ws[(r * M + I) * 64 + t] * z[r];
+          double* ep = es + (I * M - I * (I - 1) / 2 + (J - I)) * 64 + t;
+          if constexpr (FF) *ep = (double)sacc - *ep;
+          else *ep = (double)sacc;
+        }
+      }
+    }
+  }
+  double e[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : 0.0;
   block_partial_64<K, double>(e, p.part + b * K);
 }
 
-// deterministic reduction of [nblk][K] partials: block k reduces column k
-// (Neumaier-compensated per thread over a fixed stride, fixed-order tree across threads)
+// deterministic reduction of [nblk][K] partials. Column k is split over gridDim.y blocks;
+// each reduces its row range (Neumaier-compensated per thread over a fixed stride, then a
+// fixed-order tree), writes (sum, compensation) to scratch, and the block that arrives last
+// (atomic ticket) combines the gridDim.y pairs in index order and runs the epilogue. The
+// result does not depend on which block arrives last; no block waits for another.
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  const double tt = s + x;
+  c += fabs(s) >= fabs(x) ? (s - tt) + x : (x - tt) + s;
+  s = tt;
+}
+
 __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part, int64_t nblk,
-                                                int K, double* __restrict__ out) {
+                                                int ld, double* __restrict__ out, RedEpi epi,
+                                                double* __restrict__ scratch,
+                                                unsigned* __restrict__ ticket) {
   __shared__ double ss[256], sc[256];
-  const int k = blockIdx.x;
+  __shared__ bool last;
+  const int k = blockIdx.x, sp = blockIdx.y, S = gridDim.y;
+  const int64_t chunk = (nblk + S - 1) / S;
+  const int64_t lo = (int64_t)sp * chunk;
+  const int64_t hi = lo + chunk < nblk ? lo + chunk : nblk;
   double s = 0.0, c = 0.0;
-  for (int64_t i = threadIdx.x; i < nblk; i += 256) {
-    const double x = part[i * K + k];
-    const double tt = s + x;
-    c += fabs(s) >= fabs(x) ? (s - tt) + x : (x - tt) + s;
-    s = tt;
+  for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += 256 * 4) {
+    double x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + (int64_t)j * 256;
+      x[j] = i < hi ? part[i * ld + k] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) neumaier(s, c, x[j]);
   }
   ss[threadIdx.x] = s;
   sc[threadIdx.x] = c;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      const double a = ss[threadIdx.x], x = ss[threadIdx.x + o];
-      const double tt = a + x;
-      sc[threadIdx.x] += sc[threadIdx.x + o] + (fabs(a) >= fabs(x) ? (a - tt) + x : (x - tt) + a);
-      ss[threadIdx.x] = tt;
+      double a = ss[threadIdx.x], ca = sc[threadIdx.x] + sc[threadIdx.x + o];
+      neumaier(a, ca, ss[threadIdx.x + o]);
+      ss[threadIdx.x] = a;
+      sc[threadIdx.x] = ca;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[k] = ss[0] + sc[0];
+  if (threadIdx.x == 0) {
+    if (S == 1) {
+      last = true;
+    } else {
+      scratch[((int64_t)k * S + sp) * 2] = ss[0];
+      scratch[((int64_t)k * S + sp) * 2 + 1] = sc[0];
+      __threadfence();
+      last = atomicAdd(&ticket[k], 1u) == (unsigned)(S - 1);
+    }
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  double v;
+  if (S == 1) {
+    v = ss[0] + sc[0];
+  } else {
+    __threadfence();
+    double a = 0.0, ca = 0.0;
+    for (int j = 0; j < S; ++j) {
+      ca += __ldcg(&scratch[((int64_t)k * S + j) * 2 + 1]);
+      neumaier(a, ca, __ldcg(&scratch[((int64_t)k * S + j) * 2]));
+    }
+    v = a + ca;
+    ticket[k] = 0u;  // ready for the next launch on this stream
+  }
+  out[k] = v;
+  const bool act = epi.active == nullptr || epi.active[k] != 0;
+  if (epi.mode == 1) {
+    epi.ratio[k] = (act && v != 0.0) ? epi.other[k] / v : 0.0;
+  } else if (epi.mode == 2) {
+    epi.ratio[k] = (act && epi.other[k] != 0.0) ? v / epi.other[k] : 0.0;
+  } else if (epi.mode == 3) {
+    epi.out32[k] = (float)(v * epi.scale);
+  } else if (epi.mode == 4) {
+    const double x = v * epi.scale;
+    const float hf = (float)x;
+    epi.out32[k] = hf;
+    epi.out32[epi.count + k] = (float)(x - (double)hf);
+  } else if (epi.mode == 5) {
+    epi.ratio[k] = 1.0 / sqrt(fmax(v, 1e-300));
+  }
 }
 
 // ------------------------------------------------------------------ vector kernels
@@ -895,62 +1074,65 @@ __global__ void __launch_bounds__(64) k_vdot(const TS* __restrict__ x, const TS*
   block_partial_64<M, A>(d, part + (int64_t)blockIdx.x * M);
 }
 
-// per-case step ratio num/den (0 for inactive cases), computed once per block
+// per-case step ratio from the device (0 for inactive cases), staged once per block
 template <typename A, int M>
-__device__ __forceinline__ void block_ratios(const double* num, const double* den,
-                                             const int* active, A* out) {
+__device__ __forceinline__ void block_ratios(const double* ratio, const int* active, A* out) {
   if (threadIdx.x < M) {
     const int m = threadIdx.x;
-    out[m] = (active[m] && den[m] != 0.0) ? (A)(num[m] / den[m]) : A(0);
+    out[m] = (active == nullptr || active[m]) ? (A)ratio[m] : A(0);
   }
   __syncthreads();
 }
 
-template <typename TS, int M, int C>
+// SUMS: partials [M + C]: ||r||^2 per case, then the sums of r per value (r is zero at
+// inactive slots)
+template <typename TS, int M, int C, bool SUMS>
 __global__ void __launch_bounds__(64)
-    k_cg_update(const double* __restrict__ num, const double* __restrict__ den,
-                const int* __restrict__ active, TS* __restrict__ x, const TS* __restrict__ pp,
-                TS* __restrict__ r, const TS* __restrict__ q, double* __restrict__ part) {
+    k_cg_update(const double* __restrict__ ratio, const int* __restrict__ active,
+                TS* __restrict__ x, const TS* __restrict__ pp, TS* __restrict__ r,
+                const TS* __restrict__ q, double* __restrict__ part) {
   using A = typename ArithOf<TS>::type;
+  constexpr int K = SUMS ? M + C : M;
   __shared__ A alpha[M];
-  block_ratios<A, M>(num, den, active, alpha);
+  block_ratios<A, M>(ratio, active, alpha);
   const int64_t base = (int64_t)blockIdx.x * 64 * C + threadIdx.x;
-  A nr[M];
+  A nr[K];
 #pragma unroll
-  for (int m = 0; m < M; ++m) nr[m] = A(0);
+  for (int k = 0; k < K; ++k) nr[k] = A(0);
 #pragma unroll
   for (int v = 0; v < C; ++v) {
     const A al = alpha[v % M];
     const int64_t a = base + v * 64;
     x[a] = store_as<TS>(load_as<A>(x + a) + al * load_as<A>(pp + a));
-    const A rn = load_as<A>(r + a) - al * load_as<A>(q + a);
-    r[a] = store_as<TS>(rn);
+    const TS rs = store_as<TS>(load_as<A>(r + a) - al * load_as<A>(q + a));
+    r[a] = rs;
+    const A rn = load_as<A>(&rs);
     nr[v % M] += rn * rn;
+    if constexpr (SUMS) nr[M + v] += rn;
   }
-  block_partial_64<M, A>(nr, part + (int64_t)blockIdx.x * M);
+  block_partial_64<K, A>(nr, part + (int64_t)blockIdx.x * K);
 }
 
+// one block per brick: p = (z - zmean) + beta p, the mean removed at active slots only
 template <typename TS, int M, int C>
-__global__ void __launch_bounds__(256) k_cg_dir(const double* __restrict__ num,
-                                                const double* __restrict__ den,
-                                                const int* __restrict__ active,
-                                                const TS* __restrict__ z, TS* __restrict__ pp,
-                                                int64_t n, const double* __restrict__ zsum,
-                                                double inv_n, const uint8_t* __restrict__ mask) {
+__global__ void __launch_bounds__(64) k_cg_dir(const double* __restrict__ ratio,
+                                               const TS* __restrict__ z, TS* __restrict__ pp,
+                                               const float* __restrict__ zmean,
+                                               const uint8_t* __restrict__ mask) {
   using A = typename ArithOf<TS>::type;
   __shared__ A beta[M];
-  __shared__ A zmean[C];
-  block_ratios<A, M>(num, den, active, beta);
-  if (zsum != nullptr) {
-    if (threadIdx.x < C) zmean[threadIdx.x] = (A)(zsum[threadIdx.x] * inv_n);
-    __syncthreads();
+  block_ratios<A, M>(ratio, nullptr, beta);
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  const bool sub = zmean != nullptr && mask[b * 64 + t] != 0;
+  const int64_t base = b * 64 * C + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int64_t a = base + v * 64;
+    A zv = load_as<A>(z + a);
+    if (sub) zv -= (A)zmean[v];
+    pp[a] = store_as<TS>(zv + beta[v % M] * load_as<A>(pp + a));
   }
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int v = (int)((i >> 6) % C);
-  A zv = load_as<A>(z + i);
-  if (zsum != nullptr && mask[((i >> 6) / C) * 64 + (i & 63)]) zv -= zmean[v];
-  pp[i] = store_as<TS>(zv + beta[v % M] * load_as<A>(pp + i));
 }
 
 // float-float accumulate (hi, lo) += d with Knuth's TwoSum and a fast renormalisation
@@ -968,26 +1150,61 @@ __global__ void k_ff_add(const float* __restrict__ d, float* __restrict__ hi,
   lo[i] = l - (h2 - s);
 }
 
-// float-float minus a double mean, with the mean split into two floats
+// float-float minus a mean given as float pairs, one block per brick, active slots only
 template <int C>
-__global__ void k_ff_sub_mean(const double* __restrict__ mean, const uint8_t* __restrict__ mask,
-                              float* __restrict__ hi, float* __restrict__ lo, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
-  if (!mask[slot]) return;
-  const int v = (int)((i >> 6) % C);
-  const double mu = mean[v];
-  const float mh = (float)mu;
-  const float ml = (float)(mu - (double)mh);
-  const float a = hi[i], b = -mh;
-  const float s = a + b;
-  const float bb = s - a;
-  const float err = (a - (s - bb)) + (b - bb);
-  const float l = lo[i] - ml + err;
-  const float h2 = s + l;
-  hi[i] = h2;
-  lo[i] = l - (h2 - s);
+__global__ void __launch_bounds__(64) k_ff_sub_mean(const float* __restrict__ mean,
+                                                    const uint8_t* __restrict__ mask,
+                                                    float* __restrict__ hi,
+                                                    float* __restrict__ lo) {
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  if (!mask[b * 64 + t]) return;
+  const int64_t base = b * 64 * C + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    const int64_t i = base + v * 64;
+    const float a = hi[i], bm = -mean[v];
+    const float s = a + bm;
+    const float bb = s - a;
+    const float err = (a - (s - bb)) + (bm - bb);
+    const float l = lo[i] - mean[C + v] + err;
+    const float h2 = s + l;
+    hi[i] = h2;
+    lo[i] = l - (h2 - s);
+  }
+}
+
+// per-block sums of hi + lo per value over active slots: lanes and warps reduce float-float
+// pairs (TwoSum), the two warp sums are combined in FP64
+template <int C>
+__global__ void __launch_bounds__(64) k_sum_ff(const float* __restrict__ hi,
+                                               const float* __restrict__ lo,
+                                               const uint8_t* __restrict__ mask,
+                                               double* __restrict__ part) {
+  __shared__ double red[2][C];
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  const bool act = mask[b * 64 + t] != 0;
+  const int64_t base = b * 64 * C + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    float sh = act ? hi[base + v * 64] : 0.f;
+    float sl = act ? lo[base + v * 64] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, sh, o);
+      const float ol = __shfl_down_sync(0xffffffffu, sl, o);
+      const float s = sh + oh;
+      const float bb = s - sh;
+      const float err = (sh - (s - bb)) + (oh - bb);
+      const float l = sl + ol + err;
+      sh = s + l;
+      sl = l - (sh - s);
+    }
+    if ((t & 31) == 0) red[t >> 5][v] = (double)sh + (double)sl;
+  }
+  __syncthreads();
+  if (t < C) part[b * C + t] = red[0][t] + red[1][t];
 }
 
 template <typename TS, int C>
@@ -1023,13 +1240,15 @@ __global__ void __launch_bounds__(64) k_sum_values32(const float* __restrict__ x
 }
 
 template <int C>
-__global__ void k_sub_mean32(const double* __restrict__ sums, double inv_n,
-                             const uint8_t* __restrict__ mask, float* __restrict__ x, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t slot = ((i >> 6) / C) * 64 + (i & 63);
-  if (!mask[slot]) return;
-  x[i] -= (float)(sums[(i >> 6) % C] * inv_n);
+__global__ void __launch_bounds__(64) k_sub_mean32(const float* __restrict__ mean,
+                                                   const uint8_t* __restrict__ mask,
+                                                   float* __restrict__ x) {
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  if (!mask[b * 64 + t]) return;
+  float* xb = x + b * 64 * C + t;
+#pragma unroll
+  for (int v = 0; v < C; ++v) xb[v * 64] -= mean[v];
 }
 
 template <int C>
@@ -1165,11 +1384,20 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   }
   TraceScope ts(&h->tracer, s, cat, (double)lv.n_nodes * nvec * D * M * sizeof(TS));
 #define GMT_ST(KIND, MODE) k_stencil<TS, A, D, M, KIND, MODE><<<g, 64, 0, s>>>(p)
+  const bool sums = fine && va.part != nullptr;   // smoother modes: fused r.z and sums of z
   switch (mode) {
     case ST_APPLY: if (fine) GMT_ST(0, ST_APPLY); else GMT_ST(1, ST_APPLY); break;
     case ST_RESID: if (fine) GMT_ST(0, ST_RESID); else GMT_ST(1, ST_RESID); break;
-    case ST_JACOBI: if (fine) GMT_ST(0, ST_JACOBI); else GMT_ST(1, ST_JACOBI); break;
-    case ST_CHEB: if (fine) GMT_ST(0, ST_CHEB); else GMT_ST(1, ST_CHEB); break;
+    case ST_JACOBI:
+      if (sums) k_stencil<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
+      else if (fine) GMT_ST(0, ST_JACOBI);
+      else GMT_ST(1, ST_JACOBI);
+      break;
+    case ST_CHEB:
+      if (sums) k_stencil<TS, A, D, M, 0, ST_CHEB, true><<<g, 64, 0, s>>>(p);
+      else if (fine) GMT_ST(0, ST_CHEB);
+      else GMT_ST(1, ST_CHEB);
+      break;
   }
 #undef GMT_ST
   GMT_LAUNCH_CHECK();
@@ -1233,7 +1461,8 @@ static void resid_ff_t(gmt_hierarchy* h, const float* hi, const float* lo, float
   p.part = part;
   fill_fine<float, D, M>(h->mat, p.fc);
   TraceScope ts(&h->tracer, h->stream, TR_OUTER, (double)lv.n_nodes * 3 * D * M * sizeof(float));
-  k_resid_ff<D, M><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  if (hi == nullptr) k_resid_ff<D, M, true><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  else k_resid_ff<D, M, false><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
   GMT_LAUNCH_CHECK();
 }
 
@@ -1275,20 +1504,22 @@ static void coarse_t(gmt_hierarchy* h, const void* f, void* u) {
   const unsigned rows = (unsigned)h->m;
   if constexpr (sizeof(TS) == 8) build_coarse_inverse64(h);
   TraceScope ts(&h->tracer, h->stream, TR_CSOLVE, (double)h->m * h->m * 8.0);
-  k_coarse_gather<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>((const TS*)f, c.canon_slot,
-                                                                       c.n_nodes, h->cb);
+  constexpr bool f64 = sizeof(TS) == 8;
+  k_coarse_gather<TS, D, M><<<grid_for(cnt, 256), 256, 0, h->stream>>>(
+      (const TS*)f, c.canon_slot, c.n_nodes, h->cb, f64 ? nullptr : h->cb32);
   GMT_LAUNCH_CHECK();
-  if constexpr (sizeof(TS) == 8) {
+  if constexpr (f64) {
     // all-FP64 path: exact inverse
     k_coarse_gemv<double, M><<<rows, 128, 0, h->stream>>>(h->Ainv, h->cb, h->m, nullptr, h->cu);
     GMT_LAUNCH_CHECK();
   } else {
-    // u = X f, then one FP64 refinement u += X (f - A u) against the FP64 matrix
-    k_coarse_gemv<float, M><<<rows, 128, 0, h->stream>>>(h->X32, h->cb, h->m, nullptr, h->cu);
+    // u = X f (FP32), then one refinement u += X (f - A u) with the residual in FP64
+    const unsigned g8 = (unsigned)((h->m + 7) / 8);
+    k_coarse_gemv32<M><<<g8, 256, 0, h->stream>>>(h->X32, h->cb32, h->m, nullptr, h->cu);
     GMT_LAUNCH_CHECK();
-    k_coarse_resid<M><<<rows, 128, 0, h->stream>>>(h->A64, h->cu, h->cb, h->m, h->cr);
+    k_coarse_resid<M><<<rows, 128, 0, h->stream>>>(h->A64, h->cu, h->cb, h->m, h->cr, h->cb32);
     GMT_LAUNCH_CHECK();
-    k_coarse_gemv<float, M><<<rows, 128, 0, h->stream>>>(h->X32, h->cr, h->m, h->cu, h->cu);
+    k_coarse_gemv32<M><<<g8, 256, 0, h->stream>>>(h->X32, h->cb32, h->m, h->cu, h->cu);
     GMT_LAUNCH_CHECK();
   }
   vec_zero(h, h->L - 1, sizeof(TS) == 8 ? P64 : (sizeof(TS) == 4 ? P32 : PBF), u);
@@ -1319,8 +1550,15 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
     p.Fh[i] = (A)h->mat.Fe[i];
     p.Fl[i] = (A)(h->mat.Fe[i] - (double)p.Fh[i]);
   }
+  constexpr size_t smem = energy_smem_bytes<A, D, M, FF>();
+  static bool attr = false;   // per template instance; the attribute is per device function
+  if (!attr) {
+    GMT_CUDA(cudaFuncSetAttribute(k_energy<A, D, M, FF>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
   TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
-  k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
   GMT_LAUNCH_CHECK();
 }
 
@@ -1336,9 +1574,20 @@ void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u
   }
 }
 
-void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out) {
+void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out,
+                   RedEpi epi, int ld) {
+  if (ld <= 0) ld = K;
+  GMT_REQUIRE(K >= 1 && K <= kRedMaxCols, GMT_ERR_ARG, "reduction over %d columns", K);
+  if (h->red_scratch == nullptr) {
+    h->red_scratch = h->geo.alloc<double>(kRedMaxCols * kRedSplit * 2);
+    h->red_ticket = h->geo.alloc<unsigned>(kRedMaxCols);
+    GMT_CUDA(cudaMemsetAsync(h->red_ticket, 0, kRedMaxCols * sizeof(unsigned), h->stream));
+  }
+  // about 2048 rows per block, at most kRedSplit blocks per column
+  const int S = (int)std::min<int64_t>(kRedSplit, std::max<int64_t>(1, (nblk + 2047) / 2048));
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)nblk * K * 8.0);
-  k_reduce<<<K, 256, 0, h->stream>>>(part, nblk, K, out);
+  k_reduce<<<dim3(K, S), 256, 0, h->stream>>>(part, nblk, ld, out, epi, h->red_scratch,
+                                             h->red_ticket);
   GMT_LAUNCH_CHECK();
 }
 
@@ -1387,46 +1636,47 @@ void vec_dot(gmt_hierarchy* h, int level, Prec prec, const void* x, const void* 
 }
 
 template <typename TS, int M, int C>
-static void cgu(const double* num, const double* den, const int* act, void* x, const void* p,
-                void* r, const void* q, double* part, unsigned g, cudaStream_t s) {
-  k_cg_update<TS, M, C><<<g, 64, 0, s>>>(num, den, act, (TS*)x, (const TS*)p, (TS*)r,
-                                         (const TS*)q, part);
+static void cgu(const double* alpha, const int* act, void* x, const void* p, void* r,
+                const void* q, double* part, bool sums, unsigned g, cudaStream_t s) {
+  if (sums)
+    k_cg_update<TS, M, C, true><<<g, 64, 0, s>>>(alpha, act, (TS*)x, (const TS*)p, (TS*)r,
+                                                 (const TS*)q, part);
+  else
+    k_cg_update<TS, M, C, false><<<g, 64, 0, s>>>(alpha, act, (TS*)x, (const TS*)p, (TS*)r,
+                                                  (const TS*)q, part);
 }
 
-void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                   const int* active, void* x, const void* p, void* r, const void* q,
-                   double* part) {
+void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* alpha, const int* active,
+                   void* x, const void* p, void* r, const void* q, double* part, bool sums) {
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 6 * prec_bytes(prec));
   const unsigned g = (unsigned)h->lv[0].nb;
   if (h->mat.D == 3) {
-    if (prec == P64) cgu<double, 6, 18>(num, den, active, x, p, r, q, part, g, h->stream);
-    else cgu<float, 6, 18>(num, den, active, x, p, r, q, part, g, h->stream);
+    if (prec == P64) cgu<double, 6, 18>(alpha, active, x, p, r, q, part, sums, g, h->stream);
+    else cgu<float, 6, 18>(alpha, active, x, p, r, q, part, sums, g, h->stream);
   } else {
-    if (prec == P64) cgu<double, 3, 3>(num, den, active, x, p, r, q, part, g, h->stream);
-    else cgu<float, 3, 3>(num, den, active, x, p, r, q, part, g, h->stream);
+    if (prec == P64) cgu<double, 3, 3>(alpha, active, x, p, r, q, part, sums, g, h->stream);
+    else cgu<float, 3, 3>(alpha, active, x, p, r, q, part, sums, g, h->stream);
   }
   GMT_LAUNCH_CHECK();
 }
 
 template <typename TS, int M, int C>
-static void cgd(const double* num, const double* den, const int* act, const void* z, void* p,
-                int64_t n, cudaStream_t s, const double* zsum, double inv_n, const uint8_t* mask) {
-  k_cg_dir<TS, M, C><<<grid_for(n, 256), 256, 0, s>>>(num, den, act, (const TS*)z, (TS*)p, n,
-                                                      zsum, inv_n, mask);
+static void cgd(const double* beta, const void* z, void* p, const float* zmean,
+                const uint8_t* mask, unsigned g, cudaStream_t s) {
+  k_cg_dir<TS, M, C><<<g, 64, 0, s>>>(beta, (const TS*)z, (TS*)p, zmean, mask);
 }
 
-void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                const int* active, const void* z, void* p, const double* zsum) {
+void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* beta, const void* z, void* p,
+                const float* zmean) {
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 3 * prec_bytes(prec));
-  const int64_t n = nvals(h, 0);
-  const double inv = 1.0 / (double)h->lv[0].n_nodes;
+  const unsigned g = (unsigned)h->lv[0].nb;
   const uint8_t* mk = h->lv[0].mask;
   if (h->mat.D == 3) {
-    if (prec == P64) cgd<double, 6, 18>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
-    else cgd<float, 6, 18>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
+    if (prec == P64) cgd<double, 6, 18>(beta, z, p, nullptr, mk, g, h->stream);
+    else cgd<float, 6, 18>(beta, z, p, zmean, mk, g, h->stream);
   } else {
-    if (prec == P64) cgd<double, 3, 3>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
-    else cgd<float, 3, 3>(num, den, active, z, p, n, h->stream, zsum, inv, mk);
+    if (prec == P64) cgd<double, 3, 3>(beta, z, p, nullptr, mk, g, h->stream);
+    else cgd<float, 3, 3>(beta, z, p, zmean, mk, g, h->stream);
   }
   GMT_LAUNCH_CHECK();
 }
@@ -1438,10 +1688,19 @@ void vec_ff_add(gmt_hierarchy* h, const float* d, float* hi, float* lo) {
   GMT_LAUNCH_CHECK();
 }
 
-void vec_ff_sub_mean(gmt_hierarchy* h, const double* mean, float* hi, float* lo) {
-  const int64_t n = nvals(h, 0);
-  if (h->mat.C == 18) k_ff_sub_mean<18><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo, n);
-  else k_ff_sub_mean<3><<<grid_for(n, 256), 256, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo, n);
+void vec_ff_sub_mean(gmt_hierarchy* h, const float* mean, float* hi, float* lo) {
+  const unsigned g = (unsigned)h->lv[0].nb;
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 16.0);
+  if (h->mat.C == 18) k_ff_sub_mean<18><<<g, 64, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo);
+  else k_ff_sub_mean<3><<<g, 64, 0, h->stream>>>(mean, h->lv[0].mask, hi, lo);
+  GMT_LAUNCH_CHECK();
+}
+
+void vec_sum_ff(gmt_hierarchy* h, const float* hi, const float* lo, double* part) {
+  const unsigned g = (unsigned)h->lv[0].nb;
+  TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 8.0);
+  if (h->mat.C == 18) k_sum_ff<18><<<g, 64, 0, h->stream>>>(hi, lo, h->lv[0].mask, part);
+  else k_sum_ff<3><<<g, 64, 0, h->stream>>>(hi, lo, h->lv[0].mask, part);
   GMT_LAUNCH_CHECK();
 }
 
@@ -1467,14 +1726,11 @@ void vec_sum_values32(gmt_hierarchy* h, const float* x, double* part) {
   GMT_LAUNCH_CHECK();
 }
 
-void vec_sub_mean32(gmt_hierarchy* h, const double* sums, float* x) {
-  const int64_t n = nvals(h, 0);
-  const double inv = 1.0 / (double)h->lv[0].n_nodes;
+void vec_sub_mean32(gmt_hierarchy* h, const float* mean, float* x) {
+  const unsigned g = (unsigned)h->lv[0].nb;
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)h->lv[0].n_nodes * h->mat.C * 8.0);
-  if (h->mat.C == 18)
-    k_sub_mean32<18><<<grid_for(n, 256), 256, 0, h->stream>>>(sums, inv, h->lv[0].mask, x, n);
-  else
-    k_sub_mean32<3><<<grid_for(n, 256), 256, 0, h->stream>>>(sums, inv, h->lv[0].mask, x, n);
+  if (h->mat.C == 18) k_sub_mean32<18><<<g, 64, 0, h->stream>>>(mean, h->lv[0].mask, x);
+  else k_sub_mean32<3><<<g, 64, 0, h->stream>>>(mean, h->lv[0].mask, x);
   GMT_LAUNCH_CHECK();
 }
 

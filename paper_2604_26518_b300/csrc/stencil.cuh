@@ -16,7 +16,8 @@ struct VecArgs {
   const void* dprev = nullptr; // Chebyshev previous direction
   void* out = nullptr;
   void* dout = nullptr;
-  double* part = nullptr;      // per-block partial sums [blocks][M]
+  double* part = nullptr;      // per-block partial sums [blocks][M] (APPLY, RESID); level-0
+                               // smoother: [blocks][M + C] of f . out and sums of out
   double omega = 0, c1 = 0, c2 = 0;
 };
 
@@ -27,7 +28,8 @@ void launch_stencil(gmt_hierarchy* h, int level, Prec prec, StencilMode mode, co
 // first smoothing step from a zero guess: out = scale * D^-1 f (and dout = out if non-null)
 void launch_diag(gmt_hierarchy* h, int level, Prec prec, const void* f, void* out, void* dout,
                  double scale);
-// float-float level-0 residual r = f - K (hi + lo) in difference form, FP32 arithmetic
+// float-float level-0 residual r = f - K (hi + lo) in difference form, FP32 arithmetic;
+// hi == nullptr means u = 0 (r = f)
 void launch_resid_ff(gmt_hierarchy* h, const float* hi, const float* lo, float* r, double* part);
 // restriction level -> level+1, prolongation+correction level+1 -> level
 void launch_restrict(gmt_hierarchy* h, int level, Prec prec, const void* rf, void* fc);
@@ -40,21 +42,45 @@ void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u
 
 // deterministic fixed-order reduction of [nblk][K] partials into out[K] (device);
 // compensated (Neumaier) per thread
-void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out);
+// column reductions: at most kRedMaxCols columns, each split over at most kRedSplit blocks
+constexpr int kRedMaxCols = 32;
+constexpr int kRedSplit = 16;
+// Epilogue of a column reduction (thread 0 of the column's block), so that per-case step
+// ratios and per-value means are formed once on the device instead of in every block of
+// the vector kernel that consumes them.
+struct RedEpi {
+  int mode = 0;                  // 0: none; 1: ratio = other / out; 2: ratio = out / other;
+                                 // 3: out32 = (float)(out * scale);
+                                 // 4: out * scale split into floats: out32[k] (hi) and
+                                 //    out32[count + k] (lo);
+                                 // 5: ratio = 1 / sqrt(max(out, 1e-300))
+  const double* other = nullptr;
+  const int* active = nullptr;   // modes 1, 2: ratio 0 for inactive cases (may be null)
+  double* ratio = nullptr;
+  float* out32 = nullptr;
+  double scale = 0.0;
+  int count = 0;
+};
+// columns k < K of rows part[i * ld + k] (ld = K when <= 0)
+void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out,
+                   RedEpi epi = RedEpi(), int ld = 0);
 
 // vector kernels on slot layouts (level `level`, C values per slot)
 void vec_zero(gmt_hierarchy* h, int level, Prec prec, void* x);
 void vec_copy(gmt_hierarchy* h, int level, Prec prec, const void* src, void* dst);
 // part[b][m] = sum x.y over case m (same precision)
 void vec_dot(gmt_hierarchy* h, int level, Prec prec, const void* x, const void* y, double* part);
-// CG: alpha_m = num[m] / den[m]; x += alpha p; r -= alpha q; part = ||r||^2 per case
-void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                   const int* active, void* x, const void* p, void* r, const void* q,
-                   double* part);
-// CG: beta_m = num[m] / den[m]; p = z + beta p; with zsum (device sums of z per value over
-// active nodes) the mean of z is removed on the fly: p = (z - zsum / n) + beta p
-void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* num, const double* den,
-                const int* active, const void* z, void* p, const double* zsum = nullptr);
+// CG: x += alpha p; r -= alpha q; part = ||r||^2 per case; alpha per case from the device
+// (RedEpi mode 1), 0 where active[m] == 0. sums: part rows are [M + C], the sums of the new
+// r per value following the norms.
+void vec_cg_update(gmt_hierarchy* h, Prec prec, const double* alpha, const int* active,
+                   void* x, const void* p, void* r, const void* q, double* part,
+                   bool sums = false);
+// CG: p = z + beta p with beta per case from the device (RedEpi mode 2); with zmean (device
+// means of z per value over active nodes) the mean of z is removed on the fly:
+// p = (z - zmean) + beta p
+void vec_cg_dir(gmt_hierarchy* h, Prec prec, const double* beta, const void* z, void* p,
+                const float* zmean = nullptr);
 // per-block FP32 sums of each value of a level-0 FP32 field over active slots
 void vec_sum_values32(gmt_hierarchy* h, const float* x, double* part);
 // x += y (same precision)
@@ -62,12 +88,16 @@ void vec_add(gmt_hierarchy* h, int level, Prec prec, const void* y, void* x);
 // float-float: (hi, lo) += d
 void vec_ff_add(gmt_hierarchy* h, const float* d, float* hi, float* lo);
 // float-float: (hi, lo) -= mean[v] (double means, device)
-void vec_ff_sub_mean(gmt_hierarchy* h, const double* mean, float* hi, float* lo);
+// (hi, lo) -= mean over active slots, mean as float pairs on the device: hi parts
+// mean[0..C), lo parts mean[C..2C) (RedEpi mode 4)
+void vec_ff_sub_mean(gmt_hierarchy* h, const float* mean, float* hi, float* lo);
+// per-block float-float sums of each value of the level-0 field hi + lo over active slots
+void vec_sum_ff(gmt_hierarchy* h, const float* hi, const float* lo, double* part);
 // per-block sums of each value over active slots: part[b][C]; ff adds hi + lo
 void vec_sum_values(gmt_hierarchy* h, int level, Prec prec, const void* x, const float* lo,
                     double* part);
-// x -= sums[v] / n_active (level-0 FP32 field; sums on the device)
-void vec_sub_mean32(gmt_hierarchy* h, const double* sums, float* x);
+// x -= mean[v] over active slots (level-0 FP32 field; means on the device, RedEpi mode 3)
+void vec_sub_mean32(gmt_hierarchy* h, const float* mean, float* x);
 // x -= mean[v] (FP64 field)
 void vec_sub_mean64(gmt_hierarchy* h, int level, const double* mean, double* x);
 // scale case m of x by s[m] (device doubles)
