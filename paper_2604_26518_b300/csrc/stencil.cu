@@ -20,12 +20,42 @@
 
 namespace gmt {
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// Blackwell f32x2 arithmetic: one instruction on two FP32 values held in a 64-bit register
+// pair, each lane rounded exactly as the scalar instruction. The stencils pair the load
+// cases m = (2k, 2k + 1), which sit next to each other in the 16-byte tile groups.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {  // a * b + c
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // ------------------------------------------------------------------ parameters
 template <typename A, int D, int M>
 struct FineC {
-  A Ke[64 * D * D];  // (8D) x (8D)
-  A Fe[8 * D * M];   // K_e x0, (8D) x M
-  A Sf[27 * D * D];  // S_n(d) of a node whose 8 incident elements are all active
+  A Ke[64 * D * D];         // (8D) x (8D)
+  A Fe[8 * D * M];          // K_e x0, (8D) x M
+  A Sf[27 * D * D];         // S_n(d) of a node whose 8 incident elements are all active
+  f2_t Sf2[27 * D * D];     // FP32: Sf entries duplicated into packed pairs
 };
 
 template <typename TS, typename A, int D, int M>
@@ -242,6 +272,46 @@ __global__ void __launch_bounds__(64)
   A acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = A(0);
+  // FP32 with an even number of cases: accumulate in packed pairs of cases
+  constexpr bool PK = sizeof(A) == 4 && M % 2 == 0;
+  constexpr int H = M / 2, CP = PK ? C / 2 : 1;
+  f2_t acc2[CP], self2[CP];
+  if constexpr (PK) {
+#pragma unroll
+    for (int k = 0; k < CP; ++k) {
+      acc2[k] = 0ull;
+      self2[k] = f2_pack((float)self[2 * k], (float)self[2 * k + 1]);
+    }
+  }
+  // neighbour d's contribution with S given as packed duplicated pairs
+  auto contribute2 = [&](int d, const f2_t (&S2)[DD]) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const int q = q0 + dx + 6 * dy + 36 * dz;
+    const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
+    f2_t u2[CP];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const ulonglong2 w = t2[g * 216 + q];
+      if (2 * g < CP) u2[2 * g] = w.x;
+      if (2 * g + 1 < CP) u2[2 * g + 1] = w.y;
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+#pragma unroll
+      for (int h2 = 0; h2 < H; ++h2) {
+        f2_t x = u2[j * H + h2];
+        if constexpr (DIFF) x = f2_sub(x, self2[j * H + h2]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc2[i * H + h2] = f2_fma(S2[i * D + j], x, acc2[i * H + h2]);
+      }
+    }
+  };
+  auto contribute_s = [&](int d, const A (&S)[DD]) {
+    f2_t S2[DD];
+#pragma unroll
+    for (int k = 0; k < DD; ++k) S2[k] = f2_pack((float)S[k], (float)S[k]);
+    contribute2(d, S2);
+  };
   // neighbour d's contribution with the D x D block S
   auto contribute = [&](int d, const A (&S)[DD]) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
@@ -270,18 +340,35 @@ __global__ void __launch_bounds__(64)
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
           if (DIFF && d == 13) continue;
-          A S[DD];
+          if constexpr (PK) {
+            f2_t S2[DD];
 #pragma unroll
-          for (int k = 0; k < DD; ++k) S[k] = p.fc.Sf[d * DD + k];
-          if (d == 13) {  // own node: no shared-memory round trip
+            for (int k = 0; k < DD; ++k) S2[k] = p.fc.Sf2[d * DD + k];
+            if (d == 13) {  // own node: no shared-memory round trip
 #pragma unroll
-            for (int j = 0; j < D; ++j)
+              for (int j = 0; j < D; ++j)
 #pragma unroll
-              for (int m = 0; m < M; ++m)
+                for (int h2 = 0; h2 < H; ++h2)
 #pragma unroll
-                for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * self[j * M + m];
+                  for (int i = 0; i < D; ++i)
+                    acc2[i * H + h2] = f2_fma(S2[i * D + j], self2[j * H + h2], acc2[i * H + h2]);
+            } else {
+              contribute2(d, S2);
+            }
           } else {
-            contribute(d, S);
+            A S[DD];
+#pragma unroll
+            for (int k = 0; k < DD; ++k) S[k] = p.fc.Sf[d * DD + k];
+            if (d == 13) {  // own node: no shared-memory round trip
+#pragma unroll
+              for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+#pragma unroll
+                  for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * self[j * M + m];
+            } else {
+              contribute(d, S);
+            }
           }
         }
       } else {
@@ -306,7 +393,8 @@ __global__ void __launch_bounds__(64)
               for (int j = 0; j < D; ++j)
                 S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
           }
-          contribute(d, S);
+          if constexpr (PK) contribute_s(d, S);
+          else contribute(d, S);
         }
       }
     } else {
@@ -317,8 +405,18 @@ __global__ void __launch_bounds__(64)
         A S[DD];
 #pragma unroll
         for (int k = 0; k < DD; ++k) S[k] = sten[(d * DD + k) * 64];
-        contribute(d, S);
+        if constexpr (PK) contribute_s(d, S);
+        else contribute(d, S);
       }
+    }
+  }
+  if constexpr (PK) {
+#pragma unroll
+    for (int k = 0; k < CP; ++k) {
+      float lo, hi;
+      f2_unpack(acc2[k], lo, hi);
+      acc[2 * k] = (A)lo;
+      acc[2 * k + 1] = (A)hi;
     }
   }
   const int64_t base = b * (64 * C) + loc;
@@ -539,6 +637,17 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   float acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = 0.f;
+  constexpr bool PK = M % 2 == 0;   // packed pairs of cases (f32x2)
+  constexpr int H = M / 2, CP = PK ? C / 2 : 1;
+  f2_t acc2[CP], sh2[CP], sl2[CP];
+  if constexpr (PK && !ZERO) {
+#pragma unroll
+    for (int k = 0; k < CP; ++k) {
+      acc2[k] = 0ull;
+      sh2[k] = f2_pack(sh[2 * k], sh[2 * k + 1]);
+      sl2[k] = f2_pack(sl[2 * k], sl[2 * k + 1]);
+    }
+  }
   if (!ZERO && mk) {
     float bf[8];
 #pragma unroll
@@ -548,9 +657,13 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
       if (d == 13) continue;  // d = 0 carries no difference
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
       float S[D * D];
+      f2_t S2[D * D];
       if (warp_full) {
 #pragma unroll
-        for (int k = 0; k < D * D; ++k) S[k] = p.fc.Sf[d * D * D + k];
+        for (int k = 0; k < D * D; ++k) {
+          if constexpr (PK) S2[k] = p.fc.Sf2[d * D * D + k];
+          else S[k] = p.fc.Sf[d * D * D + k];
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < D * D; ++k) S[k] = 0.f;
@@ -565,26 +678,54 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
             for (int j = 0; j < D; ++j)
               S[i * D + j] += bf[a] * p.fc.Ke[(a * D + i) * R + bb * D + j];
         }
+        if constexpr (PK) {
+#pragma unroll
+          for (int k = 0; k < D * D; ++k) S2[k] = f2_pack(S[k], S[k]);
+        }
       }
       const int q = q0 + dx + 6 * dy + 36 * dz;
-      float uh[G * 4], ul[G * 4];
+      if constexpr (PK) {
+        const ulonglong2* th2 = reinterpret_cast<const ulonglong2*>(th);
+        const ulonglong2* tl2 = reinterpret_cast<const ulonglong2*>(tl);
+        f2_t du2[CP];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const V wh = th[g * 216 + q], wl = tl[g * 216 + q];
-        uh[4 * g] = wh.x; uh[4 * g + 1] = wh.y; uh[4 * g + 2] = wh.z; uh[4 * g + 3] = wh.w;
-        ul[4 * g] = wl.x; ul[4 * g + 1] = wl.y; ul[4 * g + 2] = wl.z; ul[4 * g + 3] = wl.w;
-      }
+        for (int g = 0; g < G; ++g) {
+          const ulonglong2 wh = th2[g * 216 + q], wl = tl2[g * 216 + q];
+          if (2 * g < CP) du2[2 * g] = f2_add(f2_sub(wh.x, sh2[2 * g]), f2_sub(wl.x, sl2[2 * g]));
+          if (2 * g + 1 < CP)
+            du2[2 * g + 1] = f2_add(f2_sub(wh.y, sh2[2 * g + 1]), f2_sub(wl.y, sl2[2 * g + 1]));
+        }
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
+        for (int j = 0; j < D; ++j)
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const int v = j * M + m;
-          const float du = (uh[v] - sh[v]) + (ul[v] - sl[v]);
+          for (int h2 = 0; h2 < H; ++h2)
 #pragma unroll
-          for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * du;
+            for (int i = 0; i < D; ++i)
+              acc2[i * H + h2] = f2_fma(S2[i * D + j], du2[j * H + h2], acc2[i * H + h2]);
+      } else {
+        float uh[G * 4], ul[G * 4];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const V wh = th[g * 216 + q], wl = tl[g * 216 + q];
+          uh[4 * g] = wh.x; uh[4 * g + 1] = wh.y; uh[4 * g + 2] = wh.z; uh[4 * g + 3] = wh.w;
+          ul[4 * g] = wl.x; ul[4 * g + 1] = wl.y; ul[4 * g + 2] = wl.z; ul[4 * g + 3] = wl.w;
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const int v = j * M + m;
+            const float du = (uh[v] - sh[v]) + (ul[v] - sl[v]);
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[i * M + m] += S[i * D + j] * du;
+          }
         }
       }
     }
+  }
+  if constexpr (PK && !ZERO) {
+#pragma unroll
+    for (int k = 0; k < CP; ++k) f2_unpack(acc2[k], acc[2 * k], acc[2 * k + 1]);
   }
   float nrm[M];
 #pragma unroll
@@ -816,6 +957,8 @@ struct EnArgs {
   A X0[8 * D * M];        // FP64 path: x0
   A Fh[8 * D * M];        // ff path: f_e = K_e x0, hi and lo parts
   A Fl[8 * D * M];
+  f2_t Ke2[32 * D * D];   // ff path: rows (2 rp, 2 rp + 1) of Ke / Kl packed per column
+  f2_t Kl2[32 * D * D];
 };
 
 // Per active element e (origin slot n) and load cases I <= J, the energy
@@ -924,15 +1067,29 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
       A w[R], z[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) w[r] = ws[(r * M + J) * 64 + t];
+      if constexpr (FF) {
+        // two rows per f32x2 instruction, the same operations in the same order per row
+        f2_t w2[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        A shi = A(0), slo = A(0);
+        for (int c = 0; c < R; ++c) w2[c] = f2_pack(w[c], w[c]);
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-          shi += p.Ke[r * R + c] * w[c];
-          if constexpr (FF) slo += p.Kl[r * R + c] * w[c];
+        for (int rp = 0; rp < R / 2; ++rp) {
+          f2_t sh2 = 0ull, sl2 = 0ull;
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            sh2 = f2_fma(p.Ke2[rp * R + c], w2[c], sh2);
+            sl2 = f2_fma(p.Kl2[rp * R + c], w2[c], sl2);
+          }
+          f2_unpack(f2_add(sh2, sl2), z[2 * rp], z[2 * rp + 1]);
         }
-        z[r] = shi + slo;
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          A sacc = A(0);
+#pragma unroll
+          for (int c = 0; c < R; ++c) sacc += p.Ke[r * R + c] * w[c];
+          z[r] = sacc;
+        }
       }
 #pragma unroll
       for (int I = 0; I < M; ++I) {
@@ -1342,6 +1499,10 @@ static void fill_fine(const Material& mt, FineC<A, D, M>& fc) {
         acc += mt.Ke[(a * D + k / D) * R + bb * D + k % D];
       }
       fc.Sf[d * D * D + k] = (A)acc;
+      const float sf = (float)acc;
+      uint32_t bits;
+      std::memcpy(&bits, &sf, 4);
+      fc.Sf2[d * D * D + k] = ((f2_t)bits << 32) | (f2_t)bits;
     }
   }
 }
@@ -1544,6 +1705,21 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
   for (int i = 0; i < 64 * D * D; ++i) {
     p.Ke[i] = (A)h->mat.Ke[i];
     p.Kl[i] = (A)(h->mat.Ke[i] - (double)p.Ke[i]);
+  }
+  if constexpr (FF) {
+    const int R = 8 * D;
+    auto bits = [](float x) {
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      return (f2_t)u;
+    };
+    for (int rp = 0; rp < R / 2; ++rp)
+      for (int c = 0; c < R; ++c) {
+        p.Ke2[rp * R + c] = bits((float)p.Ke[2 * rp * R + c]) |
+                            (bits((float)p.Ke[(2 * rp + 1) * R + c]) << 32);
+        p.Kl2[rp * R + c] = bits((float)p.Kl[2 * rp * R + c]) |
+                            (bits((float)p.Kl[(2 * rp + 1) * R + c]) << 32);
+      }
   }
   for (int i = 0; i < 8 * D * M; ++i) {
     p.X0[i] = (A)h->mat.X0[i];
