@@ -138,6 +138,9 @@ gmt_status gmt_build_hierarchy(const uint8_t* voxels, int res, int voxels_on_dev
   try {
     GMT_CUDA(cudaGetDevice(&h->device));
     h->stream = (cudaStream_t)stream;
+    h->geo.bind(h->stream);
+    h->op.bind(h->stream);
+    h->work.bind(h->stream);
     h->opts = o;
     h->N = res;
     h->L = L;
@@ -164,7 +167,12 @@ void gmt_free_hierarchy(gmt_hierarchy* h) {
 gmt_status gmt_set_stream(gmt_hierarchy* h, void* stream) {
   GMT_API_BEGIN
   GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  // work queued on the previous stream finishes before the new stream may reuse buffers
+  if (h->stream != (cudaStream_t)stream) GMT_CUDA(cudaStreamSynchronize(h->stream));
   h->stream = (cudaStream_t)stream;
+  h->geo.bind(h->stream);
+  h->op.bind(h->stream);
+  h->work.bind(h->stream);
   return GMT_OK;
   GMT_API_END
 }

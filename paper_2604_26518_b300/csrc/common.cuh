@@ -115,14 +115,31 @@ void pool_free(void* p);
 void pool_trim();
 size_t pool_cached_bytes();
 
+// Blocks from the caching pool, returned on release() after the work that may still use
+// them has finished: the arena's stream when it has one (so that hierarchies on other
+// streams keep running), else the whole device.
 struct Arena {
   std::vector<void*> ptrs;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool has_stream = false;
+  Arena() = default;
+  explicit Arena(cudaStream_t s) : stream(s), has_stream(true) {}
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  void bind(cudaStream_t s) {
+    stream = s;
+    has_stream = true;
+  }
   void* raw(size_t n);
   template <typename T> T* alloc(size_t count) { return (T*)raw(count * sizeof(T)); }
   void release();
   ~Arena() { release(); }
 };
+
+// dynamic shared memory above the 48 KB default for a kernel on the current device (set
+// once per kernel and device; thread-safe)
+void ensure_smem_attr(const void* kernel, int bytes);
 
 // ------------------------------------------------------------------ hierarchy
 struct Level {

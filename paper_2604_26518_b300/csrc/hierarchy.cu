@@ -10,6 +10,7 @@
 // bricks with exclusive scans. Counts are read back once per level to size allocations.
 #include <atomic>
 #include <map>
+#include <set>
 #include <mutex>
 #include <unordered_map>
 #include <cstdarg>
@@ -126,12 +127,26 @@ void* Arena::raw(size_t n) {
 }
 
 void Arena::release() {
-  // like cudaFree, wait for device work that may still use the blocks (any stream) before
-  // they can be handed to another allocation
-  if (!ptrs.empty()) cudaDeviceSynchronize();
+  // like cudaFree, wait for device work that may still use the blocks before they can be
+  // handed to another allocation
+  if (!ptrs.empty()) {
+    if (has_stream) cudaStreamSynchronize(stream);
+    else cudaDeviceSynchronize();
+  }
   for (void* p : ptrs) pool_free(p);
   ptrs.clear();
   bytes = 0;
+}
+
+void ensure_smem_attr(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  GMT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kernel, dev})) return;
+  GMT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({kernel, dev});
 }
 
 // ------------------------------------------------------------------ launch counting, tracing
@@ -418,7 +433,7 @@ void build_hierarchy(gmt_hierarchy* h, const uint8_t* vox, bool on_device) {
   TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
   const int N = h->N;
   const int64_t n3 = (int64_t)N * N * N;
-  Arena tmp;
+  Arena tmp(s);
   uint8_t* dvox = nullptr;
   if (on_device) {
     dvox = const_cast<uint8_t*>(vox);

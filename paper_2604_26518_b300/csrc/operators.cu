@@ -14,6 +14,8 @@
 //     returns the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS
 //     is replaced by this exact solve.
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <cmath>
 #include <cstring>
 
@@ -245,6 +247,20 @@ static ChildWeights make_child_weights() {
         }
       }
   return cw;
+}
+
+// the weight table is the same for every hierarchy: uploaded once per device, before any
+// kernel that reads it (a synchronous copy, so no stream of another hierarchy sees it change)
+static void upload_child_weights() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  GMT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(dev)) return;
+  const ChildWeights cw = make_child_weights();
+  GMT_CUDA(cudaMemcpyToSymbol(c_cw, &cw, sizeof(cw)));
+  done.insert(dev);
 }
 
 // levels >= 2: K(E) = sum over active children c of P_c^T K(child) P_c, using only the
@@ -550,7 +566,7 @@ void build_coarse_inverse64(gmt_hierarchy* h) {
   h->Ainv = h->op.alloc<double>(m * m);
   GMT_CUDA(cudaMemcpyAsync(h->Ainv, h->A64, m * m * sizeof(double), cudaMemcpyDeviceToDevice,
                            h->stream));
-  Arena tmp;
+  Arena tmp(h->stream);
   gauss_jordan<double>(h, h->Ainv, m, h->ctol, tmp);
   GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
@@ -580,7 +596,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   mt.C = mt.D * mt.M;
   const int D = mt.D, M = mt.M, R = 8 * D, MM = R * R;
   mt.MM = MM;
-  Arena tmp;
+  Arena tmp(s);
   // element matrices
   double* eout = tmp.alloc<double>(MM + 2 * R * M + M * M);
   k_element<<<1, 576, 0, s>>>(physics, E, nu, kappa, eout);
@@ -608,10 +624,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     GMT_CUDA(cudaStreamSynchronize(s));
   }
   // Galerkin coarse operators
-  {
-    static const ChildWeights cw = make_child_weights();
-    GMT_CUDA(cudaMemcpyToSymbolAsync(c_cw, &cw, sizeof(cw), 0, cudaMemcpyHostToDevice, s));
-  }
+  upload_child_weights();
   double* Q = nullptr;
   if (h->L >= 2) {
     Q = tmp.alloc<double>(8 * MM);

@@ -55,7 +55,7 @@ __global__ void k_mask_hist(const uint8_t* __restrict__ mask, int64_t n,
 static void load_norms2(gmt_hierarchy* h, double* fn2) {
   if (!h->have_hist) {
     const Level& l0 = h->lv[0];
-    Arena tmp;
+    Arena tmp(h->stream);
     unsigned long long* d = tmp.alloc<unsigned long long>(256);
     GMT_CUDA(cudaMemsetAsync(d, 0, 256 * sizeof(unsigned long long), h->stream));
     const unsigned g = std::min<unsigned>(grid_for(l0.nslots, 256), 148u * 8u);

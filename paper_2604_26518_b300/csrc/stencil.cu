@@ -15,6 +15,7 @@
 // One 64-thread block owns one 4^3 brick and stages the brick plus a one-node halo
 // (6^3 nodes x C values) in shared memory; every output sum runs in a fixed order.
 #include <cstring>
+#include <type_traits>
 
 #include "stencil.cuh"
 
@@ -169,6 +170,17 @@ __device__ __forceinline__ int own_q0(int t) {
 template <typename A> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+// node-stencil layout of the coarse levels: 27 * DD coefficients per node in 16-byte groups
+template <typename A>
+__host__ __device__ constexpr int node_stencil_groups(int DD) {
+  return (27 * DD + Vec16<A>::n - 1) / Vec16<A>::n;
+}
+__host__ __device__ __forceinline__ int64_t node_stencil_index(int64_t slot, int c, int groups,
+                                                             int W) {
+  return (slot >> 6) * ((int64_t)groups * 64 * W) + (int64_t)(c / W) * (64 * W) +
+         (slot & 63) * W + c % W;
+}
 
 template <typename A>
 __device__ __forceinline__ void vec_put(typename Vec16<A>::type& w, int k, A x) {
@@ -398,13 +410,21 @@ __global__ void __launch_bounds__(64)
         }
       }
     } else {
-      const A* sten = p.kmat + b * (64 * 27 * DD) + loc;
+      // coefficient c = d * DD + k of this node sits in 16-byte group c / W (see
+      // node_stencil_index); each group is loaded once, when its first coefficient is needed
+      constexpr int W = Vec16<A>::n, NGW = node_stencil_groups<A>(DD) * W;
+      const A* sten = p.kmat + b * (NGW * 64) + loc * W;
+      V cur;
 #pragma unroll
       for (int d = 0; d < 27; ++d) {
-        if (DIFF && d == 13) continue;
         A S[DD];
 #pragma unroll
-        for (int k = 0; k < DD; ++k) S[k] = sten[(d * DD + k) * 64];
+        for (int k = 0; k < DD; ++k) {
+          const int c = d * DD + k;
+          if (c % W == 0) cur = *reinterpret_cast<const V*>(sten + (c / W) * (64 * W));
+          S[k] = vec_get<A>(cur, c % W);
+        }
+        if (DIFF && d == 13) continue;
         if constexpr (PK) contribute_s(d, S);
         else contribute(d, S);
       }
@@ -506,7 +526,10 @@ __global__ void __launch_bounds__(64)
 }
 
 // per-node assembled stencil of a coarse level: S_n(d) = sum over active elements e = n - a
-// with a + d in {0,1}^3 of K(e)[a, a + d], written as [brick][27 * D * D][64]
+// with a + d in {0,1}^3 of K(e)[a, a + d], written as [brick][group][64][W]: coefficient
+// c = d * D * D + k of a node in 16-byte group c / W (W = 4 floats or 2 doubles), so that a
+// thread reads its node's coefficients with one 16-byte load per group and a warp's loads
+// are contiguous
 __global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bxyz,
                                const int* __restrict__ bmap, bool dense, int64_t nslots,
                                const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
@@ -518,7 +541,7 @@ __global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bx
   const unsigned mk = mask[sl];
   int x = 0, y = 0, z = 0;
   if (mk) slot_coords(sl, n, dense, bxyz, x, y, z);
-  const int64_t base = (sl >> 6) * (64 * 27 * DD) + (sl & 63);
+  const int G64 = node_stencil_groups<double>(DD), G32 = node_stencil_groups<float>(DD);
   for (int d = 0; d < 27; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -537,8 +560,9 @@ __global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bx
       }
     }
     for (int k = 0; k < DD; ++k) {
-      if (S64) S64[base + (int64_t)(d * DD + k) * 64] = S[k];
-      if (S32) S32[base + (int64_t)(d * DD + k) * 64] = (float)S[k];
+      const int c = d * DD + k;
+      if (S64) S64[node_stencil_index(sl, c, G64, 2)] = S[k];
+      if (S32) S32[node_stencil_index(sl, c, G32, 4)] = (float)S[k];
     }
   }
 }
@@ -546,15 +570,18 @@ __global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bx
 void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
   Level& lv = h->lv[level];
   const int D = h->mat.D;
-  const size_t cnt = (size_t)lv.nslots * 27 * D * D;
   double* s64 = nullptr;
   float* s32 = nullptr;
   if (fp64) {
     if (lv.S64) return;
+    const size_t cnt = (size_t)lv.nslots * node_stencil_groups<double>(D * D) * 2;
     s64 = lv.S64 = h->op.alloc<double>(cnt);
+    GMT_CUDA(cudaMemsetAsync(s64, 0, cnt * sizeof(double), h->stream));
   } else {
     if (lv.S32) return;
+    const size_t cnt = (size_t)lv.nslots * node_stencil_groups<float>(D * D) * 4;
     s32 = lv.S32 = h->op.alloc<float>(cnt);
+    GMT_CUDA(cudaMemsetAsync(s32, 0, cnt * sizeof(float), h->stream));
   }
   k_node_stencil<<<grid_for(lv.nslots, 128), 128, 0, h->stream>>>(
       D, lv.n, lv.nbx, lv.brick_xyz, lv.brick_map, lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K64,
@@ -823,6 +850,108 @@ __global__ void k_prolong(const TS* __restrict__ uc, TS* __restrict__ uf, LvView
   }
 }
 
+// Bricked levels: the same sums, staged through shared memory. One block per coarse brick
+// stages the 9^3 fine sites its 64 nodes gather from (coalesced within fine bricks), then
+// each thread forms its node's sum over d in the order of k_restrict (bitwise equal).
+template <typename A>
+constexpr int vec_groups(int C) { return (C + Vec16<A>::n - 1) / Vec16<A>::n; }
+
+template <typename TS, typename A, int C>
+__global__ void __launch_bounds__(64) k_restrict_tile(const TS* __restrict__ rf,
+                                                      TS* __restrict__ fc, LvView f, LvView c) {
+  using V = typename Vec16<A>::type;
+  constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  V* tile = reinterpret_cast<V*>(tr_smem);   // [G][729]
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int ox = 8 * c.bxyz[3 * b] - 1, oy = 8 * c.bxyz[3 * b + 1] - 1,
+            oz = 8 * c.bxyz[3 * b + 2] - 1;
+  for (int q = t; q < 729; q += 64) {
+    const int rx = q % 9, ry = (q / 9) % 9, rz = q / 81;
+    const int fx = (ox + rx + f.n) % f.n, fy = (oy + ry + f.n) % f.n, fz = (oz + rz + f.n) % f.n;
+    const int64_t fs = site_slot(fx, fy, fz, f.n, f.nbx, f.bmap, false);
+    A vals[G * NV];
+#pragma unroll
+    for (int v = 0; v < G * NV; ++v) vals[v] = A(0);
+    if (fs >= 0) {
+      const TS* src = rf + vaddr(fs, 0, C);
+#pragma unroll
+      for (int v = 0; v < C; ++v) vals[v] = load_as<A>(src + v * 64);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      V w;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) vec_put<A>(w, k, vals[g * NV + k]);
+      tile[g * 729 + q] = w;
+    }
+  }
+  __syncthreads();
+  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
+  A acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = A(0);
+  if (c.mask[b * 64 + t]) {
+    const int qc = (2 * lx + 1) + 9 * (2 * ly + 1) + 81 * (2 * lz + 1);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const A w = (dx ? A(0.5) : A(1)) * (dy ? A(0.5) : A(1)) * (dz ? A(0.5) : A(1));
+      const int q = qc + dx + 9 * dy + 81 * dz;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const V x = tile[g * 729 + q];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+          if (g * NV + k < C) acc[g * NV + k] += w * vec_get<A>(x, k);
+      }
+    }
+  }
+  TS* dst = fc + vaddr(b * 64 + t, 0, C);
+#pragma unroll
+  for (int v = 0; v < C; ++v) dst[v * 64] = store_as<TS>(acc[v]);
+}
+
+// One block per fine brick: the 3^3 coarse sites its nodes interpolate from are staged in
+// shared memory; each node adds its weighted terms in the order of k_prolong.
+template <typename TS, typename A, int C>
+__global__ void __launch_bounds__(64) k_prolong_tile(const TS* __restrict__ uc,
+                                                     TS* __restrict__ uf, LvView f, LvView c) {
+  __shared__ A cv[C][27];
+  const int64_t b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int bx = f.bxyz[3 * b], by = f.bxyz[3 * b + 1], bz = f.bxyz[3 * b + 2];
+  for (int k = t; k < 27 * C; k += 64) {
+    const int pos = k / C, v = k % C;
+    const int px = pos % 3, py = (pos / 3) % 3, pz = pos / 9;
+    const int64_t cs = site_slot((2 * bx + px) % c.n, (2 * by + py) % c.n, (2 * bz + pz) % c.n,
+                                 c.n, c.nbx, c.bmap, false);
+    cv[v][pos] = cs >= 0 ? load_as<A>(uc + vaddr(cs, v, C)) : A(0);
+  }
+  __syncthreads();
+  const int64_t s = b * 64 + t;
+  if (!f.mask[s]) return;
+  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
+  const int cnt[3] = {(lx & 1) ? 2 : 1, (ly & 1) ? 2 : 1, (lz & 1) ? 2 : 1};
+  const int j0[3] = {lx >> 1, ly >> 1, lz >> 1};
+  const A w = (cnt[0] == 2 ? A(0.5) : A(1)) * (cnt[1] == 2 ? A(0.5) : A(1)) *
+              (cnt[2] == 2 ? A(0.5) : A(1));
+  A acc[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) acc[v] = A(0);
+  for (int cz = 0; cz < cnt[2]; ++cz)
+    for (int cy = 0; cy < cnt[1]; ++cy)
+      for (int cx = 0; cx < cnt[0]; ++cx) {
+        const int pos = (j0[0] + cx) + 3 * (j0[1] + cy) + 9 * (j0[2] + cz);
+#pragma unroll
+        for (int v = 0; v < C; ++v) acc[v] += w * cv[v][pos];
+      }
+  TS* dst = uf + vaddr(s, 0, C);
+#pragma unroll
+  for (int v = 0; v < C; ++v) dst[v * 64] = store_as<TS>(load_as<A>(dst + v * 64) + acc[v]);
+}
+
 // ------------------------------------------------------------------ coarsest solve
 template <typename TS, int D, int M>
 __global__ void k_coarse_gather(const TS* __restrict__ f, const int* __restrict__ canon_slot,
@@ -990,7 +1119,10 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
   V* th = reinterpret_cast<V*>(en_smem);
   V* tl = th + G * 216;                                              // FF only
   A* ws = reinterpret_cast<A*>(en_smem + (size_t)(FF ? 2 : 1) * G * 216 * 16);  // [R*M][64]
-  double* es = reinterpret_cast<double*>(en_smem);                   // [K][64], after phase 1
+  // per-pair energies [K][64] after phase 1 (FP32 on the float-float path: per-element
+  // rounding, not common to the elements, is summed away in FP64 across blocks)
+  using ES = typename std::conditional<FF, float, double>::type;
+  ES* es = reinterpret_cast<ES*>(en_smem);
   __shared__ int nb[27];
   const int t = threadIdx.x;
   const int64_t b = blockIdx.x;
@@ -1059,7 +1191,7 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
       for (int I = 0; I < M; ++I)
 #pragma unroll
         for (int J = I; J < M; ++J)
-          es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t] = (double)phi[I][J] + (double)phi[J][I];
+          es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t] = phi[I][J] + phi[J][I];
     }
     // phase 3: z = K_e d^J (hi + lo in FF), pair sums d^I . z for I <= J
 #pragma unroll 1
@@ -1097,17 +1229,17 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
           A sacc = A(0);
 #pragma unroll
           for (int r = 0; r < R; ++r) sacc += ws[(r * M + I) * 64 + t] * z[r];
-          double* ep = es + (I * M - I * (I - 1) / 2 + (J - I)) * 64 + t;
-          if constexpr (FF) *ep = (double)sacc - *ep;
-          else *ep = (double)sacc;
+          ES* ep = es + (I * M - I * (I - 1) / 2 + (J - I)) * 64 + t;
+          if constexpr (FF) *ep = sacc - *ep;
+          else *ep = sacc;
         }
       }
     }
   }
-  double e[K];
+  ES e[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : 0.0;
-  block_partial_64<K, double>(e, p.part + b * K);
+  for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : ES(0);
+  block_partial_64<K, ES>(e, p.part + b * K);
 }
 
 // deterministic reduction of [nblk][K] partials. Column k is split over gridDim.y blocks;
@@ -1637,8 +1769,17 @@ static void restrict_t(gmt_hierarchy* h, int level, const void* rf, void* fc) {
   const Level& c = h->lv[level + 1];
   TraceScope ts(&h->tracer, h->stream, TR_RESTRICT,
                 (double)(h->lv[level].n_nodes + c.n_nodes) * D * M * sizeof(TS));
-  k_restrict<TS, A, D * M><<<grid_for(c.nslots, 64), 64, 0, h->stream>>>(
-      (const TS*)rf, (TS*)fc, view(h->lv[level]), view(c));
+  const Level& f = h->lv[level];
+  if (!f.dense && !c.dense) {
+    constexpr int C = D * M;
+    constexpr size_t smem = (size_t)vec_groups<A>(C) * 729 * 16;
+    ensure_smem_attr((const void*)k_restrict_tile<TS, A, C>, (int)smem);
+    k_restrict_tile<TS, A, C><<<(unsigned)c.nb, 64, smem, h->stream>>>((const TS*)rf, (TS*)fc,
+                                                                      view(f), view(c));
+  } else {
+    k_restrict<TS, A, D * M><<<grid_for(c.nslots, 64), 64, 0, h->stream>>>(
+        (const TS*)rf, (TS*)fc, view(f), view(c));
+  }
   GMT_LAUNCH_CHECK();
 }
 void launch_restrict(gmt_hierarchy* h, int level, Prec prec, const void* rf, void* fc) {
@@ -1650,8 +1791,14 @@ static void prolong_t(gmt_hierarchy* h, int level, const void* uc, void* uf) {
   const Level& f = h->lv[level];
   TraceScope ts(&h->tracer, h->stream, TR_PROLONG,
                 (double)(2 * f.n_nodes + h->lv[level + 1].n_nodes) * D * M * sizeof(TS));
-  k_prolong<TS, A, D * M><<<grid_for(f.nslots, 64), 64, 0, h->stream>>>(
-      (const TS*)uc, (TS*)uf, view(f), view(h->lv[level + 1]));
+  const Level& c = h->lv[level + 1];
+  if (!f.dense && !c.dense) {
+    k_prolong_tile<TS, A, D * M><<<(unsigned)f.nb, 64, 0, h->stream>>>((const TS*)uc, (TS*)uf,
+                                                                       view(f), view(c));
+  } else {
+    k_prolong<TS, A, D * M><<<grid_for(f.nslots, 64), 64, 0, h->stream>>>(
+        (const TS*)uc, (TS*)uf, view(f), view(c));
+  }
   GMT_LAUNCH_CHECK();
 }
 void launch_prolong(gmt_hierarchy* h, int level, Prec prec, const void* uc, void* uf) {
@@ -1727,12 +1874,7 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
     p.Fl[i] = (A)(h->mat.Fe[i] - (double)p.Fh[i]);
   }
   constexpr size_t smem = energy_smem_bytes<A, D, M, FF>();
-  static bool attr = false;   // per template instance; the attribute is per device function
-  if (!attr) {
-    GMT_CUDA(cudaFuncSetAttribute(k_energy<A, D, M, FF>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  ensure_smem_attr((const void*)k_energy<A, D, M, FF>, (int)smem);
   TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
   k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
   GMT_LAUNCH_CHECK();
