@@ -52,6 +52,10 @@ def workload(name: str, rank: int):
     elif name == "c32":
         cells = [(lattices.tpms_network("gyroid", 32, 0.30), {"family": "gyroid", "n": 32})]
         desc = "gyroid 32^3, phi 0.30"
+    elif name == "batch64":
+        cells = [lattices.batch_cell(3000 + 64 * rank + i) for i in range(64)]
+        desc = "64 seeded cells, N uniform in {32,48,64,96,128}: TPMS network/plate, " \
+               "BCC/octet trusses, spinodal; phi 0.1-0.4"
     elif name == "c512":
         cells = [(lattices.tpms_network("gyroid", 512, 0.20), {"family": "gyroid", "n": 512})]
         desc = "gyroid 512^3, phi 0.20"
@@ -196,6 +200,7 @@ def run_gmt(args, rank: int, world: int):
             dist.barrier()
 
     cycles_seen = []
+    unconverged, fallbacks = [], []   # cell indices, appended by every step
     # Cells are independent: with --streams S > 1, S host threads each solve every S-th cell
     # on a stream of their own, so that one cell's host synchronisations and small coarse-
     # level kernels overlap another cell's work. The step starts and ends on `stream`.
@@ -211,8 +216,12 @@ def run_gmt(args, rank: int, world: int):
                 h.trace(True)
             st, _, info = h.solve(ph, E=1.0, nu=0.3, k=1.0, tol=TOL, want_field=False,
                                   allow_not_converged=True)
-            if st != gmt.OK:
+            if st == gmt.NOT_CONVERGED:
+                unconverged.append(i)          # reported; the cell's time stays in the step
+            elif st != gmt.OK:
                 raise RuntimeError(f"solve status {st}: {info.as_dict()}")
+            if info.fp64_fallback:
+                fallbacks.append(i)
             CH[i] = h.homogenize(ph, E=1.0, nu=0.3, k=1.0)
             cyc.append((i, info.inner_total))
             if trace:
@@ -320,7 +329,9 @@ def run_gmt(args, rank: int, world: int):
         "dtype": "f32" if prec == gmt.FP32 else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "cells_per_step_per_gpu": len(cells),
-                   "n": cells[0][1]["n"], "physics": args.physics, "tol": TOL,
+                   "n": (cells[0][1]["n"] if len({c[1]["n"] for c in cells}) == 1
+                         else sorted({c[1]["n"] for c in cells})),
+                   "physics": args.physics, "tol": TOL,
                    "precision": ("fp32 V-cycle CG, float-float outer residual, fp64 coarsest "
                                  "solve and C^H accumulation") if prec == gmt.FP32 else "fp64",
                    "step": "hierarchy + operators + solve + C^H per cell",
@@ -345,6 +356,8 @@ def run_gmt(args, rank: int, world: int):
         "phases_note": "one extra step, cells one after another, every launch bracketed by "
                        "CUDA events on its stream (not part of value)",
         "vcycles_per_cell": cycles_seen[-len(cells):],
+        "unconverged_cells": sorted(set(unconverged)),
+        "fp64_fallback_cells": sorted(set(fallbacks)),
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu:
@@ -365,7 +378,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmt", choices=["gmt", "reference"])
-    ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c512"])
+    ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c512", "batch64"])
     ap.add_argument("--physics", default="elastic", choices=["elastic", "heat"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")

@@ -57,13 +57,19 @@ typedef enum {
 } gmt_status;
 
 typedef enum { GMT_PREC_FP64 = 0, GMT_PREC_FP32 = 1, GMT_PREC_BF16 = 2 } gmt_precision;
-typedef enum { GMT_SMOOTH_JACOBI = 0, GMT_SMOOTH_CHEBYSHEV = 1 } gmt_smoother;
+typedef enum { GMT_SMOOTH_JACOBI = 0, GMT_SMOOTH_CHEBYSHEV = 1, GMT_SMOOTH_GS8 = 2 } gmt_smoother;
+/* Multigrid cycle of Sec. 5's schedules: V (one coarse correction per level), W (two),
+   F (one F-cycle then one V-cycle on the next level). */
+typedef enum { GMT_CYCLE_V = 0, GMT_CYCLE_W = 1, GMT_CYCLE_F = 2 } gmt_cycle;
 
 /* Solver options. gmt_default_options fills the defaults given in brackets. */
 typedef struct {
   int levels;          /* [0] number of levels L; 0 = smallest L with coarsest <= coarsest_max */
   int coarsest_max;    /* [8] automatic level rule: coarsest grid side at most this */
-  int smoother;        /* [GMT_SMOOTH_JACOBI] damped block-Jacobi or Chebyshev */
+  int smoother;        /* [GMT_SMOOTH_JACOBI] damped block-Jacobi, Chebyshev, or 8-colour
+                          Gauss-Seidel (Sec. 4.6 "Parallel Smoothing": nodes coloured by the
+                          parity of (x, y, z); one sweep updates the 8 colours in turn, each
+                          with the damped block-Jacobi step on the latest values) */
   int nu_pre;          /* [2] pre-smoothing sweeps (Chebyshev: polynomial degree) */
   int nu_post;         /* [2] post-smoothing sweeps */
   double omega;        /* [0.6] Jacobi damping */
@@ -77,6 +83,9 @@ typedef struct {
                           iterated one) whenever the iterated residual fell by this factor */
   int max_inner;       /* [40] with max_outer: at most max_inner * max(1, max_outer) V-cycles */
   int max_outer;       /* [8] */
+  int cycle;           /* [GMT_CYCLE_V] */
+  int fp64_fallback;   /* [1] when the mixed-precision solve diverges, gmt_solve solves the
+                          cell again in plain FP64 (gmt_info.fp64_fallback reports it) */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,
@@ -88,6 +97,7 @@ typedef struct {
   double rel_residual[6];
   double t_setup_ms;     /* operator setup for this material (0 if cached) */
   double t_solve_ms;     /* solve time (host wall clock around the device work) */
+  int fp64_fallback;     /* 1 if the mixed-precision solve diverged and FP64 took over */
 } gmt_info;
 
 void gmt_default_options(gmt_options* opts);
@@ -187,6 +197,16 @@ gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
    or NULL for the field of the last gmt_solve on this hierarchy. */
 gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                           double k, const double* u, double* CH_out);
+
+/* Inverse-homogenization sensitivities (App. F.3): for the SIMP interpolation
+   C_e = (rho_min + rho_e^p) C0, dC^H_IJ / d rho_e = p rho_e^(p-1) / |Omega|
+   (x0^I - u_e^I)^T K0 (x0^J - u_e^J), evaluated for the solid elements of this hierarchy's
+   binary design (rho_e = 1, so the factor is p / N^3). simp_p: the penalisation p (> 0).
+   u: device canonical field, or NULL for the field of the last gmt_solve. dCH_out: device,
+   caller-owned double[n_elems][M][M] in canonical element order (gmt_element_coords,
+   level 0), symmetric in (I, J). Summed over the elements it equals p C^H. */
+gmt_status gmt_sensitivities(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
+                             double k, double simp_p, const double* u, double* dCH_out);
 
 /* Relative residuals ||f_m - K u_m|| / ||f_m|| of a device canonical field u (host out[M]),
    with the solver's outer residual (precision FP32: float-float difference form;

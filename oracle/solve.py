@@ -13,6 +13,7 @@ kappa^H (App. F.2) is the same expression with the thermal matrices.
 Relative residual (Sec. 5 metrics): r = ||f - K u||_2 / ||f||_2 per load case.
 Gauge (Sec. 3.1, Sec. 4.5): the zero-mean constraint, applied as a hard projection
 (subtract the mean over active nodes per component and load case).
+Sensitivities (App. F.3): the per-element energies above, scaled by p / |Omega|.
 """
 from __future__ import annotations
 
@@ -167,6 +168,15 @@ def element_energies(level: Level, U, Ke, x0, D, coef=None) -> np.ndarray:
     W = x0[None, :, :] - U[dofs]
     KW = np.einsum("rc,ecm->erm", Ke, W)
     return np.einsum("e,eri,erj->eij", s, W, KW)
+
+
+def sensitivities(level: Level, U, Ke, x0, D, p: float) -> np.ndarray:
+    """Inverse-homogenization sensitivities (App. F.3) of the SIMP model
+    C_e = (rho_min + rho_e^p) C0 at the solid elements (rho_e = 1):
+        dC^H_IJ / d rho_e = p rho_e^(p-1) / |Omega| (x0^I - u_e^I)^T K0 (x0^J - u_e^J),
+    shape (ne, cases, cases), canonical element order, |Omega| = N^3."""
+    N = level.active.shape[0]
+    return p / float(N) ** 3 * element_energies(level, U, Ke, x0, D)
 
 
 def solve_cell(vox: np.ndarray, kind: str = "elastic", E: float = 1.0, nu: float = 0.3,

@@ -15,6 +15,16 @@ Alg. 1's GS(K^L ...) step, replaced by an exact solve) is the solution of
 K^L: for right-hand sides orthogonal to translations this is the zero-mean solution of
 K^L u = f^L.
 
+8-colour Gauss-Seidel (Sec. 4.6 "Parallel Smoothing", colour by colour): the nodes of a
+level are coloured by the parity of their coordinates, c = (x&1) + 2(y&1) + 4(z&1); nodes of
+one colour share no stencil entry, so each colour is updated at once with the damped
+block-Jacobi step u_c <- u_c + omega (D^{-1} (f - K u))_c on the latest u, colours 0..7 in
+turn, per sweep.
+
+Cycle schedules (Sec. 5 "V-/W-/F-cycles"): the coarse problem of level l is solved by one
+cycle of the same kind (V), by two W-cycles (the second starting from the first's result),
+or by an F-cycle followed by a V-cycle; the coarsest level is solved once.
+
 Chebyshev: one polynomial of degree k = nu (the sweep count, so that both smoothers apply K
 the same number of times) on D^{-1}K over [a, b] = [lmax/ratio, upper*lmax]:
 theta = (b+a)/2, delta = (b-a)/2, sigma = theta/delta, rho_0 = 1/sigma; d = D^{-1} r/theta;
@@ -55,7 +65,7 @@ def coarsest_matrix(KL, D: int) -> np.ndarray:
 
 class VCycle:
     def __init__(self, Ks, Ps, D: int, nu_pre=2, nu_post=2, omega=0.6, smoother="jacobi",
-                 cheb_lmax=None, cheb_ratio=30.0, cheb_upper=1.1):
+                 cheb_lmax=None, cheb_ratio=30.0, cheb_upper=1.1, kind="V", levels=None):
         self.Ks, self.Ps, self.D = Ks, Ps, D
         self.nu_pre, self.nu_post, self.omega = nu_pre, nu_post, omega
         self.smoother = smoother
@@ -63,12 +73,29 @@ class VCycle:
         self.Ainv = np.linalg.inv(coarsest_matrix(Ks[-1], D))
         self.lmax = cheb_lmax
         self.ratio, self.upper = cheb_ratio, cheb_upper
+        self.kind = kind
+        # per-dof colour masks for the 8-colour smoother (levels: the oracle grid.Level list)
+        self.colour_masks = None
+        if smoother == "gs8":
+            self.colour_masks = []
+            for lev in levels[:-1]:
+                xyz = lev.node_xyz()
+                col = (xyz[:, 0] & 1) + 2 * (xyz[:, 1] & 1) + 4 * (xyz[:, 2] & 1)
+                self.colour_masks.append([np.repeat(col == c, D) for c in range(8)])
 
     def smooth(self, l: int, u, f, sweeps: int):
         K, Di = self.Ks[l], self.Dinv[l]
         if self.smoother == "jacobi":
             for _ in range(sweeps):
                 u = u + self.omega * (Di @ (f - K @ u))
+            return u
+        if self.smoother == "gs8":
+            for _ in range(sweeps):
+                for c in range(8):
+                    m = self.colour_masks[l][c]
+                    step = self.omega * (Di @ (f - K @ u))
+                    u = u.copy()
+                    u[m] += step[m]
             return u
         lmax = self.lmax[l]
         b = self.upper * lmax
@@ -87,8 +114,9 @@ class VCycle:
             rho = rho_new
         return u
 
-    def cycle(self, f, u=None, level: int = 0):
+    def cycle(self, f, u=None, level: int = 0, kind=None):
         L = len(self.Ks)
+        kind = self.kind if kind is None else kind
         if level == L - 1:
             return self.Ainv @ f
         if u is None:
@@ -96,7 +124,9 @@ class VCycle:
         u = self.smooth(level, u, f, self.nu_pre)
         r = f - self.Ks[level] @ u
         fc = self.Ps[level].T @ r
-        uc = self.cycle(fc, None, level + 1)
+        uc = self.cycle(fc, None, level + 1, kind)
+        if level + 2 < L and kind != "V":
+            uc = self.cycle(fc, uc, level + 1, "W" if kind == "W" else "V")
         u = u + self.Ps[level] @ uc
         u = self.smooth(level, u, f, self.nu_post)
         return u

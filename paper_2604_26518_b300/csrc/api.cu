@@ -10,6 +10,7 @@
 namespace gmt {
 gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, gmt_info* info);
 void homogenize(gmt_hierarchy* h, const double* u, double* CH);
+void sensitivities(gmt_hierarchy* h, const double* u, double simp_p, double* out);
 void residual_of(gmt_hierarchy* h, int precision, const double* u, double* out);
 void estimate_lmax(gmt_hierarchy* h);
 void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);
@@ -41,7 +42,8 @@ using gmt::Fail;
   }
 
 static bool opts_valid(const gmt_options& o) {
-  return o.levels >= 0 && o.coarsest_max >= 4 && (o.smoother == 0 || o.smoother == 1) &&
+  return o.levels >= 0 && o.coarsest_max >= 4 && o.smoother >= 0 && o.smoother <= 2 &&
+         o.cycle >= 0 && o.cycle <= 2 &&
          o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post > 0 && o.omega > 0 &&
          o.cheb_ratio > 1 && o.cheb_upper >= 1 && o.precision >= 0 && o.precision <= 2 &&
          o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0;
@@ -95,6 +97,8 @@ void gmt_default_options(gmt_options* o) {
   o->inner_tol = 0.1;
   o->max_inner = 40;
   o->max_outer = 8;
+  o->cycle = GMT_CYCLE_V;
+  o->fp64_fallback = 1;
 }
 
 const char* gmt_status_string(gmt_status s) {
@@ -357,7 +361,28 @@ gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
   ensure_device(h);
   double setup = 0.0;
   ensure_material(h, physics, E, nu, k, &setup);
-  gmt_status st = gmt::solve(h, tol, u0, u_out, info);
+  gmt_info first;
+  gmt_status st = gmt::solve(h, tol, u0, u_out, info ? info : &first);
+  if (info) info->fp64_fallback = 0;
+  if (st == GMT_DIVERGED && h->opts.precision != GMT_PREC_FP64 && h->opts.fp64_fallback) {
+    // the mixed-precision iteration failed on this cell: solve again in plain FP64
+    const gmt_info f = info ? *info : first;
+    const int keep = h->opts.precision;
+    h->opts.precision = GMT_PREC_FP64;
+    try {
+      st = gmt::solve(h, tol, u0, u_out, info);
+    } catch (...) {
+      h->opts.precision = keep;
+      throw;
+    }
+    h->opts.precision = keep;
+    if (info) {
+      info->inner_total += f.inner_total;
+      info->outer += f.outer;
+      info->t_solve_ms += f.t_solve_ms;
+      info->fp64_fallback = 1;
+    }
+  }
   if (info) info->t_setup_ms = setup;
   return st;
   GMT_API_END
@@ -373,6 +398,21 @@ gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, doubl
   ensure_material(h, physics, E, nu, k, nullptr);
   if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "stored solution belongs to another material");
   gmt::homogenize(h, u, CH_out);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_sensitivities(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
+                             double k, double simp_p, const double* u, double* dCH_out) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h && dCH_out, GMT_ERR_ARG, "null argument");
+  GMT_REQUIRE(std::isfinite(simp_p) && simp_p > 0.0, GMT_ERR_ARG, "simp_p must be > 0");
+  ensure_device(h);
+  const bool stored = u == nullptr;
+  if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "no stored solution");
+  ensure_material(h, physics, E, nu, k, nullptr);
+  if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "stored solution belongs to another material");
+  gmt::sensitivities(h, u, simp_p, dCH_out);
   return GMT_OK;
   GMT_API_END
 }

@@ -161,6 +161,7 @@ struct Level {
   int* kidx = nullptr;          // nslots -> element-matrix index of the element with origin
                                 // at this slot (level 1: child mask; >= 2: element id), -1
   int* elem_slot = nullptr;     // n_elems -> slot of the element's origin (canonical order)
+  int* slot_elem = nullptr;     // level 0, lazy: slot -> canonical element or -1
   // material-dependent operator data (device)
   double* K64 = nullptr;        // level 1: [256][MM] table; level >= 2: [n_elems][MM]
   float* K32 = nullptr;

@@ -163,11 +163,32 @@ static void fetch(gmt_hierarchy* h, const double* dev, double* host, int n) {
 // (it alternates between the level's two buffers). part (level 0, zero == false): the last
 // sweep also writes [blocks][M + C] partials of f . u and the sums of u (fused).
 static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** u, void** other,
-                   int sweeps, bool zero, double* part = nullptr) {
+                   int sweeps, bool zero, double* part = nullptr, const void* aux = nullptr) {
   const gmt_options& o = h->opts;
   const Prec pr = w->prec;
   if (sweeps <= 0) {
     if (zero) vec_zero(h, l, pr, *u);
+    return;
+  }
+  if (o.smoother == GMT_SMOOTH_GS8) {
+    // 8-colour Gauss-Seidel: per sweep the colours in turn, each a damped block-Jacobi step
+    // on the nodes of that colour with the values the previous colours left
+    if (zero) vec_zero(h, l, pr, *u);
+    for (int s = 0; s < sweeps; ++s)
+      for (int c = 0; c < 8; ++c) {
+        VecArgs a;
+        a.u = *u;
+        a.f = f;
+        a.out = *other;
+        a.omega = o.omega;
+        a.colour = c;
+        if (s + 1 == sweeps && c == 7) {
+          a.part = part;
+          a.aux = aux;
+        }
+        launch_stencil(h, l, pr, ST_JACOBI, a);
+        std::swap(*u, *other);
+      }
     return;
   }
   if (o.smoother == GMT_SMOOTH_JACOBI) {
@@ -182,7 +203,10 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
       a.f = f;
       a.out = *other;
       a.omega = o.omega;
-      if (s + 1 == sweeps) a.part = part;
+      if (s + 1 == sweeps) {
+        a.part = part;
+        a.aux = aux;
+      }
       launch_stencil(h, l, pr, ST_JACOBI, a);
       std::swap(*u, *other);
     }
@@ -207,7 +231,10 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
     a.dout = d;
     a.c1 = 0.0;
     a.c2 = 1.0 / theta;
-    if (sweeps == 1) a.part = part;
+    if (sweeps == 1) {
+      a.part = part;
+      a.aux = aux;
+    }
     launch_stencil(h, l, pr, ST_CHEB, a);
     std::swap(*u, *other);
     s0 = 1;
@@ -222,7 +249,10 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
     a.dout = (s + 1 < sweeps) ? d : nullptr;
     a.c1 = rho_new * rho;
     a.c2 = 2.0 * rho_new / delta;
-    if (s + 1 == sweeps) a.part = part;
+    if (s + 1 == sweeps) {
+      a.part = part;
+      a.aux = aux;
+    }
     launch_stencil(h, l, pr, ST_CHEB, a);
     std::swap(*u, *other);
     rho = rho_new;
@@ -233,9 +263,12 @@ static void smooth(gmt_hierarchy* h, Workspace* w, int l, const void* f, void** 
 // buffer that holds the result: one of the level's two ping-pong buffers (level 0: ua/ub).
 // part (level 0, nu_post >= 1): the last post-smoothing sweep writes [blocks][M + C]
 // partials of f . u and the sums of u (see smooth()).
+// cycle: GMT_CYCLE_V, _W or _F (the coarse problem of level l gets one V-cycle, two
+// W-cycles, or an F-cycle followed by a V-cycle; the coarsest level is solved once).
 static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* u_init, bool zero,
-                    double* part = nullptr) {
+                    double* part = nullptr, int cycle = -1, const void* aux = nullptr) {
   const Prec pr = w->prec;
+  if (cycle < 0) cycle = h->opts.cycle;
   if (l == h->L - 1) {
     launch_coarse_solve(h, pr, f, w->ua[l]);
     return w->ua[l];
@@ -249,9 +282,12 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
   a.out = w->r[l];
   launch_stencil(h, l, pr, ST_RESID, a);
   launch_restrict(h, l, pr, w->r[l], w->f[l + 1]);
-  void* uc = vcycle(h, w, l + 1, w->f[l + 1], nullptr, true);
+  void* uc = vcycle(h, w, l + 1, w->f[l + 1], nullptr, true, nullptr, cycle);
+  if (l + 2 < h->L && cycle != GMT_CYCLE_V)
+    uc = vcycle(h, w, l + 1, w->f[l + 1], uc, false, nullptr,
+                cycle == GMT_CYCLE_W ? GMT_CYCLE_W : GMT_CYCLE_V);
   launch_prolong(h, l, pr, uc, u);
-  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false, part);
+  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false, part, aux);
   return u;
 }
 
@@ -399,7 +435,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     sum_values(vec);
     vec_sub_mean32(h, vmean, (float*)vec);
   };
-  int cycles = 0, updates = 0, restarts = 0;
+  int cycles = 0, updates = 0, restarts = 0, trips = 0;
   static const bool verbose = std::getenv("GMT_VERBOSE") != nullptr;
   gmt_status st = GMT_NOT_CONVERGED;
   double mx = true_residual();
@@ -470,13 +506,19 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         for (int m = 0; m < M; ++m) std::fprintf(stderr, " %.3e", std::sqrt(rn[m]) / fn[m]);
         std::fprintf(stderr, "\n");
       }
-      bool replace = false, nan = false;
+      bool replace = false, nan = false, grew = false;
+      double rit[8] = {0};   // iterated residuals of this cycle
       for (int m = 0; m < M; ++m) {
         if (!act[m]) continue;
         const double r = std::sqrt(rn[m]) / fn[m];
+        rit[m] = r;
         if (std::isnan(r)) nan = true;
         if (r <= 0.5 * tol || (mixed && r <= o.inner_tol * ref[m])) replace = true;
+        // growth guard: an iterated residual 10x above the last true one means the
+        // recurrence has lost its conjugacy in the inner precision
+        if (krylov && r > 10.0 * ref[m]) grew = true;
       }
+      if (grew) replace = true;
       const bool last = cycles >= max_cycles;
       bool restart = false;
       if (replace || nan || last) {
@@ -501,40 +543,64 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
           break;
         }
         if (last) break;
-        // stagnation guard: a replacement that gained less than 10 % restarts the Krylov
-        // recurrence from the true residual
-        for (int m = 0; m < M; ++m)
-          if (act[m] && rel[m] > 0.9 * ref[m]) restart = true;
+        // a second growth-guard trip in the inner precision: the FP32 V-cycle is too far from
+        // symmetric for CG on this cell (near-singular modes that FP32 cannot resolve); stop
+        // and let the caller fall back to the FP64 solve
+        if (grew && ++trips >= 2 && mixed) {
+          st = GMT_DIVERGED;
+          break;
+        }
+        // restart the Krylov recurrence from the true residual when the replacement gained
+        // less than 10 % (stagnation), when the iterated residual had grown (growth guard),
+        // or when the true residual is more than 2x the iterated one (the recurrence no
+        // longer tracks the residual it claims)
+        if (grew) restart = true;
+        for (int m = 0; m < M; ++m) {
+          if (!act[m]) continue;
+          if (rel[m] > 0.9 * ref[m]) restart = true;
+          if (rit[m] > 0.0 && rel[m] > 2.0 * rit[m]) restart = true;
+        }
         for (int m = 0; m < M; ++m) ref[m] = rel[m];
         deactivate_converged();
         push_active();
       }
-      // the last post-smoothing sweep writes the partials of r.z and of the sums of z
+      // the last post-smoothing sweep writes the partials of r.z, q.z (q = K p of the last
+      // direction) and of the sums of z
       const bool fused = krylov && h->L > 1 && o.nu_post >= 1;
-      z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr);
+      z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr, -1,
+                 fused ? w->q : nullptr);
       ++cycles;
       if (krylov) {
         // rr is mean-free, so r.z needs no correction for the mean of z; the mean of z is
-        // removed while forming the new direction
-        const int ld = fused ? M + C : M;
+        // removed while forming the new direction.
+        // Flexible CG (Polak-Ribiere): beta = z_new.(r_new - r_old) / (z_old.r_old)
+        //   = -alpha (z_new.q) / (z_old.r_old), since r_new - r_old = -alpha q. With a fixed
+        // symmetric preconditioner this is the Fletcher-Reeves beta of plain PCG; it stays
+        // robust when FP32 rounding makes the V-cycle slightly non-symmetric.
+        const int ld = fused ? 2 * M + C : M;
+        double* zq = w->part + (fused ? M : (int64_t)h->lv[0].nb * M);   // partials of q.z
+        const int zq_ld = fused ? ld : M;
         if (fused) {
           if (mixed) {
             RedEpi em;
             em.mode = 3;
             em.out32 = vmean;
             em.scale = 1.0 / (double)h->lv[0].n_nodes;
-            launch_reduce(h, w->part + M, h->lv[0].nb, C, vsums, em, ld);
+            launch_reduce(h, w->part + 2 * M, h->lv[0].nb, C, vsums, em, ld);
           }
         } else {
           if (mixed) sum_values(z);
+          vec_dot(h, 0, ar, w->q, z, zq);
           vec_dot(h, 0, ar, w->rr, z, w->part);
         }
+        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new, RedEpi(), ld);
         RedEpi e;
-        e.mode = 2;   // beta = rz_new / rz
+        e.mode = 6;   // beta = -alpha (q.z) / rz
         e.other = rz;
+        e.other2 = alpha;
         e.active = w->active;
         e.ratio = beta;
-        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new, e, ld);
+        launch_reduce(h, zq, h->lv[0].nb, M, w->red + 10 * 32 + 16, e, zq_ld);
         if (restart) {
           if (mixed) vec_sub_mean32(h, vmean, (float*)z);
           vec_copy(h, 0, ar, z, w->p);
@@ -595,12 +661,18 @@ void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
   Workspace* w = h->ws;
   Prec pr = w ? w->prec : P32;
   if (!w) w = workspace(h, P32);
+  const void* u64 = w->u64;
   if (u) {
-    // external field: float-float split of the FP64 input
-    canon_to_ff(h, u, w->hi, w->lo);
-    pr = P32;
+    // external field: FP64 on an FP64 workspace (scratch copy, the stored solution stays),
+    // else the float-float split of the FP64 input
+    if (pr == P64) {
+      canon_to_slots(h, 0, P64, u, w->f64);
+      u64 = w->f64;
+    } else {
+      canon_to_ff(h, u, w->hi, w->lo);
+    }
   }
-  if (pr == P64) launch_energy(h, P64, w->u64, nullptr, w->part);
+  if (pr == P64) launch_energy(h, P64, u64, nullptr, w->part);
   else launch_energy(h, P32, w->hi, w->lo, w->part);
   double e[21];
   fetch(h, reduce_to(h, w, 0, K, 0), e, K);
@@ -612,6 +684,27 @@ void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
       CH[I * M + J] = v;
       CH[J * M + I] = v;
     }
+}
+
+// dC^H_IJ / d rho_e of the SIMP model C_e = (rho_min + rho_e^p) C0 at the solid elements
+// (rho_e = 1): p / |Omega| (x0^I - u_e^I)^T K0 (x0^J - u_e^J) (App. F.3), per element
+void sensitivities(gmt_hierarchy* h, const double* u, double simp_p, double* out) {
+  Workspace* w = h->ws;
+  Prec pr = w ? w->prec : P32;
+  if (!w) w = workspace(h, P32);
+  const void* u64 = w->u64;
+  if (u) {
+    if (pr == P64) {
+      canon_to_slots(h, 0, P64, u, w->f64);
+      u64 = w->f64;
+    } else {
+      canon_to_ff(h, u, w->hi, w->lo);
+    }
+  }
+  const double scale = simp_p / ((double)h->N * h->N * h->N);
+  if (pr == P64) launch_energy_per(h, P64, u64, nullptr, out, scale);
+  else launch_energy_per(h, P32, w->hi, w->lo, out, scale);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
 
 // relative residuals of a canonical field

@@ -69,10 +69,12 @@ struct StArgs {
   const TS* u;
   const TS* f;
   const TS* dprev;
+  const TS* aux;
   TS* out;
   TS* dout;
   double* part;
   A omega, c1, c2;
+  int colour;
   FineC<A, D, M> fc;
 };
 
@@ -256,9 +258,9 @@ __device__ __forceinline__ void stage_tile(const TS* __restrict__ u, int64_t b, 
 // product accurate (about 20x closer to the FP64 product than the direct form on V-cycle
 // output). It annihilates translations exactly, so the mixed-precision solver keeps its
 // residual and preconditioned directions free of translations (see solver.cu).
-// SUMS (smoother modes): also write per-block partials [M + C] of f . out per case and of
-// out per value over active nodes (the V-cycle's last sweep: r.z and the mean of z for the
-// Krylov step, without another pass over the vectors).
+// SUMS (smoother modes): also write per-block partials [2M + C]: f . out per case, aux . out
+// per case (0 without aux) and out per value over active nodes (the V-cycle's last sweep:
+// r.z, (K p).z and the mean of z for the Krylov step, without another pass over vectors).
 template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS = false>
 __global__ void __launch_bounds__(64)
     k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
@@ -485,10 +487,13 @@ __global__ void __launch_bounds__(64)
         for (int k = 0; k < DD; ++k) Iv[k] = p.dinv[slot * DD + k];
       }
     }
-    A sums[SUMS ? M + C : 1];
+    // colour of this node: the parity of its coordinates (bricks start at multiples of 4)
+    const int lx = t & 3, ly = t >> 4, lz = (t >> 2) & 3;
+    const bool upd = p.colour < 0 || p.colour == (lx & 1) + 2 * (ly & 1) + 4 * (lz & 1);
+    A sums[SUMS ? 2 * M + C : 1];
     if constexpr (SUMS) {
 #pragma unroll
-      for (int k = 0; k < M + C; ++k) sums[k] = A(0);
+      for (int k = 0; k < 2 * M + C; ++k) sums[k] = A(0);
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -506,7 +511,7 @@ __global__ void __launch_bounds__(64)
         const int v = i * M + m;
         A o;
         if constexpr (MODE == ST_JACOBI) {
-          o = mk ? self[v] + p.omega * z : A(0);
+          o = mk ? (upd ? self[v] + p.omega * z : self[v]) : A(0);
         } else {
           const A dn = (p.c1 != A(0) ? p.c1 * load_as<A>(p.dprev + base + v * 64) : A(0)) + p.c2 * z;
           o = mk ? self[v] + dn : A(0);
@@ -517,11 +522,12 @@ __global__ void __launch_bounds__(64)
         if constexpr (SUMS) {
           const A ov = load_as<A>(&os);   // the stored value
           sums[m] += mk ? fv[i] * ov : A(0);
-          sums[M + v] += ov;
+          if (p.aux) sums[M + m] += mk ? load_as<A>(p.aux + base + v * 64) * ov : A(0);
+          sums[2 * M + v] += ov;
         }
       }
     }
-    if constexpr (SUMS) block_partial_64<M + C, A>(sums, p.part + b * (M + C));
+    if constexpr (SUMS) block_partial_64<2 * M + C, A>(sums, p.part + b * (2 * M + C));
   }
 }
 
@@ -1088,6 +1094,12 @@ struct EnArgs {
   A Fl[8 * D * M];
   f2_t Ke2[32 * D * D];   // ff path: rows (2 rp, 2 rp + 1) of Ke / Kl packed per column
   f2_t Kl2[32 * D * D];
+  // per-element output (sensitivities): out[e][I][J] = scale * (E_IJ of element e), with e
+  // the canonical element index of the slot (slot_elem) and C0 added back on the ff path
+  double* per;
+  const int* slot_elem;
+  double scale;
+  double C0[M * M];
 };
 
 // Per active element e (origin slot n) and load cases I <= J, the energy
@@ -1108,7 +1120,8 @@ constexpr size_t energy_smem_bytes() {
   return (size_t)(FF ? 2 : 1) * G * 216 * 16 + (size_t)8 * D * M * 64 * sizeof(A);
 }
 
-template <typename A, int D, int M, bool FF>
+// PER: write each element's energies (times p.scale) instead of the block sums.
+template <typename A, int D, int M, bool FF, bool PER = false>
 __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
@@ -1236,10 +1249,25 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
       }
     }
   }
-  ES e[K];
+  if constexpr (PER) {
+    if (!act) return;
+    const int64_t el = p.slot_elem[b * 64 + loc];
 #pragma unroll
-  for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : ES(0);
-  block_partial_64<K, ES>(e, p.part + b * K);
+    for (int I = 0; I < M; ++I)
+#pragma unroll
+      for (int J = I; J < M; ++J) {
+        double v = (double)es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t];
+        if constexpr (FF) v += p.C0[I * M + J];
+        v *= p.scale;
+        p.per[(el * M + I) * M + J] = v;
+        p.per[(el * M + J) * M + I] = v;
+      }
+  } else {
+    ES e[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : ES(0);
+    block_partial_64<K, ES>(e, p.part + b * K);
+  }
 }
 
 // deterministic reduction of [nblk][K] partials. Column k is split over gridDim.y blocks;
@@ -1326,6 +1354,8 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
     epi.out32[epi.count + k] = (float)(x - (double)hf);
   } else if (epi.mode == 5) {
     epi.ratio[k] = 1.0 / sqrt(fmax(v, 1e-300));
+  } else if (epi.mode == 6) {
+    epi.ratio[k] = (act && epi.other[k] != 0.0) ? -epi.other2[k] * v / epi.other[k] : 0.0;
   }
 }
 
@@ -1658,12 +1688,14 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   p.u = (const TS*)va.u;
   p.f = (const TS*)va.f;
   p.dprev = (const TS*)va.dprev;
+  p.aux = (const TS*)va.aux;
   p.out = (TS*)va.out;
   p.dout = (TS*)va.dout;
   p.part = va.part;
   p.omega = (A)va.omega;
   p.c1 = (A)va.c1;
   p.c2 = (A)va.c2;
+  p.colour = va.colour;
   const bool fine = level == 0;
   if (fine) fill_fine<A, D, M>(h->mat, p.fc);
   const unsigned g = (unsigned)lv.nb;
@@ -1840,7 +1872,8 @@ void launch_coarse_solve(gmt_hierarchy* h, Prec prec, const void* f, void* u) {
 }
 
 template <typename A, int D, int M, bool FF>
-static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* part) {
+static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* part,
+                     double* per = nullptr, double scale = 0.0) {
   const Level& lv = h->lv[0];
   EnArgs<A, D, M> p;
   std::memset(&p, 0, sizeof(p));
@@ -1874,10 +1907,50 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
     p.Fl[i] = (A)(h->mat.Fe[i] - (double)p.Fh[i]);
   }
   constexpr size_t smem = energy_smem_bytes<A, D, M, FF>();
-  ensure_smem_attr((const void*)k_energy<A, D, M, FF>, (int)smem);
   TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
-  k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
+  if (per) {
+    p.per = per;
+    p.slot_elem = level0_slot_elem(h);
+    p.scale = scale;
+    for (int i = 0; i < M * M; ++i) p.C0[i] = h->mat.C0[i];
+    ensure_smem_attr((const void*)k_energy<A, D, M, FF, true>, (int)smem);
+    k_energy<A, D, M, FF, true><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
+  } else {
+    ensure_smem_attr((const void*)k_energy<A, D, M, FF>, (int)smem);
+    k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
+  }
   GMT_LAUNCH_CHECK();
+}
+
+// canonical element index of each level-0 slot whose element (origin at the slot) is
+// active, -1 elsewhere; built on first use from the element -> slot map
+__global__ void k_slot_elem(const int* __restrict__ elem_slot, int64_t ne, int* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ne) out[elem_slot[e]] = (int)e;
+}
+
+const int* level0_slot_elem(gmt_hierarchy* h) {
+  Level& l0 = h->lv[0];
+  if (!l0.slot_elem) {
+    l0.slot_elem = h->geo.alloc<int>(l0.nslots);
+    GMT_CUDA(cudaMemsetAsync(l0.slot_elem, 0xff, l0.nslots * sizeof(int), h->stream));
+    k_slot_elem<<<grid_for(l0.n_elems, 256), 256, 0, h->stream>>>(l0.elem_slot, l0.n_elems,
+                                                                  l0.slot_elem);
+    GMT_LAUNCH_CHECK();
+  }
+  return l0.slot_elem;
+}
+
+void launch_energy_per(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u_lo,
+                       double* per, double scale) {
+  const bool d3 = h->mat.D == 3;
+  if (prec == P64) {
+    if (d3) energy_t<double, 3, 6, false>(h, u_hi, nullptr, nullptr, per, scale);
+    else energy_t<double, 1, 3, false>(h, u_hi, nullptr, nullptr, per, scale);
+  } else {
+    if (d3) energy_t<float, 3, 6, true>(h, u_hi, u_lo, nullptr, per, scale);
+    else energy_t<float, 1, 3, true>(h, u_hi, u_lo, nullptr, per, scale);
+  }
 }
 
 void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u_lo,

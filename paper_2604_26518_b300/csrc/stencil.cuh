@@ -17,8 +17,12 @@ struct VecArgs {
   void* out = nullptr;
   void* dout = nullptr;
   double* part = nullptr;      // per-block partial sums [blocks][M] (APPLY, RESID); level-0
-                               // smoother: [blocks][M + C] of f . out and sums of out
+                               // smoother: [blocks][2M + C] of f . out, aux . out (0 when
+                               // aux is null) and the sums of out
+  const void* aux = nullptr;   // level-0 smoother with part: second vector dotted with out
   double omega = 0, c1 = 0, c2 = 0;
+  int colour = -1;             // ST_JACOBI: update only nodes of this parity colour
+                               // (x & 1) + 2 (y & 1) + 4 (z & 1), copy the others; -1 = all
 };
 
 // per-node assembled stencils of a coarse level (FP32 or FP64 copy; built once)
@@ -39,6 +43,11 @@ void launch_coarse_solve(gmt_hierarchy* h, Prec prec, const void* f, void* u);
 // per-element energies of level 0 -> block partials [blocks][M(M+1)/2]; ff: u = (hi, lo)
 void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u_lo,
                    double* part);
+// per-element energies times scale into per[n_elems][M][M] (canonical element order)
+void launch_energy_per(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u_lo,
+                       double* per, double scale);
+// level-0 slot -> canonical element index (-1 where no element has its origin)
+const int* level0_slot_elem(gmt_hierarchy* h);
 
 // deterministic fixed-order reduction of [nblk][K] partials into out[K] (device);
 // compensated (Neumaier) per thread
@@ -53,9 +62,11 @@ struct RedEpi {
                                  // 3: out32 = (float)(out * scale);
                                  // 4: out * scale split into floats: out32[k] (hi) and
                                  //    out32[count + k] (lo);
-                                 // 5: ratio = 1 / sqrt(max(out, 1e-300))
+                                 // 5: ratio = 1 / sqrt(max(out, 1e-300));
+                                 // 6: ratio = -other2[k] * out / other[k] (flexible CG beta)
   const double* other = nullptr;
-  const int* active = nullptr;   // modes 1, 2: ratio 0 for inactive cases (may be null)
+  const double* other2 = nullptr;
+  const int* active = nullptr;   // modes 1, 2, 6: ratio 0 for inactive cases (may be null)
   double* ratio = nullptr;
   float* out32 = nullptr;
   double scale = 0.0;

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libgmt.so")
 
 ELASTIC, HEAT = 0, 1
 FP64, FP32, BF16 = 0, 1, 2
-JACOBI, CHEBYSHEV = 0, 1
+JACOBI, CHEBYSHEV, GS8 = 0, 1, 2
+CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
 
 OK, ERR_ARG, ERR_RES, ERR_EMPTY, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, ERR_STATE = range(9)
 
@@ -41,6 +42,8 @@ class Options(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("max_inner", ctypes.c_int),
         ("max_outer", ctypes.c_int),
+        ("cycle", ctypes.c_int),
+        ("fp64_fallback", ctypes.c_int),
     ]
 
 
@@ -52,12 +55,14 @@ class Info(ctypes.Structure):
         ("rel_residual", ctypes.c_double * 6),
         ("t_setup_ms", ctypes.c_double),
         ("t_solve_ms", ctypes.c_double),
+        ("fp64_fallback", ctypes.c_int),
     ]
 
     def as_dict(self):
         return {"outer": self.outer, "cycles": self.inner_total,
                 "rel_residual": list(self.rel_residual)[: self.cases],
-                "t_setup_ms": self.t_setup_ms, "t_solve_ms": self.t_solve_ms}
+                "t_setup_ms": self.t_setup_ms, "t_solve_ms": self.t_solve_ms,
+                "fp64_fallback": self.fp64_fallback}
 
 
 class GmtError(RuntimeError):
@@ -99,6 +104,7 @@ _SIGS = {
     "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
+    "gmt_sensitivities": (_I, [_P, _I, _D, _D, _D, _D, _P, _P]),
     "gmt_residual": (_I, [_P, _I, _P, _P]),
     "gmt_trace_enable": (_I, [_P, _I]),
     "gmt_trace_query": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -339,6 +345,18 @@ class Hierarchy:
         _check(lib().gmt_homogenize(self._h, physics, E, nu, k, _ptr(ut),
                                     CH.ctypes.data_as(ctypes.c_void_p)), "gmt_homogenize")
         return CH
+
+    def sensitivities(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, p=3.0, u=None):
+        """dC^H / d rho_e per solid element (SIMP penalisation p), a device tensor
+        [n_elems][M][M] in canonical element order (gmt_sensitivities)."""
+        torch = _torch()
+        self.physics = physics
+        D, M = self._dm()
+        out = torch.empty((self.num_elements(0), M, M), dtype=torch.float64, device="cuda")
+        ut = None if u is None else self._field(0, u)
+        _check(lib().gmt_sensitivities(self._h, physics, E, nu, k, p, _ptr(ut), _ptr(out)),
+               "gmt_sensitivities")
+        return out
 
     # ---------------------------------------------------------------- tracing
     def trace(self, on=True):

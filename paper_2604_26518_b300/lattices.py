@@ -26,6 +26,7 @@ from scipy import ndimage
 __all__ = [
     "gyroid_field", "schwarz_p_field", "diamond_field", "tpms_network", "tpms_plate",
     "truss", "spinodal", "largest_component", "laminate_z", "rods_x", "random_binary",
+    "batch_cell",
     "mixed_cell", "FAMILIES",
 ]
 
@@ -234,3 +235,14 @@ def mixed_cell(seed: int, n: int, families=FAMILIES, phi_range=(0.10, 0.40),
         vox = largest_component(vox)
     desc["phi"] = float(vox.mean())
     return vox, desc
+
+
+BATCH_RESOLUTIONS = (32, 48, 64, 96, 128)
+
+
+def batch_cell(seed: int, resolutions=BATCH_RESOLUTIONS):
+    """One cell of the uneven-resolution batch: N drawn uniformly from `resolutions` by its
+    own PCG64(seed) stream, then mixed_cell(seed, N) over all families (spinodal included)."""
+    rng = np.random.default_rng(np.random.PCG64([seed, 1]))
+    n = int(resolutions[int(rng.integers(0, len(resolutions)))])
+    return mixed_cell(seed, n, families=FAMILIES)

@@ -145,3 +145,39 @@ def test_lambda_max_estimate(gmt_lib):
         lam = float(np.abs(spla.eigs(A, k=1, which="LM", return_eigenvectors=False))[0])
         est = h.lambda_max(l)
         assert 0.9 * lam <= est <= lam * (1 + 1e-6), (l, est, lam)
+
+
+@pytest.mark.parametrize("smoother,kind", [("gs8", "V"), ("jacobi", "W"), ("jacobi", "F"),
+                                           ("gs8", "W")])
+@pytest.mark.parametrize("name", ["gyroid32", "octet16"])
+def test_cycle_schedules_and_gs8_parity(gmt_lib, name, smoother, kind):
+    """8-colour Gauss-Seidel smoothing and W-/F-cycles against the oracle's cycle."""
+    gmt = gmt_lib
+    vox = CELLS[name]
+    sm = gmt.GS8 if smoother == "gs8" else gmt.JACOBI
+    cyc = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[kind]
+    h = gmt.Hierarchy(vox, gmt.default_options(smoother=sm, cycle=cyc))
+    O = oracle_setup(vox, "elastic", h.levels)
+    h.prepare(gmt.ELASTIC)
+    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, kind=kind, levels=O["levels"])
+    F = O["F"]
+    u1 = to_np(h.vcycle(F, None, gmt.FP64), 3, 6)
+    r1 = vc.cycle(F)
+    assert rel_err(u1, r1) < 1e-10, rel_err(u1, r1)
+    u2 = to_np(h.vcycle(F, u1, gmt.FP64), 3, 6)
+    assert rel_err(u2, vc.cycle(F, r1)) < 1e-10
+    assert rel_err(to_np(h.vcycle(F, None, gmt.FP32), 3, 6), r1) < 1e-4
+
+
+@pytest.mark.parametrize("smoother,kind", [("gs8", "V"), ("jacobi", "W"), ("jacobi", "F")])
+def test_solve_with_other_schedules(gmt_lib, smoother, kind):
+    gmt = gmt_lib
+    vox = CELLS["gyroid32"]
+    sm = gmt.GS8 if smoother == "gs8" else gmt.JACOBI
+    cyc = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[kind]
+    ref = solve.solve_cell(vox, "elastic", tol=1e-8)
+    h = gmt.Hierarchy(vox, gmt.default_options(smoother=sm, cycle=cyc))
+    st, u, info = h.solve(gmt.ELASTIC, tol=1e-5)
+    assert st == gmt.OK
+    CH = h.homogenize(gmt.ELASTIC)
+    assert np.abs(CH - ref["CH"]).max() <= 1e-4 * np.abs(ref["CH"]).max()

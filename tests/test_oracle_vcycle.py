@@ -74,3 +74,92 @@ def test_coarsest_solve_is_zero_mean_solution():
     u = np.linalg.solve(A, f)
     assert np.abs(Ks[-1] @ u - f).max() < 1e-10 * np.abs(f).max()
     assert np.abs(u.reshape(-1, D, 2).mean(axis=0)).max() < 1e-12 * np.abs(u).max()
+
+
+# ---------------------------------------------------------------- 8-colour Gauss-Seidel
+def test_same_colour_nodes_are_decoupled():
+    vox = L.tpms_network("diamond", 16, 0.35)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, "elastic")
+    for lev, K in zip(lv[:-1], Ks[:-1]):
+        xyz = lev.node_xyz()
+        col = (xyz[:, 0] & 1) + 2 * (xyz[:, 1] & 1) + 4 * (xyz[:, 2] & 1)
+        Kc = K.tocoo()
+        a, b = Kc.row // D, Kc.col // D
+        off = (a != b) & (np.abs(Kc.data) > 0)
+        assert not np.any(col[a[off]] == col[b[off]])
+
+
+def test_gs8_sweep_equals_nodewise_block_gauss_seidel():
+    """With omega = 1 the colour-by-colour sweep is block Gauss-Seidel over the nodes in
+    colour order (written here as a plain loop solving each node's D x D block)."""
+    vox = L.tpms_network("gyroid", 8, 0.4)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, "elastic", 2)
+    vc = vcycle.VCycle(Ks, Ps, D, omega=1.0, smoother="gs8", levels=lv)
+    rng = np.random.default_rng(3)
+    u0 = rng.standard_normal(F.shape)
+    got = vc.smooth(0, u0, F, 1)
+    K = Ks[0].toarray()
+    xyz = lv[0].node_xyz()
+    col = (xyz[:, 0] & 1) + 2 * (xyz[:, 1] & 1) + 4 * (xyz[:, 2] & 1)
+    u = u0.copy()
+    for c in range(8):
+        for n in np.nonzero(col == c)[0]:
+            rows = slice(n * D, n * D + D)
+            r = F[rows] - K[rows] @ u
+            u[rows] += np.linalg.solve(K[rows, rows], r)
+    assert np.abs(got - u).max() <= 1e-12 * np.abs(u).max()
+
+
+# ---------------------------------------------------------------- W- and F-cycles
+def test_two_level_cycles_coincide():
+    vox = L.tpms_network("schwarz_p", 16, 0.3)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, "elastic", 2)
+    outs = [vcycle.VCycle(Ks, Ps, D, kind=k).cycle(F) for k in ("V", "W", "F")]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_three_level_w_cycle_is_v_with_two_coarse_cycles():
+    """On three levels the W-cycle's coarse correction is two level-1 cycles (the second
+    starting from the first), each ending in the exact coarsest solve; written out here from
+    the assembled matrices with the smoother formula, not through VCycle.cycle."""
+    vox = L.tpms_network("gyroid", 16, 0.3)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, "elastic", 3)
+    vc = vcycle.VCycle(Ks, Ps, D, kind="W")
+    Di = [vcycle.block_diag_inverse(K, D) for K in Ks[:-1]]
+    Ainv = np.linalg.inv(vcycle.coarsest_matrix(Ks[-1], D))
+
+    def jac(l, u, f, n):
+        for _ in range(n):
+            u = u + 0.6 * (Di[l] @ (f - Ks[l] @ u))
+        return u
+
+    def two_grid(l, f, u):
+        u = jac(l, u, f, 2)
+        uc = Ainv @ (Ps[l].T @ (f - Ks[l] @ u))
+        return jac(l, u + Ps[l] @ uc, f, 2)
+
+    u = jac(0, np.zeros_like(F), F, 2)
+    fc = Ps[0].T @ (F - Ks[0] @ u)
+    uc = two_grid(1, fc, np.zeros_like(fc))
+    uc = two_grid(1, fc, uc)
+    expect = jac(0, u + Ps[0] @ uc, F, 2)
+    got = vc.cycle(F)
+    assert np.abs(got - expect).max() <= 1e-12 * np.abs(expect).max()
+    # F on three levels: F-cycle then V-cycle on level 1 = the same two two-grid cycles
+    assert np.abs(vcycle.VCycle(Ks, Ps, D, kind="F").cycle(F) - expect).max() <= 1e-12 * np.abs(expect).max()
+
+
+@pytest.mark.parametrize("kind", ["W", "F"])
+def test_w_and_f_cycles_contract_at_least_as_well_as_v(kind):
+    vox = L.tpms_network("gyroid", 32, 0.3)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, "elastic", 4)
+    fn = np.linalg.norm(F, axis=0)
+
+    def rate(k):
+        vc = vcycle.VCycle(Ks, Ps, D, kind=k)
+        U = np.zeros_like(F)
+        for _ in range(6):
+            U = vc.cycle(F, U)
+        return (np.linalg.norm(F - Ks[0] @ U, axis=0) / fn).max()
+
+    assert rate(kind) <= rate("V") * 1.0001
