@@ -38,9 +38,10 @@ C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_
                "plate_diamond", "bcc", "octet")
 METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
 TOL = 1e-5
-# ncu DRAM bytes (read + write) per active node of one level-0 smoother sweep, from the
-# capture summarised in profiles/ (None until a capture of the current kernel exists)
-NCU_DRAM_BYTES_PER_NODE = None
+# ncu DRAM bytes (read + write) per active node of one level-0 smoother sweep of the
+# current kernel: 138.5 MB over the 651,308 active nodes of the first 128^3 bench cell
+# (profiles/k_stencil_smoother_c128_elastic.md); scaled by the nodes of each sweep
+NCU_DRAM_BYTES_PER_NODE = 212.7
 
 
 def workload(name: str, rank: int):
@@ -348,6 +349,9 @@ def run_gmt(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "kernel": "level-0 smoother sweep (k_stencil JACOBI)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read + write of one level-0 sweep on "
+                                       "the first 128^3 cell, per active node, times this "
+                                       "workload's nodes per sweep",
                      "peak_source": peak_src,
                      "algorithmic_bytes": "3 vectors x 18 values x 4 B per active node",
                      "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
