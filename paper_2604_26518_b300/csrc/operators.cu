@@ -442,37 +442,38 @@ __global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, double rho) 
 // After all panels the matrix holds the (generalized) inverse.
 constexpr int GJB = 32;
 
-// one block: invert the bb x bb diagonal panel block (pivots <= tol are dropped)
+// one warp inverts the bb x bb diagonal panel block (pivots <= tol dropped), the panel in
+// registers: lane j holds column j, and step k broadcasts the pivot column from lane k
+// with shuffles, so the 32 pivot steps need no shared memory and no block barrier
 template <typename T>
-__global__ void __launch_bounds__(1024) k_gj_panel(const T* __restrict__ A, int64_t m,
-                                                   int64_t k0, int bb, T tol,
-                                                   T* __restrict__ inv) {
-  __shared__ T P[GJB][GJB + 1];
-  __shared__ T rowk[GJB], colk[GJB];
-  __shared__ int ok;
-  const int t = threadIdx.x, i = t / GJB, j = t % GJB;
-  if (i < bb && j < bb) P[i][j] = A[(k0 + i) * m + k0 + j];
-  __syncthreads();
-  for (int k = 0; k < bb; ++k) {
-    if (t < bb) {
-      rowk[t] = P[k][t];
-      colk[t] = P[t][k];
+__global__ void __launch_bounds__(32) k_gj_panel_warp(const T* __restrict__ A, int64_t m,
+                                                      int64_t k0, int bb, T tol,
+                                                      T* __restrict__ inv) {
+  const int j = threadIdx.x;
+  T P[GJB];
+#pragma unroll
+  for (int i = 0; i < GJB; ++i) P[i] = (i < bb && j < bb) ? A[(k0 + i) * m + k0 + j] : T(0);
+#pragma unroll
+  for (int k = 0; k < GJB; ++k) {
+    if (k >= bb) break;  // uniform across the warp
+    const T p = __shfl_sync(0xffffffffu, P[k], k);   // P[k][k]
+    const bool ok = p > tol;
+    const T ip = ok ? T(1) / p : T(0);
+    const T rk = P[k];                                // P[k][j], before the step
+#pragma unroll
+    for (int i = 0; i < GJB; ++i) {
+      const T c = __shfl_sync(0xffffffffu, P[i], k);  // P[i][k], before the step
+      T v;
+      if (!ok) v = (i == k || j == k) ? T(0) : P[i];
+      else if (i == k) v = (j == k) ? ip : rk * ip;
+      else if (j == k) v = -c * ip;
+      else v = P[i] - c * (rk * ip);
+      P[i] = v;
     }
-    if (t == 0) ok = P[k][k] > tol;
-    __syncthreads();
-    if (i < bb && j < bb) {
-      if (!ok) {
-        if (i == k || j == k) P[i][j] = T(0);
-      } else {
-        const T p = rowk[k];
-        if (i == k) P[i][j] = (j == k) ? T(1) / p : rowk[j] / p;
-        else if (j == k) P[i][j] = -colk[i] / p;
-        else P[i][j] -= colk[i] * rowk[j] / p;
-      }
-    }
-    __syncthreads();
   }
-  if (i < bb && j < bb) inv[i * GJB + j] = P[i][j];
+#pragma unroll
+  for (int i = 0; i < GJB; ++i)
+    if (i < bb && j < bb) inv[i * GJB + j] = P[i];
 }
 
 // T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns);
@@ -550,7 +551,7 @@ static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, T tol, Arena& tmp) {
   const dim3 ug((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
   for (int64_t k0 = 0; k0 < m; k0 += GJB) {
     const int bb = (int)std::min<int64_t>(GJB, m - k0);
-    k_gj_panel<T><<<1, 1024, 0, s>>>(A, m, k0, bb, tol, inv);
+    k_gj_panel_warp<T><<<1, 32, 0, s>>>(A, m, k0, bb, tol, inv);
     GMT_LAUNCH_CHECK();
     k_gj_rows<T><<<grid_for(GJB * m, 256), 256, 0, s>>>(A, m, k0, bb, inv, Tp, O);
     GMT_LAUNCH_CHECK();

@@ -536,62 +536,85 @@ __global__ void __launch_bounds__(64)
 // c = d * D * D + k of a node in 16-byte group c / W (W = 4 floats or 2 doubles), so that a
 // thread reads its node's coefficients with one 16-byte load per group and a warp's loads
 // are contiguous
-__global__ void k_node_stencil(int D, int n, int nbx, const int* __restrict__ bxyz,
+// T = float: the FP32 stencils summed from the FP32 element copies (the stencils are FP32
+// anyway; FP64 sums would cost 1/64 of the FP32 rate on B300); T = double: FP64 throughout.
+template <typename T, int D>
+__global__ void k_node_stencil(int n, int nbx, const int* __restrict__ bxyz,
                                const int* __restrict__ bmap, bool dense, int64_t nslots,
                                const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
-                               const double* __restrict__ K, double* __restrict__ S64,
-                               float* __restrict__ S32) {
-  const int R = 8 * D, MM = R * R, DD = D * D;
+                               const T* __restrict__ K, T* __restrict__ S) {
+  constexpr int R = 8 * D, MM = R * R, DD = D * D, W = Vec16<T>::n;
+  constexpr int G = node_stencil_groups<T>(DD);
   const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslots) return;
   const unsigned mk = mask[sl];
   int x = 0, y = 0, z = 0;
   if (mk) slot_coords(sl, n, dense, bxyz, x, y, z);
-  const int G64 = node_stencil_groups<double>(DD), G32 = node_stencil_groups<float>(DD);
+  const T* Ka[8];   // element matrix of each incident element (nullptr when inactive)
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    Ka[a] = nullptr;
+    if ((mk >> a) & 1u) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+      const int64_t es = site_slot((x - ax + n) % n, (y - ay + n) % n, (z - az + n) % n, n, nbx,
+                                   bmap, dense);
+      Ka[a] = K + (int64_t)kidx[es] * MM;
+    }
+  }
+#pragma unroll 1
   for (int d = 0; d < 27; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (mk) {
-      for (int a = 0; a < 8; ++a) {
-        if (!((mk >> a) & 1u)) continue;
-        const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-        const int ex = ax + dx, ey = ay + dy, ez = az + dz;
-        if (ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
-        const int bb = ex + 2 * ey + 4 * ez;
-        const int64_t es = site_slot((x - ax + n) % n, (y - ay + n) % n, (z - az + n) % n, n, nbx,
-                                     bmap, dense);
-        const double* Ke = K + (int64_t)kidx[es] * MM;
-        for (int i = 0; i < D; ++i)
-          for (int j = 0; j < D; ++j) S[i * D + j] += Ke[(a * D + i) * R + bb * D + j];
-      }
+    T Sd[DD];
+#pragma unroll
+    for (int k = 0; k < DD; ++k) Sd[k] = T(0);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+      const int ex = ax + dx, ey = ay + dy, ez = az + dz;
+      if (!Ka[a] || ex < 0 || ex > 1 || ey < 0 || ey > 1 || ez < 0 || ez > 1) continue;
+      const int bb = ex + 2 * ey + 4 * ez;
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) Sd[i * D + j] += Ka[a][(a * D + i) * R + bb * D + j];
     }
-    for (int k = 0; k < DD; ++k) {
-      const int c = d * DD + k;
-      if (S64) S64[node_stencil_index(sl, c, G64, 2)] = S[k];
-      if (S32) S32[node_stencil_index(sl, c, G32, 4)] = (float)S[k];
-    }
+#pragma unroll
+    for (int k = 0; k < DD; ++k) S[node_stencil_index(sl, d * DD + k, G, W)] = Sd[k];
   }
 }
 
 void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
   Level& lv = h->lv[level];
   const int D = h->mat.D;
-  double* s64 = nullptr;
-  float* s32 = nullptr;
+  const unsigned g = grid_for(lv.nslots, 128);
+  cudaStream_t s = h->stream;
   if (fp64) {
     if (lv.S64) return;
     const size_t cnt = (size_t)lv.nslots * node_stencil_groups<double>(D * D) * 2;
-    s64 = lv.S64 = h->op.alloc<double>(cnt);
-    GMT_CUDA(cudaMemsetAsync(s64, 0, cnt * sizeof(double), h->stream));
+    lv.S64 = h->op.alloc<double>(cnt);
+    GMT_CUDA(cudaMemsetAsync(lv.S64, 0, cnt * sizeof(double), s));
+    if (D == 3)
+      k_node_stencil<double, 3><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
+                                                  lv.dense, lv.nslots, lv.mask, lv.kidx,
+                                                  lv.K64, lv.S64);
+    else
+      k_node_stencil<double, 1><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
+                                                  lv.dense, lv.nslots, lv.mask, lv.kidx,
+                                                  lv.K64, lv.S64);
   } else {
     if (lv.S32) return;
     const size_t cnt = (size_t)lv.nslots * node_stencil_groups<float>(D * D) * 4;
-    s32 = lv.S32 = h->op.alloc<float>(cnt);
-    GMT_CUDA(cudaMemsetAsync(s32, 0, cnt * sizeof(float), h->stream));
+    lv.S32 = h->op.alloc<float>(cnt);
+    GMT_CUDA(cudaMemsetAsync(lv.S32, 0, cnt * sizeof(float), s));
+    if (D == 3)
+      k_node_stencil<float, 3><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
+                                                 lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K32,
+                                                 lv.S32);
+    else
+      k_node_stencil<float, 1><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
+                                                 lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K32,
+                                                 lv.S32);
   }
-  k_node_stencil<<<grid_for(lv.nslots, 128), 128, 0, h->stream>>>(
-      D, lv.n, lv.nbx, lv.brick_xyz, lv.brick_map, lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K64,
-      s64, s32);
   GMT_LAUNCH_CHECK();
 }
 
