@@ -189,7 +189,8 @@ struct Workspace;  // solver buffers (solver.cu)
 enum TraceCat {
   TR_SMOOTH0 = 0, TR_RESID0 = 1, TR_APPLY0 = 2, TR_OUTER = 3, TR_DIAG0 = 4, TR_COARSE_ST = 5,
   TR_RESTRICT = 6, TR_PROLONG = 7, TR_CSOLVE = 8, TR_ENERGY = 9, TR_VEC = 10, TR_SETUP = 11,
-  TR_NCAT = 12
+  TR_OPS = 12, TR_CINV = 13,
+  TR_NCAT = 14
 };
 struct Tracer {
   bool on = false;
@@ -241,7 +242,7 @@ struct gmt_hierarchy {
   double* A64 = nullptr;
   float* X32 = nullptr;
   double* Ainv = nullptr;
-  double ctol = 0.0;
+  double* cscal = nullptr;  // device [rho, FP32 pivot tolerance, FP64 pivot tolerance]
   double* cb = nullptr;   // m x M gather buffer
   double* cu = nullptr;   // m x M result buffer
   double* cr = nullptr;   // m x M refinement residual

@@ -15,6 +15,7 @@
 //     is replaced by this exact solve.
 #include <algorithm>
 #include <mutex>
+#include <optional>
 #include <set>
 #include <cmath>
 #include <cstring>
@@ -428,11 +429,26 @@ __global__ void k_diag_sum(const double* __restrict__ A, int64_t m, double* __re
   if (threadIdx.x == 0) out[1] = sh[0];
 }
 
-__global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, double rho) {
+// rho J adds rho * n to the eigenvalue of each translation; rho = mean diagonal / n puts it
+// at the mean diagonal, inside the spectrum of K_L, so the regularized matrix is as well
+// conditioned as K_L on the complement of the translations (for right-hand sides orthogonal
+// to translations the solution does not depend on rho > 0). Pivot tolerances are relative
+// to the largest diagonal entry of the regularized matrix. All on the device: no host
+// round trip.
+__global__ void k_coarse_scalars(const double* __restrict__ ds, int64_t m, int64_t n_nodes,
+                                 double* __restrict__ out) {
+  const double rho = ds[0] / (double)m / (double)n_nodes;
+  const double dmax = ds[1] + rho * (double)n_nodes;
+  out[0] = rho;
+  out[1] = 1e-6 * dmax;
+  out[2] = 1e-12 * dmax;
+}
+
+__global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, const double* __restrict__ sc) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= m * m) return;
   int64_t r = g / m, c = g % m;
-  if (r % D == c % D) A[g] += rho;
+  if (r % D == c % D) A[g] += sc[0];
 }
 
 // Blocked in-place Gauss-Jordan inversion with 32-wide pivot panels. For the panel
@@ -447,9 +463,11 @@ constexpr int GJB = 32;
 // with shuffles, so the 32 pivot steps need no shared memory and no block barrier
 template <typename T>
 __global__ void __launch_bounds__(32) k_gj_panel_warp(const T* __restrict__ A, int64_t m,
-                                                      int64_t k0, int bb, T tol,
+                                                      int64_t k0, int bb,
+                                                      const double* __restrict__ tolp,
                                                       T* __restrict__ inv) {
   const int j = threadIdx.x;
+  const T tol = (T)*tolp;
   T P[GJB];
 #pragma unroll
   for (int i = 0; i < GJB; ++i) P[i] = (i < bb && j < bb) ? A[(k0 + i) * m + k0 + j] : T(0);
@@ -493,46 +511,70 @@ __global__ void k_gj_rows(const T* __restrict__ A, int64_t m, int64_t k0, int bb
   }
 }
 
-// the rank-bb update of everything, tiled 32 x 32 per block
+// the rank-bb update of everything: 64 x 64 tiles per 256-thread block, each thread a
+// 4 x 4 register tile (8 shared-memory loads per 16 multiply-adds per panel column)
 template <typename T>
 __global__ void __launch_bounds__(256) k_gj_update(T* __restrict__ A, int64_t m, int64_t k0,
                                                    int bb, const T* __restrict__ inv,
                                                    const T* __restrict__ Tp,
                                                    const T* __restrict__ O) {
-  __shared__ T sO[32][GJB + 1];   // O rows of this tile: O[i][r]
-  __shared__ T sT[GJB][32 + 1];   // T columns of this tile: T[r][j]
-  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int q = threadIdx.x; q < 32 * GJB; q += 256) {
+  __shared__ T sO[GJB][64 + 1];   // O^T of this tile's rows: sO[r][a] = O[i0 + a][r]
+  __shared__ T sT[GJB][64 + 1];   // T of this tile's columns: sT[r][b] = T[r][j0 + b]
+  __shared__ T sI[GJB][GJB + 1];  // the panel inverse
+  const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+  const int t = threadIdx.x;
+  for (int q = t; q < 64 * GJB; q += 256) {
     const int a = q / GJB, r = q % GJB;
-    sO[a][r] = (i0 + a < m && r < bb) ? O[(i0 + a) * GJB + r] : T(0);
-    const int rr = q / 32, b = q % 32;
-    sT[rr][b] = (rr < bb && j0 + b < m) ? Tp[rr * m + j0 + b] : T(0);
+    sO[r][a] = (i0 + a < m && r < bb) ? O[(i0 + a) * GJB + r] : T(0);
+    const int rr = q / 64, c = q % 64;
+    sT[rr][c] = (rr < bb && j0 + c < m) ? Tp[rr * m + j0 + c] : T(0);
   }
+  for (int q = t; q < GJB * GJB; q += 256) sI[q / GJB][q % GJB] = inv[q];
   __syncthreads();
-  const int64_t j = j0 + tx;
-  if (j >= m) return;
-  const bool jp = j >= k0 && j < k0 + bb;
-  for (int a = ty; a < 32; a += 8) {
-    const int64_t i = i0 + a;
-    if (i >= m) break;
-    const bool ip = i >= k0 && i < k0 + bb;
-    T v;
-    if (ip && jp) {
-      v = inv[(i - k0) * GJB + (j - k0)];
-    } else if (ip) {
-      v = sT[i - k0][tx];
-    } else if (jp) {
-      T acc = T(0);
-      for (int r = 0; r < bb; ++r) acc += sO[a][r] * inv[r * GJB + (j - k0)];
-      v = -acc;
-    } else {
-      T acc = T(0);
+  const int tx = t & 15, ty = t >> 4;   // 16 x 16 threads, rows ty + 16 k, columns tx + 16 l
+  T acc[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[k][l] = T(0);
 #pragma unroll 8
-      for (int r = 0; r < GJB; ++r) acc += sO[a][r] * sT[r][tx];
-      v = A[i * m + j] - acc;
+  for (int r = 0; r < GJB; ++r) {
+    T o[4], tv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = sO[r][ty + 16 * k];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) tv[l] = sT[r][tx + 16 * l];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) acc[k][l] += o[k] * tv[l];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a = ty + 16 * k;
+    const int64_t i = i0 + a;
+    if (i >= m) continue;
+    const bool ip = i >= k0 && i < k0 + bb;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int c = tx + 16 * l;
+      const int64_t j = j0 + c;
+      if (j >= m) continue;
+      const bool jp = j >= k0 && j < k0 + bb;
+      T v;
+      if (ip && jp) {
+        v = sI[i - k0][j - k0];
+      } else if (ip) {
+        v = sT[i - k0][c];
+      } else if (jp) {
+        T s2 = T(0);
+        for (int r = 0; r < bb; ++r) s2 += sO[r][a] * sI[r][j - k0];
+        v = -s2;
+      } else {
+        v = A[i * m + j] - acc[k][l];
+      }
+      A[i * m + j] = v;
     }
-    A[i * m + j] = v;
   }
 }
 
@@ -543,12 +585,12 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 
 // in-place blocked Gauss-Jordan of an m x m matrix (generalized inverse, pivots <= tol dropped)
 template <typename T>
-static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, T tol, Arena& tmp) {
+static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, const double* tol, Arena& tmp) {
   cudaStream_t s = h->stream;
   T* inv = tmp.alloc<T>(GJB * GJB);
   T* Tp = tmp.alloc<T>(GJB * m);
   T* O = tmp.alloc<T>(GJB * m);
-  const dim3 ug((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+  const dim3 ug((unsigned)((m + 63) / 64), (unsigned)((m + 63) / 64));
   for (int64_t k0 = 0; k0 < m; k0 += GJB) {
     const int bb = (int)std::min<int64_t>(GJB, m - k0);
     k_gj_panel_warp<T><<<1, 32, 0, s>>>(A, m, k0, bb, tol, inv);
@@ -568,18 +610,20 @@ void build_coarse_inverse64(gmt_hierarchy* h) {
   GMT_CUDA(cudaMemcpyAsync(h->Ainv, h->A64, m * m * sizeof(double), cudaMemcpyDeviceToDevice,
                            h->stream));
   Arena tmp(h->stream);
-  gauss_jordan<double>(h, h->Ainv, m, h->ctol, tmp);
+  gauss_jordan<double>(h, h->Ainv, m, h->cscal + 2, tmp);
   GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
 
 // ------------------------------------------------------------------ host driver
 void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double kappa) {
   cudaStream_t s = h->stream;
-  TraceScope ts(&h->tracer, s, TR_SETUP, 0.0);
+  std::optional<TraceScope> ts_ops;
+  ts_ops.emplace(&h->tracer, s, TR_OPS, 0.0);
   h->op.release();
   h->A64 = nullptr;
   h->X32 = nullptr;
   h->Ainv = nullptr;
+  h->cscal = nullptr;
   for (Level& l : h->lv) {
     l.K64 = l.S64 = l.dinv64 = nullptr;
     l.K32 = l.S32 = l.dinv32 = nullptr;
@@ -672,6 +716,8 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   }
   for (int l = 1; l + 1 < h->L; ++l) build_node_stencils(h, l, false);
   // coarsest generalized inverse
+  ts_ops.reset();
+  TraceScope ts_cinv(&h->tracer, s, TR_CINV, 0.0);
   {
     const int lc = h->L - 1;
     Level& c = h->lv[lc];
@@ -690,23 +736,16 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     double* ds = tmp.alloc<double>(2);
     k_diag_sum<<<1, 1024, 0, s>>>(h->A64, m, ds);
     GMT_LAUNCH_CHECK();
-    double dh[2];
-    GMT_CUDA(cudaMemcpyAsync(dh, ds, sizeof(dh), cudaMemcpyDeviceToHost, s));
-    GMT_CUDA(cudaStreamSynchronize(s));
-    // rho J adds rho * n to the eigenvalue of each translation; rho = mean diagonal / n puts
-    // it at the mean diagonal, inside the spectrum of K_L, so the regularized matrix is as
-    // well conditioned as K_L on the complement of the translations (for right-hand sides
-    // orthogonal to translations the solution does not depend on rho > 0)
-    const double rho = dh[0] / (double)m / (double)c.n_nodes;
-    k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, m, D, rho);
+    h->cscal = h->op.alloc<double>(3);
+    k_coarse_scalars<<<1, 1, 0, s>>>(ds, m, c.n_nodes, h->cscal);
     GMT_LAUNCH_CHECK();
-    const double dmax = dh[1] + rho * (double)c.n_nodes;
-    h->ctol = 1e-12 * dmax;
+    k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, m, D, h->cscal);
+    GMT_LAUNCH_CHECK();
     // FP32 generalized inverse for the mixed-precision solves (refined against A64 per use)
     h->X32 = h->op.alloc<float>(m * m);
     k_to_f32<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, h->X32, m * m);
     GMT_LAUNCH_CHECK();
-    gauss_jordan<float>(h, h->X32, m, (float)(1e-6 * dmax), tmp);
+    gauss_jordan<float>(h, h->X32, m, h->cscal + 1, tmp);
   }
   GMT_CUDA(cudaStreamSynchronize(s));
   h->prepared = true;

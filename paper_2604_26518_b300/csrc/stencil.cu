@@ -599,6 +599,8 @@ __global__ void k_node_stencil(int n, int nbx, const int* __restrict__ bxyz,
 
 void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
   Level& lv = h->lv[level];
+  if (fp64 ? lv.S64 != nullptr : lv.S32 != nullptr) return;
+  TraceScope ts(&h->tracer, h->stream, TR_OPS, 0.0);
   const int D = h->mat.D;
   const unsigned g = grid_for(lv.nslots, 128);
   cudaStream_t s = h->stream;

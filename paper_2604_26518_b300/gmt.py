@@ -115,7 +115,7 @@ _SIGS = {
     "gmt_cached_bytes": (_L, []),
 }
 
-TRACE_CATEGORIES = 12
+TRACE_CATEGORIES = 14
 
 
 def release_cached_memory():

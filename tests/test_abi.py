@@ -29,3 +29,13 @@ def test_host_only_calls():
     st = L.gmt_build_hierarchy(buf, 30, 0, None, None, ctypes.byref(h))
     assert st == gmt.ERR_RES and b"multiple of 4" in L.gmt_last_error()
     assert L.gmt_num_levels(None) == 0
+
+
+def test_trace_category_names():
+    from paper_2604_26518_b300 import gmt
+    L = gmt.lib()
+    names = [L.gmt_trace_name(c).decode() for c in range(gmt.TRACE_CATEGORIES)]
+    assert len(set(names)) == gmt.TRACE_CATEGORIES and all(names)
+    assert {"smooth_l0", "setup_hierarchy", "setup_operators", "setup_coarse_inverse"} <= set(names)
+    assert L.gmt_trace_name(gmt.TRACE_CATEGORIES).decode() == ""
+    assert L.gmt_trace_name(-1).decode() == ""

@@ -155,3 +155,17 @@ def test_full_size_128_properties(gmt_lib):
     phi = vox.mean()
     assert np.linalg.eigvalsh(phi * C0 - CH).min() > -1e-9       # Voigt bound
     assert np.linalg.eigvalsh(CH).min() > -1e-9 and np.abs(CH - CH.T).max() < 1e-12
+
+
+def test_trace_totals_cover_the_solve(gmt_lib):
+    gmt = gmt_lib
+    h = gmt.Hierarchy(L.tpms_network("gyroid", 32, 0.30))
+    h.trace(True)
+    h.solve(gmt.ELASTIC, tol=1e-5, want_field=False)
+    h.homogenize(gmt.ELASTIC)
+    tot = h.trace_totals()
+    for k in ("smooth_l0", "resid_l0", "apply_l0", "outer_resid", "restrict", "prolong",
+              "coarse_solve", "energy", "vector", "setup_operators", "setup_coarse_inverse"):
+        n, ms, b = tot[k]
+        assert n > 0 and ms > 0.0, (k, tot[k])
+    assert tot["smooth_l0"][2] > 0
