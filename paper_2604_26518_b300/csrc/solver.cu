@@ -488,13 +488,16 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       }
       double* rn_dev = w->red;
       if (mixed) {
-        // ||r||^2 and the sums of r from the update's partials, then r loses its mean
-        launch_reduce(h, w->part, h->lv[0].nb, M, rn_dev, RedEpi(), M + C);
+        // ||r||^2 and the sums of r from the update's partials (one launch), then r loses
+        // its mean
         RedEpi em;
         em.mode = 3;
         em.out32 = vmean;
         em.scale = 1.0 / (double)h->lv[0].n_nodes;
-        launch_reduce(h, w->part + M, h->lv[0].nb, C, vsums, em, M + C);
+        const int col0[2] = {0, M}, ncols[2] = {M, C};
+        double* outs[2] = {rn_dev, vsums};
+        const RedEpi epis[2] = {RedEpi(), em};
+        launch_reduce_multi(h, w->part, h->lv[0].nb, M + C, 2, col0, ncols, outs, epis);
         vec_sub_mean32(h, vmean, (float*)w->rr);
       } else {
         rn_dev = reduce_to(h, w, 0, M, 0);
@@ -577,30 +580,31 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
         //   = -alpha (z_new.q) / (z_old.r_old), since r_new - r_old = -alpha q. With a fixed
         // symmetric preconditioner this is the Fletcher-Reeves beta of plain PCG; it stays
         // robust when FP32 rounding makes the V-cycle slightly non-symmetric.
-        const int ld = fused ? 2 * M + C : M;
-        double* zq = w->part + (fused ? M : (int64_t)h->lv[0].nb * M);   // partials of q.z
-        const int zq_ld = fused ? ld : M;
+        RedEpi eb;
+        eb.mode = 6;   // beta = -alpha (q.z) / rz
+        eb.other = rz;
+        eb.other2 = alpha;
+        eb.active = w->active;
+        eb.ratio = beta;
+        RedEpi em;
+        em.mode = 3;   // per-value means of z
+        em.out32 = vmean;
+        em.scale = 1.0 / (double)h->lv[0].n_nodes;
         if (fused) {
-          if (mixed) {
-            RedEpi em;
-            em.mode = 3;
-            em.out32 = vmean;
-            em.scale = 1.0 / (double)h->lv[0].n_nodes;
-            launch_reduce(h, w->part + 2 * M, h->lv[0].nb, C, vsums, em, ld);
-          }
+          // one launch: r.z, q.z (beta) and the sums of z (means) from the fused partials
+          const int col0[3] = {0, M, 2 * M}, ncols[3] = {M, M, C};
+          double* outs[3] = {rz_new, w->red + 10 * 32 + 16, vsums};
+          const RedEpi epis[3] = {RedEpi(), eb, em};
+          launch_reduce_multi(h, w->part, h->lv[0].nb, 2 * M + C, mixed ? 3 : 2, col0, ncols,
+                              outs, epis);
         } else {
+          double* zq = w->part + (int64_t)h->lv[0].nb * M;   // partials of q.z
           if (mixed) sum_values(z);
           vec_dot(h, 0, ar, w->q, z, zq);
           vec_dot(h, 0, ar, w->rr, z, w->part);
+          launch_reduce(h, w->part, h->lv[0].nb, M, rz_new);
+          launch_reduce(h, zq, h->lv[0].nb, M, w->red + 10 * 32 + 16, eb);
         }
-        launch_reduce(h, w->part, h->lv[0].nb, M, rz_new, RedEpi(), ld);
-        RedEpi e;
-        e.mode = 6;   // beta = -alpha (q.z) / rz
-        e.other = rz;
-        e.other2 = alpha;
-        e.active = w->active;
-        e.ratio = beta;
-        launch_reduce(h, zq, h->lv[0].nb, M, w->red + 10 * 32 + 16, e, zq_ld);
         if (restart) {
           if (mixed) vec_sub_mean32(h, vmean, (float*)z);
           vec_copy(h, 0, ar, z, w->p);

@@ -1320,13 +1320,27 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   s = tt;
 }
 
+// Several column groups of the same partials in one launch: blockIdx.x runs over the
+// groups' columns in order; each group has its own first column, output and epilogue.
+struct RedGroups {
+  int n = 0;
+  int col0[3] = {0, 0, 0}, ncols[3] = {0, 0, 0};
+  double* out[3] = {nullptr, nullptr, nullptr};
+  RedEpi epi[3];
+};
+
 __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part, int64_t nblk,
-                                                int ld, double* __restrict__ out, RedEpi epi,
+                                                int ld, const __grid_constant__ RedGroups grp,
                                                 double* __restrict__ scratch,
                                                 unsigned* __restrict__ ticket) {
   __shared__ double ss[256], sc[256];
   __shared__ bool last;
-  const int k = blockIdx.x, sp = blockIdx.y, S = gridDim.y;
+  const int kg = blockIdx.x, sp = blockIdx.y, S = gridDim.y;   // kg: column among all groups
+  int gi = 0, k = kg;
+  while (gi + 1 < grp.n && k >= grp.ncols[gi]) k -= grp.ncols[gi++];
+  const int col = grp.col0[gi] + k;                               // column of the partials
+  double* __restrict__ out = grp.out[gi];
+  const RedEpi& epi = grp.epi[gi];
   const int64_t chunk = (nblk + S - 1) / S;
   const int64_t lo = (int64_t)sp * chunk;
   const int64_t hi = lo + chunk < nblk ? lo + chunk : nblk;
@@ -1336,7 +1350,7 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t i = i0 + (int64_t)j * 256;
-      x[j] = i < hi ? part[i * ld + k] : 0.0;
+      x[j] = i < hi ? part[i * ld + col] : 0.0;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) neumaier(s, c, x[j]);
@@ -1357,10 +1371,10 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
     if (S == 1) {
       last = true;
     } else {
-      scratch[((int64_t)k * S + sp) * 2] = ss[0];
-      scratch[((int64_t)k * S + sp) * 2 + 1] = sc[0];
+      scratch[((int64_t)kg * S + sp) * 2] = ss[0];
+      scratch[((int64_t)kg * S + sp) * 2 + 1] = sc[0];
       __threadfence();
-      last = atomicAdd(&ticket[k], 1u) == (unsigned)(S - 1);
+      last = atomicAdd(&ticket[kg], 1u) == (unsigned)(S - 1);
     }
   }
   __syncthreads();
@@ -1372,11 +1386,11 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
     __threadfence();
     double a = 0.0, ca = 0.0;
     for (int j = 0; j < S; ++j) {
-      ca += __ldcg(&scratch[((int64_t)k * S + j) * 2 + 1]);
-      neumaier(a, ca, __ldcg(&scratch[((int64_t)k * S + j) * 2]));
+      ca += __ldcg(&scratch[((int64_t)kg * S + j) * 2 + 1]);
+      neumaier(a, ca, __ldcg(&scratch[((int64_t)kg * S + j) * 2]));
     }
     v = a + ca;
-    ticket[k] = 0u;  // ready for the next launch on this stream
+    ticket[kg] = 0u;  // ready for the next launch on this stream
   }
   out[k] = v;
   const bool act = epi.active == nullptr || epi.active[k] != 0;
@@ -2004,10 +2018,12 @@ void launch_energy(gmt_hierarchy* h, Prec prec, const void* u_hi, const float* u
   }
 }
 
-void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out,
-                   RedEpi epi, int ld) {
-  if (ld <= 0) ld = K;
-  GMT_REQUIRE(K >= 1 && K <= kRedMaxCols, GMT_ERR_ARG, "reduction over %d columns", K);
+static void reduce_groups(gmt_hierarchy* h, const double* part, int64_t nblk, int ld,
+                          const RedGroups& g) {
+  int K = 0;
+  for (int i = 0; i < g.n; ++i) K += g.ncols[i];
+  GMT_REQUIRE(g.n >= 1 && g.n <= 3 && K >= 1 && K <= kRedMaxCols, GMT_ERR_ARG,
+              "reduction over %d columns", K);
   if (h->red_scratch == nullptr) {
     h->red_scratch = h->geo.alloc<double>(kRedMaxCols * kRedSplit * 2);
     h->red_ticket = h->geo.alloc<unsigned>(kRedMaxCols);
@@ -2016,9 +2032,33 @@ void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, do
   // about 2048 rows per block, at most kRedSplit blocks per column
   const int S = (int)std::min<int64_t>(kRedSplit, std::max<int64_t>(1, (nblk + 2047) / 2048));
   TraceScope ts(&h->tracer, h->stream, TR_VEC, (double)nblk * K * 8.0);
-  k_reduce<<<dim3(K, S), 256, 0, h->stream>>>(part, nblk, ld, out, epi, h->red_scratch,
+  k_reduce<<<dim3(K, S), 256, 0, h->stream>>>(part, nblk, ld, g, h->red_scratch,
                                              h->red_ticket);
   GMT_LAUNCH_CHECK();
+}
+
+void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out,
+                   RedEpi epi, int ld) {
+  RedGroups g;
+  g.n = 1;
+  g.ncols[0] = K;
+  g.out[0] = out;
+  g.epi[0] = epi;
+  reduce_groups(h, part, nblk, ld <= 0 ? K : ld, g);
+}
+
+void launch_reduce_multi(gmt_hierarchy* h, const double* part, int64_t nblk, int ld, int n,
+                         const int* col0, const int* ncols, double* const* out,
+                         const RedEpi* epi) {
+  RedGroups g;
+  g.n = n;
+  for (int i = 0; i < n && i < 3; ++i) {
+    g.col0[i] = col0[i];
+    g.ncols[i] = ncols[i];
+    g.out[i] = out[i];
+    g.epi[i] = epi[i];
+  }
+  reduce_groups(h, part, nblk, ld, g);
 }
 
 static int64_t nvals(gmt_hierarchy* h, int level) { return h->lv[level].nslots * h->mat.C; }

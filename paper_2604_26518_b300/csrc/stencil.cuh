@@ -75,6 +75,11 @@ struct RedEpi {
 // columns k < K of rows part[i * ld + k] (ld = K when <= 0)
 void launch_reduce(gmt_hierarchy* h, const double* part, int64_t nblk, int K, double* out,
                    RedEpi epi = RedEpi(), int ld = 0);
+// n <= 3 column groups of the same [nblk][ld] partials in one launch: group i reduces
+// columns col0[i] .. col0[i] + ncols[i] - 1 into out[i] with epilogue epi[i]
+void launch_reduce_multi(gmt_hierarchy* h, const double* part, int64_t nblk, int ld, int n,
+                         const int* col0, const int* ncols, double* const* out,
+                         const RedEpi* epi);
 
 // vector kernels on slot layouts (level `level`, C values per slot)
 void vec_zero(gmt_hierarchy* h, int level, Prec prec, void* x);
