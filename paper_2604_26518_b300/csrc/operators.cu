@@ -458,40 +458,39 @@ __global__ void k_add_rho(double* __restrict__ A, int64_t m, int D, const double
 // After all panels the matrix holds the (generalized) inverse.
 constexpr int GJB = 32;
 
-// one warp inverts the bb x bb diagonal panel block (pivots <= tol dropped), the panel in
-// registers: lane j holds column j, and step k broadcasts the pivot column from lane k
-// with shuffles, so the 32 pivot steps need no shared memory and no block barrier
+// one block of GJB x GJB threads inverts the bb x bb diagonal panel block (pivots <= tol
+// dropped), thread (i, j) owning entry (i, j). Step k reads the pivot row and column from a
+// double buffer that the owners of row / column k filled while updating in step k - 1, so
+// each step needs a single block barrier.
 template <typename T>
-__global__ void __launch_bounds__(32) k_gj_panel_warp(const T* __restrict__ A, int64_t m,
-                                                      int64_t k0, int bb,
-                                                      const double* __restrict__ tolp,
-                                                      T* __restrict__ inv) {
-  const int j = threadIdx.x;
+__global__ void __launch_bounds__(GJB * GJB) k_gj_panel(const T* __restrict__ A, int64_t m,
+                                                       int64_t k0, int bb,
+                                                       const double* __restrict__ tolp,
+                                                       T* __restrict__ inv) {
+  __shared__ T rowk[2][GJB], colk[2][GJB];
+  const int t = threadIdx.x, i = t / GJB, j = t % GJB;
+  const bool in = i < bb && j < bb;
   const T tol = (T)*tolp;
-  T P[GJB];
-#pragma unroll
-  for (int i = 0; i < GJB; ++i) P[i] = (i < bb && j < bb) ? A[(k0 + i) * m + k0 + j] : T(0);
-#pragma unroll
-  for (int k = 0; k < GJB; ++k) {
-    if (k >= bb) break;  // uniform across the warp
-    const T p = __shfl_sync(0xffffffffu, P[k], k);   // P[k][k]
+  T v = in ? A[(k0 + i) * m + k0 + j] : T(0);
+  if (i == 0) rowk[0][j] = v;
+  if (j == 0) colk[0][i] = v;
+  for (int k = 0; k < bb; ++k) {
+    const int buf = k & 1;
+    __syncthreads();
+    const T p = rowk[buf][k];
     const bool ok = p > tol;
     const T ip = ok ? T(1) / p : T(0);
-    const T rk = P[k];                                // P[k][j], before the step
-#pragma unroll
-    for (int i = 0; i < GJB; ++i) {
-      const T c = __shfl_sync(0xffffffffu, P[i], k);  // P[i][k], before the step
-      T v;
-      if (!ok) v = (i == k || j == k) ? T(0) : P[i];
+    const T rk = rowk[buf][j], ck = colk[buf][i];
+    if (in) {
+      if (!ok) v = (i == k || j == k) ? T(0) : v;
       else if (i == k) v = (j == k) ? ip : rk * ip;
-      else if (j == k) v = -c * ip;
-      else v = P[i] - c * (rk * ip);
-      P[i] = v;
+      else if (j == k) v = -ck * ip;
+      else v = v - ck * (rk * ip);
     }
+    if (i == k + 1) rowk[buf ^ 1][j] = v;
+    if (j == k + 1) colk[buf ^ 1][i] = v;
   }
-#pragma unroll
-  for (int i = 0; i < GJB; ++i)
-    if (i < bb && j < bb) inv[i * GJB + j] = P[i];
+  if (in) inv[i * GJB + j] = v;
 }
 
 // T = A_PP^+ A_P* (rows of the panel, all columns) and O = A_*P (copy of the panel columns);
@@ -593,7 +592,7 @@ static void gauss_jordan(gmt_hierarchy* h, T* A, int64_t m, const double* tol, A
   const dim3 ug((unsigned)((m + 63) / 64), (unsigned)((m + 63) / 64));
   for (int64_t k0 = 0; k0 < m; k0 += GJB) {
     const int bb = (int)std::min<int64_t>(GJB, m - k0);
-    k_gj_panel_warp<T><<<1, 32, 0, s>>>(A, m, k0, bb, tol, inv);
+    k_gj_panel<T><<<1, GJB * GJB, 0, s>>>(A, m, k0, bb, tol, inv);
     GMT_LAUNCH_CHECK();
     k_gj_rows<T><<<grid_for(GJB * m, 256), 256, 0, s>>>(A, m, k0, bb, inv, Tp, O);
     GMT_LAUNCH_CHECK();
