@@ -39,9 +39,9 @@ C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_
 METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
 TOL = 1e-5
 # ncu DRAM bytes (read + write) per active node of one level-0 smoother sweep of the
-# current kernel: 138.5 MB over the 651,308 active nodes of the first 128^3 bench cell
+# current kernel: 137.1 MB over the 651,308 active nodes of the first 128^3 bench cell
 # (profiles/k_stencil_smoother_c128_elastic.md); scaled by the nodes of each sweep
-NCU_DRAM_BYTES_PER_NODE = 212.7
+NCU_DRAM_BYTES_PER_NODE = 210.5
 
 
 def workload(name: str, rank: int):
