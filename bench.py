@@ -187,6 +187,10 @@ def run_gmt(args, rank: int, world: int):
     opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
     if args.nu:
         opts.nu_pre = opts.nu_post = args.nu
+    if args.nu_post >= 0:
+        opts.nu_post = args.nu_post
+    if args.inner_tol > 0:
+        opts.inner_tol = args.inner_tol
     if args.smoother:
         opts.smoother = gmt.JACOBI if args.smoother == "jacobi" else gmt.CHEBYSHEV
     if args.cells:
@@ -347,8 +351,10 @@ def run_gmt(args, rank: int, world: int):
                                  "solve and C^H accumulation") if prec == gmt.FP32 else "fp64",
                    "step": "hierarchy + operators + solve + C^H per cell",
                    "coarsest_max": args.coarsest,
-                   "smoother": "%s, nu_pre = nu_post = %d" % (
-                       "jacobi" if opts.smoother == gmt.JACOBI else "chebyshev", opts.nu_pre),
+                   "smoother": "%s, nu_pre %d, nu_post %d" % (
+                       {gmt.JACOBI: "jacobi", gmt.CHEBYSHEV: "chebyshev", gmt.GS8: "gs8"}
+                       [opts.smoother], opts.nu_pre, opts.nu_post),
+                   "inner_tol": opts.inner_tol,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
                    "concurrent_cells": nstreams},
@@ -398,6 +404,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--coarsest", type=int, default=8, help="coarsest grid side bound")
     ap.add_argument("--nu", type=int, default=0, help="pre/post smoothing sweeps (0: default)")
+    ap.add_argument("--nu-post", type=int, default=-1, help="post-smoothing sweeps (-1: as --nu)")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="mixed precision: true-residual replacement factor (0: default)")
     ap.add_argument("--streams", type=int, default=4,
                     help="cells solved concurrently, one host thread and CUDA stream each")
     ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev"])
