@@ -56,6 +56,8 @@ typedef enum {
   GMT_ERR_STATE = 8         /* call needs gmt_prepare / gmt_solve to have run first */
 } gmt_status;
 
+/* GMT_PREC_BF16 (BF16 storage of the V-cycle vectors) is reserved: gmt_solve returns
+   GMT_ERR_ARG for it in this build. */
 typedef enum { GMT_PREC_FP64 = 0, GMT_PREC_FP32 = 1, GMT_PREC_BF16 = 2 } gmt_precision;
 typedef enum { GMT_SMOOTH_JACOBI = 0, GMT_SMOOTH_CHEBYSHEV = 1, GMT_SMOOTH_GS8 = 2 } gmt_smoother;
 /* Multigrid cycle of Sec. 5's schedules: V (one coarse correction per level), W (two),

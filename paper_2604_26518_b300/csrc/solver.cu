@@ -2,7 +2,9 @@
 // coarsest solve, prolongation, smoother), used either as the preconditioner of a
 // conjugate-gradient loop or as a stationary iteration (the paper's GMG loop, Sec. 5
 // baselines), with the solution kept in FP64 (precision FP64) or as a float-float pair
-// refined by reliable residual replacement (precision FP32; see solve()).
+// refined by reliable residual replacement (precision FP32; see solve()). The Krylov step
+// uses the flexible (Polak-Ribiere) beta; a mixed solve that diverges is reported as such
+// and gmt_solve repeats it in FP64.
 // Tolerances below 2e-6 evaluate the mixed-precision true residual in native FP64.
 // Stopping rule (Sec. 5 metric r, reading: the maximum over load cases must meet tol).
 // Gauge (Sec. 3.1 zero-mean constraint): the mean over active nodes of every component
