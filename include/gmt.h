@@ -72,8 +72,8 @@ typedef struct {
                           Gauss-Seidel (Sec. 4.6 "Parallel Smoothing": nodes coloured by the
                           parity of (x, y, z); one sweep updates the 8 colours in turn, each
                           with the damped block-Jacobi step on the latest values) */
-  int nu_pre;          /* [2] pre-smoothing sweeps (Chebyshev: polynomial degree) */
-  int nu_post;         /* [2] post-smoothing sweeps */
+  int nu_pre;          /* [1] pre-smoothing sweeps on level 0 (Chebyshev: polynomial degree) */
+  int nu_post;         /* [1] post-smoothing sweeps on level 0 */
   double omega;        /* [0.6] Jacobi damping */
   double cheb_ratio;   /* [30] Chebyshev interval [lmax/cheb_ratio, cheb_upper*lmax] */
   double cheb_upper;   /* [1.1] */
@@ -88,6 +88,10 @@ typedef struct {
   int cycle;           /* [GMT_CYCLE_V] */
   int fp64_fallback;   /* [1] when the mixed-precision solve diverges, gmt_solve solves the
                           cell again in plain FP64 (gmt_info.fp64_fallback reports it) */
+  int nu_coarse;       /* [2] pre- and post-smoothing sweeps on levels >= 1; 0: nu_pre and
+                          nu_post on every level. The defaults (1 on the fine level, 2 on
+                          the coarse ones) were the fastest of the sweeps measured on the
+                          128^3 benchmark batch */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,

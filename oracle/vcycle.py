@@ -65,9 +65,13 @@ def coarsest_matrix(KL, D: int) -> np.ndarray:
 
 class VCycle:
     def __init__(self, Ks, Ps, D: int, nu_pre=2, nu_post=2, omega=0.6, smoother="jacobi",
-                 cheb_lmax=None, cheb_ratio=30.0, cheb_upper=1.1, kind="V", levels=None):
+                 cheb_lmax=None, cheb_ratio=30.0, cheb_upper=1.1, kind="V", levels=None,
+                 nu_coarse=0):
+        """nu_pre / nu_post sweeps on level 0; nu_coarse (> 0) sweeps before and after the
+        coarse correction on every level >= 1 (0: nu_pre / nu_post there too)."""
         self.Ks, self.Ps, self.D = Ks, Ps, D
         self.nu_pre, self.nu_post, self.omega = nu_pre, nu_post, omega
+        self.nu_coarse = nu_coarse
         self.smoother = smoother
         self.Dinv = [block_diag_inverse(K, D) for K in Ks[:-1]]
         self.Ainv = np.linalg.inv(coarsest_matrix(Ks[-1], D))
@@ -121,12 +125,15 @@ class VCycle:
             return self.Ainv @ f
         if u is None:
             u = np.zeros_like(f)
-        u = self.smooth(level, u, f, self.nu_pre)
+        pre, post = self.nu_pre, self.nu_post
+        if level > 0 and self.nu_coarse > 0:
+            pre = post = self.nu_coarse
+        u = self.smooth(level, u, f, pre)
         r = f - self.Ks[level] @ u
         fc = self.Ps[level].T @ r
         uc = self.cycle(fc, None, level + 1, kind)
         if level + 2 < L and kind != "V":
             uc = self.cycle(fc, uc, level + 1, "W" if kind == "W" else "V")
         u = u + self.Ps[level] @ uc
-        u = self.smooth(level, u, f, self.nu_post)
+        u = self.smooth(level, u, f, post)
         return u

@@ -43,7 +43,7 @@ using gmt::Fail;
 
 static bool opts_valid(const gmt_options& o) {
   return o.levels >= 0 && o.coarsest_max >= 4 && o.smoother >= 0 && o.smoother <= 2 &&
-         o.cycle >= 0 && o.cycle <= 2 &&
+         o.cycle >= 0 && o.cycle <= 2 && o.nu_coarse >= 0 &&
          o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post > 0 && o.omega > 0 &&
          o.cheb_ratio > 1 && o.cheb_upper >= 1 && o.precision >= 0 && o.precision <= 2 &&
          o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0;
@@ -87,8 +87,8 @@ void gmt_default_options(gmt_options* o) {
   o->levels = 0;
   o->coarsest_max = 8;
   o->smoother = GMT_SMOOTH_JACOBI;
-  o->nu_pre = 2;
-  o->nu_post = 2;
+  o->nu_pre = 1;
+  o->nu_post = 1;
   o->omega = 0.6;
   o->cheb_ratio = 30.0;
   o->cheb_upper = 1.1;
@@ -99,6 +99,7 @@ void gmt_default_options(gmt_options* o) {
   o->max_outer = 8;
   o->cycle = GMT_CYCLE_V;
   o->fp64_fallback = 1;
+  o->nu_coarse = 2;
 }
 
 const char* gmt_status_string(gmt_status s) {

@@ -277,7 +277,10 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
   }
   void* u = zero ? w->ua[l] : u_init;
   void* other = (u == w->ua[l]) ? w->ub[l] : w->ua[l];
-  smooth(h, w, l, f, &u, &other, h->opts.nu_pre, zero);
+  const gmt_options& o = h->opts;
+  const int nu1 = (l > 0 && o.nu_coarse > 0) ? o.nu_coarse : o.nu_pre;
+  const int nu2 = (l > 0 && o.nu_coarse > 0) ? o.nu_coarse : o.nu_post;
+  smooth(h, w, l, f, &u, &other, nu1, zero);
   VecArgs a;
   a.u = u;
   a.f = f;
@@ -289,7 +292,7 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
     uc = vcycle(h, w, l + 1, w->f[l + 1], uc, false, nullptr,
                 cycle == GMT_CYCLE_W ? GMT_CYCLE_W : GMT_CYCLE_V);
   launch_prolong(h, l, pr, uc, u);
-  smooth(h, w, l, f, &u, &other, h->opts.nu_post, false, part, aux);
+  smooth(h, w, l, f, &u, &other, nu2, false, part, aux);
   return u;
 }
 

@@ -44,6 +44,7 @@ class Options(ctypes.Structure):
         ("max_outer", ctypes.c_int),
         ("cycle", ctypes.c_int),
         ("fp64_fallback", ctypes.c_int),
+        ("nu_coarse", ctypes.c_int),
     ]
 
 

@@ -19,7 +19,8 @@ def test_library_builds_and_exports_declared_symbols():
 def test_host_only_calls():
     L = gmt.lib()
     o = gmt.default_options()
-    assert o.levels == 0 and o.coarsest_max == 8 and o.nu_pre == 2 and o.precision == gmt.FP32
+    assert o.levels == 0 and o.coarsest_max == 8 and o.nu_pre == 1 and o.nu_coarse == 2
+    assert o.precision == gmt.FP32
     assert L.gmt_status_string(gmt.ERR_RES).decode().startswith("unsupported")
     # argument errors are reported as statuses, not crashes (checked before any CUDA call)
     h = ctypes.c_void_p()

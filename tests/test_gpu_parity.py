@@ -121,7 +121,9 @@ def test_vcycle_parity(gmt_lib, name, smoother):
     kw = {}
     if smoother == "chebyshev":
         kw = {"cheb_lmax": [h.lambda_max(l) for l in range(h.levels - 1)]}
-    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, **kw)
+    o = gmt.default_options()
+    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, nu_pre=o.nu_pre,
+                       nu_post=o.nu_post, nu_coarse=o.nu_coarse, **kw)
     F = O["F"]
     u1 = to_np(h.vcycle(F, None, gmt.FP64), 3, 6)
     r1 = vc.cycle(F)
@@ -159,7 +161,9 @@ def test_cycle_schedules_and_gs8_parity(gmt_lib, name, smoother, kind):
     h = gmt.Hierarchy(vox, gmt.default_options(smoother=sm, cycle=cyc))
     O = oracle_setup(vox, "elastic", h.levels)
     h.prepare(gmt.ELASTIC)
-    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, kind=kind, levels=O["levels"])
+    o = gmt.default_options()
+    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, kind=kind, levels=O["levels"],
+                       nu_pre=o.nu_pre, nu_post=o.nu_post, nu_coarse=o.nu_coarse)
     F = O["F"]
     u1 = to_np(h.vcycle(F, None, gmt.FP64), 3, 6)
     r1 = vc.cycle(F)
