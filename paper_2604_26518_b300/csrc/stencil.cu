@@ -902,8 +902,8 @@ template <typename A>
 constexpr int vec_groups(int C) { return (C + Vec16<A>::n - 1) / Vec16<A>::n; }
 
 template <typename TS, typename A, int C>
-__global__ void __launch_bounds__(64) k_restrict_tile(const TS* __restrict__ rf,
-                                                      TS* __restrict__ fc, LvView f, LvView c) {
+__global__ void __launch_bounds__(256) k_restrict_tile(const TS* __restrict__ rf,
+                                                       TS* __restrict__ fc, LvView f, LvView c) {
   using V = typename Vec16<A>::type;
   constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
   extern __shared__ __align__(16) unsigned char tr_smem[];
@@ -912,7 +912,8 @@ __global__ void __launch_bounds__(64) k_restrict_tile(const TS* __restrict__ rf,
   const int t = threadIdx.x;
   const int ox = 8 * c.bxyz[3 * b] - 1, oy = 8 * c.bxyz[3 * b + 1] - 1,
             oz = 8 * c.bxyz[3 * b + 2] - 1;
-  for (int q = t; q < 729; q += 64) {
+  // 256 threads stage the 729 sites (about 3 each, all loads of a site in flight together)
+  for (int q = t; q < 729; q += 256) {
     const int rx = q % 9, ry = (q / 9) % 9, rz = q / 81;
     const int fx = (ox + rx + f.n) % f.n, fy = (oy + ry + f.n) % f.n, fz = (oz + rz + f.n) % f.n;
     const int64_t fs = site_slot(fx, fy, fz, f.n, f.nbx, f.bmap, false);
@@ -933,29 +934,30 @@ __global__ void __launch_bounds__(64) k_restrict_tile(const TS* __restrict__ rf,
     }
   }
   __syncthreads();
-  const int lx = t & 3, ly = (t >> 2) & 3, lz = t >> 4;
-  A acc[C];
+  // thread (node, part): coarse node t & 63 of the brick, value groups g = part, part + 4
+  const int node = t & 63, part = t >> 6;
+  const int lx = node & 3, ly = (node >> 2) & 3, lz = node >> 4;
+  const bool act = c.mask[b * 64 + node] != 0;
+  const int qc = (2 * lx + 1) + 9 * (2 * ly + 1) + 81 * (2 * lz + 1);
+  TS* dst = fc + vaddr(b * 64 + node, 0, C);
+  for (int g = part; g < G; g += 4) {
+    A acc[NV];
 #pragma unroll
-  for (int v = 0; v < C; ++v) acc[v] = A(0);
-  if (c.mask[b * 64 + t]) {
-    const int qc = (2 * lx + 1) + 9 * (2 * ly + 1) + 81 * (2 * lz + 1);
+    for (int k = 0; k < NV; ++k) acc[k] = A(0);
+    if (act) {
 #pragma unroll
-    for (int d = 0; d < 27; ++d) {
-      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      const A w = (dx ? A(0.5) : A(1)) * (dy ? A(0.5) : A(1)) * (dz ? A(0.5) : A(1));
-      const int q = qc + dx + 9 * dy + 81 * dz;
+      for (int d = 0; d < 27; ++d) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const A w = (dx ? A(0.5) : A(1)) * (dy ? A(0.5) : A(1)) * (dz ? A(0.5) : A(1));
+        const V x = tile[g * 729 + qc + dx + 9 * dy + 81 * dz];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const V x = tile[g * 729 + q];
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-          if (g * NV + k < C) acc[g * NV + k] += w * vec_get<A>(x, k);
+        for (int k = 0; k < NV; ++k) acc[k] += w * vec_get<A>(x, k);
       }
     }
-  }
-  TS* dst = fc + vaddr(b * 64 + t, 0, C);
 #pragma unroll
-  for (int v = 0; v < C; ++v) dst[v * 64] = store_as<TS>(acc[v]);
+    for (int k = 0; k < NV; ++k)
+      if (g * NV + k < C) dst[(g * NV + k) * 64] = store_as<TS>(acc[k]);
+  }
 }
 
 // One block per fine brick: the 3^3 coarse sites its nodes interpolate from are staged in
@@ -1859,8 +1861,8 @@ static void restrict_t(gmt_hierarchy* h, int level, const void* rf, void* fc) {
     constexpr int C = D * M;
     constexpr size_t smem = (size_t)vec_groups<A>(C) * 729 * 16;
     ensure_smem_attr((const void*)k_restrict_tile<TS, A, C>, (int)smem);
-    k_restrict_tile<TS, A, C><<<(unsigned)c.nb, 64, smem, h->stream>>>((const TS*)rf, (TS*)fc,
-                                                                      view(f), view(c));
+    k_restrict_tile<TS, A, C><<<(unsigned)c.nb, 256, smem, h->stream>>>((const TS*)rf, (TS*)fc,
+                                                                       view(f), view(c));
   } else {
     k_restrict<TS, A, D * M><<<grid_for(c.nslots, 64), 64, 0, h->stream>>>(
         (const TS*)rf, (TS*)fc, view(f), view(c));
