@@ -38,10 +38,12 @@ C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_
                "plate_diamond", "bcc", "octet")
 METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
 TOL = 1e-5
-# ncu DRAM bytes (read + write) per active node of one level-0 smoother sweep of the
-# current kernel: 137.1 MB over the 651,308 active nodes of the first 128^3 bench cell
-# (profiles/k_stencil_smoother_c128_elastic.md); scaled by the nodes of each sweep
-NCU_DRAM_BYTES_PER_NODE = 210.5
+# ncu DRAM bytes (read + write) per active node of the timed level-0 sweep of the current
+# kernel: with the default one level-0 sweep per visit that is the V-cycle's last sweep
+# (u, f and K p read, u' written, Krylov partials): 197.3 MB over the 651,308 active nodes
+# of the first 128^3 bench cell (profiles/k_stencil_smoother_c128_elastic.md); scaled by
+# the nodes of each sweep
+NCU_DRAM_BYTES_PER_NODE = 302.9
 
 
 def workload(name: str, rank: int):
@@ -245,7 +247,10 @@ def run_gmt(args, rank: int, world: int):
             CH[i] = h.homogenize(ph, E=1.0, nu=0.3, k=1.0)
             cyc.append((i, info.inner_total))
             if trace:
-                for k, (n, ms, b) in h.trace_totals().items():
+                tt = h.trace_totals()
+                a = tot.setdefault("_smooth_node_launches", [0, 0.0, 0.0])
+                a[2] += float(h.num_nodes(0)) * tt["smooth_l0"][0]   # nodes x sweeps
+                for k, (n, ms, b) in tt.items():
                     if k == "setup_hierarchy":
                         continue
                     a = tot.setdefault(k, [0, 0.0, 0.0])
@@ -341,7 +346,7 @@ def run_gmt(args, rank: int, world: int):
     n_sm, ms_sm, b_sm = totals.get("smooth_l0", [0, 0.0, 0.0])
     peak, peak_src = measured_peak_gbs()
     achieved = (b_sm / (ms_sm / 1000.0)) / 1e9 if ms_sm > 0 else None
-    avg_nodes = b_sm / max(n_sm, 1) / (3 * 18 * (4 if prec == gmt.FP32 else 8))
+    avg_nodes = totals.pop("_smooth_node_launches", [0, 0.0, 0.0])[2] / max(n_sm, 1)
     traffic = (NCU_DRAM_BYTES_PER_NODE * avg_nodes) if NCU_DRAM_BYTES_PER_NODE else None
     total_dev_ms = sum(v[1] for v in totals.values())
     line = {
@@ -370,14 +375,20 @@ def run_gmt(args, rank: int, world: int):
                 "h2d_bytes_per_step": int(sum(v.numel() for v in vox_host)),
                 "d2h_bytes_per_step": int(len(cells) * (36 if ph == gmt.ELASTIC else 9) * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "level-0 smoother sweep (k_stencil JACOBI)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "level-0 smoother sweeps (k_stencil JACOBI; with the default one "
+                               "sweep per level-0 visit, the V-cycle's last sweep, which also "
+                               "writes the Krylov partials)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_source": "ncu dram__bytes_read + write of one level-0 sweep on "
-                                       "the first 128^3 cell, per active node, times this "
-                                       "workload's nodes per sweep",
+                     "traffic_source": "ncu dram__bytes_read + write of the V-cycle's last "
+                                       "level-0 sweep on the first 128^3 cell, per active "
+                                       "node, times this workload's nodes per sweep",
                      "peak_source": peak_src,
-                     "algorithmic_bytes": "3 vectors x 18 values x 4 B per active node",
+                     "algorithmic_bytes": "18 values x 4 B per active node for each vector: "
+                                          "u and f read, u' written, plus K p read in the "
+                                          "V-cycle's last sweep (4 vectors, 288 B)",
+                     "avg_nodes_per_launch": avg_nodes,
                      "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
         "phases_ms_per_step": {k: v[1] / trace_steps for k, v in sorted(totals.items())},
         "traced_device_ms_per_step": total_dev_ms / trace_steps,

@@ -1757,7 +1757,7 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   cudaStream_t s = h->stream;
   int nvec = 2, cat = TR_COARSE_ST;
   if (mode == ST_RESID) nvec = va.f ? 3 : 2;
-  if (mode == ST_JACOBI) nvec = 3;
+  if (mode == ST_JACOBI) nvec = 3 + (va.aux != nullptr);   // the last sweep also reads K p
   if (mode == ST_CHEB) nvec = 3 + (va.c1 != 0.0) + (va.dout != nullptr);
   if (fine) {
     cat = mode == ST_APPLY ? TR_APPLY0 : (mode == ST_RESID ? (va.f ? TR_RESID0 : TR_OUTER) : TR_SMOOTH0);
