@@ -192,6 +192,10 @@ def run_gmt(args, rank: int, world: int):
     elif args.workload == "c512":
         # at 512^3 two level-0 sweeps win (2.62 vs 2.49 solves/s: 7 instead of 9 cycles)
         opts.nu_pre = opts.nu_post = 2
+    elif ph == gmt.HEAT:
+        # scalar conduction: two level-0 sweeps win on the 128^3 batch (522 vs 481 solves/s
+        # over 30 steps: 72 instead of 99 cycles)
+        opts.nu_pre = opts.nu_post = 2
     if args.nu_post >= 0:
         opts.nu_post = args.nu_post
     if args.inner_tol > 0:
@@ -347,7 +351,12 @@ def run_gmt(args, rank: int, world: int):
     peak, peak_src = measured_peak_gbs()
     achieved = (b_sm / (ms_sm / 1000.0)) / 1e9 if ms_sm > 0 else None
     avg_nodes = totals.pop("_smooth_node_launches", [0, 0.0, 0.0])[2] / max(n_sm, 1)
-    traffic = (NCU_DRAM_BYTES_PER_NODE * avg_nodes) if NCU_DRAM_BYTES_PER_NODE else None
+    # the ncu figure was taken on the FP32 elasticity sweep; other forms report no traffic
+    ncu_matches = (ph == gmt.ELASTIC and prec == gmt.FP32)
+    traffic = (NCU_DRAM_BYTES_PER_NODE * avg_nodes) \
+        if (NCU_DRAM_BYTES_PER_NODE and ncu_matches) else None
+    vals = (18 if ph == gmt.ELASTIC else 3)
+    esz = 4 if prec == gmt.FP32 else 8
     total_dev_ms = sum(v[1] for v in totals.values())
     line = {
         "metric": METRIC, "value": value, "unit": "C^H solves/s", "n_gpus": world,
@@ -381,13 +390,16 @@ def run_gmt(args, rank: int, world: int):
                                "writes the Krylov partials)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_source": "ncu dram__bytes_read + write of the V-cycle's last "
-                                       "level-0 sweep on the first 128^3 cell, per active "
-                                       "node, times this workload's nodes per sweep",
+                     "traffic_source": ("ncu dram__bytes_read + write of the V-cycle's "
+                                        "last level-0 sweep on the first 128^3 cell, per "
+                                        "active node, times this workload's nodes per sweep")
+                                       if traffic is not None else
+                                       "not captured for this physics / precision",
                      "peak_source": peak_src,
-                     "algorithmic_bytes": "18 values x 4 B per active node for each vector: "
-                                          "u and f read, u' written, plus K p read in the "
-                                          "V-cycle's last sweep (4 vectors, 288 B)",
+                     "algorithmic_bytes": "%d values x %d B per active node for each "
+                                          "vector: u and f read, u' written, plus K p read "
+                                          "in the V-cycle's last sweep (4 vectors, %d B)"
+                                          % (vals, esz, 4 * vals * esz),
                      "avg_nodes_per_launch": avg_nodes,
                      "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
         "phases_ms_per_step": {k: v[1] / trace_steps for k, v in sorted(totals.items())},

@@ -91,7 +91,8 @@ typedef struct {
   int nu_coarse;       /* [2] pre- and post-smoothing sweeps on levels >= 1; 0: nu_pre and
                           nu_post on every level. The defaults (1 on the fine level, 2 on
                           the coarse ones) were the fastest of the sweeps measured on the
-                          128^3 benchmark batch */
+                          128^3 elasticity batch; heat conduction on the same cells and
+                          elasticity at 512^3 ran faster with nu_pre = nu_post = 2 */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,
