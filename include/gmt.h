@@ -271,6 +271,74 @@ int64_t gmt_launch_count(void);
 void gmt_release_cached_memory(void);
 int64_t gmt_cached_bytes(void);
 
+/* ---- learned initializer (Sec. 4.2-4.3, Alg. 2) -------------------------------------------
+   A sparse 3D convolutional U-Net over levels 0-2 of a hierarchy predicts the fine-level
+   field from the geometry; gmt_solve then refines it as its warm start u0, and the plain
+   V-cycles run on until the tolerance is met (the fallback). The paper's initializer is a
+   transformer; this network is a convolutional U-Net of about 2M parameters with the same
+   role (input: the octant masks; output: the fine field; trained on solved fields).
+   Activations are FP32 [node][channel] over the canonical active nodes of a level. Every
+   convolution has 27 taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1); a missing neighbour adds 0:
+     same-level  z[n] = b + sum_t W[t]^T x[node n + d_t]            (periodic wrap)
+     down l->l+1 z[q] = b + sum_t W[t]^T x[fine node 2q + d_t]
+     up l+1->l   z[p] = b + sum_t W[t]^T x[coarse node q, p = 2q + d_t]
+   y = relu(z + skip). Twelve layers for widths (w0, w1, w2) and cout outputs:
+     0 same@0 8->w0, 1 same@0 w0->w0, 2 down w0->w1, 3 same@1 w1->w1, 4 down w1->w2,
+     5 and 6 same@2 w2->w2, 7 up w2->w1 + skip(act 4), 8 same@1 w1->w1,
+     9 up w1->w0 + skip(act 2), 10 same@0 w0->w0, 11 same@0 w0->cout without relu.
+   (activation 0 is the input, activation i+1 the output of layer i). Input channels: the
+   node's octant mask bits. Output: cout = D*M channels = the field in canonical
+   [node][D][M] order divided by `scale`. Parameters: FP32, per layer W [27][cin][cout] then
+   b [cout], layers in order. Loss: mean over nodes and channels of (y - u/scale)^2.
+   Optimizer: AdamW with bias-corrected moments and decoupled weight decay. */
+typedef struct gmt_unet gmt_unet;
+typedef struct gmt_netgraph gmt_netgraph;
+typedef struct {
+  double lr, beta1, beta2, eps, weight_decay;
+} gmt_adamw;
+
+/* Parameter count for out_channels and widths[3]; -1 for a bad shape. */
+int64_t gmt_unet_param_count(int out_channels, const int* widths);
+/* Layer table, host int32[12][6]: kind (0 same, 1 down, 2 up), output level, input
+   activation, skip activation (-1 none), cin, cout. */
+gmt_status gmt_unet_layers(int out_channels, const int* widths, int32_t* layers_out);
+/* New network on the current device with parameters copied from `params` (host or device
+   float[gmt_unet_param_count]); the initial values are the caller's (random draws are
+   inputs). AdamW moments start at zero. Release with gmt_unet_free. */
+gmt_status gmt_unet_create(int out_channels, const int* widths, const float* params,
+                           gmt_unet** out);
+void gmt_unet_free(gmt_unet* net);
+int64_t gmt_unet_num_params(const gmt_unet* net);
+/* Copy the parameters out / in (host or device float[P]); set also zeroes the moments. */
+gmt_status gmt_unet_get_params(const gmt_unet* net, float* dst);
+gmt_status gmt_unet_set_params(gmt_unet* net, const float* src);
+
+/* Neighbour tables and input features of a hierarchy with at least 3 levels (GMT_ERR_RES
+   otherwise), on the hierarchy's stream at build time; owns the activation buffers of the
+   last network shape used with it. Release with gmt_netgraph_free (the hierarchy may be
+   freed first). */
+gmt_status gmt_netgraph_build(gmt_hierarchy* h, gmt_netgraph** out);
+void gmt_netgraph_free(gmt_netgraph* g);
+int64_t gmt_netgraph_nodes(const gmt_netgraph* g, int level);   /* level 0..2, else -1 */
+/* Tables of `level` (host or device int32, each nullable): same [n_l][27] canonical
+   neighbours; for level < 2, down [n_{l+1}][27] fine nodes 2q + d_t and up [n_l][27]
+   coarse nodes q with p = 2q + d_t; -1 where none. */
+gmt_status gmt_netgraph_tables(const gmt_netgraph* g, int level, int32_t* same_out,
+                               int32_t* down_out, int32_t* up_out);
+
+/* u_out (device double[n_0][cout]) = scale * network output: the predicted canonical field,
+   ready to pass to gmt_solve as u0. */
+gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* g, double scale, double* u_out);
+/* Loss against the canonical field u_target (device double[n_0][cout]) and its gradient
+   with respect to every parameter (grad_out: host or device float[P], nullable; loss_out:
+   host, nullable). The parameters do not change. */
+gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* g, const double* u_target,
+                             double scale, float* grad_out, double* loss_out);
+/* One training step: forward, loss, backward, AdamW update of the parameters. loss_out
+   (host, nullable): the loss before the update. */
+gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* g, const double* u_target,
+                               double scale, const gmt_adamw* hp, double* loss_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,8 @@ Modules:
   solve     global assembly, conjugate-gradient solve, dense brute force, residual and
             the energy-averaged homogenized tensor (Sec. 3.1, Sec. 5 metrics, App. F)
   galerkin  global prolongation matrix and Galerkin coarse operators (Sec. 3.2, Sec. 4.6)
+  unet      the learned initializer's sparse convolutional U-Net, its loss, autograd
+            gradient and AdamW step (Sec. 4.2-4.3, Alg. 2)
 
 Parity pins: every function here is checked in tests/ against closed forms, invariants
 or brute force (see the test files); no function is "parity unpinned".

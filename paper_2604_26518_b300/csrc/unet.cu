@@ -1,0 +1,720 @@
+// Learned initializer: a sparse 3D convolutional U-Net over the node hierarchy that
+// predicts the fine-level cell-problem field from the geometry (Sec. 4.2-4.3 describe the
+// paper's learned initial guess; its transformer is replaced here by a convolutional
+// U-Net). The prediction enters the solver as its warm start u0 (Alg. 2: the network's
+// field followed by V-cycles, with the plain V-cycles continuing until the tolerance is met).
+//
+// Network (all activations are [node][channel] FP32 over the canonical active-node list of
+// a hierarchy level; every convolution has 27 taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)):
+//   same-level conv:  z[n] = b + sum_t W[t]^T x[nbr(n, d_t)]            (periodic wrap)
+//   down (l -> l+1):  z[q] = b + sum_t W[t]^T x[fine node at 2q + d_t]
+//   up   (l+1 -> l):  z[p] = b + sum_t W[t]^T x[coarse node q with p = 2q + d_t]
+// (down and up use the parent/child relation of the trilinear transfer of App. E.2), a
+// missing neighbour contributes zero, y = relu(z + skip). Layers, widths (w0, w1, w2):
+//   0 same@0 8->w0   1 same@0 w0->w0   2 down 0->1 w0->w1   3 same@1 w1->w1
+//   4 down 1->2 w1->w2   5 same@2   6 same@2   7 up 2->1 w2->w1 (+ skip from 3)
+//   8 same@1   9 up 1->0 w1->w0 (+ skip from 1)   10 same@0   11 same@0 w0->cout (linear)
+// Input: the node's 8-bit octant mask as 8 channels of 0/1. Output: cout = D*M channels,
+// the field in canonical [node][D][M] order divided by `scale`.
+// Parameters: per layer W [27][cin][cout] then b [cout], layers in order, FP32.
+// Training: mean squared error against a solved field, AdamW (decoupled weight decay).
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gmt {
+void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);  // hierarchy.cu
+}
+
+namespace {
+
+constexpr int NLAYERS = 12;
+constexpr int NACT = 13;  // activation 0 is the input, activation i+1 the output of layer i
+constexpr int IN_CH = 8;
+enum { SAME = 0, DOWN = 1, UP = 2 };
+
+struct LayerDef {
+  int kind, lvl_out, in, skip, cin, cout, relu;
+};
+
+// layer list for widths w[3] and output channels co
+void layer_defs(const int* w, int co, LayerDef* L) {
+  const LayerDef d[NLAYERS] = {
+      {SAME, 0, 0, -1, IN_CH, w[0], 1}, {SAME, 0, 1, -1, w[0], w[0], 1},
+      {DOWN, 1, 2, -1, w[0], w[1], 1},  {SAME, 1, 3, -1, w[1], w[1], 1},
+      {DOWN, 2, 4, -1, w[1], w[2], 1},  {SAME, 2, 5, -1, w[2], w[2], 1},
+      {SAME, 2, 6, -1, w[2], w[2], 1},  {UP, 1, 7, 4, w[2], w[1], 1},
+      {SAME, 1, 8, -1, w[1], w[1], 1},  {UP, 0, 9, 2, w[1], w[0], 1},
+      {SAME, 0, 10, -1, w[0], w[0], 1}, {SAME, 0, 11, -1, w[0], co, 0}};
+  for (int i = 0; i < NLAYERS; ++i) L[i] = d[i];
+}
+
+int act_level(const LayerDef* L, int a) { return a == 0 ? 0 : L[a - 1].lvl_out; }
+int act_ch(const LayerDef* L, int a) { return a == 0 ? IN_CH : L[a - 1].cout; }
+
+int64_t param_count(const LayerDef* L) {
+  int64_t p = 0;
+  for (int i = 0; i < NLAYERS; ++i) p += 27LL * L[i].cin * L[i].cout + L[i].cout;
+  return p;
+}
+
+constexpr int WG_CHUNK = 1024;  // nodes per weight-gradient partial
+
+// ------------------------------------------------------------------ tables
+__device__ __forceinline__ int wrap(int a, int n) { return ((a % n) + n) % n; }
+
+__device__ __forceinline__ int site_canon(int x, int y, int z, const gmt::Level& L) {
+  int64_t s = gmt::site_slot(x, y, z, L.n, L.nbx, L.brick_map, L.dense);
+  return s < 0 ? -1 : L.slot_canon[s];
+}
+
+__global__ void k_same_table(const int32_t* __restrict__ xyz, int64_t n, gmt::Level L,
+                             int* __restrict__ tab) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  for (int t = 0; t < 27; ++t) {
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    tab[i * 27 + t] = site_canon(wrap(x + dx, L.n), wrap(y + dy, L.n), wrap(z + dz, L.n), L);
+  }
+}
+
+// coarse node q (level l+1) -> fine node at 2q + d_t (level l)
+__global__ void k_down_table(const int32_t* __restrict__ xyzc, int64_t nc, gmt::Level F,
+                             int* __restrict__ tab) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const int x = 2 * xyzc[3 * i], y = 2 * xyzc[3 * i + 1], z = 2 * xyzc[3 * i + 2];
+  for (int t = 0; t < 27; ++t) {
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    tab[i * 27 + t] = site_canon(wrap(x + dx, F.n), wrap(y + dy, F.n), wrap(z + dz, F.n), F);
+  }
+}
+
+// fine node p (level l) -> coarse node q (level l+1) with p = 2q + d_t, or -1
+__global__ void k_up_table(const int32_t* __restrict__ xyzf, int64_t nf, int nfine, gmt::Level C,
+                           int* __restrict__ tab) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const int x = xyzf[3 * i], y = xyzf[3 * i + 1], z = xyzf[3 * i + 2];
+  for (int t = 0; t < 27; ++t) {
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    const int a = wrap(x - dx, nfine), b = wrap(y - dy, nfine), c = wrap(z - dz, nfine);
+    tab[i * 27 + t] = ((a | b | c) & 1) ? -1 : site_canon(a >> 1, b >> 1, c >> 1, C);
+  }
+}
+
+__global__ void k_features(const int* __restrict__ canon_slot, const uint8_t* __restrict__ mask,
+                           int64_t n, float* __restrict__ x0) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned m = mask[canon_slot[i]];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) x0[i * 8 + o] = (float)((m >> o) & 1u);
+}
+
+// ------------------------------------------------------------------ gather convolution
+// out[n][co] (=, or += with accum) act(b[co] + add[n][co] + sum_t sum_ci w(t,ci,co) x[s][ci]),
+// s = tab[n][flip ? 26 - t : t] (skipped when < 0); w(t,ci,co) = W[t][ci][co], or
+// W[t][co][ci] with wtrans (the backward-data form of a layer whose forward weights are
+// [27][cout'][cin']). Block: 64 nodes x 32 output channels, 8 nodes per thread.
+__global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int cin,
+                                               const int* __restrict__ tab, int flip,
+                                               const float* __restrict__ W, int wtrans,
+                                               const float* __restrict__ bias,
+                                               const float* __restrict__ add, int relu, int accum,
+                                               float* __restrict__ out, int cout, int64_t n_out) {
+  __shared__ float sX[64][33];
+  __shared__ float sW[32][33];
+  __shared__ int sIdx[64];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int64_t n0 = (int64_t)blockIdx.x * 64;
+  const int co = blockIdx.y * 32 + tx;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int t = 0; t < 27; ++t) {
+    const int tt = flip ? 26 - t : t;
+    __syncthreads();
+    if (tid < 64) {
+      const int64_t node = n0 + tid;
+      sIdx[tid] = node < n_out ? tab[node * 27 + tt] : -1;
+    }
+    const int any = __syncthreads_or(tid < 64 && sIdx[tid] >= 0);
+    if (!any) continue;
+    for (int ci0 = 0; ci0 < cin; ci0 += 32) {
+      const int ci = ci0 + tx;
+      for (int r = ty; r < 64; r += 8) {
+        const int s = sIdx[r];
+        sX[r][tx] = (s >= 0 && ci < cin) ? x[(int64_t)s * cin + ci] : 0.f;
+      }
+      for (int r = ty; r < 32; r += 8) {
+        const int c = ci0 + r;
+        float w = 0.f;
+        if (c < cin && co < cout)
+          w = wtrans ? W[((int64_t)t * cout + co) * cin + c] : W[((int64_t)t * cin + c) * cout + co];
+        sW[r][tx] = w;
+      }
+      __syncthreads();
+      const int lim = min(32, cin - ci0);
+      for (int k = 0; k < lim; ++k) {
+        const float w = sW[k][tx];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fmaf(sX[ty * 8 + j][k], w, acc[j]);
+      }
+      __syncthreads();
+    }
+  }
+  if (co >= cout) return;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t node = n0 + ty * 8 + j;
+    if (node >= n_out) break;
+    const int64_t o = node * cout + co;
+    float v = acc[j] + (bias ? bias[co] : 0.f) + (add ? add[o] : 0.f);
+    if (relu) v = fmaxf(v, 0.f);
+    out[o] = accum ? out[o] + v : v;
+  }
+}
+
+// Weight-gradient partials of the forward gather conv: for chunk c of WG_CHUNK output
+// nodes, part[c][t][ci][co] = sum_n x[tab[n][t]][ci] dz[n][co] and bpart[c][co] = sum_n
+// dz[n][co]. Grid (27, chunks, ci tiles x co tiles), block 32 x 8, each thread 4 ci x 1 co.
+__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ x, int cin,
+                                               const int* __restrict__ tab,
+                                               const float* __restrict__ dz, int cout, int64_t n,
+                                               float* __restrict__ part, float* __restrict__ bpart) {
+  __shared__ float sX[64][33];
+  __shared__ float sD[64][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int t = blockIdx.x;
+  const int64_t c = blockIdx.y;
+  const int tiles_co = (cout + 31) / 32;
+  const int ci0 = (blockIdx.z / tiles_co) * 32, co0 = (blockIdx.z % tiles_co) * 32;
+  const int64_t beg = c * WG_CHUNK, end = min(n, beg + WG_CHUNK);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float bacc = 0.f;
+  for (int64_t j0 = beg; j0 < end; j0 += 64) {
+    for (int r = ty; r < 64; r += 8) {
+      const int64_t node = j0 + r;
+      float xv = 0.f, dv = 0.f;
+      if (node < end) {
+        const int s = tab[node * 27 + t];
+        if (s >= 0 && ci0 + tx < cin) xv = x[(int64_t)s * cin + ci0 + tx];
+        if (co0 + tx < cout) dv = dz[node * cout + co0 + tx];
+      }
+      sX[r][tx] = xv;
+      sD[r][tx] = dv;
+    }
+    __syncthreads();
+    for (int r = 0; r < 64; ++r) {
+      const float d = sD[r][tx];
+      bacc += d;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = fmaf(sX[r][ty * 4 + k], d, acc[k]);
+    }
+    __syncthreads();
+  }
+  const int co = co0 + tx;
+  if (co >= cout) return;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int ci = ci0 + ty * 4 + k;
+    if (ci < cin) part[((c * 27 + t) * cin + ci) * cout + co] = acc[k];
+  }
+  if (t == 0 && ci0 == 0 && ty == 0) bpart[c * cout + co] = bacc;
+}
+
+// gW[i] = sum_c part[c][i], gb[co] = sum_c bpart[c][co] (fixed order)
+__global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart,
+                               int64_t chunks, int64_t nw, int cout, float* __restrict__ gW,
+                               float* __restrict__ gb) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nw) {
+    float s = 0.f;
+    for (int64_t c = 0; c < chunks; ++c) s += part[c * nw + i];
+    gW[i] = s;
+  } else if (i < nw + cout) {
+    const int co = (int)(i - nw);
+    float s = 0.f;
+    for (int64_t c = 0; c < chunks; ++c) s += bpart[c * cout + co];
+    gb[co] = s;
+  }
+}
+
+__global__ void k_relu_grad(const float* __restrict__ dy, const float* __restrict__ y, int64_t n,
+                            float* __restrict__ dz) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dz[i] = y[i] > 0.f ? dy[i] : 0.f;
+}
+
+__global__ void k_add_into(float* __restrict__ g, const float* __restrict__ d, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) g[i] += d[i];
+}
+
+// Mean squared error over n values: loss partial per block (double) and the gradient
+// g = 2 (pred - u / scale) / n.
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ pred,
+                                             const double* __restrict__ u, double inv_scale,
+                                             int64_t n, float* __restrict__ g,
+                                             double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  const double inv_n = 1.0 / (double)n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = (double)pred[i] - u[i] * inv_scale;
+    s += e * e;
+    if (g) g[i] = (float)(2.0 * e * inv_n);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0] * inv_n;
+}
+
+__global__ void k_sum_blocks(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                        float wd, float bc1, float bc2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float step = (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  p[i] = p[i] - lr * (step + wd * p[i]);
+}
+
+__global__ void k_to_field(const float* __restrict__ y, int64_t n, double scale,
+                           double* __restrict__ u) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) u[i] = scale * (double)y[i];
+}
+
+inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct gmt_unet {
+  int device = 0;
+  int w[3] = {0, 0, 0};
+  int cout = 0;
+  LayerDef L[NLAYERS];
+  int64_t P = 0;
+  int64_t woff[NLAYERS], boff[NLAYERS];
+  float* p = nullptr;     // parameters
+  float* g = nullptr;     // gradient
+  float* m = nullptr;     // AdamW moments
+  float* v = nullptr;
+  int64_t steps = 0;
+};
+
+struct gmt_netgraph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int N = 0;
+  int64_t n[3] = {0, 0, 0};
+  int* same[3] = {nullptr, nullptr, nullptr};
+  int* down[2] = {nullptr, nullptr};
+  int* up[2] = {nullptr, nullptr};
+  float* x0 = nullptr;
+  gmt::Arena geo;
+  // buffers for one network shape
+  gmt::Arena buf;
+  int key[4] = {0, 0, 0, 0};
+  float* a[NACT] = {};
+  float* g[NACT] = {};
+  float* dz = nullptr;
+  float* part = nullptr;
+  float* bpart = nullptr;
+  double* lpart = nullptr;
+  double* loss = nullptr;
+};
+
+namespace {
+
+constexpr int LOSS_BLOCKS = 296;
+
+void ensure_buffers(gmt_netgraph* G, const gmt_unet* net) {
+  if (G->key[0] == net->w[0] && G->key[1] == net->w[1] && G->key[2] == net->w[2] &&
+      G->key[3] == net->cout)
+    return;
+  G->buf.release();
+  G->buf.bind(G->stream);
+  int64_t maxe = 0, maxpart = 0, maxb = 0;
+  for (int a = 1; a < NACT; ++a) {
+    const int64_t e = G->n[act_level(net->L, a)] * act_ch(net->L, a);
+    G->a[a] = G->buf.alloc<float>(e);
+    G->g[a] = G->buf.alloc<float>(e);
+    maxe = std::max(maxe, e);
+  }
+  G->a[0] = G->x0;
+  G->g[0] = nullptr;
+  for (int i = 0; i < NLAYERS; ++i) {
+    const LayerDef& d = net->L[i];
+    const int64_t chunks = (G->n[d.lvl_out] + WG_CHUNK - 1) / WG_CHUNK;
+    maxpart = std::max(maxpart, chunks * 27 * d.cin * d.cout);
+    maxb = std::max(maxb, chunks * d.cout);
+  }
+  G->dz = G->buf.alloc<float>(maxe);
+  G->part = G->buf.alloc<float>(maxpart);
+  G->bpart = G->buf.alloc<float>(maxb);
+  G->lpart = G->buf.alloc<double>(LOSS_BLOCKS);
+  G->loss = G->buf.alloc<double>(1);
+  G->key[0] = net->w[0];
+  G->key[1] = net->w[1];
+  G->key[2] = net->w[2];
+  G->key[3] = net->cout;
+}
+
+// the table a layer gathers its input through, and the one its backward-data pass uses
+const int* fwd_table(const gmt_netgraph* G, const LayerDef& d) {
+  if (d.kind == SAME) return G->same[d.lvl_out];
+  if (d.kind == DOWN) return G->down[d.lvl_out - 1];
+  return G->up[d.lvl_out];
+}
+const int* bwd_table(const gmt_netgraph* G, const LayerDef& d) {
+  if (d.kind == SAME) return G->same[d.lvl_out];
+  if (d.kind == DOWN) return G->up[d.lvl_out - 1];
+  return G->down[d.lvl_out];
+}
+
+void launch_gconv(cudaStream_t s, const float* x, int cin, const int* tab, int flip,
+                  const float* W, int wtrans, const float* b, const float* add, int relu,
+                  int accum, float* out, int cout, int64_t n_out) {
+  if (n_out <= 0) return;
+  dim3 grid((unsigned)((n_out + 63) / 64), (unsigned)((cout + 31) / 32));
+  k_gconv<<<grid, dim3(32, 8), 0, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum, out,
+                                       cout, n_out);
+  GMT_LAUNCH_CHECK();
+}
+
+void forward(gmt_unet* net, gmt_netgraph* G) {
+  ensure_buffers(G, net);
+  for (int i = 0; i < NLAYERS; ++i) {
+    const LayerDef& d = net->L[i];
+    launch_gconv(G->stream, G->a[d.in], d.cin, fwd_table(G, d), 0, net->p + net->woff[i], 0,
+                 net->p + net->boff[i], d.skip >= 0 ? G->a[d.skip] : nullptr, d.relu, 0,
+                 G->a[i + 1], d.cout, G->n[d.lvl_out]);
+  }
+}
+
+// loss and gradient into net->g (forward must have run)
+void backward(gmt_unet* net, gmt_netgraph* G, const double* u, double scale) {
+  cudaStream_t s = G->stream;
+  const int64_t n_out = G->n[0] * net->cout;
+  for (int a = 1; a < NACT; ++a)
+    GMT_CUDA(cudaMemsetAsync(G->g[a], 0,
+                             sizeof(float) * G->n[act_level(net->L, a)] * act_ch(net->L, a), s));
+  k_mse<<<LOSS_BLOCKS, 256, 0, s>>>(G->a[NACT - 1], u, 1.0 / scale, n_out, G->g[NACT - 1],
+                                    G->lpart);
+  GMT_LAUNCH_CHECK();
+  k_sum_blocks<<<1, 32, 0, s>>>(G->lpart, LOSS_BLOCKS, G->loss);
+  GMT_LAUNCH_CHECK();
+  for (int i = NLAYERS - 1; i >= 0; --i) {
+    const LayerDef& d = net->L[i];
+    const int64_t no = G->n[d.lvl_out];
+    const int64_t e = no * d.cout;
+    const float* dz = G->g[i + 1];
+    if (d.relu) {
+      k_relu_grad<<<blocks(e), 256, 0, s>>>(G->g[i + 1], G->a[i + 1], e, G->dz);
+      GMT_LAUNCH_CHECK();
+      dz = G->dz;
+    }
+    if (d.skip >= 0) {
+      k_add_into<<<blocks(e), 256, 0, s>>>(G->g[d.skip], dz, e);
+      GMT_LAUNCH_CHECK();
+    }
+    const int64_t chunks = (no + WG_CHUNK - 1) / WG_CHUNK;
+    if (chunks > 0) {
+      const int tiles = ((d.cin + 31) / 32) * ((d.cout + 31) / 32);
+      k_wgrad<<<dim3(27, (unsigned)chunks, tiles), dim3(32, 8), 0, s>>>(
+          G->a[d.in], d.cin, fwd_table(G, d), dz, d.cout, no, G->part, G->bpart);
+      GMT_LAUNCH_CHECK();
+      const int64_t nw = 27LL * d.cin * d.cout;
+      k_wgrad_reduce<<<blocks(nw + d.cout), 256, 0, s>>>(G->part, G->bpart, chunks, nw, d.cout,
+                                                          net->g + net->woff[i],
+                                                          net->g + net->boff[i]);
+      GMT_LAUNCH_CHECK();
+    } else {
+      GMT_CUDA(cudaMemsetAsync(net->g + net->woff[i], 0,
+                               sizeof(float) * (27LL * d.cin * d.cout + d.cout), s));
+    }
+    if (d.in > 0)
+      launch_gconv(s, dz, d.cout, bwd_table(G, d), d.kind == SAME, net->p + net->woff[i], 1,
+                   nullptr, nullptr, 0, 1, G->g[d.in], d.cin, G->n[act_level(net->L, d.in)]);
+  }
+}
+
+void check_pair(const gmt_unet* net, const gmt_netgraph* G) {
+  GMT_REQUIRE(net && G, GMT_ERR_ARG, "null network or graph");
+  GMT_REQUIRE(net->device == G->device, GMT_ERR_ARG, "network and graph on different devices");
+  GMT_CUDA(cudaSetDevice(G->device));
+}
+
+}  // namespace
+
+#define UNET_BEGIN \
+  gmt::set_error("%s", ""); \
+  try {
+#define UNET_END                                   \
+  }                                                \
+  catch (const gmt::Fail& f) {                     \
+    return f.status;                               \
+  }                                                \
+  catch (...) {                                    \
+    gmt::set_error("unexpected host exception");   \
+    return GMT_ERR_ARG;                            \
+  }
+
+extern "C" {
+
+int64_t gmt_unet_param_count(int out_channels, const int* widths) {
+  if (!widths || out_channels <= 0 || widths[0] <= 0 || widths[1] <= 0 || widths[2] <= 0) return -1;
+  LayerDef L[NLAYERS];
+  layer_defs(widths, out_channels, L);
+  return param_count(L);
+}
+
+gmt_status gmt_unet_layers(int out_channels, const int* widths, int32_t* layers_out) {
+  UNET_BEGIN
+  GMT_REQUIRE(gmt_unet_param_count(out_channels, widths) > 0 && layers_out, GMT_ERR_ARG,
+              "bad network shape");
+  LayerDef L[NLAYERS];
+  layer_defs(widths, out_channels, L);
+  for (int i = 0; i < NLAYERS; ++i) {
+    int32_t* r = layers_out + 6 * i;
+    r[0] = L[i].kind;
+    r[1] = L[i].lvl_out;
+    r[2] = L[i].in;
+    r[3] = L[i].skip;
+    r[4] = L[i].cin;
+    r[5] = L[i].cout;
+  }
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_unet_create(int out_channels, const int* widths, const float* params,
+                           gmt_unet** out) {
+  UNET_BEGIN
+  GMT_REQUIRE(out && params, GMT_ERR_ARG, "null argument");
+  GMT_REQUIRE(gmt_unet_param_count(out_channels, widths) > 0, GMT_ERR_ARG, "bad network shape");
+  *out = nullptr;
+  std::unique_ptr<gmt_unet> net(new gmt_unet());
+  GMT_CUDA(cudaGetDevice(&net->device));
+  for (int i = 0; i < 3; ++i) net->w[i] = widths[i];
+  net->cout = out_channels;
+  layer_defs(widths, out_channels, net->L);
+  int64_t off = 0;
+  for (int i = 0; i < NLAYERS; ++i) {
+    net->woff[i] = off;
+    off += 27LL * net->L[i].cin * net->L[i].cout;
+    net->boff[i] = off;
+    off += net->L[i].cout;
+  }
+  net->P = off;
+  const size_t bytes = sizeof(float) * (size_t)off;
+  struct Guard {
+    gmt_unet* n;
+    ~Guard() {
+      if (n) {
+        cudaFree(n->p);
+        cudaFree(n->g);
+        cudaFree(n->m);
+        cudaFree(n->v);
+      }
+    }
+  } guard{net.get()};
+  GMT_CUDA(cudaMalloc(&net->p, bytes));
+  GMT_CUDA(cudaMalloc(&net->g, bytes));
+  GMT_CUDA(cudaMalloc(&net->m, bytes));
+  GMT_CUDA(cudaMalloc(&net->v, bytes));
+  GMT_CUDA(cudaMemcpy(net->p, params, bytes, cudaMemcpyDefault));
+  GMT_CUDA(cudaMemset(net->g, 0, bytes));
+  GMT_CUDA(cudaMemset(net->m, 0, bytes));
+  GMT_CUDA(cudaMemset(net->v, 0, bytes));
+  guard.n = nullptr;
+  *out = net.release();
+  return GMT_OK;
+  UNET_END
+}
+
+void gmt_unet_free(gmt_unet* net) {
+  if (!net) return;
+  cudaSetDevice(net->device);
+  cudaDeviceSynchronize();
+  cudaFree(net->p);
+  cudaFree(net->g);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  delete net;
+}
+
+int64_t gmt_unet_num_params(const gmt_unet* net) { return net ? net->P : -1; }
+
+gmt_status gmt_unet_get_params(const gmt_unet* net, float* dst) {
+  UNET_BEGIN
+  GMT_REQUIRE(net && dst, GMT_ERR_ARG, "null argument");
+  GMT_CUDA(cudaSetDevice(net->device));
+  GMT_CUDA(cudaDeviceSynchronize());
+  GMT_CUDA(cudaMemcpy(dst, net->p, sizeof(float) * net->P, cudaMemcpyDefault));
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_unet_set_params(gmt_unet* net, const float* src) {
+  UNET_BEGIN
+  GMT_REQUIRE(net && src, GMT_ERR_ARG, "null argument");
+  GMT_CUDA(cudaSetDevice(net->device));
+  GMT_CUDA(cudaDeviceSynchronize());
+  GMT_CUDA(cudaMemcpy(net->p, src, sizeof(float) * net->P, cudaMemcpyDefault));
+  GMT_CUDA(cudaMemset(net->m, 0, sizeof(float) * net->P));
+  GMT_CUDA(cudaMemset(net->v, 0, sizeof(float) * net->P));
+  net->steps = 0;
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_netgraph_build(gmt_hierarchy* h, gmt_netgraph** out) {
+  UNET_BEGIN
+  GMT_REQUIRE(h && out, GMT_ERR_ARG, "null argument");
+  GMT_REQUIRE(h->L >= 3, GMT_ERR_RES, "the network needs a hierarchy of at least 3 levels (has %d)",
+              h->L);
+  *out = nullptr;
+  GMT_CUDA(cudaSetDevice(h->device));
+  std::unique_ptr<gmt_netgraph> G(new gmt_netgraph());
+  G->device = h->device;
+  G->stream = h->stream;
+  G->geo.bind(h->stream);
+  G->N = h->N;
+  cudaStream_t s = h->stream;
+  int32_t* xyz[3];
+  for (int l = 0; l < 3; ++l) {
+    G->n[l] = h->lv[l].n_nodes;
+    xyz[l] = G->geo.alloc<int32_t>(3 * std::max<int64_t>(G->n[l], 1));
+    gmt::export_nodes(h, l, xyz[l], nullptr);
+    G->same[l] = G->geo.alloc<int>(27 * std::max<int64_t>(G->n[l], 1));
+    k_same_table<<<blocks(G->n[l]), 256, 0, s>>>(xyz[l], G->n[l], h->lv[l], G->same[l]);
+    GMT_LAUNCH_CHECK();
+  }
+  for (int l = 0; l < 2; ++l) {
+    G->down[l] = G->geo.alloc<int>(27 * std::max<int64_t>(G->n[l + 1], 1));
+    k_down_table<<<blocks(G->n[l + 1]), 256, 0, s>>>(xyz[l + 1], G->n[l + 1], h->lv[l],
+                                                     G->down[l]);
+    GMT_LAUNCH_CHECK();
+    G->up[l] = G->geo.alloc<int>(27 * std::max<int64_t>(G->n[l], 1));
+    k_up_table<<<blocks(G->n[l]), 256, 0, s>>>(xyz[l], G->n[l], h->lv[l].n, h->lv[l + 1], G->up[l]);
+    GMT_LAUNCH_CHECK();
+  }
+  G->x0 = G->geo.alloc<float>(8 * std::max<int64_t>(G->n[0], 1));
+  k_features<<<blocks(G->n[0]), 256, 0, s>>>(h->lv[0].canon_slot, h->lv[0].mask, G->n[0], G->x0);
+  GMT_LAUNCH_CHECK();
+  GMT_CUDA(cudaStreamSynchronize(s));
+  *out = G.release();
+  return GMT_OK;
+  UNET_END
+}
+
+void gmt_netgraph_free(gmt_netgraph* G) {
+  if (!G) return;
+  cudaSetDevice(G->device);
+  delete G;  // the arenas wait for the graph's stream before returning their blocks
+}
+
+int64_t gmt_netgraph_nodes(const gmt_netgraph* G, int level) {
+  return (G && level >= 0 && level < 3) ? G->n[level] : -1;
+}
+
+gmt_status gmt_netgraph_tables(const gmt_netgraph* G, int level, int32_t* same_out,
+                               int32_t* down_out, int32_t* up_out) {
+  UNET_BEGIN
+  GMT_REQUIRE(G && level >= 0 && level < 3, GMT_ERR_ARG, "bad graph level");
+  GMT_CUDA(cudaSetDevice(G->device));
+  GMT_CUDA(cudaStreamSynchronize(G->stream));
+  if (same_out)
+    GMT_CUDA(cudaMemcpy(same_out, G->same[level], sizeof(int) * 27 * G->n[level], cudaMemcpyDefault));
+  if (down_out && level < 2)
+    GMT_CUDA(cudaMemcpy(down_out, G->down[level], sizeof(int) * 27 * G->n[level + 1],
+                        cudaMemcpyDefault));
+  if (up_out && level < 2)
+    GMT_CUDA(cudaMemcpy(up_out, G->up[level], sizeof(int) * 27 * G->n[level], cudaMemcpyDefault));
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* G, double scale, double* u_out) {
+  UNET_BEGIN
+  check_pair(net, G);
+  GMT_REQUIRE(u_out && scale > 0 && std::isfinite(scale), GMT_ERR_ARG, "bad output or scale");
+  forward(net, G);
+  const int64_t e = G->n[0] * net->cout;
+  k_to_field<<<blocks(e), 256, 0, G->stream>>>(G->a[NACT - 1], e, scale, u_out);
+  GMT_LAUNCH_CHECK();
+  GMT_CUDA(cudaStreamSynchronize(G->stream));
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* G, const double* u_target, double scale,
+                             float* grad_out, double* loss_out) {
+  UNET_BEGIN
+  check_pair(net, G);
+  GMT_REQUIRE(u_target && scale > 0 && std::isfinite(scale), GMT_ERR_ARG, "bad target or scale");
+  forward(net, G);
+  backward(net, G, u_target, scale);
+  if (grad_out)
+    GMT_CUDA(cudaMemcpyAsync(grad_out, net->g, sizeof(float) * net->P, cudaMemcpyDefault,
+                             G->stream));
+  if (loss_out)
+    GMT_CUDA(cudaMemcpyAsync(loss_out, G->loss, sizeof(double), cudaMemcpyDefault, G->stream));
+  GMT_CUDA(cudaStreamSynchronize(G->stream));
+  return GMT_OK;
+  UNET_END
+}
+
+gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* G, const double* u_target,
+                               double scale, const gmt_adamw* hp, double* loss_out) {
+  UNET_BEGIN
+  check_pair(net, G);
+  GMT_REQUIRE(u_target && hp && scale > 0 && std::isfinite(scale), GMT_ERR_ARG,
+              "bad target, scale or hyper-parameters");
+  GMT_REQUIRE(hp->lr > 0 && hp->beta1 >= 0 && hp->beta1 < 1 && hp->beta2 >= 0 && hp->beta2 < 1 &&
+                  hp->eps > 0 && hp->weight_decay >= 0,
+              GMT_ERR_ARG, "bad AdamW hyper-parameters");
+  forward(net, G);
+  backward(net, G, u_target, scale);
+  net->steps += 1;
+  const float bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)net->steps));
+  const float bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)net->steps));
+  k_adamw<<<blocks(net->P), 256, 0, G->stream>>>(net->p, net->g, net->m, net->v, net->P,
+                                                 (float)hp->lr, (float)hp->beta1,
+                                                 (float)hp->beta2, (float)hp->eps,
+                                                 (float)hp->weight_decay, bc1, bc2);
+  GMT_LAUNCH_CHECK();
+  if (loss_out) {
+    GMT_CUDA(cudaMemcpyAsync(loss_out, G->loss, sizeof(double), cudaMemcpyDefault, G->stream));
+    GMT_CUDA(cudaStreamSynchronize(G->stream));
+  }
+  return GMT_OK;
+  UNET_END
+}
+
+}  // extern "C"

@@ -72,6 +72,12 @@ class GmtError(RuntimeError):
         self.status = status
 
 
+class AdamW(ctypes.Structure):
+    """gmt_adamw: AdamW hyper-parameters of gmt_unet_train_step."""
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("weight_decay", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -114,6 +120,20 @@ _SIGS = {
     "gmt_homogenize_dense_noalloc": (_I, [_P, _I, _I, _D, _D, _D, _P, _P, _P]),
     "gmt_release_cached_memory": (None, []),
     "gmt_cached_bytes": (_L, []),
+    "gmt_unet_param_count": (_L, [_I, _P]),
+    "gmt_unet_layers": (_I, [_I, _P, _P]),
+    "gmt_unet_create": (_I, [_I, _P, _P, ctypes.POINTER(_P)]),
+    "gmt_unet_free": (None, [_P]),
+    "gmt_unet_num_params": (_L, [_P]),
+    "gmt_unet_get_params": (_I, [_P, _P]),
+    "gmt_unet_set_params": (_I, [_P, _P]),
+    "gmt_netgraph_build": (_I, [_P, ctypes.POINTER(_P)]),
+    "gmt_netgraph_free": (None, [_P]),
+    "gmt_netgraph_nodes": (_L, [_P, _I]),
+    "gmt_netgraph_tables": (_I, [_P, _I, _P, _P, _P]),
+    "gmt_unet_forward": (_I, [_P, _P, _D, _P]),
+    "gmt_unet_gradient": (_I, [_P, _P, _P, _D, _P, ctypes.POINTER(_D)]),
+    "gmt_unet_train_step": (_I, [_P, _P, _P, _D, ctypes.POINTER(AdamW), ctypes.POINTER(_D)]),
 }
 
 TRACE_CATEGORIES = 14
@@ -380,6 +400,124 @@ class Hierarchy:
         _check(lib().gmt_residual(self._h, precision, _ptr(u), out.ctypes.data_as(ctypes.c_void_p)),
                "gmt_residual")
         return out
+
+
+UNET_WIDTHS = (32, 64, 128)
+
+
+def unet_layers(out_channels: int, widths=UNET_WIDTHS):
+    """Layer table of the initializer network (gmt_unet_layers): rows of (kind, output
+    level, input activation, skip activation, cin, cout); kind 0 same-level, 1 down, 2 up."""
+    w = (ctypes.c_int * 3)(*widths)
+    out = (ctypes.c_int32 * 72)()
+    _check(lib().gmt_unet_layers(int(out_channels), ctypes.addressof(w), ctypes.addressof(out)),
+           "gmt_unet_layers")
+    return [tuple(out[6 * i:6 * i + 6]) for i in range(12)]
+
+
+def unet_param_count(out_channels: int, widths=UNET_WIDTHS) -> int:
+    w = (ctypes.c_int * 3)(*widths)
+    return int(lib().gmt_unet_param_count(int(out_channels), ctypes.addressof(w)))
+
+
+class NetGraph:
+    """Neighbour tables and input features of a hierarchy for the initializer network
+    (gmt_netgraph_build); needs at least 3 levels."""
+
+    def __init__(self, hier: "Hierarchy"):
+        self._g = _P()
+        _check(lib().gmt_netgraph_build(hier._h, ctypes.byref(self._g)), "gmt_netgraph_build")
+        self.n = [int(lib().gmt_netgraph_nodes(self._g, l)) for l in range(3)]
+
+    def tables(self, level: int):
+        """(same, down, up) int32 tables of a level (down and up None at level 2)."""
+        torch = _torch()
+        n = self.n[level]
+        same = torch.empty((n, 27), dtype=torch.int32, device="cuda")
+        down = up = None
+        if level < 2:
+            down = torch.empty((self.n[level + 1], 27), dtype=torch.int32, device="cuda")
+            up = torch.empty((n, 27), dtype=torch.int32, device="cuda")
+        _check(lib().gmt_netgraph_tables(self._g, level, _ptr(same), _ptr(down), _ptr(up)),
+               "gmt_netgraph_tables")
+        return same, down, up
+
+    def free(self):
+        if self._g:
+            lib().gmt_netgraph_free(self._g)
+            self._g = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class UNet:
+    """The learned initializer (gmt_unet_*): a sparse 3D convolutional U-Net that predicts
+    the canonical fine field of a cell from its octant masks. `params`: float32 tensor of
+    the initial parameters (the caller draws them)."""
+
+    def __init__(self, out_channels: int, params, widths=UNET_WIDTHS):
+        torch = _torch()
+        self.out_channels = int(out_channels)
+        self.widths = tuple(widths)
+        p = params.detach().to(device="cuda", dtype=torch.float32).contiguous()
+        w = (ctypes.c_int * 3)(*self.widths)
+        self._n = _P()
+        _check(lib().gmt_unet_create(self.out_channels, ctypes.addressof(w), _ptr(p),
+                                     ctypes.byref(self._n)), "gmt_unet_create")
+        self.num_params = int(lib().gmt_unet_num_params(self._n))
+
+    def params(self):
+        torch = _torch()
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _check(lib().gmt_unet_get_params(self._n, _ptr(out)), "gmt_unet_get_params")
+        return out
+
+    def set_params(self, p):
+        torch = _torch()
+        p = p.detach().to(device="cuda", dtype=torch.float32).contiguous()
+        _check(lib().gmt_unet_set_params(self._n, _ptr(p)), "gmt_unet_set_params")
+
+    def forward(self, graph: NetGraph, scale: float):
+        """Predicted canonical field, float64 (n0, cout) on the device (gmt_unet_forward)."""
+        torch = _torch()
+        u = torch.empty((graph.n[0], self.out_channels), dtype=torch.float64, device="cuda")
+        _check(lib().gmt_unet_forward(self._n, graph._g, float(scale), _ptr(u)), "gmt_unet_forward")
+        return u
+
+    def gradient(self, graph: NetGraph, target, scale: float):
+        """(loss, gradient) against a canonical target field (gmt_unet_gradient)."""
+        torch = _torch()
+        t = target.detach().to(device="cuda", dtype=torch.float64).contiguous()
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        loss = _D()
+        _check(lib().gmt_unet_gradient(self._n, graph._g, _ptr(t), float(scale), _ptr(g),
+                                       ctypes.byref(loss)), "gmt_unet_gradient")
+        return float(loss.value), g
+
+    def train_step(self, graph: NetGraph, target, scale: float, lr=1e-3, beta1=0.9,
+                   beta2=0.999, eps=1e-8, weight_decay=1e-4) -> float:
+        """One AdamW step on one cell; returns the loss before the update."""
+        hp = AdamW(lr, beta1, beta2, eps, weight_decay)
+        loss = _D()
+        _check(lib().gmt_unet_train_step(self._n, graph._g, _ptr(target), float(scale),
+                                         ctypes.byref(hp), ctypes.byref(loss)),
+               "gmt_unet_train_step")
+        return float(loss.value)
+
+    def free(self):
+        if self._n:
+            lib().gmt_unet_free(self._n)
+            self._n = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def homogenize_dense_noalloc(voxels, res: int, physics=ELASTIC, E=1.0, nu=0.3, k=1.0,

@@ -26,7 +26,7 @@ from scipy import ndimage
 __all__ = [
     "gyroid_field", "schwarz_p_field", "diamond_field", "tpms_network", "tpms_plate",
     "truss", "spinodal", "largest_component", "laminate_z", "rods_x", "random_binary",
-    "batch_cell",
+    "batch_cell", "unet_init",
     "mixed_cell", "FAMILIES",
 ]
 
@@ -246,3 +246,16 @@ def batch_cell(seed: int, resolutions=BATCH_RESOLUTIONS):
     rng = np.random.default_rng(np.random.PCG64([seed, 1]))
     n = int(resolutions[int(rng.integers(0, len(resolutions)))])
     return mixed_cell(seed, n, families=FAMILIES)
+
+
+def unet_init(rows, seed: int) -> np.ndarray:
+    """Seeded initial parameters of the initializer network (float32, flat): for each layer
+    row (..., cin, cout) the weights W [27][cin][cout] drawn N(0, 2 / (27 cin)) (He
+    initialisation) by a PCG64(seed) stream, then the biases b [cout] = 0."""
+    rng = np.random.default_rng(np.random.PCG64([seed, 7]))
+    parts = []
+    for r in rows:
+        cin, cout = int(r[4]), int(r[5])
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (27 * cin)), size=27 * cin * cout))
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
