@@ -289,8 +289,15 @@ int64_t gmt_cached_bytes(void);
    (activation 0 is the input, activation i+1 the output of layer i). Input channels: the
    node's octant mask bits. Output: cout = D*M channels = the field in canonical
    [node][D][M] order divided by `scale`. Parameters: FP32, per layer W [27][cin][cout] then
-   b [cout], layers in order. Loss: mean over nodes and channels of (y - u/scale)^2.
+   b [cout], layers in order. Losses against a solved canonical field u:
+     GMT_UNET_LOSS_MSE     mean over nodes and channels of (y - u/scale)^2;
+     GMT_UNET_LOSS_ENERGY  (e^T K e) / (u^T K u), e = scale*y - u, summed over the load
+                           cases: the relative energy norm of the warm start's error, the
+                           norm conjugate gradients minimise (K: the level-0 operator of the
+                           material prepared on the graph's hierarchy, applied in FP32).
    Optimizer: AdamW with bias-corrected moments and decoupled weight decay. */
+#define GMT_UNET_LOSS_MSE 0
+#define GMT_UNET_LOSS_ENERGY 1
 typedef struct gmt_unet gmt_unet;
 typedef struct gmt_netgraph gmt_netgraph;
 typedef struct {
@@ -331,13 +338,17 @@ gmt_status gmt_netgraph_tables(const gmt_netgraph* g, int level, int32_t* same_o
 gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* g, double scale, double* u_out);
 /* Loss against the canonical field u_target (device double[n_0][cout]) and its gradient
    with respect to every parameter (grad_out: host or device float[P], nullable; loss_out:
-   host, nullable). The parameters do not change. */
-gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* g, const double* u_target,
-                             double scale, float* grad_out, double* loss_out);
+   host, nullable). The parameters do not change. h: the hierarchy the graph was built
+   from, with a material prepared whose values per node equal cout (GMT_ERR_STATE if none);
+   used by GMT_UNET_LOSS_ENERGY only (nullable for GMT_UNET_LOSS_MSE). */
+gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* g, gmt_hierarchy* h, int loss_kind,
+                             const double* u_target, double scale, float* grad_out,
+                             double* loss_out);
 /* One training step: forward, loss, backward, AdamW update of the parameters. loss_out
-   (host, nullable): the loss before the update. */
-gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* g, const double* u_target,
-                               double scale, const gmt_adamw* hp, double* loss_out);
+   (host, nullable): the loss before the update. h and loss_kind as for gmt_unet_gradient. */
+gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* g, gmt_hierarchy* h, int loss_kind,
+                               const double* u_target, double scale, const gmt_adamw* hp,
+                               double* loss_out);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,9 @@ The paper's method starts the V-cycles from a learned prediction of the fine-lev
     parent/child relation of the trilinear transfer of App. E.2);
   * y = relu(z + skip), twelve layers (the list in `layers`);
   * input: the 8 octant-mask bits of each fine node; output: the field divided by `scale`;
-  * loss: mean over nodes and channels of (y - u / scale)^2;
+  * losses: the mean over nodes and channels of (y - u / scale)^2, or the relative energy
+    norm (e^T K e) / (u^T K u) of the error e = scale y - u summed over the load cases,
+    with the assembled level-0 stiffness K (oracle/solve.py);
   * gradients by torch autograd; AdamW of Loshchilov and Hutter (decoupled weight decay,
     bias-corrected moments) written out in `adamw_step`.
 
@@ -143,12 +145,22 @@ def forward(g: Graph, params: torch.Tensor, rows):
     return acts[-1]
 
 
-def loss_and_grad(g: Graph, params: np.ndarray, rows, u: np.ndarray, scale: float):
-    """(loss, gradient) in float64 for the canonical target field u (n0, cout)."""
+def loss_and_grad(g: Graph, params: np.ndarray, rows, u: np.ndarray, scale: float, K=None):
+    """(loss, gradient) in float64 for the canonical target field u (n0, cout): the mean
+    squared error, or with K (scipy sparse, (n0 D) x (n0 D), node-major) the relative energy
+    norm of the error."""
     p = torch.tensor(np.asarray(params, dtype=np.float64), requires_grad=True)
     y = forward(g, p, rows)
-    t = torch.as_tensor(np.asarray(u, dtype=np.float64).reshape(y.shape)) / scale
-    loss = ((y - t) ** 2).mean()
+    ut = torch.as_tensor(np.asarray(u, dtype=np.float64).reshape(y.shape))
+    if K is None:
+        loss = ((y - ut / scale) ** 2).mean()
+    else:
+        Kc = K.tocoo()
+        Kt = torch.sparse_coo_tensor(np.vstack([Kc.row, Kc.col]), Kc.data, Kc.shape)
+        ncase = y.shape[1] * y.shape[0] // K.shape[0]        # M load cases
+        e = (scale * y - ut).reshape(K.shape[0], ncase)
+        uu = ut.reshape(K.shape[0], ncase)
+        loss = (e * torch.sparse.mm(Kt, e)).sum() / (uu * torch.sparse.mm(Kt, uu)).sum()
     loss.backward()
     return float(loss.detach()), p.grad.numpy().copy()
 

@@ -17,7 +17,10 @@
 // Input: the node's 8-bit octant mask as 8 channels of 0/1. Output: cout = D*M channels,
 // the field in canonical [node][D][M] order divided by `scale`.
 // Parameters: per layer W [27][cin][cout] then b [cout], layers in order, FP32.
-// Training: mean squared error against a solved field, AdamW (decoupled weight decay).
+// Training: against a solved field u, either the mean squared error of y - u/scale or the
+// relative energy norm of the error, (e^T K e) / (u^T K u) with e = scale*y - u summed over
+// the load cases (the norm the conjugate-gradient solve minimises, K the level-0 operator of
+// Sec. 4.6 applied matrix-free in FP32); AdamW (decoupled weight decay).
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -26,7 +29,8 @@
 #include "common.cuh"
 
 namespace gmt {
-void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);  // hierarchy.cu
+void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);       // hierarchy.cu
+void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);  // solver.cu
 }
 
 namespace {
@@ -288,6 +292,40 @@ __global__ void k_sum_blocks(const double* __restrict__ part, int nb, double* __
   }
 }
 
+// per-block partial sums of a . b (double)
+__global__ void __launch_bounds__(256) k_dot(const double* __restrict__ a,
+                                             const double* __restrict__ b, int64_t n,
+                                             double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_err_field(const float* __restrict__ y, const double* __restrict__ u, double scale,
+                            int64_t n, double* __restrict__ e) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) e[i] = scale * (double)y[i] - u[i];
+}
+
+// energy loss: loss = num / den, gradient g = 2 scale (K e) / den
+__global__ void k_energy_grad(const double* __restrict__ ke, const double* __restrict__ numden,
+                              double scale, int64_t n, float* __restrict__ g,
+                              double* __restrict__ loss) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double den = numden[1];
+  if (i < n) g[i] = (float)(2.0 * scale * ke[i] / den);
+  if (i == 0) *loss = numden[0] / den;
+}
+
 __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                         float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
                         float wd, float bc1, float bc2) {
@@ -346,6 +384,9 @@ struct gmt_netgraph {
   float* bpart = nullptr;
   double* lpart = nullptr;
   double* loss = nullptr;
+  double* e64 = nullptr;     // energy loss: error field and K times it, [n_0][cout]
+  double* ke64 = nullptr;
+  double* numden = nullptr;  // [e.Ke, u.Ku]
 };
 
 namespace {
@@ -378,6 +419,9 @@ void ensure_buffers(gmt_netgraph* G, const gmt_unet* net) {
   G->bpart = G->buf.alloc<float>(maxb);
   G->lpart = G->buf.alloc<double>(LOSS_BLOCKS);
   G->loss = G->buf.alloc<double>(1);
+  G->e64 = G->buf.alloc<double>(G->n[0] * net->cout);
+  G->ke64 = G->buf.alloc<double>(G->n[0] * net->cout);
+  G->numden = G->buf.alloc<double>(2);
   G->key[0] = net->w[0];
   G->key[1] = net->w[1];
   G->key[2] = net->w[2];
@@ -416,18 +460,40 @@ void forward(gmt_unet* net, gmt_netgraph* G) {
   }
 }
 
-// loss and gradient into net->g (forward must have run)
-void backward(gmt_unet* net, gmt_netgraph* G, const double* u, double scale) {
+void dot_into(cudaStream_t s, const double* a, const double* b, int64_t n, double* part,
+              double* out) {
+  k_dot<<<LOSS_BLOCKS, 256, 0, s>>>(a, b, n, part);
+  GMT_LAUNCH_CHECK();
+  k_sum_blocks<<<1, 32, 0, s>>>(part, LOSS_BLOCKS, out);
+  GMT_LAUNCH_CHECK();
+}
+
+// loss and gradient into net->g (forward must have run); h: the prepared hierarchy of the
+// graph for the energy loss
+void backward(gmt_unet* net, gmt_netgraph* G, gmt_hierarchy* h, int loss_kind, const double* u,
+              double scale) {
   cudaStream_t s = G->stream;
   const int64_t n_out = G->n[0] * net->cout;
   for (int a = 1; a < NACT; ++a)
     GMT_CUDA(cudaMemsetAsync(G->g[a], 0,
                              sizeof(float) * G->n[act_level(net->L, a)] * act_ch(net->L, a), s));
-  k_mse<<<LOSS_BLOCKS, 256, 0, s>>>(G->a[NACT - 1], u, 1.0 / scale, n_out, G->g[NACT - 1],
-                                    G->lpart);
-  GMT_LAUNCH_CHECK();
-  k_sum_blocks<<<1, 32, 0, s>>>(G->lpart, LOSS_BLOCKS, G->loss);
-  GMT_LAUNCH_CHECK();
+  if (loss_kind == GMT_UNET_LOSS_MSE) {
+    k_mse<<<LOSS_BLOCKS, 256, 0, s>>>(G->a[NACT - 1], u, 1.0 / scale, n_out, G->g[NACT - 1],
+                                      G->lpart);
+    GMT_LAUNCH_CHECK();
+    k_sum_blocks<<<1, 32, 0, s>>>(G->lpart, LOSS_BLOCKS, G->loss);
+    GMT_LAUNCH_CHECK();
+  } else {
+    gmt::step_apply(h, 0, GMT_PREC_FP32, u, G->ke64);
+    dot_into(s, u, G->ke64, n_out, G->lpart, G->numden + 1);
+    k_err_field<<<blocks(n_out), 256, 0, s>>>(G->a[NACT - 1], u, scale, n_out, G->e64);
+    GMT_LAUNCH_CHECK();
+    gmt::step_apply(h, 0, GMT_PREC_FP32, G->e64, G->ke64);
+    dot_into(s, G->e64, G->ke64, n_out, G->lpart, G->numden);
+    k_energy_grad<<<blocks(n_out), 256, 0, s>>>(G->ke64, G->numden, scale, n_out,
+                                                G->g[NACT - 1], G->loss);
+    GMT_LAUNCH_CHECK();
+  }
   for (int i = NLAYERS - 1; i >= 0; --i) {
     const LayerDef& d = net->L[i];
     const int64_t no = G->n[d.lvl_out];
@@ -467,6 +533,20 @@ void check_pair(const gmt_unet* net, const gmt_netgraph* G) {
   GMT_REQUIRE(net && G, GMT_ERR_ARG, "null network or graph");
   GMT_REQUIRE(net->device == G->device, GMT_ERR_ARG, "network and graph on different devices");
   GMT_CUDA(cudaSetDevice(G->device));
+}
+
+void check_loss(const gmt_unet* net, const gmt_netgraph* G, const gmt_hierarchy* h, int kind) {
+  GMT_REQUIRE(kind == GMT_UNET_LOSS_MSE || kind == GMT_UNET_LOSS_ENERGY, GMT_ERR_ARG,
+              "unknown loss %d", kind);
+  if (kind == GMT_UNET_LOSS_MSE) return;
+  GMT_REQUIRE(h, GMT_ERR_ARG, "the energy loss needs the graph's hierarchy");
+  GMT_REQUIRE(h->prepared, GMT_ERR_STATE, "the energy loss needs a prepared material");
+  GMT_REQUIRE(h->N == G->N && h->lv[0].n_nodes == G->n[0] && h->stream == G->stream,
+              GMT_ERR_ARG, "hierarchy does not match the graph (size or stream)");
+  GMT_REQUIRE(h->mat.C == net->cout, GMT_ERR_ARG,
+              "network outputs %d channels, the prepared material has %d values per node",
+              net->cout, h->mat.C);
+  GMT_REQUIRE(!h->lv[0].dense, GMT_ERR_ARG, "level 0 is dense");
 }
 
 }  // namespace
@@ -673,13 +753,15 @@ gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* G, double scale, double
   UNET_END
 }
 
-gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* G, const double* u_target, double scale,
-                             float* grad_out, double* loss_out) {
+gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* G, gmt_hierarchy* h, int loss_kind,
+                             const double* u_target, double scale, float* grad_out,
+                             double* loss_out) {
   UNET_BEGIN
   check_pair(net, G);
+  check_loss(net, G, h, loss_kind);
   GMT_REQUIRE(u_target && scale > 0 && std::isfinite(scale), GMT_ERR_ARG, "bad target or scale");
   forward(net, G);
-  backward(net, G, u_target, scale);
+  backward(net, G, h, loss_kind, u_target, scale);
   if (grad_out)
     GMT_CUDA(cudaMemcpyAsync(grad_out, net->g, sizeof(float) * net->P, cudaMemcpyDefault,
                              G->stream));
@@ -690,17 +772,19 @@ gmt_status gmt_unet_gradient(gmt_unet* net, gmt_netgraph* G, const double* u_tar
   UNET_END
 }
 
-gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* G, const double* u_target,
-                               double scale, const gmt_adamw* hp, double* loss_out) {
+gmt_status gmt_unet_train_step(gmt_unet* net, gmt_netgraph* G, gmt_hierarchy* h, int loss_kind,
+                               const double* u_target, double scale, const gmt_adamw* hp,
+                               double* loss_out) {
   UNET_BEGIN
   check_pair(net, G);
+  check_loss(net, G, h, loss_kind);
   GMT_REQUIRE(u_target && hp && scale > 0 && std::isfinite(scale), GMT_ERR_ARG,
               "bad target, scale or hyper-parameters");
   GMT_REQUIRE(hp->lr > 0 && hp->beta1 >= 0 && hp->beta1 < 1 && hp->beta2 >= 0 && hp->beta2 < 1 &&
                   hp->eps > 0 && hp->weight_decay >= 0,
               GMT_ERR_ARG, "bad AdamW hyper-parameters");
   forward(net, G);
-  backward(net, G, u_target, scale);
+  backward(net, G, h, loss_kind, u_target, scale);
   net->steps += 1;
   const float bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)net->steps));
   const float bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)net->steps));

@@ -132,8 +132,9 @@ _SIGS = {
     "gmt_netgraph_nodes": (_L, [_P, _I]),
     "gmt_netgraph_tables": (_I, [_P, _I, _P, _P, _P]),
     "gmt_unet_forward": (_I, [_P, _P, _D, _P]),
-    "gmt_unet_gradient": (_I, [_P, _P, _P, _D, _P, ctypes.POINTER(_D)]),
-    "gmt_unet_train_step": (_I, [_P, _P, _P, _D, ctypes.POINTER(AdamW), ctypes.POINTER(_D)]),
+    "gmt_unet_gradient": (_I, [_P, _P, _P, _I, _P, _D, _P, ctypes.POINTER(_D)]),
+    "gmt_unet_train_step": (_I, [_P, _P, _P, _I, _P, _D, ctypes.POINTER(AdamW),
+                                 ctypes.POINTER(_D)]),
 }
 
 TRACE_CATEGORIES = 14
@@ -403,6 +404,7 @@ class Hierarchy:
 
 
 UNET_WIDTHS = (32, 64, 128)
+LOSS_MSE, LOSS_ENERGY = 0, 1
 
 
 def unet_layers(out_channels: int, widths=UNET_WIDTHS):
@@ -488,25 +490,30 @@ class UNet:
         _check(lib().gmt_unet_forward(self._n, graph._g, float(scale), _ptr(u)), "gmt_unet_forward")
         return u
 
-    def gradient(self, graph: NetGraph, target, scale: float):
-        """(loss, gradient) against a canonical target field (gmt_unet_gradient)."""
+    def gradient(self, graph: NetGraph, target, scale: float, loss=LOSS_MSE,
+                 hier: "Hierarchy | None" = None):
+        """(loss, gradient) against a canonical target field (gmt_unet_gradient); the energy
+        loss needs the graph's hierarchy with the material prepared."""
         torch = _torch()
         t = target.detach().to(device="cuda", dtype=torch.float64).contiguous()
         g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
-        loss = _D()
-        _check(lib().gmt_unet_gradient(self._n, graph._g, _ptr(t), float(scale), _ptr(g),
-                                       ctypes.byref(loss)), "gmt_unet_gradient")
-        return float(loss.value), g
+        out = _D()
+        _check(lib().gmt_unet_gradient(self._n, graph._g, hier._h if hier else None, int(loss),
+                                       _ptr(t), float(scale), _ptr(g), ctypes.byref(out)),
+               "gmt_unet_gradient")
+        return float(out.value), g
 
     def train_step(self, graph: NetGraph, target, scale: float, lr=1e-3, beta1=0.9,
-                   beta2=0.999, eps=1e-8, weight_decay=1e-4) -> float:
-        """One AdamW step on one cell; returns the loss before the update."""
+                   beta2=0.999, eps=1e-8, weight_decay=1e-4, loss=LOSS_MSE,
+                   hier: "Hierarchy | None" = None) -> float:
+        """One AdamW step on one cell; returns the loss before the update. `target`: device
+        float64 canonical field."""
         hp = AdamW(lr, beta1, beta2, eps, weight_decay)
-        loss = _D()
-        _check(lib().gmt_unet_train_step(self._n, graph._g, _ptr(target), float(scale),
-                                         ctypes.byref(hp), ctypes.byref(loss)),
-               "gmt_unet_train_step")
-        return float(loss.value)
+        out = _D()
+        _check(lib().gmt_unet_train_step(self._n, graph._g, hier._h if hier else None, int(loss),
+                                         _ptr(target), float(scale), ctypes.byref(hp),
+                                         ctypes.byref(out)), "gmt_unet_train_step")
+        return float(out.value)
 
     def free(self):
         if self._n:

@@ -88,3 +88,69 @@ def test_adamw_step_parity(cell):
                                    hp["weight_decay"])
         got = net.params().cpu().numpy().astype(np.float64)
         assert np.abs(got - q).max() <= 1e-6 * max(1.0, np.abs(q).max()), step
+
+
+def test_energy_loss_and_gradient_parity(cell):
+    from oracle import fe
+    from oracle import solve as osolve
+    _, h, G, O = cell
+    rows = ounet.layers(18)
+    p = lattices.unet_init(rows, seed=21)
+    net = gmt.UNet(18, torch.tensor(p))
+    with pytest.raises(gmt.GmtError):            # the energy loss needs a prepared material
+        gmt.Hierarchy(lattices.tpms_network("gyroid", 32, 0.25)) and net.gradient(
+            G, torch.zeros(O.n[0], 18), 1.0, loss=gmt.LOSS_ENERGY, hier=None)
+    h.prepare(gmt.ELASTIC, E=1.0, nu=0.3)
+    Ke, _, D, _, _ = fe.physics("elastic", 1.0, 0.3)
+    K = osolve.assemble(O.levels[0], Ke, D)
+    u = np.random.default_rng(8).normal(size=(O.n[0], 18))
+    scale = 0.7
+    loss_g, grad_g = net.gradient(G, torch.tensor(u), scale, loss=gmt.LOSS_ENERGY, hier=h)
+    loss_r, grad_r = ounet.loss_and_grad(O, p, rows, u, scale, K=K)
+    # K applied in FP32 on the device: relative 1e-5 on the loss
+    assert abs(loss_g - loss_r) <= 1e-5 * loss_r, (loss_g, loss_r)
+    grad_g = grad_g.cpu().numpy().astype(np.float64)
+    for i, (a, b) in enumerate(_segments(rows)):
+        ref = np.abs(grad_r[a:b]).max()
+        err = np.abs(grad_g[a:b] - grad_r[a:b]).max()
+        assert err <= 1e-3 * ref, (i, err, ref)
+
+
+def test_training_lowers_energy_error_and_warm_start_keeps_accuracy():
+    """Train on 16 seeded 32^3 cells (energy loss, AdamW), then on held-out cells: the
+    prediction's energy-norm error is below the zero start's (which is 1 by definition), the
+    solve from it reaches the tolerance, and C^H equals the zero-start result; the V-cycle
+    counts of both starts are printed (the plain cycles are the fallback and the judge)."""
+    fams = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "bcc", "octet")
+    rows = ounet.layers(18)
+    net = gmt.UNet(18, torch.tensor(lattices.unet_init(rows, seed=0)))
+    scale = 0.04 * 32
+    data = []
+    for i in range(16):
+        h = gmt.Hierarchy(lattices.mixed_cell(500 + i, 32, families=fams)[0])
+        _, u, _ = h.solve(gmt.ELASTIC, tol=1e-6)
+        data.append((h, gmt.NetGraph(h), u.reshape(h.num_nodes(0), 18).contiguous()))
+    epochs = 12
+    losses = []
+    for ep in range(epochs):
+        for i in np.random.default_rng(ep).permutation(len(data)):
+            h, g, u = data[i]
+            lr = 1e-3 * 0.5 * (1 + np.cos(np.pi * len(losses) / (epochs * len(data))))
+            losses.append(net.train_step(g, u, scale, lr=lr, loss=gmt.LOSS_ENERGY, hier=h))
+    first, last = np.mean(losses[:16]), np.mean(losses[-16:])
+    assert last < 0.5 * first, (first, last)
+    for i in range(3):
+        h = gmt.Hierarchy(lattices.mixed_cell(900 + i, 32, families=fams)[0])
+        st0, u_ref, i0 = h.solve(gmt.ELASTIC, tol=1e-6)
+        CH0 = h.homogenize(gmt.ELASTIC)
+        g = gmt.NetGraph(h)
+        pred = net.forward(g, scale)
+        err, _ = net.gradient(g, u_ref.reshape(-1, 18), scale, loss=gmt.LOSS_ENERGY, hier=h)
+        assert err < 0.9, err
+        st1, _, i1 = h.solve(gmt.ELASTIC, tol=1e-5, u0=pred)
+        assert st1 == gmt.OK and max(i1.rel_residual[:6]) <= 1e-5
+        CH1 = h.homogenize(gmt.ELASTIC)
+        assert np.abs(CH1 - CH0).max() <= 1e-4 * np.abs(CH0).max()
+        _, _, iz = h.solve(gmt.ELASTIC, tol=1e-5)
+        print(f"held-out cell {i}: energy error of the prediction {err:.3f}, "
+              f"V-cycles from zero {iz.inner_total}, from the prediction {i1.inner_total}")

@@ -133,3 +133,28 @@ def test_library_layer_table_matches_oracle():
         assert [tuple(r) for r in gmt.unet_layers(cout)] == unet.layers(cout)
         assert gmt.unet_param_count(cout) == unet.param_count(unet.layers(cout))
     assert 1.5e6 < gmt.unet_param_count(18) < 2.5e6
+
+
+def test_energy_loss_gradient_matches_central_differences(graph):
+    from oracle import fe
+    from oracle import solve as osolve
+    Ke, _, D, _, _ = fe.physics("heat", 1.0, 0.3, 1.0)
+    K = osolve.assemble(graph.levels[0], Ke, D)
+    rows = unet.layers(3, widths=(2, 3, 4))
+    p = lattices.unet_init(rows, seed=6).astype(np.float64)
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(graph.n[0], 3))
+    loss, grad = unet.loss_and_grad(graph, p, rows, u, 1.5, K=K)
+    # a zero network output leaves e = -u: the loss is exactly 1
+    z = np.zeros_like(p)
+    assert abs(unet.loss_and_grad(graph, z, rows, u, 1.5, K=K)[0] - 1.0) < 1e-12
+    offs = np.cumsum([0] + [27 * r[4] * r[5] + r[5] for r in rows])
+    picks = [int(offs[i] + rng.integers(0, offs[i + 1] - offs[i])) for i in range(len(rows))]
+    h = 1e-6
+    for k in picks:
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (unet.loss_and_grad(graph, pp, rows, u, 1.5, K=K)[0] -
+              unet.loss_and_grad(graph, pm, rows, u, 1.5, K=K)[0]) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * max(1e-3, abs(grad).max()), (k, fd, grad[k])
