@@ -124,63 +124,80 @@ __global__ void k_features(const int* __restrict__ canon_slot, const uint8_t* __
 // out[n][co] (=, or += with accum) act(b[co] + add[n][co] + sum_t sum_ci w(t,ci,co) x[s][ci]),
 // s = tab[n][flip ? 26 - t : t] (skipped when < 0); w(t,ci,co) = W[t][ci][co], or
 // W[t][co][ci] with wtrans (the backward-data form of a layer whose forward weights are
-// [27][cout'][cin']). Block: 64 nodes x 32 output channels, 8 nodes per thread.
+// [27][cout'][cin']). Block: GC_NODES nodes x 32 output channels, 256 threads as 8 channel
+// quads x 32 node groups, each thread a 4 x 4 register tile: per staged input channel 4
+// shared loads (rows of the gathered inputs) and one 16-byte load (4 weights) feed 16 FMAs.
+constexpr int GC_NODES = 128;
+
 __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int cin,
                                                const int* __restrict__ tab, int flip,
                                                const float* __restrict__ W, int wtrans,
                                                const float* __restrict__ bias,
                                                const float* __restrict__ add, int relu, int accum,
                                                float* __restrict__ out, int cout, int64_t n_out) {
-  __shared__ float sX[64][33];
-  __shared__ float sW[32][33];
-  __shared__ int sIdx[64];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int64_t n0 = (int64_t)blockIdx.x * 64;
-  const int co = blockIdx.y * 32 + tx;
-  float acc[8];
+  __shared__ float sX[GC_NODES][33];
+  __shared__ __align__(16) float sW[32][32];
+  __shared__ int sIdx[GC_NODES];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 8 + tx;   // blockDim (8, 32)
+  const int64_t n0 = (int64_t)blockIdx.x * GC_NODES;
+  const int co0 = blockIdx.y * 32;
+  float acc[4][4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
   for (int t = 0; t < 27; ++t) {
     const int tt = flip ? 26 - t : t;
     __syncthreads();
-    if (tid < 64) {
+    if (tid < GC_NODES) {
       const int64_t node = n0 + tid;
       sIdx[tid] = node < n_out ? tab[node * 27 + tt] : -1;
     }
-    const int any = __syncthreads_or(tid < 64 && sIdx[tid] >= 0);
+    const int any = __syncthreads_or(tid < GC_NODES && sIdx[tid] >= 0);
     if (!any) continue;
     for (int ci0 = 0; ci0 < cin; ci0 += 32) {
-      const int ci = ci0 + tx;
-      for (int r = ty; r < 64; r += 8) {
+      for (int e = tid; e < GC_NODES * 32; e += 256) {
+        const int r = e >> 5, c = e & 31;
         const int s = sIdx[r];
-        sX[r][tx] = (s >= 0 && ci < cin) ? x[(int64_t)s * cin + ci] : 0.f;
+        sX[r][c] = (s >= 0 && ci0 + c < cin) ? x[(int64_t)s * cin + ci0 + c] : 0.f;
       }
-      for (int r = ty; r < 32; r += 8) {
-        const int c = ci0 + r;
+      for (int e = tid; e < 32 * 32; e += 256) {
+        const int r = e >> 5, c = e & 31;       // r: input channel, c: output channel
+        const int ci = ci0 + r, co = co0 + c;
         float w = 0.f;
-        if (c < cin && co < cout)
-          w = wtrans ? W[((int64_t)t * cout + co) * cin + c] : W[((int64_t)t * cin + c) * cout + co];
-        sW[r][tx] = w;
+        if (ci < cin && co < cout)
+          w = wtrans ? W[((int64_t)t * cout + co) * cin + ci] : W[((int64_t)t * cin + ci) * cout + co];
+        sW[r][c] = w;
       }
       __syncthreads();
       const int lim = min(32, cin - ci0);
       for (int k = 0; k < lim; ++k) {
-        const float w = sW[k][tx];
+        const float4 w = *reinterpret_cast<const float4*>(&sW[k][tx * 4]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = fmaf(sX[ty * 8 + j][k], w, acc[j]);
+        for (int j = 0; j < 4; ++j) {
+          const float xv = sX[ty * 4 + j][k];
+          acc[j][0] = fmaf(xv, w.x, acc[j][0]);
+          acc[j][1] = fmaf(xv, w.y, acc[j][1]);
+          acc[j][2] = fmaf(xv, w.z, acc[j][2]);
+          acc[j][3] = fmaf(xv, w.w, acc[j][3]);
+        }
       }
       __syncthreads();
     }
   }
-  if (co >= cout) return;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int64_t node = n0 + ty * 8 + j;
+  for (int j = 0; j < 4; ++j) {
+    const int64_t node = n0 + ty * 4 + j;
     if (node >= n_out) break;
-    const int64_t o = node * cout + co;
-    float v = acc[j] + (bias ? bias[co] : 0.f) + (add ? add[o] : 0.f);
-    if (relu) v = fmaxf(v, 0.f);
-    out[o] = accum ? out[o] + v : v;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int co = co0 + tx * 4 + c;
+      if (co >= cout) break;
+      const int64_t o = node * cout + co;
+      float v = acc[j][c] + (bias ? bias[co] : 0.f) + (add ? add[o] : 0.f);
+      if (relu) v = fmaxf(v, 0.f);
+      out[o] = accum ? out[o] + v : v;
+    }
   }
 }
 
@@ -444,8 +461,8 @@ void launch_gconv(cudaStream_t s, const float* x, int cin, const int* tab, int f
                   const float* W, int wtrans, const float* b, const float* add, int relu,
                   int accum, float* out, int cout, int64_t n_out) {
   if (n_out <= 0) return;
-  dim3 grid((unsigned)((n_out + 63) / 64), (unsigned)((cout + 31) / 32));
-  k_gconv<<<grid, dim3(32, 8), 0, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum, out,
+  dim3 grid((unsigned)((n_out + GC_NODES - 1) / GC_NODES), (unsigned)((cout + 31) / 32));
+  k_gconv<<<grid, dim3(8, 32), 0, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum, out,
                                        cout, n_out);
   GMT_LAUNCH_CHECK();
 }
