@@ -120,11 +120,45 @@ __global__ void k_features(const int* __restrict__ canon_slot, const uint8_t* __
   for (int o = 0; o < 8; ++o) x0[i * 8 + o] = (float)((m >> o) & 1u);
 }
 
+// Rows of an up table grouped by the parity class (x&1) + 2(y&1) + 4(z&1) of the fine node:
+// a fine node of class c has a coarse parent under tap t only when every axis with d = 0 is
+// even and every axis with d = +-1 is odd, so a block of one class visits 1 to 8 taps.
+// Row order within a class is arbitrary (atomic slots): every output row is computed on its
+// own, with the same sum order whatever its position.
+__global__ void k_class_count(const int32_t* __restrict__ xyz, int64_t n, int* __restrict__ cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  atomicAdd(&cnt[(xyz[3 * i] & 1) + 2 * (xyz[3 * i + 1] & 1) + 4 * (xyz[3 * i + 2] & 1)], 1);
+}
+
+__global__ void k_class_offsets(int* __restrict__ cnt) {   // cnt[0..8) -> cursors cnt[8..16)
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int off = 0;
+    for (int c = 0; c < 8; ++c) {
+      cnt[8 + c] = off;
+      off += cnt[c];
+    }
+  }
+}
+
+__global__ void k_class_fill(const int32_t* __restrict__ xyz, const int* __restrict__ tab, int64_t n,
+                             int* __restrict__ cursor, int* __restrict__ perm,
+                             int* __restrict__ tab_perm) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = (xyz[3 * i] & 1) + 2 * (xyz[3 * i + 1] & 1) + 4 * (xyz[3 * i + 2] & 1);
+  const int pos = atomicAdd(&cursor[c], 1);
+  perm[pos] = (int)i;
+  for (int t = 0; t < 27; ++t) tab_perm[(int64_t)pos * 27 + t] = tab[i * 27 + t];
+}
+
 // ------------------------------------------------------------------ gather convolution
 // out[n][co] (=, or += with accum) act(b[co] + add[n][co] + sum_t sum_ci w(t,ci,co) x[s][ci]),
 // s = tab[n][flip ? 26 - t : t] (skipped when < 0); w(t,ci,co) = W[t][ci][co], or
 // W[t][co][ci] with wtrans (the backward-data form of a layer whose forward weights are
-// [27][cout'][cin']). Block: GC_NODES nodes x 32 output channels, 256 threads as 8 channel
+// [27][cout'][cin']). With omap, row r of the table computes output node omap[r] (the up
+// layers' rows grouped by parity class, so that a block meets few taps).
+// Block: GC_NODES nodes x 32 output channels, 256 threads as 8 channel
 // quads x 32 node groups, each thread a 4 x 4 register tile: per staged input channel 4
 // shared loads (rows of the gathered inputs) and one 16-byte load (4 weights) feed 16 FMAs.
 constexpr int GC_NODES = 128;
@@ -134,7 +168,8 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
                                                const float* __restrict__ W, int wtrans,
                                                const float* __restrict__ bias,
                                                const float* __restrict__ add, int relu, int accum,
-                                               float* __restrict__ out, int cout, int64_t n_out) {
+                                               float* __restrict__ out, int cout, int64_t n_out,
+                                               const int* __restrict__ omap) {
   __shared__ float sX[GC_NODES][33];
   __shared__ __align__(16) float sW[32][32];
   __shared__ int sIdx[GC_NODES];
@@ -187,8 +222,9 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int64_t node = n0 + ty * 4 + j;
-    if (node >= n_out) break;
+    const int64_t row = n0 + ty * 4 + j;
+    if (row >= n_out) break;
+    const int64_t node = omap ? (int64_t)omap[row] : row;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int co = co0 + tx * 4 + c;
@@ -389,6 +425,8 @@ struct gmt_netgraph {
   int* same[3] = {nullptr, nullptr, nullptr};
   int* down[2] = {nullptr, nullptr};
   int* up[2] = {nullptr, nullptr};
+  int* up_perm[2] = {nullptr, nullptr};   // up tables with rows grouped by parity class
+  int* up_rows[2] = {nullptr, nullptr};   // row -> fine node of up_perm
   float* x0 = nullptr;
   gmt::Arena geo;
   // buffers for one network shape
@@ -459,11 +497,11 @@ const int* bwd_table(const gmt_netgraph* G, const LayerDef& d) {
 
 void launch_gconv(cudaStream_t s, const float* x, int cin, const int* tab, int flip,
                   const float* W, int wtrans, const float* b, const float* add, int relu,
-                  int accum, float* out, int cout, int64_t n_out) {
+                  int accum, float* out, int cout, int64_t n_out, const int* omap = nullptr) {
   if (n_out <= 0) return;
   dim3 grid((unsigned)((n_out + GC_NODES - 1) / GC_NODES), (unsigned)((cout + 31) / 32));
   k_gconv<<<grid, dim3(8, 32), 0, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum, out,
-                                       cout, n_out);
+                                       cout, n_out, omap);
   GMT_LAUNCH_CHECK();
 }
 
@@ -471,9 +509,11 @@ void forward(gmt_unet* net, gmt_netgraph* G) {
   ensure_buffers(G, net);
   for (int i = 0; i < NLAYERS; ++i) {
     const LayerDef& d = net->L[i];
-    launch_gconv(G->stream, G->a[d.in], d.cin, fwd_table(G, d), 0, net->p + net->woff[i], 0,
-                 net->p + net->boff[i], d.skip >= 0 ? G->a[d.skip] : nullptr, d.relu, 0,
-                 G->a[i + 1], d.cout, G->n[d.lvl_out]);
+    const bool up = d.kind == UP;
+    launch_gconv(G->stream, G->a[d.in], d.cin, up ? G->up_perm[d.lvl_out] : fwd_table(G, d), 0,
+                 net->p + net->woff[i], 0, net->p + net->boff[i],
+                 d.skip >= 0 ? G->a[d.skip] : nullptr, d.relu, 0, G->a[i + 1], d.cout,
+                 G->n[d.lvl_out], up ? G->up_rows[d.lvl_out] : nullptr);
   }
 }
 
@@ -719,6 +759,17 @@ gmt_status gmt_netgraph_build(gmt_hierarchy* h, gmt_netgraph** out) {
     GMT_LAUNCH_CHECK();
     G->up[l] = G->geo.alloc<int>(27 * std::max<int64_t>(G->n[l], 1));
     k_up_table<<<blocks(G->n[l]), 256, 0, s>>>(xyz[l], G->n[l], h->lv[l].n, h->lv[l + 1], G->up[l]);
+    GMT_LAUNCH_CHECK();
+    G->up_perm[l] = G->geo.alloc<int>(27 * std::max<int64_t>(G->n[l], 1));
+    G->up_rows[l] = G->geo.alloc<int>(std::max<int64_t>(G->n[l], 1));
+    int* cnt = G->geo.alloc<int>(16);
+    GMT_CUDA(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), s));
+    k_class_count<<<blocks(G->n[l]), 256, 0, s>>>(xyz[l], G->n[l], cnt);
+    GMT_LAUNCH_CHECK();
+    k_class_offsets<<<1, 32, 0, s>>>(cnt);
+    GMT_LAUNCH_CHECK();
+    k_class_fill<<<blocks(G->n[l]), 256, 0, s>>>(xyz[l], G->up[l], G->n[l], cnt + 8, G->up_rows[l],
+                                                 G->up_perm[l]);
     GMT_LAUNCH_CHECK();
   }
   G->x0 = G->geo.alloc<float>(8 * std::max<int64_t>(G->n[0], 1));
