@@ -162,7 +162,29 @@ __global__ void k_class_fill(const int32_t* __restrict__ xyz, const int* __restr
 // quads x 32 node groups, each thread a 4 x 4 register tile: per staged input channel 4
 // shared loads (rows of the gathered inputs) and one 16-byte load (4 weights) feed 16 FMAs.
 constexpr int GC_NODES = 128;
+// dynamic shared memory: weights [2][32][32], gathered rows [2][GC_NODES][33], the block's
+// tap table [GC_NODES][27], tap flags [27] and the active-tap list [28]
+constexpr int GC_SW = 2 * 32 * 32 * 4;
+constexpr int GC_SX = 2 * GC_NODES * 33 * 4;
+constexpr int GC_ST = GC_NODES * 27 * 4;
+constexpr int GC_SMEM = GC_SW + GC_SX + GC_ST + 27 * 4 + 28 * 4;
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Two-stage pipeline over (active tap, 32-channel input chunk): while one stage's gathered
+// rows and weights are multiplied out of shared memory, the next stage's are copied in with
+// cp.async (zero-filled where a neighbour is missing or a channel is out of range).
 __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int cin,
                                                const int* __restrict__ tab, int flip,
                                                const float* __restrict__ W, int wtrans,
@@ -170,55 +192,84 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
                                                const float* __restrict__ add, int relu, int accum,
                                                float* __restrict__ out, int cout, int64_t n_out,
                                                const int* __restrict__ omap) {
-  __shared__ float sX[GC_NODES][33];
-  __shared__ __align__(16) float sW[32][32];
-  __shared__ int sIdx[GC_NODES];
+  extern __shared__ __align__(16) unsigned char gc_smem[];
+  float (*sW)[32][32] = reinterpret_cast<float (*)[32][32]>(gc_smem);
+  float (*sX)[GC_NODES][33] = reinterpret_cast<float (*)[GC_NODES][33]>(gc_smem + GC_SW);
+  int* sTab = reinterpret_cast<int*>(gc_smem + GC_SW + GC_SX);
+  int* sAny = sTab + GC_NODES * 27;
+  int* sTaps = sAny + 27;   // [0]: count, then the active weight taps in order
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 8 + tx;   // blockDim (8, 32)
   const int64_t n0 = (int64_t)blockIdx.x * GC_NODES;
   const int co0 = blockIdx.y * 32;
+  const int64_t rows = min((int64_t)GC_NODES, n_out - n0);
+  if (tid < 27) sAny[tid] = 0;
+  for (int e = tid; e < GC_NODES * 27; e += 256)
+    sTab[e] = (e / 27 < rows) ? tab[n0 * 27 + e] : -1;
+  __syncthreads();
+  for (int e = tid; e < GC_NODES * 27; e += 256)
+    if (sTab[e] >= 0) sAny[e % 27] = 1;
+  __syncthreads();
+  if (tid == 0) {
+    int k = 0;
+    for (int t = 0; t < 27; ++t)
+      if (sAny[flip ? 26 - t : t]) sTaps[1 + k++] = t;
+    sTaps[0] = k;
+  }
+  __syncthreads();
+  const int nch = (cin + 31) / 32;
+  const int S = sTaps[0] * nch;
+
+  auto issue = [&](int k, int buf) {
+    const int t = sTaps[1 + k / nch];
+    const int tt = flip ? 26 - t : t;
+    const int ci0 = (k % nch) * 32;
+    for (int e = tid; e < GC_NODES * 32; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      const int src = sTab[r * 27 + tt];
+      const bool ok = src >= 0 && ci0 + c < cin;
+      cp_async4(&sX[buf][r][c], ok ? (const void*)(x + (int64_t)src * cin + ci0 + c) : (const void*)x,
+                ok);
+    }
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int r = e >> 5, c = e & 31;   // r: input channel, c: output channel
+      const int ci = ci0 + r, co = co0 + c;
+      const bool ok = ci < cin && co < cout;
+      const float* src = ok ? (wtrans ? W + ((int64_t)t * cout + co) * cin + ci
+                                      : W + ((int64_t)t * cin + ci) * cout + co)
+                            : W;
+      cp_async4(&sW[buf][r][c], src, ok);
+    }
+    cp_async_commit();
+  };
+
   float acc[4][4];
 #pragma unroll
   for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-  for (int t = 0; t < 27; ++t) {
-    const int tt = flip ? 26 - t : t;
+  if (S > 0) issue(0, 0);
+  for (int k = 0; k < S; ++k) {
+    const int buf = k & 1;
+    if (k + 1 < S) {
+      issue(k + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncthreads();
-    if (tid < GC_NODES) {
-      const int64_t node = n0 + tid;
-      sIdx[tid] = node < n_out ? tab[node * 27 + tt] : -1;
-    }
-    const int any = __syncthreads_or(tid < GC_NODES && sIdx[tid] >= 0);
-    if (!any) continue;
-    for (int ci0 = 0; ci0 < cin; ci0 += 32) {
-      for (int e = tid; e < GC_NODES * 32; e += 256) {
-        const int r = e >> 5, c = e & 31;
-        const int s = sIdx[r];
-        sX[r][c] = (s >= 0 && ci0 + c < cin) ? x[(int64_t)s * cin + ci0 + c] : 0.f;
-      }
-      for (int e = tid; e < 32 * 32; e += 256) {
-        const int r = e >> 5, c = e & 31;       // r: input channel, c: output channel
-        const int ci = ci0 + r, co = co0 + c;
-        float w = 0.f;
-        if (ci < cin && co < cout)
-          w = wtrans ? W[((int64_t)t * cout + co) * cin + ci] : W[((int64_t)t * cin + ci) * cout + co];
-        sW[r][c] = w;
-      }
-      __syncthreads();
-      const int lim = min(32, cin - ci0);
-      for (int k = 0; k < lim; ++k) {
-        const float4 w = *reinterpret_cast<const float4*>(&sW[k][tx * 4]);
+    const int lim = min(32, cin - (k % nch) * 32);
+    for (int kk = 0; kk < lim; ++kk) {
+      const float4 w = *reinterpret_cast<const float4*>(&sW[buf][kk][tx * 4]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float xv = sX[ty * 4 + j][k];
-          acc[j][0] = fmaf(xv, w.x, acc[j][0]);
-          acc[j][1] = fmaf(xv, w.y, acc[j][1]);
-          acc[j][2] = fmaf(xv, w.z, acc[j][2]);
-          acc[j][3] = fmaf(xv, w.w, acc[j][3]);
-        }
+      for (int j = 0; j < 4; ++j) {
+        const float xv = sX[buf][ty * 4 + j][kk];
+        acc[j][0] = fmaf(xv, w.x, acc[j][0]);
+        acc[j][1] = fmaf(xv, w.y, acc[j][1]);
+        acc[j][2] = fmaf(xv, w.z, acc[j][2]);
+        acc[j][3] = fmaf(xv, w.w, acc[j][3]);
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -500,8 +551,9 @@ void launch_gconv(cudaStream_t s, const float* x, int cin, const int* tab, int f
                   int accum, float* out, int cout, int64_t n_out, const int* omap = nullptr) {
   if (n_out <= 0) return;
   dim3 grid((unsigned)((n_out + GC_NODES - 1) / GC_NODES), (unsigned)((cout + 31) / 32));
-  k_gconv<<<grid, dim3(8, 32), 0, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum, out,
-                                       cout, n_out, omap);
+  gmt::ensure_smem_attr((const void*)k_gconv, GC_SMEM);
+  k_gconv<<<grid, dim3(8, 32), GC_SMEM, s>>>(x, cin, tab, flip, W, wtrans, b, add, relu, accum,
+                                             out, cout, n_out, omap);
   GMT_LAUNCH_CHECK();
 }
 
