@@ -162,10 +162,13 @@ __global__ void k_class_fill(const int32_t* __restrict__ xyz, const int* __restr
 // quads x 32 node groups, each thread a 4 x 4 register tile: per staged input channel 4
 // shared loads (rows of the gathered inputs) and one 16-byte load (4 weights) feed 16 FMAs.
 constexpr int GC_NODES = 128;
-// dynamic shared memory: weights [2][32][32], gathered rows [2][GC_NODES][33], the block's
-// tap table [GC_NODES][27], tap flags [27] and the active-tap list [28]
+// dynamic shared memory: weights [2][32][32], gathered rows [2][GC_NODES][GC_LD], the
+// block's tap table [GC_NODES][27], tap flags [27] and the active-tap list [28]. Row stride
+// 36 floats keeps 16-byte copies aligned; thread row r = j * 32 + ty makes the 4 rows a warp
+// reads at once fall in distinct banks.
+constexpr int GC_LD = 36;
 constexpr int GC_SW = 2 * 32 * 32 * 4;
-constexpr int GC_SX = 2 * GC_NODES * 33 * 4;
+constexpr int GC_SX = 2 * GC_NODES * GC_LD * 4;
 constexpr int GC_ST = GC_NODES * 27 * 4;
 constexpr int GC_SMEM = GC_SW + GC_SX + GC_ST + 27 * 4 + 28 * 4;
 
@@ -173,6 +176,12 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
                "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
                                                const int* __restrict__ omap) {
   extern __shared__ __align__(16) unsigned char gc_smem[];
   float (*sW)[32][32] = reinterpret_cast<float (*)[32][32]>(gc_smem);
-  float (*sX)[GC_NODES][33] = reinterpret_cast<float (*)[GC_NODES][33]>(gc_smem + GC_SW);
+  float (*sX)[GC_NODES][GC_LD] = reinterpret_cast<float (*)[GC_NODES][GC_LD]>(gc_smem + GC_SW);
   int* sTab = reinterpret_cast<int*>(gc_smem + GC_SW + GC_SX);
   int* sAny = sTab + GC_NODES * 27;
   int* sTaps = sAny + 27;   // [0]: count, then the active weight taps in order
@@ -223,12 +232,22 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
     const int t = sTaps[1 + k / nch];
     const int tt = flip ? 26 - t : t;
     const int ci0 = (k % nch) * 32;
-    for (int e = tid; e < GC_NODES * 32; e += 256) {
-      const int r = e >> 5, c = e & 31;
-      const int src = sTab[r * 27 + tt];
-      const bool ok = src >= 0 && ci0 + c < cin;
-      cp_async4(&sX[buf][r][c], ok ? (const void*)(x + (int64_t)src * cin + ci0 + c) : (const void*)x,
-                ok);
+    if ((cin & 3) == 0) {   // rows of whole 16-byte quads (x is 16-byte aligned)
+      for (int e = tid; e < GC_NODES * 8; e += 256) {
+        const int r = e >> 3, q = (e & 7) * 4;
+        const int src = sTab[r * 27 + tt];
+        const bool ok = src >= 0 && ci0 + q < cin;
+        cp_async16(&sX[buf][r][q],
+                   ok ? (const void*)(x + (int64_t)src * cin + ci0 + q) : (const void*)x, ok);
+      }
+    } else {
+      for (int e = tid; e < GC_NODES * 32; e += 256) {
+        const int r = e >> 5, c = e & 31;
+        const int src = sTab[r * 27 + tt];
+        const bool ok = src >= 0 && ci0 + c < cin;
+        cp_async4(&sX[buf][r][c],
+                  ok ? (const void*)(x + (int64_t)src * cin + ci0 + c) : (const void*)x, ok);
+      }
     }
     for (int e = tid; e < 32 * 32; e += 256) {
       const int r = e >> 5, c = e & 31;   // r: input channel, c: output channel
@@ -262,7 +281,7 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
       const float4 w = *reinterpret_cast<const float4*>(&sW[buf][kk][tx * 4]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float xv = sX[buf][ty * 4 + j][kk];
+        const float xv = sX[buf][j * 32 + ty][kk];
         acc[j][0] = fmaf(xv, w.x, acc[j][0]);
         acc[j][1] = fmaf(xv, w.y, acc[j][1]);
         acc[j][2] = fmaf(xv, w.z, acc[j][2]);
@@ -273,7 +292,7 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int64_t row = n0 + ty * 4 + j;
+    const int64_t row = n0 + j * 32 + ty;
     if (row >= n_out) break;
     const int64_t node = omap ? (int64_t)omap[row] : row;
 #pragma unroll
