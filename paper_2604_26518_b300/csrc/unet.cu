@@ -162,15 +162,15 @@ __global__ void k_class_fill(const int32_t* __restrict__ xyz, const int* __restr
 // quads x 32 node groups, each thread a 4 x 4 register tile: per staged input channel 4
 // shared loads (rows of the gathered inputs) and one 16-byte load (4 weights) feed 16 FMAs.
 constexpr int GC_NODES = 128;
-// dynamic shared memory: weights [2][32][32], gathered rows [2][GC_NODES][GC_LD], the
-// block's tap table [GC_NODES][27], tap flags [27] and the active-tap list [28]. Row stride
+// dynamic shared memory: weights [2][32][32], gathered rows [2][GC_NODES][GC_LD], tap flags
+// [27] and the active-tap list [28] (the block's tap table rows are read from global memory,
+// where they stay in L1, to keep four blocks per SM). Row stride
 // 36 floats keeps 16-byte copies aligned; thread row r = j * 32 + ty makes the 4 rows a warp
 // reads at once fall in distinct banks.
 constexpr int GC_LD = 36;
 constexpr int GC_SW = 2 * 32 * 32 * 4;
 constexpr int GC_SX = 2 * GC_NODES * GC_LD * 4;
-constexpr int GC_ST = GC_NODES * 27 * 4;
-constexpr int GC_SMEM = GC_SW + GC_SX + GC_ST + 27 * 4 + 28 * 4;
+constexpr int GC_SMEM = GC_SW + GC_SX + 27 * 4 + 28 * 4;
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -204,19 +204,17 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
   extern __shared__ __align__(16) unsigned char gc_smem[];
   float (*sW)[32][32] = reinterpret_cast<float (*)[32][32]>(gc_smem);
   float (*sX)[GC_NODES][GC_LD] = reinterpret_cast<float (*)[GC_NODES][GC_LD]>(gc_smem + GC_SW);
-  int* sTab = reinterpret_cast<int*>(gc_smem + GC_SW + GC_SX);
-  int* sAny = sTab + GC_NODES * 27;
+  int* sAny = reinterpret_cast<int*>(gc_smem + GC_SW + GC_SX);
   int* sTaps = sAny + 27;   // [0]: count, then the active weight taps in order
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 8 + tx;   // blockDim (8, 32)
   const int64_t n0 = (int64_t)blockIdx.x * GC_NODES;
   const int co0 = blockIdx.y * 32;
   const int64_t rows = min((int64_t)GC_NODES, n_out - n0);
+  const int* bTab = tab + n0 * 27;   // this block's rows of the table
   if (tid < 27) sAny[tid] = 0;
-  for (int e = tid; e < GC_NODES * 27; e += 256)
-    sTab[e] = (e / 27 < rows) ? tab[n0 * 27 + e] : -1;
   __syncthreads();
-  for (int e = tid; e < GC_NODES * 27; e += 256)
-    if (sTab[e] >= 0) sAny[e % 27] = 1;
+  for (int e = tid; e < rows * 27; e += 256)
+    if (bTab[e] >= 0) sAny[e % 27] = 1;
   __syncthreads();
   if (tid == 0) {
     int k = 0;
@@ -235,7 +233,7 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
     if ((cin & 3) == 0) {   // rows of whole 16-byte quads (x is 16-byte aligned)
       for (int e = tid; e < GC_NODES * 8; e += 256) {
         const int r = e >> 3, q = (e & 7) * 4;
-        const int src = sTab[r * 27 + tt];
+        const int src = r < rows ? __ldg(bTab + r * 27 + tt) : -1;
         const bool ok = src >= 0 && ci0 + q < cin;
         cp_async16(&sX[buf][r][q],
                    ok ? (const void*)(x + (int64_t)src * cin + ci0 + q) : (const void*)x, ok);
@@ -243,7 +241,7 @@ __global__ void __launch_bounds__(256) k_gconv(const float* __restrict__ x, int 
     } else {
       for (int e = tid; e < GC_NODES * 32; e += 256) {
         const int r = e >> 5, c = e & 31;
-        const int src = sTab[r * 27 + tt];
+        const int src = r < rows ? __ldg(bTab + r * 27 + tt) : -1;
         const bool ok = src >= 0 && ci0 + c < cin;
         cp_async4(&sX[buf][r][c],
                   ok ? (const void*)(x + (int64_t)src * cin + ci0 + c) : (const void*)x, ok);
