@@ -59,6 +59,11 @@ def workload(name: str, rank: int):
         cells = [lattices.batch_cell(3000 + 64 * rank + i) for i in range(64)]
         desc = "64 seeded cells, N uniform in {32,48,64,96,128}: TPMS network/plate, " \
                "BCC/octet trusses, spinodal; phi 0.1-0.4"
+    elif name == "c256":
+        cells = [lattices.mixed_cell(2600 + 4 * rank + i, 256, families=C2_FAMILIES)
+                 for i in range(4)]
+        desc = "4 seeded 256^3 cells: TPMS network/plate (gyroid, Schwarz-P, diamond), " \
+               "BCC/octet trusses, phi 0.1-0.4"
     elif name == "c512":
         cells = [(lattices.tpms_network("gyroid", 512, 0.20), {"family": "gyroid", "n": 512})]
         desc = "gyroid 512^3, phi 0.20"
@@ -484,7 +489,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmt", choices=["gmt", "reference"])
-    ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c512", "batch64"])
+    ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c256", "c512", "batch64"])
     ap.add_argument("--physics", default="elastic", choices=["elastic", "heat"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")

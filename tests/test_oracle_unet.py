@@ -80,6 +80,15 @@ def test_tables_are_mutually_consistent(graph):
         assert (graph.down[l][graph.up[l][f, t], t] == f).all()
         # every active fine node has at least one coarse parent (conservative coarsening)
         assert ((graph.up[l] >= 0).sum(axis=1) >= 1).all()
+        # a fine node of parity class c (odd axes = set bits of c) can only have parents
+        # under the 2^popcount(c) taps that are 0 on its even axes and +-1 on its odd ones
+        xyz = graph.levels[l].node_xyz()
+        cls = (xyz[:, 0] & 1) + 2 * (xyz[:, 1] & 1) + 4 * (xyz[:, 2] & 1)
+        for c in range(8):
+            taps = np.nonzero((graph.up[l][cls == c] >= 0).any(axis=0))[0]
+            allowed = [t for t, d in enumerate(unet.TAPS)
+                       if all((d[a] != 0) == bool((c >> a) & 1) for a in range(3))]
+            assert set(taps) <= set(allowed) and len(allowed) == 2 ** bin(c).count("1")
 
 
 def test_input_features_are_octant_bits(graph):
