@@ -120,7 +120,7 @@ def test_training_lowers_energy_error_and_warm_start_keeps_accuracy():
     """Train on 16 seeded 32^3 cells (energy loss, AdamW), then on held-out cells: the
     prediction's energy-norm error is below the zero start's (which is 1 by definition), the
     solve from it reaches the tolerance, and C^H equals the zero-start result; the V-cycle
-    counts of both starts are printed (the plain cycles are the fallback and the judge)."""
+    counts of both starts are printed (the plain cycles are the fallback and decide convergence)."""
     fams = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "bcc", "octet")
     rows = ounet.layers(18)
     net = gmt.UNet(18, torch.tensor(lattices.unet_init(rows, seed=0)))
