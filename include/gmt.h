@@ -225,10 +225,9 @@ gmt_status gmt_residual(gmt_hierarchy* h, int precision, const double* u, double
    memory (an application whose memory manager owns the device and forbids side
    allocations, a fixed-budget embedded or sandboxed process, a latency-bound loop that
    cannot pay for an allocation's implicit device synchronisation). It computes the same
-   energy average as gmt_homogenize (App. F), in FP64, for a nodal field the caller
-   already holds, without a hierarchy and without any allocation: the working memory is a
-   352 KB array inside the library that each GPU using the library keeps until the process
-   exits.
+   energy average as gmt_homogenize, in FP64, for a nodal field the caller already holds,
+   without a hierarchy and without any allocation: the working memory is a 352 KB array
+   inside the library that each GPU using the library keeps until the process exits.
    voxels: device uint8[N^3] (x fastest). u_dense: device double[N^3][D][M], the field at
    every node site x + N*y + N^2*z (values at sites without an active element are
    ignored). CH: device double[M][M] written row-major. res: N, at most 512 (larger values

@@ -1,35 +1,39 @@
-"""Reference V-cycle (Alg. 1) on the assembled Galerkin hierarchy — oracle, test infra.
+"""Reference multigrid cycle on the assembled Galerkin hierarchy — oracle, test infra.
 
-The paper's Alg. 1 ("Standard GMG V-Cycle"), step by step, with the smoother replaced by
-damped block-Jacobi or Chebyshev (the smoother choice of this build; the paper's own
-update form u_i <- u_i + omega D_i^{-1} r_i is Sec. 4.6 "Parallel Smoothing", applied to
-all nodes at once instead of colour by colour):
+The standard geometric-multigrid recursion of Alg. 1: on every level but the coarsest,
+smooth, form the residual, restrict it with R = P^T, solve the coarse problem from a zero
+guess (recursively), add the prolongated correction and smooth again; the coarsest level is
+solved directly:
 
     for l = 1..L-1: pre-smooth; r^l = f^l - K^l u^l; f^{l+1} = R r^l; u^{l+1} = 0
     coarsest solve
     for l = L-1..1: u^l += P u^{l+1}; post-smooth
 
-D^l is the block diagonal of K^l (D x D node blocks). The coarsest solve (reading of
-Alg. 1's GS(K^L ...) step, replaced by an exact solve) is the solution of
-(K^L + rho J) u = f^L, J the per-component all-ones coupling and rho the mean diagonal of
-K^L: for right-hand sides orthogonal to translations this is the zero-mean solution of
-K^L u = f^L.
+The smoother is this build's choice: damped block-Jacobi, u <- u + omega D^-1 (f - K u)
+applied to all nodes at once (the update form of Sec. 4.6), or Chebyshev, or the 8-colour
+Gauss-Seidel form of Sec. 4.6. D^l is the block diagonal of K^l (D x D node blocks). The
+coarsest solve (an exact solve in place of Alg. 1's inexact coarsest smoothing) is the
+solution of (K^L + rho J) u = f^L, J the per-component all-ones coupling and rho the mean
+diagonal of K^L: for right-hand sides orthogonal to translations this is the zero-mean
+solution of K^L u = f^L.
 
-8-colour Gauss-Seidel (Sec. 4.6 "Parallel Smoothing", colour by colour): the nodes of a
-level are coloured by the parity of their coordinates, c = (x&1) + 2(y&1) + 4(z&1); nodes of
-one colour share no stencil entry, so each colour is updated at once with the damped
-block-Jacobi step u_c <- u_c + omega (D^{-1} (f - K u))_c on the latest u, colours 0..7 in
-turn, per sweep.
+8-colour Gauss-Seidel (Sec. 4.6): the nodes of a level are coloured by the parity of their
+coordinates, c = (x&1) + 2(y&1) + 4(z&1); nodes of one colour share no stencil entry, so
+each colour is updated at once with the damped block-Jacobi step
+u_c <- u_c + omega (D^{-1} (f - K u))_c on the latest u, colours 0..7 in turn, per sweep.
 
-Cycle schedules (Sec. 5 "V-/W-/F-cycles"): the coarse problem of level l is solved by one
-cycle of the same kind (V), by two W-cycles (the second starting from the first's result),
-or by an F-cycle followed by a V-cycle; the coarsest level is solved once.
+Cycle schedules (Sec. 5 compares V-, W- and F-cycles; it prints no pseudocode): the coarse
+problem of level l is solved by one cycle of the same kind (V), by two W-cycles (the second
+starting from the first's result), or by an F-cycle followed by a V-cycle; the coarsest
+level is solved once.
 
 Chebyshev: one polynomial of degree k = nu (the sweep count, so that both smoothers apply K
 the same number of times) on D^{-1}K over [a, b] = [lmax/ratio, upper*lmax]:
 theta = (b+a)/2, delta = (b-a)/2, sigma = theta/delta, rho_0 = 1/sigma; d = D^{-1} r/theta;
 then k times: u += d; if not last: r = f - K u, rho' = 1/(2 sigma - rho),
-d = rho' rho d + (2 rho'/delta) D^{-1} r, rho = rho'.
+d = rho' rho d + (2 rho'/delta) D^{-1} r, rho = rho'. After k steps the error component
+along an eigenvector of D^{-1}K with eigenvalue lam is multiplied by
+T_k((theta - lam)/delta) / T_k(theta/delta) (the textbook Chebyshev semi-iteration).
 """
 from __future__ import annotations
 

@@ -527,17 +527,50 @@ class UNet:
             pass
 
 
+def _noalloc_check(name: str, t, dtype, numel: int, shape=None):
+    """Reject, before any library call, a tensor the allocation-free kernel would read or
+    write out of bounds: wrong dtype, wrong size or shape, or non-contiguous. (The device
+    is checked afterwards, once for all arguments.)"""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} values, got {t.numel()}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def homogenize_dense_noalloc(voxels, res: int, physics=ELASTIC, E=1.0, nu=0.3, k=1.0,
                              u_dense=None, out=None, stream=None):
     """C^H of a nodal field on the dense periodic node grid without any device allocation
-    in the library (gmt_homogenize_dense_noalloc). voxels: CUDA uint8 tensor (N,N,N);
-    u_dense: CUDA float64 tensor with N^3 * D * M values (node site major); out: CUDA
-    float64 (M, M) tensor, created if omitted (by torch, outside the library)."""
+    in the library (gmt_homogenize_dense_noalloc). voxels: contiguous CUDA uint8 tensor with
+    N^3 values (x fastest); u_dense: contiguous CUDA float64 tensor with N^3 * D * M values
+    (node site major); out: contiguous CUDA float64 (M, M) tensor, created if omitted (by
+    torch, outside the library). Every tensor is checked (dtype, size, contiguity, device)
+    before the library is called; the library itself rejects N > 512."""
+    import torch
+    if physics not in (ELASTIC, HEAT):
+        raise ValueError(f"unknown physics {physics}")
+    D, M = (3, 6) if physics == ELASTIC else (1, 3)
+    res = int(res)
+    n3 = res ** 3 if res > 0 else 0
+    _noalloc_check("voxels", voxels, torch.uint8, n3)
+    _noalloc_check("u_dense", u_dense, torch.float64, n3 * D * M)
+    if out is not None:
+        _noalloc_check("out", out, torch.float64, M * M, shape=(M, M))
+    for name, t in (("voxels", voxels), ("u_dense", u_dense), ("out", out)):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
     torch = _torch()
-    M = 6 if physics == ELASTIC else 3
     if out is None:
-        out = torch.empty((M, M), dtype=torch.float64, device="cuda")
-    s = stream if stream is not None else torch.cuda.current_stream()
+        out = torch.empty((M, M), dtype=torch.float64, device=voxels.device)
+    if voxels.device != u_dense.device or out.device != voxels.device:
+        raise ValueError("voxels, u_dense and out must be on the same CUDA device")
+    s = stream if stream is not None else torch.cuda.current_stream(voxels.device)
     st = lib().gmt_homogenize_dense_noalloc(_ptr(voxels), res, physics, E, nu, k, _ptr(u_dense),
                                             _ptr(out), s.cuda_stream)
     _check(st, "gmt_homogenize_dense_noalloc")

@@ -163,3 +163,61 @@ def test_w_and_f_cycles_contract_at_least_as_well_as_v(kind):
         return (np.linalg.norm(F - Ks[0] @ U, axis=0) / fn).max()
 
     assert rate(kind) <= rate("V") * 1.0001
+
+
+# ---------------------------------------------------------------- Chebyshev closed form
+def _cheb_T(k: int, x: np.ndarray) -> np.ndarray:
+    """T_k(x) from its closed forms: cos(k arccos x) on |x| <= 1, sign(x)^k cosh(k arccosh|x|)
+    outside (not from the three-term recurrence the smoother uses)."""
+    x = np.asarray(x, dtype=np.float64)
+    inside = np.abs(x) <= 1.0
+    out = np.empty_like(x)
+    out[inside] = np.cos(k * np.arccos(x[inside]))
+    xo = x[~inside]
+    out[~inside] = np.sign(xo) ** k * np.cosh(k * np.arccosh(np.abs(xo)))
+    return out
+
+
+@pytest.mark.parametrize("D", [1, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_chebyshev_smoother_matches_closed_form_damping(D, k):
+    """The Chebyshev semi-iteration of degree k on D^-1 K over [a, b] multiplies the error's
+    component along each eigenvector of D^-1 K (eigenvalue lam) by
+        T_k((theta - lam) / delta) / T_k(theta / delta),   theta = (b+a)/2, delta = (b-a)/2.
+    K is a random SPD matrix with a chosen spectrum; the eigenpairs of D^-1 K (D its D x D
+    block diagonal) come from a dense eigendecomposition. Eigenvalues lie both inside [a, b]
+    and below a (where the damping is weak), so a wrong interval end, recurrence coefficient
+    or dropped rho' rho factor changes the per-eigenvalue ratio."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(100 + 10 * D + k)
+    n = 12 * D
+    # eigenvalues: a few below a = lmax/ratio, the rest spread over [a, lmax]
+    lmax, ratio, upper = 3.0, 30.0, 1.1
+    a_lo = lmax / ratio
+    lam = np.concatenate([rng.uniform(0.2 * a_lo, 0.9 * a_lo, 3),
+                          rng.uniform(a_lo, lmax, n - 4), [lmax]])
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * lam) @ Q.T                            # SPD with spectrum lam
+    K = sp.csr_matrix(A)
+    Dinv = vcycle.block_diag_inverse(K, D).toarray()
+    # D^-1 K is similar to the symmetric D^-1/2 K D^-1/2: real eigenpairs (w, V)
+    w, V = np.linalg.eig(Dinv @ A)
+    w, V = w.real, V.real
+    lm = float(w.max())
+    vc = vcycle.VCycle([K, sp.identity(1, format="csr")], [None], D, smoother="chebyshev",
+                       cheb_lmax=[lm], cheb_ratio=ratio, cheb_upper=upper)
+    u_star = rng.standard_normal((n, 2))
+    f = A @ u_star
+    u0 = rng.standard_normal((n, 2))
+    got = vc.smooth(0, u0, f, k)
+    b, a = upper * lm, lm / ratio
+    theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+    damp = _cheb_T(k, (theta - w) / delta) / _cheb_T(k, np.array([theta / delta]))[0]
+    e0 = np.linalg.solve(V, u0 - u_star)           # error in the eigenbasis of D^-1 K
+    expect = u_star + V @ (damp[:, None] * e0)
+    assert np.abs(got - expect).max() <= 1e-12 * np.abs(expect).max()
+    # the spectrum has eigenvalues below a (weakly damped) and inside [a, b], where the
+    # damping is at most 1 / T_k(theta/delta)
+    inside = (w >= a) & (w <= b)
+    assert inside.sum() >= n // 2 and (w < a).sum() >= 1
+    assert np.all(np.abs(damp[inside]) <= 1.0 / _cheb_T(k, np.array([theta / delta]))[0] + 1e-12)
