@@ -9,7 +9,12 @@ the step through the same public API from pinned host voxels (host->device copy 
 timed region) and reads each C^H back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmt|reference]
-                    [--workload c128|c32|c512] [--physics elastic|heat] [--precision fp32|fp64]
+                    [--workload c128|c32|c256|c512|batch64] [--physics elastic|heat]
+                    [--precision fp32|fp64] [--smoother jacobi|chebyshev|gs8] [--cycle V|W|F]
+
+The default (c128) line also carries the 512^3 gyroid as a keyed sub-result (value_512,
+ms_per_solve_512, vcycles_512), the V-cycle roofline (roofline.vcycle: algorithmic bytes of
+every V-cycle over the traced V-cycle kernel time) and per-kernel rooflines.
 
 Multi-GPU: one process per GPU (torchrun); every rank solves its own 16 cells (weak scaling,
 no data-path collective); the timing is the max over ranks. `--impl reference` times the CPU
@@ -38,12 +43,11 @@ C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_
                "plate_diamond", "bcc", "octet")
 METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
 TOL = 1e-5
-# ncu DRAM bytes (read + write) per active node of the timed level-0 sweep of the current
-# kernel: with the default one level-0 sweep per visit that is the V-cycle's last sweep
-# (u, f and K p read, u' written, Krylov partials): 197.3 MB over the 651,308 active nodes
-# of the first 128^3 bench cell (profiles/k_stencil_smoother_c128_elastic.md); scaled by
-# the nodes of each sweep
-NCU_DRAM_BYTES_PER_NODE = 302.9
+# ncu DRAM bytes (read + write) per active node and launch, from one capture of each
+# kernel on the first 128^3 bench cell (FP32 elasticity), keyed by trace category. A
+# kernel whose source changed after its capture has no entry (its traffic is reported as
+# null until it is captured again).
+NCU_DRAM_BYTES_PER_NODE = {}
 
 
 def workload(name: str, rank: int):
@@ -126,57 +130,134 @@ def measured_peak_gbs():
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def cpu_sample(n_cells: int = 1, timeout: float = 600.0):
-    """Time the oracle on a bounded sample: the batch's first cells regenerated at 32^3
-    (same generator and seeds), full solve to r <= 1e-5 and C^H, single thread."""
-    code = (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from paper_2604_26518_b300 import lattices\n"
-        "from oracle import solve\n"
-        "fams = %r\n"
-        "cells = [lattices.mixed_cell(2000 + i, 32, families=fams)[0] for i in range(%d)]\n"
-        "t = time.perf_counter()\n"
-        "for v in cells: solve.solve_cell(v, 'elastic', 1.0, 0.3, tol=%g)\n"
-        "print(json.dumps({'seconds': time.perf_counter() - t, 'cells': len(cells)}))\n"
-    ) % (ROOT, C2_FAMILIES, n_cells, TOL)
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_ORACLE_CHILD = (
+    "import sys, time, json; sys.path.insert(0, %r)\n"
+    "from paper_2604_26518_b300 import lattices\n"
+    "from oracle import solve\n"
+    "cells = [lattices.mixed_cell(s, %d, families=%r)[0] for s in %r]\n"
+    "t = time.perf_counter()\n"
+    "nodes = 0\n"
+    "for v in cells:\n"
+    "    r = solve.solve_cell(v, 'elastic', 1.0, 0.3, tol=%g)\n"
+    "    nodes += r['level'].num_nodes\n"
+    "print(json.dumps({'seconds': time.perf_counter() - t, 'cells': len(cells), 'nodes': nodes}))\n"
+)
+
+
+def cpu_sample(seeds, n: int = 32, procs: int = 1, timeout: float = 900.0):
+    """Time the FP64 oracle (assembled K, Jacobi-PCG to max_m r_m <= tol, energy-average
+    C^H) on the bench generator's cells `seeds` regenerated at n^3. The cells are split
+    over `procs` single-threaded processes that run at the same time (cells are
+    independent); the rate is cells over the wall time of the slowest process (cell
+    generation excluded)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
-                       timeout=timeout, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    return out["cells"] / out["seconds"], out
+    seeds = list(seeds)
+    groups = [seeds[p::procs] for p in range(procs) if seeds[p::procs]]
+    ps = [subprocess.Popen([sys.executable, "-c", _ORACLE_CHILD % (ROOT, n, C2_FAMILIES, g, TOL)],
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+          for g in groups]
+    outs = []
+    for p in ps:
+        o, e = p.communicate(timeout=timeout)
+        if p.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    wall = max(o["seconds"] for o in outs)
+    cells = sum(o["cells"] for o in outs)
+    return cells / wall, {"seconds": wall, "cells": cells, "procs": len(groups),
+                          "nodes": sum(o["nodes"] for o in outs)}
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank: int, world: int):
+    """The CPU FP64 oracle on the bench's 16 cells, regenerated at 32^3 (the 128^3 cells
+    need an assembled matrix of ~8 GB and hours of Jacobi-PCG per cell), spread over the
+    host's cores (one single-threaded process per cell, at most one per core)."""
     if rank != 0:
         return
+    cores = host_cores()
+    procs = max(1, min(cores, 16))
+    seeds = range(2000, 2016)
     for _ in range(args.warmup):
-        cpu_sample(1)
-    rates = []
+        cpu_sample(seeds[:procs], 32, procs)
+    rates, nodes = [], 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rate, _ = cpu_sample(1)
+        rate, out = cpu_sample(seeds, 32, procs)
         rates.append(rate)
+        nodes = out["nodes"]
     elapsed = time.perf_counter() - t0
     value = float(np.mean(rates))
-    sample = ("per step: the batch's first cell (seed 2000) regenerated at 32^3 by the same "
-              "generator, CPU FP64 oracle: assembled K, Jacobi-PCG to max_m r_m <= 1e-5, "
-              "energy-average C^H (the 128^3 cells exceed the oracle's assembled-matrix memory)")
+    sample = ("per step: the c128 batch's 16 cells (seeds 2000-2015) regenerated at 32^3 by the "
+              "same generator, %d single-threaded processes on %d host cores; CPU FP64 oracle: "
+              "assembled K, Jacobi-PCG to max_m r_m <= 1e-5, energy-average C^H; %d active "
+              "nodes over the 16 cells (a 128^3 cell has ~40x more)" % (procs, cores, nodes))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "C^H solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c128 batch, bounded 32^3 sample (see cpu_baseline.sample)",
-                   "physics": "elastic", "tol": TOL},
-        "cpu_baseline": {"value": value, "unit": "C^H solves/s", "cores": 1,
-                         "kind": "oracle", "sample": sample},
+        "config": {"workload": "c128 batch regenerated at 32^3 (bounded sample, see "
+                               "cpu_baseline.sample)", "physics": "elastic", "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "C^H solves/s", "cores": procs,
+                         "host_cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "C^H solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_block():
+    """The oracle as it stands on bounded samples of the bench workload: 1 thread and all
+    host cores on 32^3 regenerations of the batch's cells, and 1 thread on the batch's first
+    cell at 64^3."""
+    cores = host_cores()
+    procs = max(1, min(cores, 16))
+    r1, o1 = cpu_sample([2000], 32, 1)
+    ra, oa = cpu_sample(range(2000, 2000 + procs), 32, procs)
+    r64, o64 = cpu_sample([2000], 64, 1)
+    return {
+        "value": ra, "unit": "C^H solves/s", "cores": procs, "host_cores": cores,
+        "kind": "oracle",
+        "sample": ("batch cells 2000-%d regenerated at 32^3, one single-threaded process per "
+                   "cell on %d cores, CPU FP64 oracle to r <= 1e-5 + C^H; %.1f s wall"
+                   % (2000 + procs - 1, procs, oa["seconds"])),
+        "one_thread": {"value": r1, "unit": "C^H solves/s", "cores": 1,
+                       "sample": "batch cell 2000 at 32^3; %.1f s; %d active nodes"
+                                 % (o1["seconds"], o1["nodes"])},
+        "c64": {"value": r64, "unit": "C^H solves/s", "cores": 1,
+                "sample": "batch cell 2000 (Schwarz-P network) at 64^3, 1 thread; %.1f s; %d "
+                          "active nodes" % (o64["seconds"], o64["nodes"])},
+    }
+
+
+def vcycle_bytes(nodes, C: int, b: int, nu_pre: int, nu_post: int, nu_coarse: int) -> float:
+    """Algorithmic HBM bytes of one V-cycle with the damped-Jacobi smoother, vectors only,
+    each read or written once: on level l (n_l active nodes, C values of b bytes), the first
+    pre-smoothing step from zero reads f and writes u (2), every further sweep reads u and f
+    and writes u (3), the residual + restriction reads u and f and writes f_{l+1}
+    (2 n_l + n_{l+1}), the prolongation + correction reads u_{l+1} and reads and writes u
+    (2 n_l + n_{l+1}); the coarsest solve gathers f and scatters u (2 n_L)."""
+    tot = 0.0
+    L = len(nodes)
+    for l in range(L - 1):
+        pre = nu_pre if (l == 0 or nu_coarse == 0) else nu_coarse
+        post = nu_post if (l == 0 or nu_coarse == 0) else nu_coarse
+        n, nc = nodes[l], nodes[l + 1]
+        tot += C * b * (n * (2 + 3 * max(pre - 1, 0) + 2 + 2 + 3 * post) + 2 * nc)
+    tot += C * b * 2 * nodes[L - 1]
+    return tot
+
+
+VCYCLE_CATS = ("diag_l0", "smooth_l0", "resid_l0", "stencil_l1", "stencil_l2up", "restrict",
+               "prolong", "coarse_solve")
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -210,9 +291,14 @@ def run_gmt(args, rank: int, world: int):
     if args.omega > 0:
         opts.omega = args.omega
     if args.smoother:
-        opts.smoother = gmt.JACOBI if args.smoother == "jacobi" else gmt.CHEBYSHEV
+        opts.smoother = {"jacobi": gmt.JACOBI, "chebyshev": gmt.CHEBYSHEV,
+                         "gs8": gmt.GS8}[args.smoother]
+    if args.cycle:
+        opts.cycle = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[args.cycle]
     if args.cells:
         cells = cells[:args.cells]
+    vals = 18 if ph == gmt.ELASTIC else 3        # values per node (components x cases)
+    esz = 4 if prec == gmt.FP32 else 8           # bytes per value of the V-cycle vectors
     vox_dev = [torch.from_numpy(v).to(dev) for v, _ in cells]
     vox_host = [torch.from_numpy(v).pin_memory() for v, _ in cells]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -268,6 +354,15 @@ def run_gmt(args, rank: int, world: int):
                 tt = h.trace_totals()
                 a = tot.setdefault("_smooth_node_launches", [0, 0.0, 0.0])
                 a[2] += float(h.num_nodes(0)) * tt["smooth_l0"][0]   # nodes x sweeps
+                nodes = [h.num_nodes(l) for l in range(h.levels)]
+                a = tot.setdefault("_vcycle", [0, 0.0, 0.0])
+                a[0] += info.inner_total
+                a[2] += info.inner_total * vcycle_bytes(nodes, vals, esz, opts.nu_pre,
+                                                        opts.nu_post, opts.nu_coarse)
+                for l in range(len(nodes)):
+                    a = tot.setdefault("_nodes_l%d" % l, [0, 0.0, 0.0])
+                    a[0] += 1
+                    a[2] += nodes[l]
                 for k, (n, ms, b) in tt.items():
                     if k == "setup_hierarchy":
                         continue
@@ -360,18 +455,47 @@ def run_gmt(args, rank: int, world: int):
     e2e_value = cells_total / (e2e_ms / 1000.0)
     if rank != 0:
         return
-    # ---- roofline of the dominant kernel: the level-0 smoother sweep
-    n_sm, ms_sm, b_sm = totals.get("smooth_l0", [0, 0.0, 0.0])
+    # ---- rooflines from the traced step: per kernel category, the whole V-cycle, and the
+    # dominant V-cycle kernel (the category with the most device time)
     peak, peak_src = measured_peak_gbs()
-    achieved = (b_sm / (ms_sm / 1000.0)) / 1e9 if ms_sm > 0 else None
-    avg_nodes = totals.pop("_smooth_node_launches", [0, 0.0, 0.0])[2] / max(n_sm, 1)
-    # the ncu figure was taken on the FP32 elasticity sweep; other forms report no traffic
-    ncu_matches = (ph == gmt.ELASTIC and prec == gmt.FP32)
-    traffic = (NCU_DRAM_BYTES_PER_NODE * avg_nodes) \
-        if (NCU_DRAM_BYTES_PER_NODE and ncu_matches) else None
-    vals = (18 if ph == gmt.ELASTIC else 3)
-    esz = 4 if prec == gmt.FP32 else 8
+    avg_nodes = totals.pop("_smooth_node_launches", [0, 0.0, 0.0])[2] / \
+        max(totals.get("smooth_l0", [1])[0], 1)
+    vc = totals.pop("_vcycle", [0, 0.0, 0.0])
+    level_nodes = {}
+    for k in [k for k in totals if k.startswith("_nodes_l")]:
+        a = totals.pop(k)
+        level_nodes[int(k[len("_nodes_l"):])] = a[2] / max(a[0], 1)
+    kernels = {}
+    for k, (n, ms, b) in totals.items():
+        if ms > 0 and b > 0 and k in VCYCLE_CATS + ("apply_l0", "outer_resid", "vector"):
+            gbs = b / (ms / 1000.0) / 1e9
+            kernels[k] = {"launches": n, "ms": ms, "avg_launch_us": 1000.0 * ms / max(n, 1),
+                          "achieved_gbs": gbs, "frac": gbs / peak}
+    vc_ms = sum(totals.get(k, [0, 0.0, 0.0])[1] for k in VCYCLE_CATS)
+    vc_gbs = (vc[2] / (vc_ms / 1000.0) / 1e9) if vc_ms > 0 else None
+    dom = max((k for k in VCYCLE_CATS if k in kernels), key=lambda k: kernels[k]["ms"],
+              default=None)
+    dom_n, dom_ms, dom_b = totals.get(dom, [0, 0.0, 0.0]) if dom else (0, 0.0, 0.0)
+    dom_gbs = (dom_b / (dom_ms / 1000.0) / 1e9) if dom_ms > 0 else None
+    ncu = NCU_DRAM_BYTES_PER_NODE.get(dom) if (ph == gmt.ELASTIC and prec == gmt.FP32) else None
+    dom_nodes = avg_nodes if dom in ("smooth_l0", "resid_l0", "diag_l0") else \
+        level_nodes.get(1) if dom == "stencil_l1" else None
+    traffic = ncu * dom_nodes if (ncu is not None and dom_nodes) else None
     total_dev_ms = sum(v[1] for v in totals.values())
+    vcycle_line = {
+        "achieved": vc_gbs, "peak": peak, "unit": "GB/s",
+        "frac": (vc_gbs / peak) if vc_gbs else None,
+        "vcycles": vc[0], "traced_ms": vc_ms, "algorithmic_bytes": vc[2],
+        "formula": ("sum over cells of V-cycles x sum over levels l < L-1 of C b [n_l (2 + "
+                    "3 (nu_pre_l - 1) + 2 + 2 + 3 nu_post_l) + 2 n_(l+1)] + C b 2 n_(L-1) "
+                    "(vectors only, each read/written once: first smoothing step from zero, "
+                    "further sweeps, residual + restriction, prolongation + correction, "
+                    "coarsest gather/scatter), C = %d values, b = %d B, nu = %d/%d on level 0 "
+                    "and %d on coarser levels; divided by the summed traced device time of "
+                    "the V-cycle kernels %s" % (vals, esz, opts.nu_pre, opts.nu_post,
+                                                 opts.nu_coarse, ", ".join(VCYCLE_CATS))),
+        "level_nodes_mean": level_nodes,
+    }
     line = {
         "metric": METRIC, "value": value, "unit": "C^H solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -389,6 +513,7 @@ def run_gmt(args, rank: int, world: int):
                    "smoother": "%s, nu_pre %d, nu_post %d" % (
                        {gmt.JACOBI: "jacobi", gmt.CHEBYSHEV: "chebyshev", gmt.GS8: "gs8"}
                        [opts.smoother], opts.nu_pre, opts.nu_post),
+                   "cycle": "VWF"[opts.cycle],
                    "inner_tol": opts.inner_tol, "nu_coarse": opts.nu_coarse,
                    "omega": opts.omega,
                    "l2": "flushed between timed steps (256 MB write)",
@@ -398,24 +523,20 @@ def run_gmt(args, rank: int, world: int):
                 "h2d_bytes_per_step": int(sum(v.numel() for v in vox_host)),
                 "d2h_bytes_per_step": int(len(cells) * (36 if ph == gmt.ELASTIC else 9) * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm",
-                     "kernel": "level-0 smoother sweeps (k_stencil JACOBI; with the default one "
-                               "sweep per level-0 visit, the V-cycle's last sweep, which also "
-                               "writes the Krylov partials)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_source": ("ncu dram__bytes_read + write of the V-cycle's "
-                                        "last level-0 sweep on the first 128^3 cell, per "
-                                        "active node, times this workload's nodes per sweep")
-                                       if traffic is not None else
-                                       "not captured for this physics / precision",
-                     "peak_source": peak_src,
-                     "algorithmic_bytes": "%d values x %d B per active node for each "
-                                          "vector: u and f read, u' written, plus K p read "
-                                          "in the V-cycle's last sweep (4 vectors, %d B)"
-                                          % (vals, esz, 4 * vals * esz),
-                     "avg_nodes_per_launch": avg_nodes,
-                     "launches": n_sm, "avg_launch_us": 1000.0 * ms_sm / max(n_sm, 1)},
+        "roofline": {"bound": "hbm", "kernel": dom,
+                     "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (dom_gbs / peak) if dom_gbs else None, "traffic": traffic,
+                     "traffic_source": ("ncu dram__bytes_read + write per active node of this "
+                                        "kernel on the first 128^3 bench cell, times this "
+                                        "workload's mean nodes per launch") if traffic else
+                                       "no ncu capture of the current kernel for this physics "
+                                       "/ precision",
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes": "per launch: the vectors the kernel must read and "
+                                          "write, %d values x %d B per active node each, "
+                                          "counted once" % (vals, esz),
+                     "launches": dom_n, "avg_launch_us": 1000.0 * dom_ms / max(dom_n, 1),
+                     "vcycle": vcycle_line, "kernels": kernels},
         "phases_ms_per_step": {k: v[1] / trace_steps for k, v in sorted(totals.items())},
         "traced_device_ms_per_step": total_dev_ms / trace_steps,
         "phases_note": "one extra step, cells one after another, every launch bracketed by "
@@ -429,16 +550,59 @@ def run_gmt(args, rank: int, world: int):
         line["config"]["learned_initializer"] = learned
         line["config"]["step"] = ("hierarchy + network tables + inference + solve from the "
                                   "prediction + C^H per cell")
+    if world == 1 and args.with_512 and args.workload == "c128":
+        line.update(run_512(args, gmt, ph, prec))
     if world == 1 and not args.no_cpu:
         try:
-            rate, out = cpu_sample(1)
-            line["cpu_baseline"] = {
-                "value": rate, "unit": "C^H solves/s", "cores": 1, "kind": "oracle",
-                "sample": "first cell of the batch (seed 2000) regenerated at 32^3 by the same "
-                          "generator; CPU FP64 oracle to r <= 1e-5 + C^H; %.1f s" % out["seconds"]}
+            line["cpu_baseline"] = cpu_baseline_block()
         except Exception as exc:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "error": str(exc)[-300:]}
     print(json.dumps(line), flush=True)
+
+
+def run_512(args, gmt, ph, prec):
+    """The 512^3 gyroid (phi 0.20) as a keyed sub-result of the default line: hierarchy +
+    operators + solve to r <= 1e-5 + C^H per solve, voxels resident on the device, CUDA
+    events around each solve, L2 flushed before each."""
+    import torch
+    vox = torch.from_numpy(lattices.tpms_network("gyroid", 512, 0.20)).cuda()
+    opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
+    opts.nu_pre = opts.nu_post = 2       # two level-0 sweeps win at 512^3 (7 vs 9 cycles)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def once():
+        h = gmt.Hierarchy(vox, opts, stream)
+        st, _, info = h.solve(ph, E=1.0, nu=0.3, k=1.0, tol=TOL, want_field=False,
+                              allow_not_converged=True)
+        C = h.homogenize(ph, E=1.0, nu=0.3, k=1.0)
+        h.free()
+        return st, info, C
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        once()
+    ms, cyc, sts = [], [], []
+    for _ in range(args.steps_512):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info, C = once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        cyc.append(info.inner_total)
+        sts.append(int(st))
+    mean = float(np.mean(ms))
+    del vox, flush
+    torch.cuda.empty_cache()
+    gmt.release_cached_memory()
+    return {"value_512": 1000.0 / mean, "ms_per_solve_512": mean, "vcycles_512": cyc[-1],
+            "config_512": {"workload": "gyroid 512^3, phi 0.20, elasticity" if ph == gmt.ELASTIC
+                           else "gyroid 512^3, phi 0.20, heat conduction",
+                           "solves": len(ms), "nu_pre": 2, "nu_post": 2,
+                           "status": sts, "ms_each": ms,
+                           "step": "hierarchy + operators + solve + C^H"}}
 
 
 LEARNED_SCALE = 0.04   # network output x 0.04 N = field (u / N has a spread of about 0.04)
@@ -493,6 +657,9 @@ def main():
     ap.add_argument("--physics", default="elastic", choices=["elastic", "heat"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-512", dest="with_512", action="store_false",
+                    help="skip the 512^3 gyroid sub-result of the c128 line")
+    ap.add_argument("--steps-512", type=int, default=3, help="timed 512^3 solves")
     ap.add_argument("--coarsest", type=int, default=8, help="coarsest grid side bound")
     ap.add_argument("--nu", type=int, default=0, help="pre/post smoothing sweeps (0: default)")
     ap.add_argument("--nu-post", type=int, default=-1, help="post-smoothing sweeps (-1: as --nu)")
@@ -503,7 +670,8 @@ def main():
                     help="mixed precision: true-residual replacement factor (0: default)")
     ap.add_argument("--streams", type=int, default=4,
                     help="cells solved concurrently, one host thread and CUDA stream each")
-    ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev"])
+    ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev", "gs8"])
+    ap.add_argument("--cycle", default="", choices=["", "V", "W", "F"])
     ap.add_argument("--cells", type=int, default=0, help="use only the first K cells (profiling)")
     ap.add_argument("--learned", action="store_true",
                     help="warm-start every solve from the learned initializer, trained first "

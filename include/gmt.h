@@ -248,11 +248,12 @@ gmt_status gmt_homogenize_dense_noalloc(const uint8_t* voxels, int res, gmt_phys
    active nodes: vectors read + written, counted once; no halo re-reads).
    Categories: 0 level-0 smoother sweep (Jacobi / Chebyshev stencil), 1 level-0 residual in the
    V-cycle, 2 level-0 operator apply (CG), 3 outer residual (float-float or FP64), 4 level-0
-   first smoothing step (diagonal), 5 coarse-level stencils, 6 restriction, 7 prolongation,
-   8 coarsest solve, 9 C^H energy reduction, 10 vector / reduction kernels, 11 hierarchy
-   build, 12 operators (element matrices, Galerkin products, block-diagonal inverses, node
-   stencils), 13 coarsest matrix and its inverse. */
-#define GMT_TRACE_CATEGORIES 14
+   first smoothing step (diagonal), 5 level-1 stencils (smoother, residual, first step),
+   6 restriction, 7 prolongation, 8 coarsest solve, 9 C^H energy reduction, 10 vector /
+   reduction kernels, 11 hierarchy build, 12 operators (element matrices, Galerkin products,
+   block-diagonal inverses, node stencils), 13 coarsest matrix and its inverse, 14 stencils
+   of levels >= 2. */
+#define GMT_TRACE_CATEGORIES 15
 gmt_status gmt_trace_enable(gmt_hierarchy* h, int on);   /* on != 0 enables; resets totals */
 /* Totals since enabling (synchronizes the stream): launches, device milliseconds, bytes. */
 gmt_status gmt_trace_query(gmt_hierarchy* h, int category, int64_t* launches, double* ms,

@@ -456,9 +456,9 @@ gmt_status gmt_trace_query(gmt_hierarchy* h, int category, int64_t* launches, do
 
 const char* gmt_trace_name(int c) {
   static const char* names[gmt::TR_NCAT] = {
-      "smooth_l0", "resid_l0", "apply_l0", "outer_resid", "diag_l0", "stencil_coarse",
+      "smooth_l0", "resid_l0", "apply_l0", "outer_resid", "diag_l0", "stencil_l1",
       "restrict", "prolong", "coarse_solve", "energy", "vector", "setup_hierarchy",
-      "setup_operators", "setup_coarse_inverse"};
+      "setup_operators", "setup_coarse_inverse", "stencil_l2up"};
   return (c >= 0 && c < gmt::TR_NCAT) ? names[c] : "";
 }
 

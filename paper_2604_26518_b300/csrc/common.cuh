@@ -189,8 +189,8 @@ struct Workspace;  // solver buffers (solver.cu)
 enum TraceCat {
   TR_SMOOTH0 = 0, TR_RESID0 = 1, TR_APPLY0 = 2, TR_OUTER = 3, TR_DIAG0 = 4, TR_COARSE_ST = 5,
   TR_RESTRICT = 6, TR_PROLONG = 7, TR_CSOLVE = 8, TR_ENERGY = 9, TR_VEC = 10, TR_SETUP = 11,
-  TR_OPS = 12, TR_CINV = 13,
-  TR_NCAT = 14
+  TR_OPS = 12, TR_CINV = 13, TR_COARSE_ST2 = 14,
+  TR_NCAT = 15
 };
 struct Tracer {
   bool on = false;

@@ -1755,7 +1755,7 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   if (fine) fill_fine<A, D, M>(h->mat, p.fc);
   const unsigned g = (unsigned)lv.nb;
   cudaStream_t s = h->stream;
-  int nvec = 2, cat = TR_COARSE_ST;
+  int nvec = 2, cat = level == 1 ? TR_COARSE_ST : TR_COARSE_ST2;
   if (mode == ST_RESID) nvec = va.f ? 3 : 2;
   if (mode == ST_JACOBI) nvec = 3 + (va.aux != nullptr);   // the last sweep also reads K p
   if (mode == ST_CHEB) nvec = 3 + (va.c1 != 0.0) + (va.dout != nullptr);
@@ -1812,7 +1812,8 @@ static void diag_t(gmt_hierarchy* h, int level, const void* f, void* out, void* 
   p.dout = (TS*)dout;
   p.omega = (A)scale;
   const unsigned g = grid_for(lv.nslots, 128);
-  TraceScope ts(&h->tracer, h->stream, level == 0 ? TR_DIAG0 : TR_COARSE_ST,
+  TraceScope ts(&h->tracer, h->stream,
+                level == 0 ? TR_DIAG0 : (level == 1 ? TR_COARSE_ST : TR_COARSE_ST2),
                 (double)lv.n_nodes * (dout ? 3 : 2) * D * M * sizeof(TS));
   if (level == 0) {
     fill_fine<A, D, M>(h->mat, p.fc);

@@ -137,7 +137,7 @@ _SIGS = {
                                  ctypes.POINTER(_D)]),
 }
 
-TRACE_CATEGORIES = 14
+TRACE_CATEGORIES = 15
 
 
 def release_cached_memory():

@@ -57,12 +57,21 @@ _TPMS = {"gyroid": gyroid_field, "schwarz_p": schwarz_p_field, "diamond": diamon
 
 
 def _lowest(values: np.ndarray, phi: float) -> np.ndarray:
-    """Solid = the round(phi*N^3) voxels with the smallest value (stable by linear index)."""
+    """Solid = the round(phi*N^3) voxels with the smallest value (stable by linear index):
+    everything below the count-th smallest value, then the earliest ties at that value."""
     flat = values.reshape(-1)
     count = int(round(phi * flat.size))
-    order = np.argsort(flat, kind="stable")
     out = np.zeros(flat.size, dtype=np.uint8)
-    out[order[:count]] = 1
+    if count <= 0:
+        return out.reshape(values.shape)
+    if count >= flat.size:
+        out[:] = 1
+        return out.reshape(values.shape)
+    kth = np.partition(flat, count - 1)[count - 1]
+    below = flat < kth
+    out[below] = 1
+    ties = np.flatnonzero(flat == kth)
+    out[ties[: count - int(below.sum())]] = 1
     return out.reshape(values.shape)
 
 

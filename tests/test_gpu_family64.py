@@ -1,0 +1,77 @@
+"""Converged-oracle parity of a full solve for every generator family at 64^3.
+
+For one seeded 64^3 cell of each family (TPMS networks and plates, BCC / octet trusses,
+spinodal), the library solves the cell problems to r <= 1e-5 and returns C^H; the FP64
+oracle's C^H at r <= 1e-10 is stored in tests/golden/family64.json (written by
+tests/golden/make_family64.py, which calls only the oracle and the seeded generators).
+
+Checks per cell and physics:
+  * C^H within 1e-4 of the oracle's, normalised by the largest entry (Sec. 5 error metric
+    delta, read as max-entry relative);
+  * the oracle's relative residual of the library's field (its own matrix-free product)
+    at most the tolerance;
+  * the library's C^H equals the oracle's energy average of the library's field;
+  * the field's error in the energy norm. For the exact solution u* of K u* = f and any u,
+    the energy average of App. F.1 satisfies
+        N^3 (C_II(u) - C_II(u*)) = (u - u*)^T K (u - u*)      (K u* = f, f = sum A^T K_e x0),
+    so the relative energy-norm error of case I is sqrt((C_II(u) - C*_II) / C*_II), computed
+    from the oracle's energy average of the library's field and the stored converged C*.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fe, solve
+from oracle.grid import Level
+from paper_2604_26518_b300 import lattices as L
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "family64.json")
+
+
+def _golden():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def _cells():
+    g = _golden()
+    return [(i, c["family"]) for i, c in enumerate(g["cells"])]
+
+
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+@pytest.mark.parametrize("idx,family", _cells())
+def test_family64_matches_converged_oracle(gmt_lib, idx, family, kind):
+    gmt = gmt_lib
+    g = _golden()
+    rec = g["cells"][idx]
+    vox, desc = L.mixed_cell(g["seed0"] + idx, g["res"], families=(family,))
+    assert int(vox.sum()) == rec["n_solid"]
+    C_star = np.array(rec[kind]["CH"])
+    ph = gmt.ELASTIC if kind == "elastic" else gmt.HEAT
+    h = gmt.Hierarchy(vox)
+    st, u, info = h.solve(ph, tol=TOL)
+    assert st == gmt.OK, info.as_dict()
+    CH = h.homogenize(ph)
+    err = np.abs(CH - C_star).max() / np.abs(C_star).max()
+    assert err <= 1e-4, (family, kind, err)
+
+    Ke, x0, D, M, _ = fe.physics(kind)
+    lev = Level(vox.astype(bool))
+    U = u.detach().cpu().numpy().reshape(-1, M)
+    F = solve.cancel_rounding(solve.load(lev, Ke, x0, D), solve.gross_load_norm(lev, Ke, x0, D))
+    R = F - solve.apply_ebe(lev, Ke, U, D)
+    fn = np.linalg.norm(F, axis=0)
+    res = np.where(fn > 0, np.linalg.norm(R, axis=0) / np.where(fn > 0, fn, 1), 0)
+    assert res.max() <= TOL * 1.02, (family, kind, res)
+    C_of_gpu = solve.homogenize_chunked(lev, U, Ke, x0, D)
+    assert np.abs(CH - C_of_gpu).max() <= 2e-7 * np.abs(C_star).max()
+    diag = np.diag(C_star)
+    excess = np.diag(C_of_gpu) - diag
+    # the energy of any field is at least the minimum's (up to the oracle's 1e-10 residual)
+    assert excess.min() >= -1e-9 * diag.max(), excess
+    en = np.sqrt(np.maximum(excess, 0.0) / np.maximum(diag, 1e-300))
+    assert en.max() <= 1e-4, (family, kind, en)
