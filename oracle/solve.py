@@ -170,13 +170,26 @@ def element_energies(level: Level, U, Ke, x0, D, coef=None) -> np.ndarray:
     return np.einsum("e,eri,erj->eij", s, W, KW)
 
 
-def sensitivities(level: Level, U, Ke, x0, D, p: float) -> np.ndarray:
-    """Inverse-homogenization sensitivities (App. F.3) of the SIMP model
-    C_e = (rho_min + rho_e^p) C0 at the solid elements (rho_e = 1):
-        dC^H_IJ / d rho_e = p rho_e^(p-1) / |Omega| (x0^I - u_e^I)^T K0 (x0^J - u_e^J),
-    shape (ne, cases, cases), canonical element order, |Omega| = N^3."""
+def simp_coef(level: Level, rho: np.ndarray, rho_min: float, p: float) -> np.ndarray:
+    """Dense N^3 element coefficients s_e = rho_min + rho_e^p of the SIMP interpolation
+    C_e = (rho_min + rho_e^p) C0 (App. F.3), for densities rho given per active element in
+    canonical element order; inactive voxels get 0 (they are not part of the mesh)."""
     N = level.active.shape[0]
-    return p / float(N) ** 3 * element_energies(level, U, Ke, x0, D)
+    coef = np.zeros(N ** 3)
+    coef[level.elem_lin] = rho_min + np.asarray(rho, dtype=np.float64) ** p
+    return coef.reshape(level.active.shape)
+
+
+def sensitivities(level: Level, U, Ke, x0, D, p: float, rho=None) -> np.ndarray:
+    """Inverse-homogenization sensitivities (App. F.3) of the SIMP model
+    C_e = (rho_min + rho_e^p) C0, per active element:
+        dC^H_IJ / d rho_e = p rho_e^(p-1) / |Omega| (x0^I - u_e^I)^T K0 (x0^J - u_e^J),
+    u the solution for the current densities; rho None means the binary design (rho_e = 1).
+    Shape (ne, cases, cases), canonical element order, |Omega| = N^3."""
+    N = level.active.shape[0]
+    fac = np.full(level.num_elements, float(p)) if rho is None else \
+        p * np.asarray(rho, dtype=np.float64) ** (p - 1.0)
+    return fac[:, None, None] / float(N) ** 3 * element_energies(level, U, Ke, x0, D)
 
 
 def solve_cell(vox: np.ndarray, kind: str = "elastic", E: float = 1.0, nu: float = 0.3,

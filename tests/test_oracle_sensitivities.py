@@ -5,7 +5,9 @@ derivative of C^H with respect to a scalar stiffness factor s_e of element e. C^
 minimum of the cell energy over periodic fields, so that derivative is the element's
 energy at the minimiser (no field-derivative term): it is checked here by central finite
 differences of brute-force (dense pseudo-inverse) solves with s_e = 1 +- h, which share no
-step with the energy formula. The sum over elements returns p C^H exactly.
+step with the energy formula. The sum over elements returns p C^H exactly. At intermediate densities rho_e in (0, 1)
+the derivative with respect to rho_e itself is checked by central finite differences of
+brute-force solves with the coefficients rho_min + rho^p.
 """
 import numpy as np
 import pytest
@@ -60,3 +62,39 @@ def test_solid_cell_sensitivity_is_uniform():
     U = np.zeros((lev.num_nodes * D, NC))
     sens = solve.sensitivities(lev, U, Ke, x0, D, 3.0)
     assert np.allclose(sens, 3.0 / 64.0 * C0[None], rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+def test_simp_sensitivity_at_intermediate_densities(kind):
+    vox = _cell(4, 12)
+    Ke, x0, D, NC, C0 = fe.physics(kind, 1.0, 0.3, 1.0)
+    lev = Level(vox.astype(bool))
+    rng = np.random.default_rng(21)
+    rho = rng.uniform(0.2, 0.95, lev.num_elements)
+    rho_min, p = 1e-3, 3.0
+    U, C = solve.brute_force(vox, kind, coef=solve.simp_coef(lev, rho, rho_min, p))
+    sens = solve.sensitivities(lev, U, Ke, x0, D, p, rho=rho)
+    h = 1e-5
+    for e in rng.choice(lev.num_elements, size=3, replace=False):
+        r = rho.copy()
+        r[e] += h
+        _, Cp = solve.brute_force(vox, kind, coef=solve.simp_coef(lev, r, rho_min, p))
+        r[e] -= 2 * h
+        _, Cm = solve.brute_force(vox, kind, coef=solve.simp_coef(lev, r, rho_min, p))
+        fd = (Cp - Cm) / (2 * h)
+        assert np.abs(sens[e] - fd).max() <= 1e-6 * max(np.abs(sens[e]).max(), 1e-4), (e, sens[e], fd)
+    # the sum rule with coefficients: sum_e rho_e^(1-p) s_e / p * dC/drho_e = C^H
+    s_e = rho_min + rho ** p
+    back = (s_e / (p * rho ** (p - 1.0)))[:, None, None] * sens
+    assert np.allclose(back.sum(axis=0), C, rtol=1e-11, atol=1e-14)
+
+
+def test_simp_coefficients_of_uniform_density_scale_the_tensor():
+    """A uniform density rho on every element scales C^H by rho_min + rho^p exactly
+    (the system K u = f scales as a whole, u is unchanged)."""
+    vox = lattices.tpms_network("gyroid", 8, 0.4)
+    lev = Level(vox.astype(bool))
+    base = solve.solve_cell(vox, "elastic")["CH"]
+    rho = np.full(lev.num_elements, 0.7)
+    C = solve.solve_cell(vox, "elastic", coef=solve.simp_coef(lev, rho, 1e-3, 3.0))["CH"]
+    assert np.allclose(C, (1e-3 + 0.7 ** 3) * base, rtol=1e-9, atol=1e-14)
