@@ -205,13 +205,28 @@ gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
 gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                           double k, const double* u, double* CH_out);
 
+/* Element densities of the SIMP interpolation (App. F.3): element e of level 0 (canonical
+   element order, gmt_element_coords) gets the material C_e = (rho_min + rho_e^p) C0
+   (kappa_e likewise). rho: double[n_elems] with every rho_e in [0, 1], host memory if
+   rho_on_device == 0, else device memory; read during the call. rho_min >= 0, simp_p > 0,
+   and every coefficient rho_min + rho_e^p must be positive. rho == NULL returns to the binary
+   design (every active element C0). The densities stay with the hierarchy; the operators of
+   Sec. 4.6 (level-0 operator, element-local Galerkin products) are rebuilt with them on the
+   next gmt_prepare / gmt_solve, and gmt_homogenize / gmt_sensitivities use them. The stored
+   solution is discarded. With densities the level-0 operator is applied from stored
+   per-node stencils (as the coarse levels are) instead of being formed from the octant
+   masks. Errors: GMT_ERR_ARG (bad values), GMT_ERR_OOM, GMT_ERR_CUDA. */
+gmt_status gmt_set_densities(gmt_hierarchy* h, const double* rho, int rho_on_device,
+                             double rho_min, double simp_p);
+
 /* Inverse-homogenization sensitivities (App. F.3): for the SIMP interpolation
    C_e = (rho_min + rho_e^p) C0, dC^H_IJ / d rho_e = p rho_e^(p-1) / |Omega|
-   (x0^I - u_e^I)^T K0 (x0^J - u_e^J), evaluated for the solid elements of this hierarchy's
-   binary design (rho_e = 1, so the factor is p / N^3). simp_p: the penalisation p (> 0).
-   u: device canonical field, or NULL for the field of the last gmt_solve. dCH_out: device,
-   caller-owned double[n_elems][M][M] in canonical element order (gmt_element_coords,
-   level 0), symmetric in (I, J). Summed over the elements it equals p C^H. */
+   (x0^I - u_e^I)^T K0 (x0^J - u_e^J), u the solution for the current densities (the binary
+   design, rho_e = 1 and factor p / N^3, when none are set). simp_p: the penalisation p
+   (> 0; with densities it must equal the p given to gmt_set_densities). u: device canonical
+   field, or NULL for the field of the last gmt_solve. dCH_out: device, caller-owned
+   double[n_elems][M][M] in canonical element order (gmt_element_coords, level 0), symmetric
+   in (I, J). Summed over the elements of the binary design it equals p C^H. */
 gmt_status gmt_sensitivities(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                              double k, double simp_p, const double* u, double* dCH_out);
 

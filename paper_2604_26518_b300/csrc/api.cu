@@ -146,6 +146,7 @@ gmt_status gmt_build_hierarchy(const uint8_t* voxels, int res, int voxels_on_dev
     h->geo.bind(h->stream);
     h->op.bind(h->stream);
     h->work.bind(h->stream);
+    h->dn.bind(h->stream);
     h->opts = o;
     h->N = res;
     h->L = L;
@@ -178,6 +179,7 @@ gmt_status gmt_set_stream(gmt_hierarchy* h, void* stream) {
   h->geo.bind(h->stream);
   h->op.bind(h->stream);
   h->work.bind(h->stream);
+  h->dn.bind(h->stream);
   return GMT_OK;
   GMT_API_END
 }
@@ -403,11 +405,26 @@ gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, doubl
   GMT_API_END
 }
 
+gmt_status gmt_set_densities(gmt_hierarchy* h, const double* rho, int rho_on_device,
+                             double rho_min, double simp_p) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  if (rho)
+    GMT_REQUIRE(std::isfinite(rho_min) && rho_min >= 0.0 && std::isfinite(simp_p) && simp_p > 0.0,
+                GMT_ERR_ARG, "densities need rho_min >= 0 and simp_p > 0");
+  ensure_device(h);
+  gmt::set_densities(h, rho, rho_on_device != 0, rho_min, simp_p);
+  return GMT_OK;
+  GMT_API_END
+}
+
 gmt_status gmt_sensitivities(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                              double k, double simp_p, const double* u, double* dCH_out) {
   GMT_API_BEGIN
   GMT_REQUIRE(h && dCH_out, GMT_ERR_ARG, "null argument");
   GMT_REQUIRE(std::isfinite(simp_p) && simp_p > 0.0, GMT_ERR_ARG, "simp_p must be > 0");
+  GMT_REQUIRE(!h->dens || simp_p == h->simp_p, GMT_ERR_ARG,
+              "simp_p %g differs from the p %g given with the densities", simp_p, h->simp_p);
   ensure_device(h);
   const bool stored = u == nullptr;
   if (stored) GMT_REQUIRE(h->have_solution, GMT_ERR_STATE, "no stored solution");

@@ -162,6 +162,8 @@ struct Level {
                                 // at this slot (level 1: child mask; >= 2: element id), -1
   int* elem_slot = nullptr;     // n_elems -> slot of the element's origin (canonical order)
   int* slot_elem = nullptr;     // level 0, lazy: slot -> canonical element or -1
+  int* kidx_el = nullptr;       // level 1 with element densities: slot -> element id (the
+                                // level's matrices are then stored per element, not per mask)
   // material-dependent operator data (device)
   double* K64 = nullptr;        // level 1: [256][MM] table; level >= 2: [n_elems][MM]
   float* K32 = nullptr;
@@ -258,14 +260,31 @@ struct gmt_hierarchy {
   // split-column reductions: per-block (sum, compensation) pairs and arrival tickets
   double* red_scratch = nullptr;
   unsigned* red_ticket = nullptr;
+  // element densities of the SIMP interpolation (gmt_set_densities): C_e = s_e C0 with
+  // s_e = rho_min + rho_e^p. Per level-0 slot (the element whose origin is the slot; 0 where
+  // there is none): s_e in FP64 and FP32 and rho_e. With densities the level-0 operator is
+  // stored per node (like the coarse levels) and the level-0 load is kept as a vector.
+  bool dens = false;
+  gmt::Arena dn;
+  double* coef64 = nullptr;
+  float* coef32 = nullptr;
+  double* rho64 = nullptr;
+  double rho_min = 0.0, simp_p = 0.0;
+  double coef_sum = 0.0, coef_sum2 = 0.0;   // sum of s_e and of s_e^2 over the elements
+  double* f0_64 = nullptr;   // level-0 load f = sum_e s_e A_e^T K_e x0 (slot layout; op arena)
+  float* f0_32 = nullptr;
 };
 
 namespace gmt {
+// element-matrix index of the slots of a level as the operator kernels read it
+inline const int* op_kidx(const Level& l) { return l.kidx_el ? l.kidx_el : l.kidx; }
 // hierarchy.cu
 void build_hierarchy(gmt_hierarchy* h, const uint8_t* vox, bool on_device);
 int choose_levels(int n, int coarsest_max);
 // operators.cu
 void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double k);
+void set_densities(gmt_hierarchy* h, const double* rho, bool on_device, double rho_min,
+                   double p);
 void build_coarse_inverse64(gmt_hierarchy* h);
 // solver.cu
 void free_workspace(gmt_hierarchy* h);

@@ -309,12 +309,103 @@ __global__ void k_galerkin_elem(int D, int nc, const int* __restrict__ elem_slot
   }
 }
 
-// D x D block-diagonal inverse of a coarse operator at every active slot
+// ------------------------------------------------------------------ element densities
+// s_e = rho_min + rho_e^p (SIMP, App. F.3) at the level-0 slot of each element's origin
+__global__ void k_set_density(int64_t ne, const int* __restrict__ elem_slot,
+                              const double* __restrict__ rho, double rho_min, double p,
+                              double* __restrict__ c64, float* __restrict__ c32,
+                              double* __restrict__ r64) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int64_t s = elem_slot[e];
+  const double r = rho[e];
+  const double c = rho_min + pow(r, p);
+  c64[s] = c;
+  c32[s] = (float)c;
+  r64[s] = r;
+}
+
+// level 1 with densities: element matrices indexed by element id at the element's origin
+__global__ void k_kidx_el(int64_t ne, const int* __restrict__ elem_slot, int* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ne) out[elem_slot[e]] = (int)e;
+}
+
+// level 1 with densities: K(E) = sum over active children c of s_c P_c^T K_e P_c, with
+// Q[c] = P_c^T K_e P_c and s_c the coefficient of the level-0 element at child position c
+// (the Galerkin product is linear in the child matrices)
+__global__ void k_galerkin_l1_coef(int D, int nc, const int* __restrict__ elem_slot,
+                                   const int* __restrict__ cbxyz, bool cdense,
+                                   const uint8_t* __restrict__ cchild, int nf, int fnbx,
+                                   const int* __restrict__ fbmap, bool fdense,
+                                   const double* __restrict__ fcoef, const double* __restrict__ Q,
+                                   double* __restrict__ K64, float* __restrict__ K32) {
+  const int MM = 64 * D * D;
+  const int64_t e = blockIdx.x;
+  const int t = threadIdx.x;
+  __shared__ double sc[8];
+  int X, Y, Z;
+  slot_coords(elem_slot[e], nc, cdense, cbxyz, X, Y, Z);
+  const unsigned cm = cchild[X + (int64_t)nc * (Y + (int64_t)nc * Z)];
+  if (t < 8) {
+    double v = 0.0;
+    if ((cm >> t) & 1) {
+      const int fx = 2 * X + (t & 1), fy = 2 * Y + ((t >> 1) & 1), fz = 2 * Z + ((t >> 2) & 1);
+      v = fcoef[site_slot(fx, fy, fz, nf, fnbx, fbmap, fdense)];
+    }
+    sc[t] = v;
+  }
+  __syncthreads();
+  if (t >= MM) return;
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (sc[c] != 0.0) acc += sc[c] * Q[(int64_t)c * MM + t];
+  K64[e * MM + t] = acc;
+  K32[e * MM + t] = (float)acc;
+}
+
+// level-0 load with densities: f_n = sum over active incident elements e = n - a of
+// s_e (K_e x0)[a], written in the slot layout in FP64 and FP32
+template <int D, int M>
+__global__ void k_fine_load(int n, int nbx, const int* __restrict__ bxyz,
+                            const int* __restrict__ bmap, bool dense, int64_t nslots,
+                            const uint8_t* __restrict__ mask, const double* __restrict__ coef,
+                            const double* __restrict__ Fe, double* __restrict__ f64,
+                            float* __restrict__ f32) {
+  constexpr int C = D * M;
+  const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslots) return;
+  const unsigned mk = mask[sl];
+  double f[C];
+#pragma unroll
+  for (int v = 0; v < C; ++v) f[v] = 0.0;
+  if (mk) {
+    int x, y, z;
+    slot_coords(sl, n, dense, bxyz, x, y, z);
+    for (int a = 0; a < 8; ++a) {
+      if (!((mk >> a) & 1u)) continue;
+      const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+      const double sc =
+          coef[site_slot((x - ax + n) % n, (y - ay + n) % n, (z - az + n) % n, n, nbx, bmap, dense)];
+#pragma unroll
+      for (int v = 0; v < C; ++v) f[v] += sc * Fe[(a * D + v / M) * M + v % M];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < C; ++v) {
+    f64[vaddr(sl, v, C)] = f[v];
+    f32[vaddr(sl, v, C)] = (float)f[v];
+  }
+}
+
+// D x D block-diagonal inverse of a stored operator at every active slot; coef (nullable,
+// per slot of the element's origin) scales each element matrix (level 0 with densities)
 __global__ void k_diag_inv(int D, int n, int nbx, const int* __restrict__ bxyz,
                            const int* __restrict__ bmap, bool dense, int64_t nslots,
                            const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
-                           const double* __restrict__ K, double* __restrict__ d64,
-                           float* __restrict__ d32) {
+                           const double* __restrict__ K, const double* __restrict__ coef,
+                           double* __restrict__ d64, float* __restrict__ d32) {
   const int R = 8 * D, MM = R * R;
   int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslots) return;
@@ -329,8 +420,9 @@ __global__ void k_diag_inv(int D, int n, int nbx, const int* __restrict__ bxyz,
           ez = (z - ((a >> 2) & 1) + n) % n;
       int64_t es = site_slot(ex, ey, ez, n, nbx, bmap, dense);
       const double* Kc = K + (int64_t)kidx[es] * MM;
+      const double sc = coef ? coef[es] : 1.0;
       for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j) A[i * D + j] += Kc[(a * D + i) * R + a * D + j];
+        for (int j = 0; j < D; ++j) A[i * D + j] += sc * Kc[(a * D + i) * R + a * D + j];
     }
   }
   double Inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -367,8 +459,8 @@ __global__ void k_coarse_assemble(int D, int level, int n, int nbx, const int* _
                                   const int* __restrict__ canon_slot,
                                   const int* __restrict__ slot_canon,
                                   const int* __restrict__ kidx, const double* __restrict__ K,
-                                  const double* __restrict__ Ke, int64_t nn, int64_t m,
-                                  double* __restrict__ A) {
+                                  const double* __restrict__ Ke, const double* __restrict__ coef,
+                                  int64_t nn, int64_t m, double* __restrict__ A) {
   const int R = 8 * D, MM = R * R;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nn * 27) return;
@@ -387,14 +479,16 @@ __global__ void k_coarse_assemble(int D, int level, int n, int nbx, const int* _
     int ex = (x - ax + n) % n, ey = (y - ay + n) % n, ez = (z - az + n) % n;
     if (!eflag[ex + (int64_t)n * (ey + (int64_t)n * ez)]) continue;
     const double* Kc;
+    double sc = 1.0;
     if (level == 0) {
       Kc = Ke;
+      if (coef) sc = coef[site_slot(ex, ey, ez, n, nbx, bmap, dense)];
     } else {
       int64_t es = site_slot(ex, ey, ez, n, nbx, bmap, dense);
       Kc = K + (int64_t)kidx[es] * MM;
     }
     for (int p = 0; p < D; ++p)
-      for (int q = 0; q < D; ++q) S[p * D + q] += Kc[(a * D + p) * R + b * D + q];
+      for (int q = 0; q < D; ++q) S[p * D + q] += sc * Kc[(a * D + p) * R + b * D + q];
     any = true;
   }
   if (!any) return;
@@ -626,8 +720,11 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   for (Level& l : h->lv) {
     l.K64 = l.S64 = l.dinv64 = nullptr;
     l.K32 = l.S32 = l.dinv32 = nullptr;
+    l.kidx_el = nullptr;
     l.lmax = 0.0;
   }
+  h->f0_64 = nullptr;
+  h->f0_32 = nullptr;
   h->prepared = false;
   Material& mt = h->mat;
   mt = Material();
@@ -653,10 +750,12 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   std::memcpy(mt.Fe, host.data() + MM, R * M * sizeof(double));
   std::memcpy(mt.X0, host.data() + MM + R * M, R * M * sizeof(double));
   std::memcpy(mt.C0, host.data() + MM + 2 * R * M, M * M * sizeof(double));
+  // gross load norm sqrt(sum_e ||s_e K_e x0||^2) per case (s_e = 1 without densities)
+  const double ss2 = h->dens ? h->coef_sum2 : (double)h->lv[0].n_elems;
   for (int m = 0; m < M; ++m) {
     double s2 = 0.0;
     for (int r = 0; r < R; ++r) s2 += mt.Fe[r * M + m] * mt.Fe[r * M + m];
-    mt.gross[m] = std::sqrt((double)h->lv[0].n_elems * s2);
+    mt.gross[m] = std::sqrt(ss2 * s2);
   }
   h->Ke64 = h->op.alloc<double>(MM);
   h->Ke32 = h->op.alloc<float>(MM);
@@ -675,9 +774,23 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     k_child_products<<<dim3(8, 1), MM, 0, s>>>(h->Ke64, D, Q);
     GMT_LAUNCH_CHECK();
     Level& l1 = h->lv[1];
-    l1.K64 = h->op.alloc<double>(256 * (size_t)MM);
-    l1.K32 = h->op.alloc<float>(256 * (size_t)MM);
-    k_mask_table<<<dim3(256, 1), 256, 0, s>>>(Q, MM, l1.K64, l1.K32);
+    if (h->dens) {
+      // per element: the child coefficients weight the 8 child products
+      l1.K64 = h->op.alloc<double>(l1.n_elems * (size_t)MM);
+      l1.K32 = h->op.alloc<float>(l1.n_elems * (size_t)MM);
+      l1.kidx_el = h->op.alloc<int>(l1.nslots);
+      GMT_CUDA(cudaMemsetAsync(l1.kidx_el, 0xff, l1.nslots * sizeof(int), s));
+      k_kidx_el<<<grid_for(l1.n_elems, 256), 256, 0, s>>>(l1.n_elems, l1.elem_slot, l1.kidx_el);
+      GMT_LAUNCH_CHECK();
+      const Level& l0 = h->lv[0];
+      k_galerkin_l1_coef<<<(unsigned)l1.n_elems, MM, 0, s>>>(
+          D, l1.n, l1.elem_slot, l1.brick_xyz, l1.dense, l1.child, l0.n, l0.nbx, l0.brick_map,
+          l0.dense, h->coef64, Q, l1.K64, l1.K32);
+    } else {
+      l1.K64 = h->op.alloc<double>(256 * (size_t)MM);
+      l1.K32 = h->op.alloc<float>(256 * (size_t)MM);
+      k_mask_table<<<dim3(256, 1), 256, 0, s>>>(Q, MM, l1.K64, l1.K32);
+    }
     GMT_LAUNCH_CHECK();
   }
   for (int l = 2; l < h->L; ++l) {
@@ -685,7 +798,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     Level& f = h->lv[l - 1];
     c.K64 = h->op.alloc<double>(c.n_elems * (size_t)MM);
     c.K32 = h->op.alloc<float>(c.n_elems * (size_t)MM);
-    if (l == 2) {
+    if (l == 2 && !h->dens) {
       // 8 x 8 products P_c^T Q[c'] P_c, then the 8 x 256 table T2[c][m]
       double* Q2 = tmp.alloc<double>(64 * (size_t)MM);
       k_child_products<<<dim3(8, 8), MM, 0, s>>>(Q, D, Q2);
@@ -699,18 +812,45 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     } else {
       k_galerkin_elem<<<(unsigned)c.n_elems, MM, 0, s>>>(D, c.n, c.elem_slot, c.brick_xyz,
                                                          c.dense, c.child, f.n, f.nbx,
-                                                         f.brick_map, f.dense, f.kidx, f.K64,
+                                                         f.brick_map, f.dense, op_kidx(f), f.K64,
                                                          c.K64, c.K32);
     }
     GMT_LAUNCH_CHECK();
+  }
+  if (h->dens) {
+    // level 0 with densities: block-diagonal inverses, the load vector and (unless level 0
+    // is the coarsest) the per-node stencils, like a coarse level
+    Level& l0 = h->lv[0];
+    l0.dinv64 = h->op.alloc<double>(l0.nslots * D * D);
+    l0.dinv32 = h->op.alloc<float>(l0.nslots * D * D);
+    k_diag_inv<<<grid_for(l0.nslots, 128), 128, 0, s>>>(D, l0.n, l0.nbx, l0.brick_xyz,
+                                                        l0.brick_map, l0.dense, l0.nslots, l0.mask,
+                                                        l0.kidx, h->Ke64, h->coef64, l0.dinv64,
+                                                        l0.dinv32);
+    GMT_LAUNCH_CHECK();
+    double* Fe = tmp.alloc<double>(R * M);
+    GMT_CUDA(cudaMemcpyAsync(Fe, mt.Fe, R * M * sizeof(double), cudaMemcpyHostToDevice, s));
+    h->f0_64 = h->op.alloc<double>(l0.nslots * mt.C);
+    h->f0_32 = h->op.alloc<float>(l0.nslots * mt.C);
+    if (D == 3)
+      k_fine_load<3, 6><<<grid_for(l0.nslots, 128), 128, 0, s>>>(
+          l0.n, l0.nbx, l0.brick_xyz, l0.brick_map, l0.dense, l0.nslots, l0.mask, h->coef64, Fe,
+          h->f0_64, h->f0_32);
+    else
+      k_fine_load<1, 3><<<grid_for(l0.nslots, 128), 128, 0, s>>>(
+          l0.n, l0.nbx, l0.brick_xyz, l0.brick_map, l0.dense, l0.nslots, l0.mask, h->coef64, Fe,
+          h->f0_64, h->f0_32);
+    GMT_LAUNCH_CHECK();
+    GMT_CUDA(cudaStreamSynchronize(s));   // Fe (tmp) is read by the kernel above
+    if (h->L > 1) build_node_stencils(h, 0, false);
   }
   for (int l = 1; l < h->L; ++l) {
     Level& c = h->lv[l];
     c.dinv64 = h->op.alloc<double>(c.nslots * D * D);
     c.dinv32 = h->op.alloc<float>(c.nslots * D * D);
     k_diag_inv<<<grid_for(c.nslots, 128), 128, 0, s>>>(D, c.n, c.nbx, c.brick_xyz, c.brick_map,
-                                                       c.dense, c.nslots, c.mask, c.kidx, c.K64,
-                                                       c.dinv64, c.dinv32);
+                                                       c.dense, c.nslots, c.mask, op_kidx(c),
+                                                       c.K64, nullptr, c.dinv64, c.dinv32);
     GMT_LAUNCH_CHECK();
   }
   for (int l = 1; l + 1 < h->L; ++l) build_node_stencils(h, l, false);
@@ -730,7 +870,8 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     GMT_CUDA(cudaMemsetAsync(h->A64, 0, m * m * sizeof(double), s));
     k_coarse_assemble<<<grid_for(c.n_nodes * 27, 128), 128, 0, s>>>(
         D, lc, c.n, c.nbx, c.brick_xyz, c.brick_map, c.dense, c.eflag, c.canon_slot, c.slot_canon,
-        c.kidx, c.K64, h->Ke64, c.n_nodes, m, h->A64);
+        op_kidx(c), c.K64, h->Ke64, lc == 0 && h->dens ? h->coef64 : nullptr, c.n_nodes, m,
+        h->A64);
     GMT_LAUNCH_CHECK();
     double* ds = tmp.alloc<double>(2);
     k_diag_sum<<<1, 1024, 0, s>>>(h->A64, m, ds);
@@ -748,6 +889,57 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   }
   GMT_CUDA(cudaStreamSynchronize(s));
   h->prepared = true;
+}
+
+// Element densities (App. F.3 SIMP): s_e = rho_min + rho_e^p per level-0 element, stored at
+// the slot of the element's origin; rho == nullptr returns to the binary design. The
+// operators are rebuilt on the next gmt_prepare / gmt_solve.
+void set_densities(gmt_hierarchy* h, const double* rho, bool on_device, double rho_min,
+                   double p) {
+  cudaStream_t s = h->stream;
+  free_workspace(h);
+  h->have_solution = false;
+  h->prepared = false;
+  h->dn.release();
+  h->coef64 = nullptr;
+  h->coef32 = nullptr;
+  h->rho64 = nullptr;
+  h->dens = false;
+  if (!rho) return;
+  const Level& l0 = h->lv[0];
+  const int64_t ne = l0.n_elems;
+  std::vector<double> hr((size_t)ne);
+  GMT_CUDA(cudaMemcpyAsync(hr.data(), rho, ne * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  GMT_CUDA(cudaStreamSynchronize(s));
+  double cs = 0.0, cs2 = 0.0;
+  for (int64_t e = 0; e < ne; ++e) {
+    const double r = hr[(size_t)e];
+    GMT_REQUIRE(r >= 0.0 && r <= 1.0, GMT_ERR_ARG, "density of element %lld is %g, not in [0, 1]",
+                (long long)e, r);
+    const double c = rho_min + std::pow(r, p);
+    GMT_REQUIRE(c > 0.0, GMT_ERR_ARG,
+                "element %lld has a zero coefficient (rho_min = 0 and rho = 0)", (long long)e);
+    cs += c;
+    cs2 += c * c;
+  }
+  h->coef64 = h->dn.alloc<double>(l0.nslots);
+  h->coef32 = h->dn.alloc<float>(l0.nslots);
+  h->rho64 = h->dn.alloc<double>(l0.nslots);
+  GMT_CUDA(cudaMemsetAsync(h->coef64, 0, l0.nslots * sizeof(double), s));
+  GMT_CUDA(cudaMemsetAsync(h->coef32, 0, l0.nslots * sizeof(float), s));
+  GMT_CUDA(cudaMemsetAsync(h->rho64, 0, l0.nslots * sizeof(double), s));
+  double* rd = h->dn.alloc<double>(ne);
+  GMT_CUDA(cudaMemcpyAsync(rd, hr.data(), ne * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_set_density<<<grid_for(ne, 256), 256, 0, s>>>(ne, l0.elem_slot, rd, rho_min, p, h->coef64,
+                                                  h->coef32, h->rho64);
+  GMT_LAUNCH_CHECK();
+  GMT_CUDA(cudaStreamSynchronize(s));
+  h->rho_min = rho_min;
+  h->simp_p = p;
+  h->coef_sum = cs;
+  h->coef_sum2 = cs2;
+  h->dens = true;
 }
 
 }  // namespace gmt

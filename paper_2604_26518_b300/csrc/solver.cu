@@ -54,7 +54,12 @@ __global__ void k_mask_hist(const uint8_t* __restrict__ mask, int64_t n,
 // ||f_m||^2 of the level-0 load, f_n = sum_{a in mask} (K_e x0)[a]: the load of a node
 // depends on its octant mask alone, so the norm is the mask histogram times per-mask norms
 // (FP64 on the host, masks in increasing order)
+static void dens_load_norms2(gmt_hierarchy* h, double* fn2);
 static void load_norms2(gmt_hierarchy* h, double* fn2) {
+  if (h->dens) {
+    dens_load_norms2(h, fn2);
+    return;
+  }
   if (!h->have_hist) {
     const Level& l0 = h->lv[0];
     Arena tmp(h->stream);
@@ -153,6 +158,15 @@ static double* reduce_to(gmt_hierarchy* h, Workspace* w, int level, int K, int s
   double* out = w->red + slot * 32;
   launch_reduce(h, w->part, h->lv[level].nb, K, out);
   return out;
+}
+
+static void fetch(gmt_hierarchy* h, const double* dev, double* host, int n);
+
+// element densities: ||f_m||^2 of the stored level-0 load vector, by a device reduction
+static void dens_load_norms2(gmt_hierarchy* h, double* fn2) {
+  Workspace* w = h->ws;
+  vec_dot(h, 0, P64, h->f0_64, h->f0_64, w->part);
+  fetch(h, reduce_to(h, w, 0, h->mat.M, 1), fn2, h->mat.M);
 }
 
 static void fetch(gmt_hierarchy* h, const double* dev, double* host, int n) {
@@ -686,7 +700,8 @@ void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
   double e[21];
   fetch(h, reduce_to(h, w, 0, K, 0), e, K);
   const double vol = (double)h->N * h->N * h->N;
-  const double ne = pr == P64 ? 0.0 : (double)h->lv[0].n_elems;  // ff path: + n_e C0
+  // ff path: + sum_e s_e C0 (s_e = 1 without densities)
+  const double ne = pr == P64 ? 0.0 : (h->dens ? h->coef_sum : (double)h->lv[0].n_elems);
   for (int I = 0; I < M; ++I)
     for (int J = I; J < M; ++J) {
       const double v = (e[I * M - I * (I - 1) / 2 + (J - I)] + ne * mt.C0[I * M + J]) / vol;
@@ -710,7 +725,9 @@ void sensitivities(gmt_hierarchy* h, const double* u, double simp_p, double* out
       canon_to_ff(h, u, w->hi, w->lo);
     }
   }
-  const double scale = simp_p / ((double)h->N * h->N * h->N);
+  // with densities the factor p rho_e^(p-1) is applied per element by the kernel
+  const double vol = (double)h->N * h->N * h->N;
+  const double scale = h->dens ? 1.0 / vol : simp_p / vol;
   if (pr == P64) launch_energy_per(h, P64, u64, nullptr, out, scale);
   else launch_energy_per(h, P32, w->hi, w->lo, out, scale);
   GMT_CUDA(cudaStreamSynchronize(h->stream));

@@ -552,11 +552,14 @@ __global__ void __launch_bounds__(64)
 // are contiguous
 // T = float: the FP32 stencils summed from the FP32 element copies (the stencils are FP32
 // anyway; FP64 sums would cost 1/64 of the FP32 rate on B300); T = double: FP64 throughout.
+// coef (nullable, per slot of the element's origin): element matrices scaled by s_e (level 0
+// with densities, where every element shares K_e)
 template <typename T, int D>
 __global__ void k_node_stencil(int n, int nbx, const int* __restrict__ bxyz,
                                const int* __restrict__ bmap, bool dense, int64_t nslots,
                                const uint8_t* __restrict__ mask, const int* __restrict__ kidx,
-                               const T* __restrict__ K, T* __restrict__ S) {
+                               const T* __restrict__ K, const T* __restrict__ coef,
+                               T* __restrict__ S) {
   constexpr int R = 8 * D, MM = R * R, DD = D * D, W = Vec16<T>::n;
   constexpr int G = node_stencil_groups<T>(DD);
   const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -565,14 +568,17 @@ __global__ void k_node_stencil(int n, int nbx, const int* __restrict__ bxyz,
   int x = 0, y = 0, z = 0;
   if (mk) slot_coords(sl, n, dense, bxyz, x, y, z);
   const T* Ka[8];   // element matrix of each incident element (nullptr when inactive)
+  T sa[8];          // its scale
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     Ka[a] = nullptr;
+    sa[a] = T(1);
     if ((mk >> a) & 1u) {
       const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
       const int64_t es = site_slot((x - ax + n) % n, (y - ay + n) % n, (z - az + n) % n, n, nbx,
                                    bmap, dense);
       Ka[a] = K + (int64_t)kidx[es] * MM;
+      if (coef) sa[a] = coef[es];
     }
   }
 #pragma unroll 1
@@ -590,7 +596,7 @@ __global__ void k_node_stencil(int n, int nbx, const int* __restrict__ bxyz,
 #pragma unroll
       for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) Sd[i * D + j] += Ka[a][(a * D + i) * R + bb * D + j];
+        for (int j = 0; j < D; ++j) Sd[i * D + j] += sa[a] * Ka[a][(a * D + i) * R + bb * D + j];
     }
 #pragma unroll
     for (int k = 0; k < DD; ++k) S[node_stencil_index(sl, d * DD + k, G, W)] = Sd[k];
@@ -604,31 +610,36 @@ void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
   const int D = h->mat.D;
   const unsigned g = grid_for(lv.nslots, 128);
   cudaStream_t s = h->stream;
+  // level 0 (densities only): every element carries s_e K_e
+  const bool fine = level == 0;
+  const int* kidx = op_kidx(lv);
   if (fp64) {
-    if (lv.S64) return;
     const size_t cnt = (size_t)lv.nslots * node_stencil_groups<double>(D * D) * 2;
     lv.S64 = h->op.alloc<double>(cnt);
     GMT_CUDA(cudaMemsetAsync(lv.S64, 0, cnt * sizeof(double), s));
+    const double* K = fine ? h->Ke64 : lv.K64;
+    const double* cf = fine ? h->coef64 : nullptr;
     if (D == 3)
       k_node_stencil<double, 3><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
-                                                  lv.dense, lv.nslots, lv.mask, lv.kidx,
-                                                  lv.K64, lv.S64);
+                                                  lv.dense, lv.nslots, lv.mask, kidx, K, cf,
+                                                  lv.S64);
     else
       k_node_stencil<double, 1><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
-                                                  lv.dense, lv.nslots, lv.mask, lv.kidx,
-                                                  lv.K64, lv.S64);
+                                                  lv.dense, lv.nslots, lv.mask, kidx, K, cf,
+                                                  lv.S64);
   } else {
-    if (lv.S32) return;
     const size_t cnt = (size_t)lv.nslots * node_stencil_groups<float>(D * D) * 4;
     lv.S32 = h->op.alloc<float>(cnt);
     GMT_CUDA(cudaMemsetAsync(lv.S32, 0, cnt * sizeof(float), s));
+    const float* K = fine ? h->Ke32 : lv.K32;
+    const float* cf = fine ? h->coef32 : nullptr;
     if (D == 3)
       k_node_stencil<float, 3><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
-                                                 lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K32,
+                                                 lv.dense, lv.nslots, lv.mask, kidx, K, cf,
                                                  lv.S32);
     else
       k_node_stencil<float, 1><<<g, 128, 0, s>>>(lv.n, lv.nbx, lv.brick_xyz, lv.brick_map,
-                                                 lv.dense, lv.nslots, lv.mask, lv.kidx, lv.K32,
+                                                 lv.dense, lv.nslots, lv.mask, kidx, K, cf,
                                                  lv.S32);
   }
   GMT_LAUNCH_CHECK();
@@ -676,6 +687,8 @@ struct FFArgs {
   const float* lo;
   float* out;
   double* part;
+  const float* kmat;   // STORED: per-node stencils [brick][group][64][4]
+  const float* f;      // STORED: the level-0 load (slot layout)
   FineC<float, D, M> fc;
 };
 
@@ -685,7 +698,9 @@ struct FFArgs {
 // of a smooth field are O(1) while u itself grows with N, so FP32 arithmetic on them keeps
 // the residual accurate to ~1e-7 of the load without FP64 instructions.
 // ZERO: u = 0 (a zero start), r = f without staging or the stencil.
-template <int D, int M, bool ZERO>
+// STORED (element densities): S_n(d) read from the stored per-node stencils and f from the
+// stored load, instead of both formed from the octant mask.
+template <int D, int M, bool ZERO, bool STORED = false>
 __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<D, M> p) {
   using V = float4;
   constexpr int C = D * M, R = 8 * D, G = (C + 3) / 4;
@@ -705,7 +720,7 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   const int q0 = own_q0(t), loc = own_local(t);
   const int64_t slot = b * 64 + loc;
   const unsigned mk = p.mask[slot];
-  const bool warp_full = __all_sync(0xffffffffu, mk == 0xffu);  // every lane votes
+  const bool warp_full = !STORED && __all_sync(0xffffffffu, mk == 0xffu);  // every lane votes
   float acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = 0.f;
@@ -730,7 +745,19 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
       float S[D * D];
       f2_t S2[D * D];
-      if (warp_full) {
+      if constexpr (STORED) {
+        constexpr int NG = node_stencil_groups<float>(D * D) * 4;
+        const float* sten = p.kmat + b * (NG * 64) + loc * 4;
+#pragma unroll
+        for (int k = 0; k < D * D; ++k) {
+          const int c = d * D * D + k;
+          S[k] = sten[(c / 4) * 256 + c % 4];
+        }
+        if constexpr (PK) {
+#pragma unroll
+          for (int k = 0; k < D * D; ++k) S2[k] = f2_pack(S[k], S[k]);
+        }
+      } else if (warp_full) {
 #pragma unroll
         for (int k = 0; k < D * D; ++k) {
           if constexpr (PK) S2[k] = p.fc.Sf2[d * D * D + k];
@@ -807,8 +834,13 @@ __global__ void __launch_bounds__(64) k_resid_ff(const __grid_constant__ FFArgs<
   for (int v = 0; v < C; ++v) {
     const int i = v / M, m = v % M;
     float fv = 0.f;
+    if constexpr (STORED) {
+      fv = p.f[base + v * 64];
+    } else {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) fv += (((mk >> a) & 1u) ? 1.f : 0.f) * p.fc.Fe[(a * D + i) * M + m];
+      for (int a = 0; a < 8; ++a)
+        fv += (((mk >> a) & 1u) ? 1.f : 0.f) * p.fc.Fe[(a * D + i) * M + m];
+    }
     const float r = mk ? fv - acc[v] : 0.f;
     p.out[base + v * 64] = r;
     nrm[m] += r * r;
@@ -1141,6 +1173,11 @@ struct EnArgs {
   const int* slot_elem;
   double scale;
   double C0[M * M];
+  // element densities (nullable): the block sums weight element e by coef[slot] = s_e; the
+  // per-element output is multiplied by simp_p rho[slot]^(simp_p - 1) (App. F.3)
+  const double* coef;
+  const double* rho;
+  double simp_p;
 };
 
 // Per active element e (origin slot n) and load cases I <= J, the energy
@@ -1293,20 +1330,22 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
   if constexpr (PER) {
     if (!act) return;
     const int64_t el = p.slot_elem[b * 64 + loc];
+    const double fac = p.rho ? p.simp_p * pow(p.rho[b * 64 + loc], p.simp_p - 1.0) : 1.0;
 #pragma unroll
     for (int I = 0; I < M; ++I)
 #pragma unroll
       for (int J = I; J < M; ++J) {
         double v = (double)es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t];
         if constexpr (FF) v += p.C0[I * M + J];
-        v *= p.scale;
+        v *= p.scale * fac;
         p.per[(el * M + I) * M + J] = v;
         p.per[(el * M + J) * M + I] = v;
       }
   } else {
     ES e[K];
+    const ES w = (act && p.coef) ? (ES)p.coef[b * 64 + loc] : ES(1);
 #pragma unroll
-    for (int k = 0; k < K; ++k) e[k] = act ? es[k * 64 + t] : ES(0);
+    for (int k = 0; k < K; ++k) e[k] = act ? w * es[k * 64 + t] : ES(0);
     block_partial_64<K, ES>(e, p.part + b * K);
   }
 }
@@ -1732,7 +1771,10 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   p.nbr = lv.brick_nbr;
   p.mask = lv.mask;
   p.kidx = lv.kidx;
-  if (level > 0) build_node_stencils(h, level, sizeof(A) == 8);
+  // level 0 forms its stencil from the octant masks and K_e (KIND 0), unless element
+  // densities are set: then it reads stored per-node stencils like a coarse level (KIND 1)
+  const bool fine = level == 0 && !h->dens;
+  if (!fine) build_node_stencils(h, level, sizeof(A) == 8);
   if constexpr (sizeof(A) == 8) {
     p.kmat = (const A*)lv.S64;
     p.dinv = (const A*)lv.dinv64;
@@ -1751,30 +1793,34 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   p.c1 = (A)va.c1;
   p.c2 = (A)va.c2;
   p.colour = va.colour;
-  const bool fine = level == 0;
   if (fine) fill_fine<A, D, M>(h->mat, p.fc);
+  if (level == 0 && h->dens && p.f == nullptr)   // the stored level-0 load
+    p.f = sizeof(TS) == 8 ? (const TS*)h->f0_64 : (const TS*)h->f0_32;
   const unsigned g = (unsigned)lv.nb;
   cudaStream_t s = h->stream;
   int nvec = 2, cat = level == 1 ? TR_COARSE_ST : TR_COARSE_ST2;
   if (mode == ST_RESID) nvec = va.f ? 3 : 2;
   if (mode == ST_JACOBI) nvec = 3 + (va.aux != nullptr);   // the last sweep also reads K p
   if (mode == ST_CHEB) nvec = 3 + (va.c1 != 0.0) + (va.dout != nullptr);
-  if (fine) {
+  if (level == 0) {
     cat = mode == ST_APPLY ? TR_APPLY0 : (mode == ST_RESID ? (va.f ? TR_RESID0 : TR_OUTER) : TR_SMOOTH0);
   }
   TraceScope ts(&h->tracer, s, cat, (double)lv.n_nodes * nvec * D * M * sizeof(TS));
 #define GMT_ST(KIND, MODE) k_stencil<TS, A, D, M, KIND, MODE><<<g, 64, 0, s>>>(p)
-  const bool sums = fine && va.part != nullptr;   // smoother modes: fused r.z and sums of z
+  // smoother modes at level 0: fused r.z and sums of z
+  const bool sums = level == 0 && va.part != nullptr;
   switch (mode) {
     case ST_APPLY: if (fine) GMT_ST(0, ST_APPLY); else GMT_ST(1, ST_APPLY); break;
     case ST_RESID: if (fine) GMT_ST(0, ST_RESID); else GMT_ST(1, ST_RESID); break;
     case ST_JACOBI:
-      if (sums) k_stencil<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
+      if (sums && fine) k_stencil<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
+      else if (sums) k_stencil<TS, A, D, M, 1, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
       else if (fine) GMT_ST(0, ST_JACOBI);
       else GMT_ST(1, ST_JACOBI);
       break;
     case ST_CHEB:
-      if (sums) k_stencil<TS, A, D, M, 0, ST_CHEB, true><<<g, 64, 0, s>>>(p);
+      if (sums && fine) k_stencil<TS, A, D, M, 0, ST_CHEB, true><<<g, 64, 0, s>>>(p);
+      else if (sums) k_stencil<TS, A, D, M, 1, ST_CHEB, true><<<g, 64, 0, s>>>(p);
       else if (fine) GMT_ST(0, ST_CHEB);
       else GMT_ST(1, ST_CHEB);
       break;
@@ -1815,7 +1861,7 @@ static void diag_t(gmt_hierarchy* h, int level, const void* f, void* out, void* 
   TraceScope ts(&h->tracer, h->stream,
                 level == 0 ? TR_DIAG0 : (level == 1 ? TR_COARSE_ST : TR_COARSE_ST2),
                 (double)lv.n_nodes * (dout ? 3 : 2) * D * M * sizeof(TS));
-  if (level == 0) {
+  if (level == 0 && !h->dens) {
     fill_fine<A, D, M>(h->mat, p.fc);
     k_diag<TS, A, D, M, 0><<<g, 128, 0, h->stream>>>(p, lv.nslots);
   } else {
@@ -1841,9 +1887,20 @@ static void resid_ff_t(gmt_hierarchy* h, const float* hi, const float* lo, float
   p.out = r;
   p.part = part;
   fill_fine<float, D, M>(h->mat, p.fc);
+  if (h->dens) {
+    build_node_stencils(h, 0, false);
+    p.kmat = lv.S32;
+    p.f = h->f0_32;
+  }
   TraceScope ts(&h->tracer, h->stream, TR_OUTER, (double)lv.n_nodes * 3 * D * M * sizeof(float));
-  if (hi == nullptr) k_resid_ff<D, M, true><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
-  else k_resid_ff<D, M, false><<<(unsigned)lv.nb, 64, 0, h->stream>>>(p);
+  const unsigned g = (unsigned)lv.nb;
+  if (h->dens) {
+    if (hi == nullptr) k_resid_ff<D, M, true, true><<<g, 64, 0, h->stream>>>(p);
+    else k_resid_ff<D, M, false, true><<<g, 64, 0, h->stream>>>(p);
+  } else {
+    if (hi == nullptr) k_resid_ff<D, M, true><<<g, 64, 0, h->stream>>>(p);
+    else k_resid_ff<D, M, false><<<g, 64, 0, h->stream>>>(p);
+  }
   GMT_LAUNCH_CHECK();
 }
 
@@ -1964,6 +2021,11 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
   }
   constexpr size_t smem = energy_smem_bytes<A, D, M, FF>();
   TraceScope ts(&h->tracer, h->stream, TR_ENERGY, (double)lv.n_nodes * D * M * 8.0);
+  if (h->dens) {
+    p.coef = h->coef64;
+    p.rho = h->rho64;
+    p.simp_p = h->simp_p;
+  }
   if (per) {
     p.per = per;
     p.slot_elem = level0_slot_elem(h);

@@ -112,6 +112,7 @@ _SIGS = {
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
     "gmt_sensitivities": (_I, [_P, _I, _D, _D, _D, _D, _P, _P]),
+    "gmt_set_densities": (_I, [_P, _P, _I, _D, _D]),
     "gmt_residual": (_I, [_P, _I, _P, _P]),
     "gmt_trace_enable": (_I, [_P, _I]),
     "gmt_trace_query": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -367,6 +368,27 @@ class Hierarchy:
         _check(lib().gmt_homogenize(self._h, physics, E, nu, k, _ptr(ut),
                                     CH.ctypes.data_as(ctypes.c_void_p)), "gmt_homogenize")
         return CH
+
+    def set_densities(self, rho=None, rho_min=1e-3, p=3.0):
+        """SIMP element densities (gmt_set_densities): rho per level-0 element in canonical
+        element order (numpy or torch float64, host or device), or None for the binary
+        design. C_e = (rho_min + rho_e^p) C0."""
+        if rho is None:
+            _check(lib().gmt_set_densities(self._h, None, 0, 0.0, 0.0), "gmt_set_densities")
+            return
+        ne = self.num_elements(0)
+        if isinstance(rho, np.ndarray):
+            r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+            assert r.size == ne, (r.size, ne)
+            ptr, dev, keep = r.ctypes.data, 0, r
+        else:
+            torch = _torch()
+            r = rho.to(torch.float64).contiguous().reshape(-1)
+            assert r.numel() == ne, (r.numel(), ne)
+            ptr, dev, keep = r.data_ptr(), int(r.is_cuda), r
+        _check(lib().gmt_set_densities(self._h, ptr, dev, float(rho_min), float(p)),
+               "gmt_set_densities")
+        del keep
 
     def sensitivities(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, p=3.0, u=None):
         """dC^H / d rho_e per solid element (SIMP penalisation p), a device tensor

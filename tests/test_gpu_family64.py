@@ -1,9 +1,12 @@
 """Converged-oracle parity of a full solve for every generator family at 64^3.
 
 For one seeded 64^3 cell of each family (TPMS networks and plates, BCC / octet trusses,
-spinodal), the library solves the cell problems to r <= 1e-5 and returns C^H; the FP64
-oracle's C^H at r <= 1e-10 is stored in tests/golden/family64.json (written by
-tests/golden/make_family64.py, which calls only the oracle and the seeded generators).
+spinodal; each connected across the cell), the library solves the cell problems to
+r <= 1e-5 and returns C^H; the FP64 oracle's C^H at r <= 1e-10 is stored in
+tests/golden/family64.json (written by tests/golden/make_family64.py, which calls only the
+oracle and the seeded generators). One more cell is degenerate: a Schwarz-P network below
+its percolation threshold (isolated periodic blobs), whose tensors vanish; there the
+relative metric is undefined and C^H is held to 1e-4 of the Voigt bound's scale phi |C0|.
 
 Checks per cell and physics:
   * C^H within 1e-4 of the oracle's, normalised by the largest entry (Sec. 5 error metric
@@ -39,7 +42,8 @@ def _golden():
 
 def _cells():
     g = _golden()
-    return [(i, c["family"]) for i, c in enumerate(g["cells"])]
+    return [(i, c["family"] + ("-degenerate" if c["degenerate"] else ""))
+            for i, c in enumerate(g["cells"])]
 
 
 @pytest.mark.parametrize("kind", ["elastic", "heat"])
@@ -48,7 +52,7 @@ def test_family64_matches_converged_oracle(gmt_lib, idx, family, kind):
     gmt = gmt_lib
     g = _golden()
     rec = g["cells"][idx]
-    vox, desc = L.mixed_cell(g["seed0"] + idx, g["res"], families=(family,))
+    vox, desc = L.mixed_cell(rec["seed"], g["res"], families=(rec["family"],))
     assert int(vox.sum()) == rec["n_solid"]
     C_star = np.array(rec[kind]["CH"])
     ph = gmt.ELASTIC if kind == "elastic" else gmt.HEAT
@@ -56,10 +60,15 @@ def test_family64_matches_converged_oracle(gmt_lib, idx, family, kind):
     st, u, info = h.solve(ph, tol=TOL)
     assert st == gmt.OK, info.as_dict()
     CH = h.homogenize(ph)
+    Ke, x0, D, M, C0 = fe.physics(kind)
+    if rec["degenerate"]:
+        scale = vox.mean() * np.abs(C0).max()
+        assert np.abs(C_star).max() <= 1e-10 * scale
+        assert np.abs(CH).max() <= 1e-4 * scale, (family, kind, CH)
+        return
     err = np.abs(CH - C_star).max() / np.abs(C_star).max()
-    assert err <= 1e-4, (family, kind, err)
+    assert err <= 1e-4, (family, kind, err, CH, C_star)
 
-    Ke, x0, D, M, _ = fe.physics(kind)
     lev = Level(vox.astype(bool))
     U = u.detach().cpu().numpy().reshape(-1, M)
     F = solve.cancel_rounding(solve.load(lev, Ke, x0, D), solve.gross_load_norm(lev, Ke, x0, D))
