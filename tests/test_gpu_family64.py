@@ -77,7 +77,10 @@ def test_family64_matches_converged_oracle(gmt_lib, idx, family, kind):
     res = np.where(fn > 0, np.linalg.norm(R, axis=0) / np.where(fn > 0, fn, 1), 0)
     assert res.max() <= TOL * 1.02, (family, kind, res)
     C_of_gpu = solve.homogenize_chunked(lev, U, Ke, x0, D)
-    assert np.abs(CH - C_of_gpu).max() <= 2e-7 * np.abs(C_star).max()
+    # the float-float energy path rounds each element's terms (of size ~|C0|) once in FP32;
+    # summed over the phi N^3 elements that is an absolute error ~1e-7 phi |C0|, which on
+    # soft cells (spinodal: C^H ~ phi |C0| / 20) exceeds 1e-7 of |C^H| itself
+    assert np.abs(CH - C_of_gpu).max() <= 2e-7 * vox.mean() * np.abs(C0).max()
     diag = np.diag(C_star)
     excess = np.diag(C_of_gpu) - diag
     # the energy of any field is at least the minimum's (up to the oracle's 1e-10 residual)
