@@ -4,7 +4,8 @@
 
 Each csrc/*.cu is compiled to an object with nvcc (in parallel), then linked into
 paper_2604_26518_b300/libgmt.so. A rebuild happens only when a source or header is newer
-than the library (or with --force).
+than the library (or with --force); then only the objects older than their source or a
+header are recompiled.
 """
 from __future__ import annotations
 
@@ -41,8 +42,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def _obj(src: str) -> str:
+    return os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+
+
+def _stale(src: str) -> bool:
+    """An object is rebuilt when it is missing or older than its source or any header."""
+    obj = _obj(src)
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "gmt.h")]
+    return any(os.path.getmtime(d) > t for d in [src] + headers)
+
+
 def _compile(src: str, verbose: bool, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+    obj = _obj(src)
     cmd = [NVCC, *ARCH, *FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
@@ -58,8 +73,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    todo = [s for s in _sources() if force or extra or _stale(s)]
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, list(extra)), _sources()))
+        list(ex.map(lambda s: _compile(s, verbose, list(extra)), todo))
+    objs = [_obj(s) for s in _sources()]
+    for stale in glob.glob(os.path.join(BUILD, "*.o")):
+        if stale not in objs:
+            os.remove(stale)
     cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
