@@ -34,35 +34,21 @@ namespace gmt {
 // SUMS (smoother modes): also write per-block partials [2M + C]: f . out per case, aux . out
 // per case (0 without aux) and out per value over active nodes (the V-cycle's last sweep:
 // r.z, (K p).z and the mean of z for the Krylov step, without another pass over vectors).
-template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS = false>
-__global__ void __launch_bounds__(64)
-    k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
+// The per-brick work of the stencil kernels, after the tile of brick b (own nodes plus a
+// one-node halo, 16-byte groups of values) is in shared memory: this thread's node gets
+// acc = sum_d S_n(d) u_{n+d} and the mode's epilogue. self: the node's own values; fpre
+// (FPRE): its right-hand side, already loaded.
+template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS, bool FPRE>
+__device__ __forceinline__ void stencil_brick(const StArgs<TS, A, D, M>& p, int64_t b,
+                                              const typename Vec16<A>::type* __restrict__ tile,
+                                              const A (&fpre)[FPRE ? D * M : 1],
+                                              const A (&self)[D * M]) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, DD = D * D;
   constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
   constexpr bool DIFF = MODE == ST_APPLY;
-  __shared__ V tile[G * 216];
-  __shared__ int nb[27];
+  constexpr bool PREF = FPRE;
   const int t = threadIdx.x;
-  const int64_t b = blockIdx.x;
-  if (t < 27) nb[t] = p.nbr[b * 27 + t];
-  __syncthreads();
-  // level-0 smoother sweeps and residuals: the right-hand side of this thread's node is
-  // loaded before the staging so that its latency overlaps the stencil instead of
-  // following it (measured: the level-0 sweep 20 % faster; coarse levels, with more
-  // registers in use, are left as they are)
-  constexpr bool PREF = KIND == 0 && (MODE == ST_JACOBI || MODE == ST_CHEB || MODE == ST_RESID);
-  A fpre[PREF ? C : 1];
-  if constexpr (PREF) {
-    if (p.f != nullptr) {
-      const TS* fo = p.f + b * (64 * C) + own_local(t);
-#pragma unroll
-      for (int v = 0; v < C; ++v) fpre[v] = load_as<A>(fo + v * 64);
-    }
-  }
-  A self[C];
-  stage_tile<TS, A, C>(p.u, b, t, nb, tile, self);
-  __syncthreads();
   const int q0 = own_q0(t);
   const int loc = own_local(t);
   const int64_t slot = b * 64 + loc;
@@ -244,19 +230,16 @@ __global__ void __launch_bounds__(64)
     for (int m = 0; m < M; ++m) nrm[m] = A(0);
 #pragma unroll
     for (int v = 0; v < C; ++v) {
-      A fv;
-      if constexpr (KIND == 0) {
-        if (p.f != nullptr) {
-          fv = fpre[v];
-        } else {  // level-0 load from the mask: f_n = sum_{a in mask} (K_e x0)[a]
-          fv = A(0);
-          const int i = v / M, m = v % M;
+      A fv = A(0);
+      if (p.f != nullptr) {
+        if constexpr (FPRE) fv = fpre[v];
+        else fv = load_as<A>(p.f + base + v * 64);
+      } else if constexpr (KIND == 0) {
+        // level-0 load from the mask: f_n = sum_{a in mask} (K_e x0)[a]
+        const int i = v / M, m = v % M;
 #pragma unroll
-          for (int a = 0; a < 8; ++a)
-            fv += (((mk >> a) & 1u) ? A(1) : A(0)) * p.fc.Fe[(a * D + i) * M + m];
-        }
-      } else {
-        fv = load_as<A>(p.f + base + v * 64);
+        for (int a = 0; a < 8; ++a)
+          fv += (((mk >> a) & 1u) ? A(1) : A(0)) * p.fc.Fe[(a * D + i) * M + m];
       }
       const A r = mk ? fv - acc[v] : A(0);
       p.out[base + v * 64] = store_as<TS>(r);
@@ -316,6 +299,36 @@ __global__ void __launch_bounds__(64)
     }
     if constexpr (SUMS) block_partial_64<2 * M + C, A>(sums, p.part + b * (2 * M + C));
   }
+}
+
+template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS = false>
+__global__ void __launch_bounds__(64)
+    k_stencil(const __grid_constant__ StArgs<TS, A, D, M> p) {
+  using V = typename Vec16<A>::type;
+  constexpr int C = D * M, NV = Vec16<A>::n, G = (C + NV - 1) / NV;
+  __shared__ V tile[G * 216];
+  __shared__ int nb[27];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (t < 27) nb[t] = p.nbr[b * 27 + t];
+  __syncthreads();
+  // level-0 smoother sweeps and residuals: the right-hand side of this thread's node is
+  // loaded before the staging so that its latency overlaps the stencil instead of
+  // following it (measured: the level-0 sweep 20 % faster; coarse levels, with more
+  // registers in use, are left as they are)
+  constexpr bool PREF = KIND == 0 && (MODE == ST_JACOBI || MODE == ST_CHEB || MODE == ST_RESID);
+  A fpre[PREF ? C : 1];
+  if constexpr (PREF) {
+    if (p.f != nullptr) {
+      const TS* fo = p.f + b * (64 * C) + own_local(t);
+#pragma unroll
+      for (int v = 0; v < C; ++v) fpre[v] = load_as<A>(fo + v * 64);
+    }
+  }
+  A self[C];
+  stage_tile<TS, A, C>(p.u, b, t, nb, tile, self);
+  __syncthreads();
+  stencil_brick<TS, A, D, M, KIND, MODE, SUMS, PREF>(p, b, tile, fpre, self);
 }
 
 // first smoothing step from a zero initial guess: out = scale * D^-1 f
