@@ -84,7 +84,8 @@ typedef struct {
   double inner_tol;    /* [0.1] mixed precision: the true residual is recomputed (and replaces the
                           iterated one) whenever the iterated residual fell by this factor */
   int max_inner;       /* [40] with max_outer: at most max_inner * max(1, max_outer) V-cycles */
-  int max_outer;       /* [8] */
+  int max_outer;       /* [40] (1600 V-cycles: spinodal cells of wavenumber 9-10 at 128^3
+                          need 560-1100, in FP64 as in mixed precision) */
   int cycle;           /* [GMT_CYCLE_V] */
   int fp64_fallback;   /* [1] when the mixed-precision solve diverges, gmt_solve solves the
                           cell again in plain FP64 (gmt_info.fp64_fallback reports it) */
@@ -267,8 +268,9 @@ gmt_status gmt_homogenize_dense_noalloc(const uint8_t* voxels, int res, gmt_phys
    6 restriction, 7 prolongation, 8 coarsest solve, 9 C^H energy reduction, 10 vector /
    reduction kernels, 11 hierarchy build, 12 operators (element matrices, Galerkin products,
    block-diagonal inverses, node stencils), 13 coarsest matrix and its inverse, 14 stencils
-   of levels >= 2. */
-#define GMT_TRACE_CATEGORIES 15
+   of levels >= 2, 15 whole V-cycles of gmt_solve (one event pair around each, its bytes 0).
+   on == 2 records category 15 alone, without the per-launch events inside the V-cycles. */
+#define GMT_TRACE_CATEGORIES 16
 gmt_status gmt_trace_enable(gmt_hierarchy* h, int on);   /* on != 0 enables; resets totals */
 /* Totals since enabling (synchronizes the stream): launches, device milliseconds, bytes. */
 gmt_status gmt_trace_query(gmt_hierarchy* h, int category, int64_t* launches, double* ms,

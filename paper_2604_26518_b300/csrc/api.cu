@@ -96,7 +96,7 @@ void gmt_default_options(gmt_options* o) {
   o->krylov = 1;
   o->inner_tol = 0.1;
   o->max_inner = 40;
-  o->max_outer = 8;
+  o->max_outer = 40;
   o->cycle = GMT_CYCLE_V;
   o->fp64_fallback = 1;
   o->nu_coarse = 2;
@@ -453,6 +453,7 @@ gmt_status gmt_trace_enable(gmt_hierarchy* h, int on) {
   GMT_CUDA(cudaStreamSynchronize(h->stream));
   h->tracer.reset();
   h->tracer.on = on != 0;
+  h->tracer.brackets_only = on == 2;
   return GMT_OK;
   GMT_API_END
 }
@@ -475,7 +476,7 @@ const char* gmt_trace_name(int c) {
   static const char* names[gmt::TR_NCAT] = {
       "smooth_l0", "resid_l0", "apply_l0", "outer_resid", "diag_l0", "stencil_l1",
       "restrict", "prolong", "coarse_solve", "energy", "vector", "setup_hierarchy",
-      "setup_operators", "setup_coarse_inverse", "stencil_l2up"};
+      "setup_operators", "setup_coarse_inverse", "stencil_l2up", "vcycle"};
   return (c >= 0 && c < gmt::TR_NCAT) ? names[c] : "";
 }
 

@@ -192,10 +192,12 @@ enum TraceCat {
   TR_SMOOTH0 = 0, TR_RESID0 = 1, TR_APPLY0 = 2, TR_OUTER = 3, TR_DIAG0 = 4, TR_COARSE_ST = 5,
   TR_RESTRICT = 6, TR_PROLONG = 7, TR_CSOLVE = 8, TR_ENERGY = 9, TR_VEC = 10, TR_SETUP = 11,
   TR_OPS = 12, TR_CINV = 13, TR_COARSE_ST2 = 14,
-  TR_NCAT = 15
+  TR_VCYCLE = 15,   // a whole V-cycle (one event pair around the level-0 cycle)
+  TR_NCAT = 16
 };
 struct Tracer {
   bool on = false;
+  bool brackets_only = false;   // record only TR_VCYCLE (no per-launch events inside it)
   struct Rec {
     int cat;
     double bytes;

@@ -199,7 +199,7 @@ void Tracer::destroy() {
 
 TraceScope::TraceScope(Tracer* tr, cudaStream_t st, int c, double b)
     : t(tr), s(st), cat(c), bytes(b) {
-  if (t && t->on) {
+  if (t && t->on && (!t->brackets_only || c == TR_VCYCLE)) {
     a = t->get();
     GMT_CUDA(cudaEventRecord(a, s));
   }

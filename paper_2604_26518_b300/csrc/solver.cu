@@ -479,7 +479,11 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     double* pq = w->red + 5 * 32;
     double* rz_new = w->red + 6 * 32;
     project(w->rr);
-    void* z = vcycle(h, w, 0, w->rr, nullptr, true);
+    void* z;
+    {
+      TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
+      z = vcycle(h, w, 0, w->rr, nullptr, true);
+    }
     project(z);
     ++cycles;
     if (krylov) {
@@ -589,8 +593,11 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       // the last post-smoothing sweep writes the partials of r.z, q.z (q = K p of the last
       // direction) and of the sums of z
       const bool fused = krylov && h->L > 1 && o.nu_post >= 1;
-      z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr, -1,
-                 fused ? w->q : nullptr);
+      {
+        TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
+        z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr, -1,
+                   fused ? w->q : nullptr);
+      }
       ++cycles;
       if (krylov) {
         // rr is mean-free, so r.z needs no correction for the mean of z; the mean of z is

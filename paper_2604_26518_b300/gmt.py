@@ -138,7 +138,7 @@ _SIGS = {
                                  ctypes.POINTER(_D)]),
 }
 
-TRACE_CATEGORIES = 15
+TRACE_CATEGORIES = 16
 
 
 def release_cached_memory():
@@ -403,8 +403,11 @@ class Hierarchy:
         return out
 
     # ---------------------------------------------------------------- tracing
-    def trace(self, on=True):
-        _check(lib().gmt_trace_enable(self._h, int(on)), "gmt_trace_enable")
+    def trace(self, on=True, brackets_only=False):
+        """Enable (and reset) the library's launch tracer; brackets_only records only the
+        whole-V-cycle category, without per-launch events inside the cycles."""
+        mode = (2 if brackets_only else 1) if on else 0
+        _check(lib().gmt_trace_enable(self._h, mode), "gmt_trace_enable")
 
     def trace_totals(self):
         """{category: (launches, device ms, algorithmic bytes)} since trace(True)."""
