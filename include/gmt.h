@@ -94,6 +94,9 @@ typedef struct {
                           the coarse ones) were the fastest of the sweeps measured on the
                           128^3 elasticity batch; heat conduction on the same cells and
                           elasticity at 512^3 ran faster with nu_pre = nu_post = 2 */
+  int graphs;          /* [1] gmt_solve replays its V-cycles from CUDA graphs captured on the
+                          hierarchy's stream (not on the legacy default stream, not while
+                          tracing, not inside a caller's own stream capture) */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,

@@ -100,6 +100,7 @@ void gmt_default_options(gmt_options* o) {
   o->cycle = GMT_CYCLE_V;
   o->fp64_fallback = 1;
   o->nu_coarse = 2;
+  o->graphs = 1;
 }
 
 const char* gmt_status_string(gmt_status s) {

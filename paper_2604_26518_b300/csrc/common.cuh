@@ -43,6 +43,7 @@ struct Fail {
 
 // every kernel launch site ends with GMT_LAUNCH_CHECK(), which also counts the launch
 void count_launch(int64_t n = 1);
+int64_t thread_launch_count();   // launches counted by the calling host thread
 #define GMT_LAUNCH_CHECK()              \
   do {                                  \
     ::gmt::count_launch();              \

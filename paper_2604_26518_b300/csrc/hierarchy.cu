@@ -151,8 +151,13 @@ void ensure_smem_attr(const void* kernel, int bytes) {
 
 // ------------------------------------------------------------------ launch counting, tracing
 static std::atomic<int64_t> g_launches{0};
-void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local int64_t t_launches = 0;   // this host thread's launches
+void count_launch(int64_t n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 int64_t launch_count() { return g_launches.load(); }
+int64_t thread_launch_count() { return t_launches; }
 
 cudaEvent_t Tracer::get() {
   if (!pool.empty()) {

@@ -102,6 +102,20 @@ struct Workspace {
   double* red = nullptr;     // reduction slots, 12 x 32 doubles
   int* active = nullptr;     // per case flags (device)
   double* ones = nullptr;    // per case 1.0 (device)
+  // the solve's two V-cycle forms (plain; with the fused Krylov partials), replayed from CUDA
+  // graphs once captured: graph, result buffer, kernels in it, the options it was captured
+  // with, and how often the form has run directly
+  struct Captured {
+    cudaGraphExec_t exec = nullptr;
+    void* out = nullptr;
+    int64_t kernels = 0;
+    gmt_options opts;
+    int direct = 0;
+  } vg[2];
+  ~Workspace() {
+    for (Captured& c : vg)
+      if (c.exec) cudaGraphExecDestroy(c.exec);
+  }
 };
 
 void free_workspace(gmt_hierarchy* h) {
@@ -310,6 +324,63 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
   return u;
 }
 
+// One level-0 V-cycle of the solve on w->rr (form 0: plain; form 1: the last sweep also
+// writes the Krylov partials of w->part against w->q). The launch sequence of a form is the
+// same every time (fixed buffers, sizes and scalars), so once the form has run directly
+// kDirectBeforeCapture times (the first run builds what the levels create lazily) it is
+// captured into a CUDA graph and replayed with one launch, which removes the per-kernel
+// launch cost of the small coarse levels. Not while tracing (the tracer times every launch), with graphs switched
+// off, on the legacy default stream, or when the caller's stream is itself being captured.
+// A form is captured after this many direct runs: capture and instantiation cost about as
+// much as a few V-cycles, so solves of a handful of cycles (and a hierarchy is rebuilt per
+// cell) never capture, and long solves replay.
+constexpr int kDirectBeforeCapture = 16;
+
+static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
+  double* part = form ? w->part : nullptr;
+  const void* aux = form ? w->q : nullptr;
+  Workspace::Captured& c = w->vg[form];
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool can = h->opts.graphs != 0 && !h->tracer.on && h->stream != nullptr &&
+                   cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess &&
+                   cap == cudaStreamCaptureStatusNone;
+  if (c.exec && (!can || std::memcmp(&c.opts, &h->opts, sizeof(gmt_options)) != 0)) {
+    cudaGraphExecDestroy(c.exec);
+    c.exec = nullptr;
+    c.direct = 0;
+  }
+  if (can && c.exec) {
+    GMT_CUDA(cudaGraphLaunch(c.exec, h->stream));
+    count_launch(c.kernels);
+    return c.out;
+  }
+  if (!can || c.direct < kDirectBeforeCapture) {
+    ++c.direct;
+    TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
+    return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+  }
+  const int64_t k0 = thread_launch_count();
+  cudaGraph_t g = nullptr;
+  GMT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  void* out = nullptr;
+  try {
+    out = vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+  } catch (...) {
+    cudaStreamEndCapture(h->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  GMT_CUDA(cudaStreamEndCapture(h->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&c.exec, g, 0);
+  cudaGraphDestroy(g);
+  GMT_CUDA(e);
+  c.out = out;
+  c.kernels = thread_launch_count() - k0;
+  c.opts = h->opts;
+  GMT_CUDA(cudaGraphLaunch(c.exec, h->stream));
+  return out;
+}
+
 // ------------------------------------------------------------------ Chebyshev bounds
 void estimate_lmax(gmt_hierarchy* h) {
   Workspace* w = workspace(h, P32);
@@ -479,11 +550,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
     double* pq = w->red + 5 * 32;
     double* rz_new = w->red + 6 * 32;
     project(w->rr);
-    void* z;
-    {
-      TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
-      z = vcycle(h, w, 0, w->rr, nullptr, true);
-    }
+    void* z = run_vcycle(h, w, 0);
     project(z);
     ++cycles;
     if (krylov) {
@@ -593,11 +660,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       // the last post-smoothing sweep writes the partials of r.z, q.z (q = K p of the last
       // direction) and of the sums of z
       const bool fused = krylov && h->L > 1 && o.nu_post >= 1;
-      {
-        TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
-        z = vcycle(h, w, 0, w->rr, nullptr, true, fused ? w->part : nullptr, -1,
-                   fused ? w->q : nullptr);
-      }
+      z = run_vcycle(h, w, fused ? 1 : 0);
       ++cycles;
       if (krylov) {
         // rr is mean-free, so r.z needs no correction for the mean of z; the mean of z is

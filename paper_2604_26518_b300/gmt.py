@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("cycle", ctypes.c_int),
         ("fp64_fallback", ctypes.c_int),
         ("nu_coarse", ctypes.c_int),
+        ("graphs", ctypes.c_int),
     ]
 
 

@@ -19,6 +19,10 @@ Checks per cell and physics:
         N^3 (C_II(u) - C_II(u*)) = (u - u*)^T K (u - u*)      (K u* = f, f = sum A^T K_e x0),
     so the relative energy-norm error of case I is sqrt((C_II(u) - C*_II) / C*_II), computed
     from the oracle's energy average of the library's field and the stored converged C*.
+    A residual of 1e-5 does not bound this error by 1e-4 on ill-conditioned cells: on the
+    spinodal cell the library's field at r <= 1e-5 is 2.1e-4 away, and the oracle's own
+    Jacobi-PCG field at r <= 1e-5 is 5.2e-4 away. The field check therefore continues the
+    solve (warm start) to r <= 1e-6 and holds that field to 1e-4.
 """
 import json
 import os
@@ -82,7 +86,10 @@ def test_family64_matches_converged_oracle(gmt_lib, idx, family, kind):
     # soft cells (spinodal: C^H ~ phi |C0| / 20) exceeds 1e-7 of |C^H| itself
     assert np.abs(CH - C_of_gpu).max() <= 2e-7 * vox.mean() * np.abs(C0).max()
     diag = np.diag(C_star)
-    excess = np.diag(C_of_gpu) - diag
+    st, u6, info6 = h.solve(ph, tol=1e-6, u0=u)
+    assert st == gmt.OK, info6.as_dict()
+    U6 = u6.detach().cpu().numpy().reshape(-1, M)
+    excess = np.diag(solve.homogenize_chunked(lev, U6, Ke, x0, D)) - diag
     # the energy of any field is at least the minimum's (up to the oracle's 1e-10 residual)
     assert excess.min() >= -1e-9 * diag.max(), excess
     en = np.sqrt(np.maximum(excess, 0.0) / np.maximum(diag, 1e-300))
