@@ -346,108 +346,139 @@ struct EnArgs {
 //     E_IJ - C0_IJ = d^I . K_e d^J - f^I . d^J - d^I . f^J,      f = K_e x0,
 // with K_e and f split into FP32 hi + lo parts; C0_IJ (exact) is added once per element in
 // FP64 on the host side (n_e C0).
-// One thread per element: its d (or w) for every case goes to a thread-private column of
-// shared memory, then each case J forms z = K_e d^J once and dots it with d^I for I <= J.
-// The per-pair sums live in shared memory (runtime J, no local-memory arrays); they reuse
-// the space of the staged tiles once d is formed.
+// A 128-thread block takes the 64 elements whose origins are the nodes of one brick, two
+// threads per element (halves h = 0, 1 of the block). The element's d (or w) for every case
+// goes to a column of shared memory (the two halves form the corners 0-3 and 4-7; on the
+// float-float path the hi tile is staged and differenced first, then the lo tile in the
+// same space). Each case J then forms z = K_e d^J once, in the half that owns J, and dots
+// it with d^I for I <= J. The per-pair sums (and the load terms f^I . d^J) live in shared
+// memory, reusing the tile space once d is formed. Every value is computed by one thread
+// with the same operations in the same order whatever the split.
+// shared memory: a first region holding the tile, later the pair sums and load terms, then
+// the element columns [R*M][64]
+template <typename A, int D, int M, bool FF>
+constexpr size_t energy_region0_bytes() {
+  constexpr int C = D * M, NV = Vec16<A>::n, G = (C + NV - 1) / NV, K = M * (M + 1) / 2;
+  constexpr size_t tile = (size_t)G * 216 * 16;
+  constexpr size_t sums = (size_t)K * 64 * (FF ? sizeof(float) : sizeof(double)) +
+                          (FF ? (size_t)M * M * 64 * sizeof(A) : 0);
+  return (tile > sums ? tile : sums + 15) / 16 * 16;
+}
 template <typename A, int D, int M, bool FF>
 constexpr size_t energy_smem_bytes() {
-  constexpr int C = D * M, NV = Vec16<A>::n, G = (C + NV - 1) / NV;
-  return (size_t)(FF ? 2 : 1) * G * 216 * 16 + (size_t)8 * D * M * 64 * sizeof(A);
+  return energy_region0_bytes<A, D, M, FF>() + (size_t)8 * D * M * 64 * sizeof(A);
+}
+
+// the half of the block that forms z = K_e d^J for case J (K_e products balanced 3 : 3, the
+// dot products 10 : 11 for six cases)
+template <int M>
+__device__ __forceinline__ int energy_owner(int J) {
+  if constexpr (M == 6) return (J == 0 || J == 2 || J == 5) ? 0 : 1;
+  else return J == M - 1 ? 0 : 1;
 }
 
 // PER: write each element's energies (times p.scale) instead of the block sums.
 template <typename A, int D, int M, bool FF, bool PER = false>
-__global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
+__global__ void __launch_bounds__(128) k_energy(const __grid_constant__ EnArgs<A, D, M> p) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, R = 8 * D, K = M * (M + 1) / 2;
   constexpr int NV = Vec16<A>::n, G = (C + NV - 1) / NV;
-  static_assert((size_t)K * 64 * 8 <= (size_t)(FF ? 2 : 1) * G * 216 * 16,
-                "pair sums must fit in the tile space");
-  extern __shared__ __align__(16) unsigned char en_smem[];
-  V* th = reinterpret_cast<V*>(en_smem);
-  V* tl = th + G * 216;                                              // FF only
-  A* ws = reinterpret_cast<A*>(en_smem + (size_t)(FF ? 2 : 1) * G * 216 * 16);  // [R*M][64]
-  // per-pair energies [K][64] after phase 1 (FP32 on the float-float path: per-element
-  // rounding, not common to the elements, is summed away in FP64 across blocks)
+  // per-pair energies [K][64] (FP32 on the float-float path: per-element rounding, not
+  // common to the elements, is summed away in FP64 across blocks), then the load terms
+  // phi[I][J] = f^I . d^J [M * M][64], in the tile's region
   using ES = typename std::conditional<FF, float, double>::type;
+  extern __shared__ __align__(16) unsigned char en_smem[];
+  V* tile = reinterpret_cast<V*>(en_smem);
+  A* ws = reinterpret_cast<A*>(en_smem + energy_region0_bytes<A, D, M, FF>());   // [R*M][64]
   ES* es = reinterpret_cast<ES*>(en_smem);
+  A* ph = reinterpret_cast<A*>(en_smem + (size_t)K * 64 * sizeof(ES));
   __shared__ int nb[27];
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, el = t & 63, half = t >> 6;
   const int64_t b = blockIdx.x;
   if (t < 27) nb[t] = p.nbr[b * 27 + t];
   __syncthreads();
-  {
+  if (t < 64) {
     A own[C];
-    stage_tile<A, A, C>((const A*)p.hi, b, t, nb, th, own);
-    if constexpr (FF) stage_tile<float, A, C>(p.lo, b, t, nb, tl, own);
+    stage_tile<A, A, C>((const A*)p.hi, b, t, nb, tile, own);
   }
   __syncthreads();
-  const int q0 = own_q0(t), loc = own_local(t);
+  const int q0 = own_q0(el), loc = own_local(el);
   const bool act = (p.mask[b * 64 + loc] & 1u) != 0;  // element with origin at this node
-  // phase 1: d (FF) or w = x0 - d (FP64) of this element, every dof r and case m
-  if (act) {
+  // phase 1: d (FF: hi part, then lo part added) or w = x0 - d (FP64), corners 4 h .. 4 h + 3
+  auto differences = [&](bool lo) {
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
+    for (int c = 0; c < 4; ++c) {
+      const int bb = 4 * half + c;
       const int q = q0 + (bb & 1) + 6 * ((bb >> 1) & 1) + 36 * (bb >> 2);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const V a = th[g * 216 + q], a0 = th[g * 216 + q0];
-        V l = a, l0 = a0;
-        if constexpr (FF) {
-          l = tl[g * 216 + q];
-          l0 = tl[g * 216 + q0];
-        }
+        const V a = tile[g * 216 + q], a0 = tile[g * 216 + q0];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
           const int v = g * NV + k;
           if (v < C) {
             const int r = (v / M) + D * bb, m = v % M;
-            A du = vec_get<A>(a, k) - vec_get<A>(a0, k);
-            if constexpr (FF) {
-              du += vec_get<A>(l, k) - vec_get<A>(l0, k);
-              ws[(r * M + m) * 64 + t] = du;
-            } else {
-              ws[(r * M + m) * 64 + t] = p.X0[r * M + m] - du;
-            }
+            const A du = vec_get<A>(a, k) - vec_get<A>(a0, k);
+            A* wp = ws + (r * M + m) * 64 + el;
+            if constexpr (FF) *wp = lo ? *wp + du : du;
+            else *wp = p.X0[r * M + m] - du;
           }
         }
       }
     }
+  };
+  if (act) differences(false);
+  if constexpr (FF) {
+    __syncthreads();   // the hi tile is dead: stage lo in its place
+    if (t < 64) {
+      A own[C];
+      stage_tile<float, A, C>(p.lo, b, t, nb, tile, own);
+    }
+    __syncthreads();
+    if (act) differences(true);
   }
-  __syncthreads();  // tiles dead: es takes their space
-  if (act) {
-    // phase 2 (FF): the load terms f^I . d^J + f^J . d^I, kept as the pair's start value
-    if constexpr (FF) {
-      A phi[M][M];
-#pragma unroll
+  __syncthreads();  // tiles dead: es (and ph) take their space
+  // phase 2 (FF): the load terms, phi[I][J] = (f_hi + f_lo)^I . d^J for the I of this half,
+  // then the pair start values phi[I][J] + phi[J][I]
+  if constexpr (FF) {
+    if (act) {
+#pragma unroll 1
       for (int J = 0; J < M; ++J) {
         A d[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[r] = ws[(r * M + J) * 64 + t];
+        for (int r = 0; r < R; ++r) d[r] = ws[(r * M + J) * 64 + el];
 #pragma unroll
-        for (int I = 0; I < M; ++I) {
+        for (int I = half; I < M; I += 2) {
           A sh = A(0), sl = A(0);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             sh += p.Fh[r * M + I] * d[r];
             sl += p.Fl[r * M + I] * d[r];
           }
-          phi[I][J] = sh + sl;
+          ph[(I * M + J) * 64 + el] = sh + sl;
         }
       }
+    }
+    __syncthreads();
+    if (act) {
 #pragma unroll
       for (int I = 0; I < M; ++I)
 #pragma unroll
         for (int J = I; J < M; ++J)
-          es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t] = phi[I][J] + phi[J][I];
+          if (energy_owner<M>(J) == half)
+            es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + el] =
+                ph[(I * M + J) * 64 + el] + ph[(J * M + I) * 64 + el];
     }
-    // phase 3: z = K_e d^J (hi + lo in FF), pair sums d^I . z for I <= J
+    // each pair's start value is read back below by the thread that wrote it
+  }
+  // phase 3: z = K_e d^J (hi + lo in FF), pair sums d^I . z for I <= J, J owned by this half
+  if (act) {
 #pragma unroll 1
     for (int J = 0; J < M; ++J) {
+      if (energy_owner<M>(J) != half) continue;
       A w[R], z[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) w[r] = ws[(r * M + J) * 64 + t];
+      for (int r = 0; r < R; ++r) w[r] = ws[(r * M + J) * 64 + el];
       if constexpr (FF) {
         // two rows per f32x2 instruction, the same operations in the same order per row
         f2_t w2[R];
@@ -477,34 +508,37 @@ __global__ void __launch_bounds__(64) k_energy(const __grid_constant__ EnArgs<A,
         if (I <= J) {
           A sacc = A(0);
 #pragma unroll
-          for (int r = 0; r < R; ++r) sacc += ws[(r * M + I) * 64 + t] * z[r];
-          ES* ep = es + (I * M - I * (I - 1) / 2 + (J - I)) * 64 + t;
+          for (int r = 0; r < R; ++r) sacc += ws[(r * M + I) * 64 + el] * z[r];
+          ES* ep = es + (I * M - I * (I - 1) / 2 + (J - I)) * 64 + el;
           if constexpr (FF) *ep = sacc - *ep;
           else *ep = sacc;
         }
       }
     }
   }
+  __syncthreads();
   if constexpr (PER) {
-    if (!act) return;
-    const int64_t el = p.slot_elem[b * 64 + loc];
+    if (!act || half) return;
+    const int64_t e = p.slot_elem[b * 64 + loc];
     const double fac = p.rho ? p.simp_p * pow(p.rho[b * 64 + loc], p.simp_p - 1.0) : 1.0;
 #pragma unroll
     for (int I = 0; I < M; ++I)
 #pragma unroll
       for (int J = I; J < M; ++J) {
-        double v = (double)es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + t];
+        double v = (double)es[(I * M - I * (I - 1) / 2 + (J - I)) * 64 + el];
         if constexpr (FF) v += p.C0[I * M + J];
         v *= p.scale * fac;
-        p.per[(el * M + I) * M + J] = v;
-        p.per[(el * M + J) * M + I] = v;
+        p.per[(e * M + I) * M + J] = v;
+        p.per[(e * M + J) * M + I] = v;
       }
   } else {
+    // the first two warps hold the 64 elements; the other two add zeros
     ES e[K];
-    const ES w = (act && p.coef) ? (ES)p.coef[b * 64 + loc] : ES(1);
+    const bool mine = act && half == 0;
+    const ES w = (mine && p.coef) ? (ES)p.coef[b * 64 + loc] : ES(1);
 #pragma unroll
-    for (int k = 0; k < K; ++k) e[k] = act ? w * es[k * 64 + t] : ES(0);
-    block_partial_64<K, ES>(e, p.part + b * K);
+    for (int k = 0; k < K; ++k) e[k] = mine ? w * es[k * 64 + el] : ES(0);
+    block_partial_64<K, ES, 4>(e, p.part + b * K);
   }
 }
 
@@ -1019,10 +1053,10 @@ static void energy_t(gmt_hierarchy* h, const void* hi, const float* lo, double* 
     p.scale = scale;
     for (int i = 0; i < M * M; ++i) p.C0[i] = h->mat.C0[i];
     ensure_smem_attr((const void*)k_energy<A, D, M, FF, true>, (int)smem);
-    k_energy<A, D, M, FF, true><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
+    k_energy<A, D, M, FF, true><<<(unsigned)lv.nb, 128, smem, h->stream>>>(p);
   } else {
     ensure_smem_attr((const void*)k_energy<A, D, M, FF>, (int)smem);
-    k_energy<A, D, M, FF><<<(unsigned)lv.nb, 64, smem, h->stream>>>(p);
+    k_energy<A, D, M, FF><<<(unsigned)lv.nb, 128, smem, h->stream>>>(p);
   }
   GMT_LAUNCH_CHECK();
 }

@@ -78,13 +78,14 @@ template <> struct ArithOf<double> { using type = double; };
 // lane holds one column summed over P lanes; plain xor steps finish the sum over the warp.
 // That is P - 1 + (5 - p) shuffles instead of 5 K. Lanes and warps add in the values' own
 // type T (FP32 kernels keep FP64 off the per-element path, where B300's FP64 rate is 1/64
-// of FP32); the two warp sums are combined in FP64.
-template <int K, typename T>
+// of FP32); the two warp sums are combined in FP64. NW: the block's warps (2 for 64 threads;
+// a larger block calls it with every thread, and the warp sums are added in warp order).
+template <int K, typename T, int NW = 2>
 __device__ __forceinline__ void block_partial_64(T (&v)[K], double* __restrict__ out) {
   static_assert(K >= 1 && K <= 32, "at most 32 values per thread");
   constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
   constexpr int LP = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;
-  __shared__ double red[2][P];
+  __shared__ double red[NW][P];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T x[P];
 #pragma unroll
@@ -106,7 +107,12 @@ __device__ __forceinline__ void block_partial_64(T (&v)[K], double* __restrict__
   for (int o = 16 >> LP; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
   if ((lane & ((32 >> LP) - 1)) == 0) red[w][col] = (double)x[0];
   __syncthreads();
-  if (threadIdx.x < K) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+  if (threadIdx.x < K) {
+    double acc = red[0][threadIdx.x] + red[1][threadIdx.x];
+#pragma unroll
+    for (int i = 2; i < NW; ++i) acc += red[i][threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
 }
 
 // symmetric-positive D x D inverse (D = 1 or 3)
