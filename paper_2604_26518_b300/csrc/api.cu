@@ -94,7 +94,7 @@ void gmt_default_options(gmt_options* o) {
   o->cheb_upper = 1.1;
   o->precision = GMT_PREC_FP32;
   o->krylov = 1;
-  o->inner_tol = 0.1;
+  o->inner_tol = 0.03;
   o->max_inner = 40;
   o->max_outer = 40;
   o->cycle = GMT_CYCLE_V;

@@ -250,7 +250,6 @@ struct gmt_hierarchy {
   double* cscal = nullptr;  // device [rho, FP32 pivot tolerance, FP64 pivot tolerance]
   double* cb = nullptr;   // m x M gather buffer
   double* cu = nullptr;   // m x M result buffer
-  double* cr = nullptr;   // m x M refinement residual
   float* cb32 = nullptr;  // m x M FP32 copy of the right-hand side / refinement residual
   gmt::Workspace* ws = nullptr;
   gmt::Tracer tracer;

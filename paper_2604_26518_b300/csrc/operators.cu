@@ -7,12 +7,12 @@
 //     8-bit child mask, so it is a 256-entry table; levels >= 2 are stored per element;
 //   * D x D block-diagonal inverses of the coarse operators (smoother, Sec. 4.6);
 //   * the coarsest level's dense matrix K_L + rho J (J couples equal components of all
-//     nodes, rho = mean diagonal / number of coarse nodes) kept in FP64, and its generalized inverse by blocked
-//     in-place Gauss-Jordan with semidefinite pivot dropping: in FP32 for the
-//     mixed-precision solves (each use is refined once against the FP64 matrix), and in
-//     FP64 (built on first use) for the all-FP64 path. For right-hand sides orthogonal to translations this
-//     returns the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS
-//     is replaced by this exact solve.
+//     nodes, rho = mean diagonal / number of coarse nodes) kept in FP64, and its
+//     generalized inverse by blocked in-place Gauss-Jordan with semidefinite pivot
+//     dropping: in FP32 for the mixed-precision solves, and in FP64 (built on first use)
+//     for the all-FP64 path. For right-hand sides orthogonal to translations this returns
+//     the zero-mean solution (the gauge of Sec. 3.1); Alg. 1's inexact coarsest GS is
+//     replaced by this exact solve.
 #include <algorithm>
 #include <mutex>
 #include <optional>
@@ -865,7 +865,6 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     h->A64 = h->op.alloc<double>(m * m);
     h->cb = h->op.alloc<double>(m * M);
     h->cu = h->op.alloc<double>(m * M);
-    h->cr = h->op.alloc<double>(m * M);
     h->cb32 = h->op.alloc<float>(m * M);
     GMT_CUDA(cudaMemsetAsync(h->A64, 0, m * m * sizeof(double), s));
     k_coarse_assemble<<<grid_for(c.n_nodes * 27, 128), 128, 0, s>>>(
@@ -881,7 +880,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
     GMT_LAUNCH_CHECK();
     k_add_rho<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, m, D, h->cscal);
     GMT_LAUNCH_CHECK();
-    // FP32 generalized inverse for the mixed-precision solves (refined against A64 per use)
+    // FP32 generalized inverse for the mixed-precision solves
     h->X32 = h->op.alloc<float>(m * m);
     k_to_f32<<<grid_for(m * m, 256), 256, 0, s>>>(h->A64, h->X32, m * m);
     GMT_LAUNCH_CHECK();
