@@ -198,7 +198,7 @@ def run_reference(args, rank: int, world: int):
     sample = ("per step: the c128 batch's 16 cells (seeds 2000-2015) regenerated at 32^3 by the "
               "same generator, %d single-threaded processes on %d host cores; CPU FP64 oracle: "
               "assembled K, Jacobi-PCG to max_m r_m <= 1e-5, energy-average C^H; %d active "
-              "nodes over the 16 cells (a 128^3 cell has ~40x more)" % (procs, cores, nodes))
+              "nodes over the 16 cells (a 128^3 cell of the batch has about 50x more)" % (procs, cores, nodes))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "C^H solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
