@@ -47,7 +47,11 @@ TOL = 1e-5
 # kernel on the first 128^3 bench cell (FP32 elasticity), keyed by trace category. A
 # kernel whose source changed after its capture has no entry (its traffic is reported as
 # null until it is captured again).
-NCU_DRAM_BYTES_PER_NODE = {}
+NCU_DRAM_BYTES_PER_NODE = {
+    # level-1 damped-Jacobi sweep (k_stencil KIND 1): 116.9 MB read + 3.1 MB written over
+    # the 88,670 level-1 nodes of the first bench cell (stored per-node stencils + vectors)
+    "stencil_l1": (116.924672e6 + 3.106304e6) / 88670,
+}
 
 
 def workload(name: str, rank: int):
@@ -542,9 +546,10 @@ def run_gmt(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "kernel": dom,
                      "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": (dom_gbs / peak) if dom_gbs else None, "traffic": traffic,
-                     "traffic_source": ("ncu dram__bytes_read + write per active node of this "
-                                        "kernel on the first 128^3 bench cell, times this "
-                                        "workload's mean nodes per launch") if traffic else
+                     "traffic_source": ("ncu dram__bytes_read + write per active node of "
+                                        "this category's Jacobi-sweep launch on the first "
+                                        "128^3 bench cell, times this workload's mean nodes "
+                                        "of the level") if traffic else
                                        "no ncu capture of the current kernel for this physics "
                                        "/ precision",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
