@@ -98,7 +98,11 @@ typedef struct {
                           elasticity at 512^3 ran faster with nu_pre = nu_post = 2 */
   int graphs;          /* [1] gmt_solve replays its V-cycles from CUDA graphs captured on the
                           hierarchy's stream (not on the legacy default stream, not while
-                          tracing, not inside a caller's own stream capture) */
+                          tracing, not inside a caller's own stream capture, and not while
+                          another host thread is inside a call of this library: graph
+                          operations concurrent with other threads' kernel launches
+                          crashed the driver). Kernels that the caller launches from other
+                          threads itself are not covered: such a caller sets 0. */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,
@@ -192,6 +196,24 @@ gmt_status gmt_coarse_solve(gmt_hierarchy* h, const double* f, double* u);
    (zero_init != 0: taken as 0) and the result on exit. */
 gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u,
                       int zero_init);
+
+/* Largest number of hierarchies one gmt_vcycle_batch call takes. */
+#define GMT_BATCH_MAX 64
+
+/* One FP32 V-cycle (Alg. 1) on each of n (1..GMT_BATCH_MAX) distinct prepared hierarchies
+   at once: hs[i], f[i], u[i] as for gmt_vcycle(hs[i], GMT_PREC_FP32, f[i], u[i], zero_init)
+   (device canonical FP64 fields, u[i] the initial guess unless zero_init, the result on
+   exit), and every u[i] is bitwise what that call returns. Each phase of the cycle
+   (smoothing sweep, residual, restriction, coarsest solve, prolongation) runs as one launch
+   over the bricks of all n lattices, so the small coarse levels of many cells fill the GPU
+   together and the launch count does not grow with n. The hierarchies must share the
+   material (physics and parameters of gmt_prepare), have no element densities, use the
+   damped-Jacobi smoother and the V-cycle with the same omega, nu_pre, nu_post, nu_coarse,
+   have the same number of levels, and run on the same device and stream; otherwise
+   GMT_ERR_ARG (GMT_ERR_STATE if one is not prepared). The launches go to that stream and
+   the call returns after it has finished them. */
+gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
+                            double* const* u, int zero_init);
 
 /* Largest eigenvalue estimate of D^-1 K at `level` used by the Chebyshev smoother
    (host double out). */

@@ -20,6 +20,8 @@ void step_restrict(gmt_hierarchy* h, int level, int precision, const double* rf,
 void step_prolong(gmt_hierarchy* h, int level, int precision, const double* uc, double* uf);
 void step_coarse(gmt_hierarchy* h, const double* f, double* u);
 void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero);
+void step_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
+                       double* const* u, bool zero);
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);
 void export_elems(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* c);
 void export_stencil(gmt_hierarchy* h, int l, int32_t* idx, double* w);
@@ -29,6 +31,7 @@ int64_t launch_count();
 using gmt::Fail;
 
 #define GMT_API_BEGIN \
+  gmt::ApiGuard gmt_api_guard; \
   gmt::set_error("%s", ""); \
   try {
 #define GMT_API_END                                           \
@@ -164,6 +167,7 @@ gmt_status gmt_build_hierarchy(const uint8_t* voxels, int res, int voxels_on_dev
 
 void gmt_free_hierarchy(gmt_hierarchy* h) {
   if (!h) return;
+  gmt::ApiGuard guard;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   h->tracer.destroy();
@@ -342,6 +346,42 @@ gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* 
   GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
   ensure_device(h);
   gmt::step_vcycle(h, precision, f, u, zero_init != 0);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
+                            double* const* u, int zero_init) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(hs && f && u, GMT_ERR_ARG, "null array");
+  GMT_REQUIRE(n >= 1 && n <= GMT_BATCH_MAX, GMT_ERR_ARG, "batch of %d hierarchies (1..%d)", n,
+              GMT_BATCH_MAX);
+  for (int i = 0; i < n; ++i) {
+    need_prepared(hs[i]);
+    GMT_REQUIRE(f[i] && u[i], GMT_ERR_ARG, "null field of hierarchy %d", i);
+    for (int j = 0; j < i; ++j)
+      GMT_REQUIRE(hs[j] != hs[i], GMT_ERR_ARG, "hierarchy %d appears twice", i);
+  }
+  const gmt_hierarchy* a = hs[0];
+  for (int i = 0; i < n; ++i) {
+    const gmt_hierarchy* h = hs[i];
+    const gmt_options& o = h->opts;
+    GMT_REQUIRE(o.smoother == GMT_SMOOTH_JACOBI && o.cycle == GMT_CYCLE_V, GMT_ERR_ARG,
+                "batched V-cycle: damped-Jacobi smoother and V-cycle only (hierarchy %d)", i);
+    GMT_REQUIRE(!h->dens, GMT_ERR_ARG, "batched V-cycle: hierarchy %d has element densities", i);
+    GMT_REQUIRE(h->device == a->device && h->stream == a->stream, GMT_ERR_ARG,
+                "batched V-cycle: hierarchy %d is on another device or stream", i);
+    GMT_REQUIRE(h->L == a->L, GMT_ERR_ARG, "batched V-cycle: hierarchy %d has %d levels, not %d",
+                i, h->L, a->L);
+    GMT_REQUIRE(o.omega == a->opts.omega && o.nu_pre == a->opts.nu_pre &&
+                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse,
+                GMT_ERR_ARG, "batched V-cycle: hierarchy %d has other smoothing options", i);
+    GMT_REQUIRE(h->mat.physics == a->mat.physics && h->mat.E == a->mat.E &&
+                    h->mat.nu == a->mat.nu && h->mat.k == a->mat.k,
+                GMT_ERR_ARG, "batched V-cycle: hierarchy %d has another material", i);
+  }
+  ensure_device(hs[0]);
+  gmt::step_vcycle_batch(hs, n, f, u, zero_init != 0);
   return GMT_OK;
   GMT_API_END
 }

@@ -44,6 +44,33 @@ struct Fail {
 // every kernel launch site ends with GMT_LAUNCH_CHECK(), which also counts the launch
 void count_launch(int64_t n = 1);
 int64_t thread_launch_count();   // launches counted by the calling host thread
+
+// CUDA-graph operations (capture, instantiation, replay, destruction) never overlap a
+// kernel launch of another host thread through this library: concurrent solves on separate
+// streams, with one thread capturing or replaying a V-cycle graph while others launched,
+// crashed inside the driver's kernel launch (a null dereference in cuLaunchKernel).
+// Every entry point holds an ApiGuard: it counts the calls in flight and, on entry, waits
+// for a graph operation that holds the graph lock. A GraphLock takes that lock; its
+// `alone` says that no other library call is in flight, and only then may the holder run
+// graph operations. Graph executables released while other calls are in flight are
+// retired and destroyed at the next moment the library is alone.
+struct ApiGuard {
+  explicit ApiGuard(bool may_drain = true);   // false: never destroys retired graphs
+  ~ApiGuard();
+  bool drain;
+  ApiGuard(const ApiGuard&) = delete;
+  ApiGuard& operator=(const ApiGuard&) = delete;
+};
+struct GraphLock {
+  GraphLock();
+  ~GraphLock();
+  void release();   // unlock early (idempotent)
+  bool alone = false;
+  bool held = false;
+  GraphLock(const GraphLock&) = delete;
+  GraphLock& operator=(const GraphLock&) = delete;
+};
+void retire_graph(cudaGraphExec_t e);
 #define GMT_LAUNCH_CHECK()              \
   do {                                  \
     ::gmt::count_launch();              \

@@ -149,6 +149,54 @@ void ensure_smem_attr(const void* kernel, int bytes) {
   done.insert({kernel, dev});
 }
 
+// ------------------------------------------------------------------ graph lock
+namespace {
+std::atomic<int> g_inflight{0};
+std::mutex g_graph_mu;
+// graph executables waiting for a moment without other calls in flight (under g_graph_mu;
+// never destroyed: they may outlive static destructors)
+std::vector<cudaGraphExec_t>* g_retired = new std::vector<cudaGraphExec_t>();
+void drain_retired_locked() {
+  for (cudaGraphExec_t e : *g_retired) cudaGraphExecDestroy(e);
+  g_retired->clear();
+}
+}  // namespace
+
+ApiGuard::ApiGuard(bool may_drain) : drain(may_drain) {
+  g_inflight.fetch_add(1);
+  std::lock_guard<std::mutex> lock(g_graph_mu);   // wait for a graph operation in progress
+}
+
+ApiGuard::~ApiGuard() {
+  if (g_inflight.fetch_sub(1) == 1 && drain) {   // the last call in flight: destroy retired graphs
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_inflight.load() == 0 && !g_retired->empty()) drain_retired_locked();
+  }
+}
+
+GraphLock::GraphLock() {
+  g_graph_mu.lock();
+  held = true;
+  // a call that entered after this point waits in its ApiGuard until release(); one that
+  // entered before is counted here
+  alone = g_inflight.load() == 1;
+  if (alone && !g_retired->empty()) drain_retired_locked();
+}
+
+void GraphLock::release() {
+  if (held) g_graph_mu.unlock();
+  held = false;
+  alone = false;
+}
+
+GraphLock::~GraphLock() { release(); }
+
+void retire_graph(cudaGraphExec_t e) {
+  if (!e) return;
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  g_retired->push_back(e);
+}
+
 // ------------------------------------------------------------------ launch counting, tracing
 static std::atomic<int64_t> g_launches{0};
 static thread_local int64_t t_launches = 0;   // this host thread's launches

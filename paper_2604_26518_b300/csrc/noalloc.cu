@@ -125,6 +125,7 @@ extern "C" gmt_status gmt_homogenize_dense_noalloc(const uint8_t* voxels, int re
                                                    gmt_physics physics, double E, double nu,
                                                    double k, const double* u_dense, double* CH,
                                                    void* stream) {
+  gmt::ApiGuard guard(false);   // a lock and a counter; frees and allocates nothing
   gmt::set_error("%s", "");
   if (!voxels || !u_dense || !CH) {
     gmt::set_error("gmt_homogenize_dense_noalloc: null pointer");

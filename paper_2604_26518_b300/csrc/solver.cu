@@ -113,8 +113,7 @@ struct Workspace {
     int direct = 0;
   } vg[2];
   ~Workspace() {
-    for (Captured& c : vg)
-      if (c.exec) cudaGraphExecDestroy(c.exec);
+    for (Captured& c : vg) retire_graph(c.exec);   // destroyed once no other call is in flight
   }
 };
 
@@ -329,8 +328,10 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
 // same every time (fixed buffers, sizes and scalars), so once the form has run directly
 // kDirectBeforeCapture times (the first run builds what the levels create lazily) it is
 // captured into a CUDA graph and replayed with one launch, which removes the per-kernel
-// launch cost of the small coarse levels. Not while tracing (the tracer times every launch), with graphs switched
-// off, on the legacy default stream, or when the caller's stream is itself being captured.
+// launch cost of the small coarse levels. Not while tracing (the tracer times every
+// launch), with graphs switched off, on the legacy default stream, when the caller's stream
+// is itself being captured, or while another library call is in flight in another host
+// thread (then the form runs directly; see GraphLock).
 // A form is captured after this many direct runs: capture and instantiation cost about as
 // much as a few V-cycles, so solves of a handful of cycles (and a hierarchy is rebuilt per
 // cell) never capture, and long solves replay.
@@ -340,24 +341,46 @@ static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
   double* part = form ? w->part : nullptr;
   const void* aux = form ? w->q : nullptr;
   Workspace::Captured& c = w->vg[form];
+  auto direct = [&]() {
+    TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
+    return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+  };
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   const bool can = h->opts.graphs != 0 && !h->tracer.on && h->stream != nullptr &&
                    cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess &&
                    cap == cudaStreamCaptureStatusNone;
-  if (c.exec && (!can || std::memcmp(&c.opts, &h->opts, sizeof(gmt_options)) != 0)) {
+  if (!can) {
+    if (c.exec) {
+      retire_graph(c.exec);
+      c.exec = nullptr;
+      c.direct = 0;
+    }
+    return direct();
+  }
+  if (!c.exec && c.direct < kDirectBeforeCapture) {
+    ++c.direct;
+    return direct();
+  }
+  // graph operations only while no other library call is in flight (see GraphLock)
+  GraphLock gl;
+  if (!gl.alone) {
+    gl.release();
+    return direct();
+  }
+  if (c.exec && std::memcmp(&c.opts, &h->opts, sizeof(gmt_options)) != 0) {
     cudaGraphExecDestroy(c.exec);
     c.exec = nullptr;
     c.direct = 0;
   }
-  if (can && c.exec) {
+  if (c.exec) {
     GMT_CUDA(cudaGraphLaunch(c.exec, h->stream));
     count_launch(c.kernels);
     return c.out;
   }
-  if (!can || c.direct < kDirectBeforeCapture) {
+  if (c.direct < kDirectBeforeCapture) {
+    gl.release();
     ++c.direct;
-    TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
-    return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+    return direct();
   }
   const int64_t k0 = thread_launch_count();
   cudaGraph_t g = nullptr;
@@ -898,6 +921,79 @@ void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bo
   void* res = vcycle(h, w, 0, w->f[0], init, zero);
   slots_to_canon(h, 0, pr, res, u);
   GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ------------------------------------------------------------------ batched V-cycle
+// The FP32 damped-Jacobi V-cycle of step_vcycle on n hierarchies at once: each phase (diag
+// start, sweep, residual, restriction, coarsest solve, prolongation) is one launch over all
+// n lattices' bricks (batch.cu), in the order the single-lattice cycle runs them, so every
+// lattice's result is bitwise its own V-cycle's. The caller has checked that the lattices
+// share the material, the options, the level count and the stream.
+using PtrVec = std::vector<void*>;
+
+static void bsmooth(gmt_hierarchy* const* hs, int n, int l, const PtrVec& f, PtrVec& u,
+                    PtrVec& o, int sweeps, bool zero) {
+  if (sweeps <= 0) {
+    if (zero)
+      for (int i = 0; i < n; ++i) vec_zero(hs[i], l, P32, u[i]);
+    return;
+  }
+  int s0 = 0;
+  if (zero) {
+    batch_diag(hs, n, l, f.data(), u.data(), hs[0]->opts.omega);
+    s0 = 1;
+  }
+  for (int s = s0; s < sweeps; ++s) {
+    batch_stencil(hs, n, l, ST_JACOBI, u.data(), f.data(), o.data());
+    std::swap(u, o);
+  }
+}
+
+static PtrVec bvcycle(gmt_hierarchy* const* hs, Workspace* const* ws, int n, int l,
+                      const PtrVec& f, const PtrVec* init) {
+  PtrVec u(n), o(n);
+  if (l == hs[0]->L - 1) {
+    for (int i = 0; i < n; ++i) u[i] = ws[i]->ua[l];
+    batch_coarse_solve(hs, n, f.data(), u.data());
+    return u;
+  }
+  for (int i = 0; i < n; ++i) {
+    u[i] = init ? (*init)[i] : ws[i]->ua[l];
+    o[i] = u[i] == ws[i]->ua[l] ? ws[i]->ub[l] : ws[i]->ua[l];
+  }
+  const gmt_options& op = hs[0]->opts;
+  const int nu1 = (l > 0 && op.nu_coarse > 0) ? op.nu_coarse : op.nu_pre;
+  const int nu2 = (l > 0 && op.nu_coarse > 0) ? op.nu_coarse : op.nu_post;
+  bsmooth(hs, n, l, f, u, o, nu1, init == nullptr);
+  PtrVec r(n), fc(n);
+  for (int i = 0; i < n; ++i) {
+    r[i] = ws[i]->r[l];
+    fc[i] = ws[i]->f[l + 1];
+  }
+  batch_stencil(hs, n, l, ST_RESID, u.data(), f.data(), r.data());
+  batch_restrict(hs, n, l, r.data(), fc.data());
+  const PtrVec uc = bvcycle(hs, ws, n, l + 1, fc, nullptr);
+  batch_prolong(hs, n, l, uc.data(), u.data());
+  bsmooth(hs, n, l, f, u, o, nu2, false);
+  return u;
+}
+
+void step_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
+                       double* const* u, bool zero) {
+  std::vector<Workspace*> ws(n);
+  PtrVec fs(n), init(n);
+  for (int i = 0; i < n; ++i) {
+    ws[i] = workspace(hs[i], P32);
+    canon_to_slots(hs[i], 0, P32, f[i], ws[i]->f[0]);
+    fs[i] = ws[i]->f[0];
+    if (!zero) {
+      canon_to_slots(hs[i], 0, P32, u[i], ws[i]->ua[0]);
+      init[i] = ws[i]->ua[0];
+    }
+  }
+  const PtrVec res = bvcycle(hs, ws.data(), n, 0, fs, zero ? nullptr : &init);
+  for (int i = 0; i < n; ++i) slots_to_canon(hs[i], 0, P32, res[i], u[i]);
+  GMT_CUDA(cudaStreamSynchronize(hs[0]->stream));
 }
 
 }  // namespace gmt

@@ -129,6 +129,23 @@ void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst);
 void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst);
 
 inline int64_t blocks_of(const Level& lv) { return lv.nb; }
+
+// ---- batched V-cycle phases (batch.cu): one launch over level `level` of n <= kBatchMax
+// lattices (FP32 vectors; the same material prepared on each; the stream of hs[0]).
+// Per-lattice arguments are arrays of n pointers, as for the single-lattice launchers.
+constexpr int kBatchMax = GMT_BATCH_MAX;
+// damped-Jacobi sweep (mode ST_JACOBI: out = u + omega D^-1 (f - K u)) or residual
+// (ST_RESID: out = f - K u)
+void batch_stencil(gmt_hierarchy* const* hs, int n, int level, StencilMode mode,
+                   const void* const* u, const void* const* f, void* const* out);
+// first smoothing step from zero: out = scale D^-1 f
+void batch_diag(gmt_hierarchy* const* hs, int n, int level, const void* const* f,
+                void* const* out, double scale);
+void batch_restrict(gmt_hierarchy* const* hs, int n, int level, const void* const* rf,
+                    void* const* fc);
+void batch_prolong(gmt_hierarchy* const* hs, int n, int level, const void* const* uc,
+                   void* const* uf);
+void batch_coarse_solve(gmt_hierarchy* const* hs, int n, const void* const* f, void* const* u);
 inline size_t prec_bytes(Prec p) { return p == P64 ? 8 : (p == P32 ? 4 : 2); }
 
 }  // namespace gmt

@@ -38,8 +38,11 @@ namespace gmt {
 // one-node halo, 16-byte groups of values) is in shared memory: this thread's node gets
 // acc = sum_d S_n(d) u_{n+d} and the mode's epilogue. self: the node's own values; fpre
 // (FPRE): its right-hand side, already loaded.
-template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS, bool FPRE>
-__device__ __forceinline__ void stencil_brick(const StArgs<TS, A, D, M>& p, int64_t b,
+// P: StArgs, or any parameter view with the same members (the batched launches of
+// batch.cu pass one lattice's pointers with the shared material's FineC).
+template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS, bool FPRE,
+          class P>
+__device__ __forceinline__ void stencil_brick(const P& p, int64_t b,
                                               const typename Vec16<A>::type* __restrict__ tile,
                                               const A (&fpre)[FPRE ? D * M : 1],
                                               const A (&self)[D * M]) {
@@ -331,12 +334,10 @@ __global__ void __launch_bounds__(64)
   stencil_brick<TS, A, D, M, KIND, MODE, SUMS, PREF>(p, b, tile, fpre, self);
 }
 
-// first smoothing step from a zero initial guess: out = scale * D^-1 f
-template <typename TS, typename A, int D, int M, int KIND>
-__global__ void k_diag(const __grid_constant__ StArgs<TS, A, D, M> p, int64_t nslots) {
+// first smoothing step from a zero initial guess: out = scale * D^-1 f, at one slot
+template <typename TS, typename A, int D, int M, int KIND, class P>
+__device__ __forceinline__ void diag_slot(const P& p, int64_t slot) {
   constexpr int C = D * M;
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nslots) return;
   const unsigned mk = p.mask[slot];
   A Iv[D * D];
   if (mk) {
@@ -362,6 +363,12 @@ __global__ void k_diag(const __grid_constant__ StArgs<TS, A, D, M> p, int64_t ns
       if (p.dout) p.dout[vaddr(slot, i * M + m, C)] = store_as<TS>(o);
     }
   }
+}
+
+template <typename TS, typename A, int D, int M, int KIND>
+__global__ void k_diag(const __grid_constant__ StArgs<TS, A, D, M> p, int64_t nslots) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot < nslots) diag_slot<TS, A, D, M, KIND>(p, slot);
 }
 
 // ------------------------------------------------------------------ float-float residual

@@ -678,6 +678,7 @@ void check_loss(const gmt_unet* net, const gmt_netgraph* G, const gmt_hierarchy*
 }  // namespace
 
 #define UNET_BEGIN \
+  gmt::ApiGuard gmt_api_guard; \
   gmt::set_error("%s", ""); \
   try {
 #define UNET_END                                   \

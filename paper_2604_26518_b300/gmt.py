@@ -109,6 +109,7 @@ _SIGS = {
     "gmt_prolong": (_I, [_P, _I, _I, _P, _P]),
     "gmt_coarse_solve": (_I, [_P, _P, _P]),
     "gmt_vcycle": (_I, [_P, _I, _P, _P, _I]),
+    "gmt_vcycle_batch": (_I, [_P, _I, _P, _P, _I]),
     "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
@@ -431,6 +432,26 @@ class Hierarchy:
 
 UNET_WIDTHS = (32, 64, 128)
 LOSS_MSE, LOSS_ENERGY = 0, 1
+
+
+BATCH_MAX = 64
+
+
+def vcycle_batch(hierarchies, fs, us=None):
+    """One FP32 V-cycle on each hierarchy at once (gmt_vcycle_batch): returns the fields
+    u_i = V-cycle(f_i) (from zero, or from us[i]), each bitwise the one Hierarchy.vcycle
+    returns at FP32 precision. The hierarchies share the material, options and stream."""
+    n = len(hierarchies)
+    if not 1 <= n <= BATCH_MAX or len(fs) != n or (us is not None and len(us) != n):
+        raise ValueError(f"batch of {n} hierarchies with {len(fs)} loads (1..{BATCH_MAX})")
+    f = [h._field(0, x) for h, x in zip(hierarchies, fs)]
+    u = [h._field(0, None if us is None else x).clone() for h, x in
+         zip(hierarchies, us if us is not None else [None] * n)]
+    hp = (_P * n)(*[h._h for h in hierarchies])
+    fp = (_P * n)(*[_ptr(x) for x in f])
+    up = (_P * n)(*[_ptr(x) for x in u])
+    _check(lib().gmt_vcycle_batch(hp, n, fp, up, int(us is None)), "gmt_vcycle_batch")
+    return u
 
 
 def unet_layers(out_channels: int, widths=UNET_WIDTHS):
