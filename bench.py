@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 from concurrent.futures import ThreadPoolExecutor
 
@@ -52,6 +53,21 @@ NCU_DRAM_BYTES_PER_NODE = {
     # the 88,670 level-1 nodes of the first bench cell (stored per-node stencils + vectors)
     "stencil_l1": (116.924672e6 + 3.106304e6) / 88670,
 }
+
+
+class _CellQueue:
+    """Cell indices handed out one at a time to the worker threads."""
+
+    def __init__(self, items):
+        self._it = iter(items)
+        self._lock = threading.Lock()
+
+    def __iter__(self):
+        return self
+
+    def __next__(self):
+        with self._lock:
+            return next(self._it)
 
 
 def workload(name: str, rank: int):
@@ -314,15 +330,18 @@ def run_gmt(args, rank: int, world: int):
 
     cycles_seen = []
     unconverged, fallbacks = [], []   # cell indices, appended by every step
-    # Cells are independent: with --streams S > 1, S host threads each solve every S-th cell
-    # on a stream of their own, so that one cell's host synchronisations and small coarse-
-    # level kernels overlap another cell's work. The step starts and ends on `stream`.
+    # Cells are independent: with --streams S > 1, S host threads take cells from a shared
+    # queue (largest first) and solve each on the thread's own stream, so that one cell's
+    # host synchronisations and small coarse-level kernels overlap another cell's work. The
+    # step starts and ends on `stream`.
     nstreams = max(1, args.streams)
     wstreams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)] if nstreams > 1 else [stream]
     pool = ThreadPoolExecutor(max_workers=nstreams) if nstreams > 1 else None
 
     net, learned = None, None
     if args.learned:
+        if args.batched:
+            raise SystemExit("--learned runs per-cell solves (no --batched)")
         net, learned = train_initializer(args, ph, opts)
 
     def run_cells(src, idx, s, trace):
@@ -378,7 +397,54 @@ def run_gmt(args, rank: int, world: int):
             h.free()
         return tot, CH, cyc
 
+    # --batched: the cells of a step are split into `nstreams` groups, each solved by one
+    # gmt_solve_batch call from a worker thread (the V-cycles of a group's cells as shared
+    # batched launches; the groups overlap like the per-cell streams do); every cell has a
+    # stream of its own for its hierarchy and the per-cell solver work
+    cstreams = [torch.cuda.Stream(device=dev) for _ in cells] if args.batched else []
+
+    def run_group(src, idx):
+        hs = [gmt.Hierarchy(src[i], opts, cstreams[i]) for i in idx]
+        CH, cyc = {}, []
+        for j0 in range(0, len(hs), gmt.BATCH_MAX):
+            res = gmt.solve_batch(hs[j0:j0 + gmt.BATCH_MAX], ph, E=1.0, nu=0.3, k=1.0, tol=TOL,
+                                  want_fields=False, allow_not_converged=True)
+            for j, (st, _, info) in enumerate(res):
+                i = idx[j0 + j]
+                if st == gmt.NOT_CONVERGED:
+                    unconverged.append(i)
+                elif st != gmt.OK:
+                    raise RuntimeError(f"solve status {st}: {info.as_dict()}")
+                if info.fp64_fallback:
+                    fallbacks.append(i)
+                cyc.append((i, info.inner_total))
+        for i, h in zip(idx, hs):
+            CH[i] = h.homogenize(ph, E=1.0, nu=0.3, k=1.0)
+            h.free()
+        return CH, cyc
+
+    def batched_step(src):
+        start = torch.cuda.Event()
+        start.record(stream)
+        for s in cstreams:
+            s.wait_event(start)
+        groups = [list(range(w, len(src), nstreams)) for w in range(nstreams)]
+        parts = (list(pool.map(lambda g: run_group(src, g), groups)) if pool
+                 else [run_group(src, groups[0])])
+        for s in cstreams:
+            done = torch.cuda.Event()
+            done.record(s)
+            stream.wait_event(done)
+        CH, cyc = {}, []
+        for c_, y_ in parts:
+            CH.update(c_)
+            cyc.extend(y_)
+        cycles_seen.extend(c for _, c in sorted(cyc))
+        return {}, [CH[i] for i in range(len(src))]
+
     def one_step(src, trace, serial=False):
+        if args.batched and not trace:
+            return batched_step(src)
         if pool is None or serial:
             parts = [run_cells(src, range(len(src)), stream, trace)]
         else:
@@ -386,8 +452,10 @@ def run_gmt(args, rank: int, world: int):
             start.record(stream)
             for s in wstreams:
                 s.wait_event(start)
-            futs = [pool.submit(run_cells, src, range(w, len(src), nstreams), wstreams[w], trace)
-                    for w in range(nstreams)]
+            # a shared queue, largest cells first: a worker held up by a slow cell leaves
+            # the remaining cells to the others
+            q = _CellQueue(sorted(range(len(src)), key=lambda i: -src[i].numel()))
+            futs = [pool.submit(run_cells, src, q, wstreams[w], trace) for w in range(nstreams)]
             parts = [f.result() for f in futs]
             for s in wstreams:
                 done = torch.cuda.Event()
@@ -538,7 +606,9 @@ def run_gmt(args, rank: int, world: int):
                    "omega": opts.omega,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
-                   "concurrent_cells": nstreams},
+                   "concurrent_cells": nstreams,
+                   "solve": ("gmt_solve_batch: the cells' V-cycles as shared batched launches"
+                             if args.batched else "gmt_solve per cell")},
         "e2e": {"value": e2e_value, "unit": "C^H solves/s",
                 "h2d_bytes_per_step": int(sum(v.numel() for v in vox_host)),
                 "d2h_bytes_per_step": int(len(cells) * (36 if ph == gmt.ELASTIC else 9) * 8)},
@@ -689,6 +759,8 @@ def main():
                     help="smoothing sweeps on levels >= 1 (0: as on level 0)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="mixed precision: true-residual replacement factor (0: default)")
+    ap.add_argument("--batched", action="store_true",
+                    help="solve the cells of a step together (gmt_solve_batch)")
     ap.add_argument("--streams", type=int, default=4,
                     help="cells solved concurrently, one host thread and CUDA stream each")
     ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev", "gs8"])

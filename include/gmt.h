@@ -209,9 +209,10 @@ gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* 
    together and the launch count does not grow with n. The hierarchies must share the
    material (physics and parameters of gmt_prepare), have no element densities, use the
    damped-Jacobi smoother and the V-cycle with the same omega, nu_pre, nu_post, nu_coarse,
-   have the same number of levels, and run on the same device and stream; otherwise
-   GMT_ERR_ARG (GMT_ERR_STATE if one is not prepared). The launches go to that stream and
-   the call returns after it has finished them. */
+   and run on the same device and stream; otherwise GMT_ERR_ARG (GMT_ERR_STATE if one is
+   not prepared). Sizes and level counts may differ: at each level the lattices whose
+   coarsest level it is take their coarsest solve in one launch, the others go on down.
+   The launches go to that stream and the call returns after it has finished them. */
 gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
                             double* const* u, int zero_init);
 
@@ -226,6 +227,23 @@ gmt_status gmt_lambda_max(gmt_hierarchy* h, int level, double* out);
    an error. Fields are gauge-fixed: zero mean over active nodes per component/case. */
 gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
                      double tol, const double* u0, double* u_out, gmt_info* info);
+
+/* Solves the cell problems of n (1..GMT_BATCH_MAX) distinct hierarchies together, each
+   exactly as gmt_solve(hs[i], physics, E, nu, k, tol, u0[i], u_out[i], &info[i]) would:
+   every field, gmt_info and stored solution is bitwise what that call returns, including
+   the FP64 fallback of a diverging cell. One host thread per hierarchy runs its solve on
+   the hierarchy's own stream; the mixed-precision V-cycles of all lattices still iterating
+   run as one batched V-cycle (as gmt_vcycle_batch) on a stream of the call's own, so the
+   small coarse levels of all cells share each launch. The hierarchies must be on one
+   device and use mixed precision (GMT_PREC_FP32), the damped-Jacobi smoother and the
+   V-cycle with the same omega, nu_pre, nu_post and nu_coarse, without element densities;
+   their sizes and level counts may differ. u0 and u_out are arrays of n device pointers,
+   or NULL (entries may be NULL: zero start / no copy out, as for gmt_solve); info and
+   status, if not NULL, receive n entries. Returns GMT_OK when every lattice returned
+   GMT_OK, else the first lattice's other status (gmt_last_error names the lattice). */
+gmt_status gmt_solve_batch(gmt_hierarchy* const* hs, int n, gmt_physics physics, double E,
+                           double nu, double k, double tol, const double* const* u0,
+                           double* const* u_out, gmt_info* info, gmt_status* status);
 
 /* Homogenized tensor (App. F.1 C^H, App. F.2 kappa^H): CH_out host double[M][M]
    row-major = 1/N^3 sum_e (x0^I - u_e^I)^T K_e (x0^J - u_e^J). u: device canonical field,

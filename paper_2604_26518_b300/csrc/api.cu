@@ -2,6 +2,9 @@
 // Every entry point validates its arguments, converts internal failures into a
 // gmt_status, and never lets an exception or a CUDA error escape.
 #include <chrono>
+#include <functional>
+#include <string>
+#include <vector>
 #include <cmath>
 #include <cstring>
 
@@ -22,6 +25,10 @@ void step_coarse(gmt_hierarchy* h, const double* f, double* u);
 void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero);
 void step_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
                        double* const* u, bool zero);
+void run_batched(gmt_hierarchy* const* hs, int n, const std::function<void(int)>& body);
+void leave_batch_group();
+void prepare_batched_levels(gmt_hierarchy* h);
+bool batch_thread();
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);
 void export_elems(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* c);
 void export_stencil(gmt_hierarchy* h, int l, int32_t* idx, double* w);
@@ -371,8 +378,6 @@ gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const
     GMT_REQUIRE(!h->dens, GMT_ERR_ARG, "batched V-cycle: hierarchy %d has element densities", i);
     GMT_REQUIRE(h->device == a->device && h->stream == a->stream, GMT_ERR_ARG,
                 "batched V-cycle: hierarchy %d is on another device or stream", i);
-    GMT_REQUIRE(h->L == a->L, GMT_ERR_ARG, "batched V-cycle: hierarchy %d has %d levels, not %d",
-                i, h->L, a->L);
     GMT_REQUIRE(o.omega == a->opts.omega && o.nu_pre == a->opts.nu_pre &&
                     o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse,
                 GMT_ERR_ARG, "batched V-cycle: hierarchy %d has other smoothing options", i);
@@ -397,16 +402,19 @@ gmt_status gmt_lambda_max(gmt_hierarchy* h, int level, double* out) {
   GMT_API_END
 }
 
-gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
-                     double tol, const double* u0, double* u_out, gmt_info* info) {
-  GMT_API_BEGIN
-  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
-  GMT_REQUIRE(tol > 0 && tol < 1, GMT_ERR_ARG, "tol must be in (0, 1)");
+// gmt_solve's work (throws Fail): the solve at the hierarchy's precision and, when the
+// mixed-precision iteration diverges, the plain FP64 solve. Inside gmt_solve_batch the
+// lattice leaves the batch's shared V-cycles when its mixed-precision iteration ends.
+static gmt_status solve_one(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
+                            double k, double tol, const double* u0, double* u_out,
+                            gmt_info* info) {
   ensure_device(h);
   double setup = 0.0;
   ensure_material(h, physics, E, nu, k, &setup);
+  if (gmt::batch_thread()) gmt::prepare_batched_levels(h);
   gmt_info first;
   gmt_status st = gmt::solve(h, tol, u0, u_out, info ? info : &first);
+  gmt::leave_batch_group();
   if (info) info->fp64_fallback = 0;
   if (st == GMT_DIVERGED && h->opts.precision != GMT_PREC_FP64 && h->opts.fp64_fallback) {
     // the mixed-precision iteration failed on this cell: solve again in plain FP64
@@ -429,6 +437,70 @@ gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
   }
   if (info) info->t_setup_ms = setup;
   return st;
+}
+
+gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                     double tol, const double* u0, double* u_out, gmt_info* info) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  GMT_REQUIRE(tol > 0 && tol < 1, GMT_ERR_ARG, "tol must be in (0, 1)");
+  return solve_one(h, physics, E, nu, k, tol, u0, u_out, info);
+  GMT_API_END
+}
+
+gmt_status gmt_solve_batch(gmt_hierarchy* const* hs, int n, gmt_physics physics, double E,
+                           double nu, double k, double tol, const double* const* u0,
+                           double* const* u_out, gmt_info* info, gmt_status* status) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(hs, GMT_ERR_ARG, "null hierarchy array");
+  GMT_REQUIRE(n >= 1 && n <= GMT_BATCH_MAX, GMT_ERR_ARG, "batch of %d hierarchies (1..%d)", n,
+              GMT_BATCH_MAX);
+  GMT_REQUIRE(tol > 0 && tol < 1, GMT_ERR_ARG, "tol must be in (0, 1)");
+  for (int i = 0; i < n; ++i) {
+    GMT_REQUIRE(hs[i], GMT_ERR_ARG, "null hierarchy %d", i);
+    for (int j = 0; j < i; ++j)
+      GMT_REQUIRE(hs[j] != hs[i], GMT_ERR_ARG, "hierarchy %d appears twice", i);
+  }
+  const gmt_hierarchy* a = hs[0];
+  for (int i = 0; i < n; ++i) {
+    const gmt_hierarchy* h = hs[i];
+    const gmt_options& o = h->opts;
+    GMT_REQUIRE(o.precision == GMT_PREC_FP32, GMT_ERR_ARG,
+                "batched solve: mixed precision only (hierarchy %d)", i);
+    GMT_REQUIRE(o.smoother == GMT_SMOOTH_JACOBI && o.cycle == GMT_CYCLE_V, GMT_ERR_ARG,
+                "batched solve: damped-Jacobi smoother and V-cycle only (hierarchy %d)", i);
+    GMT_REQUIRE(!h->dens, GMT_ERR_ARG, "batched solve: hierarchy %d has element densities", i);
+    GMT_REQUIRE(h->device == a->device, GMT_ERR_ARG,
+                "batched solve: hierarchy %d is on another device", i);
+    GMT_REQUIRE(o.omega == a->opts.omega && o.nu_pre == a->opts.nu_pre &&
+                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse,
+                GMT_ERR_ARG, "batched solve: hierarchy %d has other smoothing options", i);
+  }
+  std::vector<gmt_status> st(n, GMT_OK);
+  std::vector<std::string> msg(n);
+  gmt::run_batched(hs, n, [&](int i) {
+    try {
+      st[i] = solve_one(hs[i], physics, E, nu, k, tol, u0 ? u0[i] : nullptr,
+                        u_out ? u_out[i] : nullptr, info ? &info[i] : nullptr);
+    } catch (const Fail& f) {
+      gmt::leave_batch_group();
+      st[i] = f.status;
+      msg[i] = gmt::last_error();
+    } catch (...) {
+      gmt::leave_batch_group();
+      st[i] = GMT_ERR_ARG;
+      msg[i] = "unexpected host exception";
+    }
+  });
+  gmt_status worst = GMT_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = st[i];
+    if (worst == GMT_OK && st[i] != GMT_OK) {
+      worst = st[i];
+      if (!msg[i].empty()) gmt::set_error("lattice %d: %s", i, msg[i].c_str());
+    }
+  }
+  return worst;
   GMT_API_END
 }
 

@@ -53,6 +53,8 @@ struct StPtrs {
   const TS* f;
   TS* out;
   int64_t nslots;
+  double* part;    // SUMS: the sweep's per-brick partials (see stencil_brick)
+  const TS* aux;   // SUMS: the vector dotted with the result per case (or nullptr)
 };
 
 template <typename TS, typename A, int D, int M>
@@ -64,8 +66,9 @@ struct MultiSt {
   StPtrs<TS, A> lp[kBatchMax];
 };
 
-// the stencil sweep (Jacobi or residual) of brick b of lattice l, as k_stencil does it
-template <typename TS, typename A, int D, int M, int KIND, int MODE>
+// the stencil sweep (Jacobi or residual) of brick b of lattice l, as k_stencil does it;
+// SUMS: a Jacobi sweep that also writes the fused Krylov partials
+template <typename TS, typename A, int D, int M, int KIND, int MODE, bool SUMS = false>
 __global__ void __launch_bounds__(64) k_stencil_multi(const __grid_constant__ MultiSt<TS, A, D, M> mp) {
   using V = typename Vec16<A>::type;
   constexpr int C = D * M, NV = Vec16<A>::n, G = (C + NV - 1) / NV;
@@ -87,9 +90,9 @@ __global__ void __launch_bounds__(64) k_stencil_multi(const __grid_constant__ Mu
   A self[C];
   stage_tile<TS, A, C>(lp.u, b, t, nb, tile, self);
   __syncthreads();
-  const LatView<TS, A, D, M> v{lp.mask, lp.kmat, lp.dinv, lp.f, nullptr, nullptr, lp.out,
-                               nullptr, nullptr, mp.omega, A(0), A(0), -1, mp.fc};
-  stencil_brick<TS, A, D, M, KIND, MODE, false, PREF>(v, b, tile, fpre, self);
+  const LatView<TS, A, D, M> v{lp.mask, lp.kmat, lp.dinv, lp.f, nullptr, lp.aux, lp.out,
+                               nullptr, lp.part, mp.omega, A(0), A(0), -1, mp.fc};
+  stencil_brick<TS, A, D, M, KIND, MODE, SUMS, PREF>(v, b, tile, fpre, self);
 }
 
 // first smoothing step from zero, slots of lattice l in blocks of 128
@@ -203,34 +206,43 @@ __global__ void k_zero_multi(const __grid_constant__ MultiCs mp) {
 // ------------------------------------------------------------------ host launchers
 static unsigned nblocks(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// one launch over the lattices `sel` of hs (diag: the first smoothing step from zero)
 template <int D, int M>
-static void stencil_multi_t(gmt_hierarchy* const* hs, int n, int level, StencilMode mode,
-                            const void* const* u, const void* const* f, void* const* out,
-                            double omega, bool diag) {
+static void stencil_multi_t(gmt_hierarchy* const* hs, const std::vector<int>& sel,
+                            cudaStream_t s, int level, StencilMode mode, const void* const* u,
+                            const void* const* f, void* const* out, double* const* part,
+                            const void* const* aux, double omega, bool diag) {
   using TS = float;
   using A = float;
+  if (sel.empty()) return;
   auto mp = std::make_unique<MultiSt<TS, A, D, M>>();
   std::memset(mp.get(), 0, sizeof(*mp));
   fill_fine<A, D, M>(hs[0]->mat, mp->fc);
   mp->omega = (A)omega;
-  mp->n = n;
+  mp->n = (int)sel.size();
   const bool fine = level == 0;
+  const bool sums = part != nullptr && part[sel[0]] != nullptr;
   int64_t tot = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int k = 0; k < mp->n; ++k) {
+    const int i = sel[k];
     Level& lv = hs[i]->lv[level];
-    if (!fine) build_node_stencils(hs[i], level, false);
-    mp->start[i] = tot;
+    GMT_REQUIRE(fine || lv.S32 != nullptr, GMT_ERR_STATE,
+                "batched sweep: level %d stencils of lattice %d are not built", level, i);
+    mp->start[k] = tot;
     tot += diag ? (int64_t)nblocks(lv.nslots, 128) : lv.nb;
-    mp->lp[i] = StPtrs<TS, A>{lv.brick_nbr, lv.mask, (const A*)lv.S32, (const A*)lv.dinv32,
-                              (const TS*)u[i], (const TS*)f[i], (TS*)out[i], lv.nslots};
+    mp->lp[k] = StPtrs<TS, A>{lv.brick_nbr, lv.mask, (const A*)lv.S32, (const A*)lv.dinv32,
+                              (const TS*)u[i], (const TS*)f[i], (TS*)out[i], lv.nslots,
+                              sums ? part[i] : nullptr,
+                              sums && aux ? (const TS*)aux[i] : nullptr};
   }
-  mp->start[n] = tot;
+  mp->start[mp->n] = tot;
   if (tot == 0) return;
-  cudaStream_t s = hs[0]->stream;
   const unsigned g = (unsigned)tot;
   if (diag) {
     if (fine) k_diag_multi<TS, A, D, M, 0><<<g, 128, 0, s>>>(*mp);
     else k_diag_multi<TS, A, D, M, 1><<<g, 128, 0, s>>>(*mp);
+  } else if (mode == ST_JACOBI && sums) {
+    k_stencil_multi<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(*mp);
   } else if (mode == ST_JACOBI) {
     if (fine) k_stencil_multi<TS, A, D, M, 0, ST_JACOBI><<<g, 64, 0, s>>>(*mp);
     else k_stencil_multi<TS, A, D, M, 1, ST_JACOBI><<<g, 64, 0, s>>>(*mp);
@@ -241,31 +253,54 @@ static void stencil_multi_t(gmt_hierarchy* const* hs, int n, int level, StencilM
   GMT_LAUNCH_CHECK();
 }
 
-static void check_batch(int n) {
+static void check_batch(gmt_hierarchy* const* hs, int n) {
   GMT_REQUIRE(n >= 1 && n <= kBatchMax, GMT_ERR_ARG, "batch of %d lattices (1..%d)", n, kBatchMax);
+  for (int i = 1; i < n; ++i)
+    GMT_REQUIRE(hs[i]->mat.D == hs[0]->mat.D, GMT_ERR_ARG, "batched launch mixes physics");
 }
 
-void batch_stencil(gmt_hierarchy* const* hs, int n, int level, StencilMode mode,
-                   const void* const* u, const void* const* f, void* const* out) {
-  check_batch(n);
+template <int D, int M>
+static void stencil_split_t(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                            StencilMode mode, const void* const* u, const void* const* f,
+                            void* const* out, double* const* part, const void* const* aux,
+                            double omega, bool diag) {
+  // lattices with and without the fused partials go to separate launches
+  std::vector<int> with, without;
+  for (int i = 0; i < n; ++i) (part && part[i] ? with : without).push_back(i);
+  stencil_multi_t<D, M>(hs, without, s, level, mode, u, f, out, nullptr, nullptr, omega, diag);
+  stencil_multi_t<D, M>(hs, with, s, level, mode, u, f, out, part, aux, omega, diag);
+}
+
+void prepare_batched_levels(gmt_hierarchy* h) {
+  for (int l = 1; l + 1 < h->L; ++l) build_node_stencils(h, l, false);
+}
+
+void batch_stencil(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                   StencilMode mode, const void* const* u, const void* const* f,
+                   void* const* out, double* const* part, const void* const* aux) {
+  check_batch(hs, n);
   GMT_REQUIRE(mode == ST_JACOBI || mode == ST_RESID, GMT_ERR_ARG, "batched stencil mode");
-  if (hs[0]->mat.D == 3) stencil_multi_t<3, 6>(hs, n, level, mode, u, f, out, hs[0]->opts.omega, false);
-  else stencil_multi_t<1, 3>(hs, n, level, mode, u, f, out, hs[0]->opts.omega, false);
+  GMT_REQUIRE(part == nullptr || (level == 0 && mode == ST_JACOBI), GMT_ERR_ARG,
+              "fused partials belong to a level-0 smoothing sweep");
+  const double om = hs[0]->opts.omega;
+  if (hs[0]->mat.D == 3) stencil_split_t<3, 6>(hs, n, s, level, mode, u, f, out, part, aux, om, false);
+  else stencil_split_t<1, 3>(hs, n, s, level, mode, u, f, out, part, aux, om, false);
 }
 
-void batch_diag(gmt_hierarchy* const* hs, int n, int level, const void* const* f,
-                void* const* out, double scale) {
-  check_batch(n);
-  if (hs[0]->mat.D == 3) stencil_multi_t<3, 6>(hs, n, level, ST_JACOBI, f, f, out, scale, true);
-  else stencil_multi_t<1, 3>(hs, n, level, ST_JACOBI, f, f, out, scale, true);
+void batch_diag(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                const void* const* f, void* const* out, double scale) {
+  check_batch(hs, n);
+  if (hs[0]->mat.D == 3)
+    stencil_split_t<3, 6>(hs, n, s, level, ST_JACOBI, f, f, out, nullptr, nullptr, scale, true);
+  else
+    stencil_split_t<1, 3>(hs, n, s, level, ST_JACOBI, f, f, out, nullptr, nullptr, scale, true);
 }
 
 template <int C>
-static void transfer_multi_t(gmt_hierarchy* const* hs, int n, int level, const void* const* in,
-                             void* const* out, bool restrict_) {
+static void transfer_multi_t(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                             const void* const* in, void* const* out, bool restrict_) {
   using TS = float;
   using A = float;
-  cudaStream_t s = hs[0]->stream;
   // two launches at most: lattices whose two levels are both bricked (tiled form) and the
   // others (a dense coarsest level: per-node form)
   for (int tiled = 1; tiled >= 0; --tiled) {
@@ -304,18 +339,18 @@ static void transfer_multi_t(gmt_hierarchy* const* hs, int n, int level, const v
   }
 }
 
-void batch_restrict(gmt_hierarchy* const* hs, int n, int level, const void* const* rf,
-                    void* const* fc) {
-  check_batch(n);
-  if (hs[0]->mat.D == 3) transfer_multi_t<18>(hs, n, level, rf, fc, true);
-  else transfer_multi_t<3>(hs, n, level, rf, fc, true);
+void batch_restrict(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                    const void* const* rf, void* const* fc) {
+  check_batch(hs, n);
+  if (hs[0]->mat.D == 3) transfer_multi_t<18>(hs, n, s, level, rf, fc, true);
+  else transfer_multi_t<3>(hs, n, s, level, rf, fc, true);
 }
 
-void batch_prolong(gmt_hierarchy* const* hs, int n, int level, const void* const* uc,
-                   void* const* uf) {
-  check_batch(n);
-  if (hs[0]->mat.D == 3) transfer_multi_t<18>(hs, n, level, uc, uf, false);
-  else transfer_multi_t<3>(hs, n, level, uc, uf, false);
+void batch_prolong(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                   const void* const* uc, void* const* uf) {
+  check_batch(hs, n);
+  if (hs[0]->mat.D == 3) transfer_multi_t<18>(hs, n, s, level, uc, uf, false);
+  else transfer_multi_t<3>(hs, n, s, level, uc, uf, false);
 }
 
 template <typename Kern, typename Count>
@@ -332,9 +367,9 @@ static void launch_cs(MultiCs& mp, int n, Kern kern, Count count, int per, cudaS
 }
 
 template <int D, int M>
-static void coarse_multi_t(gmt_hierarchy* const* hs, int n, const void* const* f, void* const* u) {
+static void coarse_multi_t(gmt_hierarchy* const* hs, int n, cudaStream_t s, const void* const* f,
+                           void* const* u) {
   constexpr int C = D * M;
-  cudaStream_t s = hs[0]->stream;
   auto mp = std::make_unique<MultiCs>();
   std::memset(mp.get(), 0, sizeof(*mp));
   mp->n = n;
@@ -350,10 +385,23 @@ static void coarse_multi_t(gmt_hierarchy* const* hs, int n, const void* const* f
   launch_cs(*mp, n, k_coarse_scatter_multi<D, M>, [](const CsPtrs& p) { return p.nn * C; }, 256, s);
 }
 
-void batch_coarse_solve(gmt_hierarchy* const* hs, int n, const void* const* f, void* const* u) {
-  check_batch(n);
-  if (hs[0]->mat.D == 3) coarse_multi_t<3, 6>(hs, n, f, u);
-  else coarse_multi_t<1, 3>(hs, n, f, u);
+void batch_coarse_solve(gmt_hierarchy* const* hs, int n, cudaStream_t s, const void* const* f,
+                        void* const* u) {
+  check_batch(hs, n);
+  if (hs[0]->mat.D == 3) coarse_multi_t<3, 6>(hs, n, s, f, u);
+  else coarse_multi_t<1, 3>(hs, n, s, f, u);
+}
+
+void batch_zero(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level, void* const* x) {
+  check_batch(hs, n);
+  auto mp = std::make_unique<MultiCs>();
+  std::memset(mp.get(), 0, sizeof(*mp));
+  mp->n = n;
+  for (int i = 0; i < n; ++i) {
+    mp->lp[i].u = (float*)x[i];
+    mp->lp[i].nvals = hs[i]->lv[level].nslots * hs[i]->mat.C;
+  }
+  launch_cs(*mp, n, k_zero_multi, [](const CsPtrs& p) { return p.nvals; }, 256, s);
 }
 
 }  // namespace gmt

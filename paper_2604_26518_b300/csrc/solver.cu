@@ -10,7 +10,13 @@
 // Gauge (Sec. 3.1 zero-mean constraint): the mean over active nodes of every component
 // and case is removed from the final field. Load cases whose assembled load cancels
 // (||f_m|| <= 1e-12 of its gross element-load norm) have u_m = 0 and r_m = 0.
+#include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
@@ -337,7 +343,12 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
 // cell) never capture, and long solves replay.
 constexpr int kDirectBeforeCapture = 16;
 
+static void* group_vcycle(gmt_hierarchy* h, Workspace* w, int form);
+bool in_batch_group(const Workspace* w);
+bool batch_thread();
+
 static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
+  if (in_batch_group(w)) return group_vcycle(h, w, form);   // gmt_solve_batch
   double* part = form ? w->part : nullptr;
   const void* aux = form ? w->q : nullptr;
   Workspace::Captured& c = w->vg[form];
@@ -346,7 +357,7 @@ static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
     return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
   };
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  const bool can = h->opts.graphs != 0 && !h->tracer.on && h->stream != nullptr &&
+  const bool can = h->opts.graphs != 0 && !h->tracer.on && h->stream != nullptr && !batch_thread() &&
                    cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess &&
                    cap == cudaStreamCaptureStatusNone;
   if (!can) {
@@ -924,76 +935,267 @@ void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bo
 }
 
 // ------------------------------------------------------------------ batched V-cycle
-// The FP32 damped-Jacobi V-cycle of step_vcycle on n hierarchies at once: each phase (diag
-// start, sweep, residual, restriction, coarsest solve, prolongation) is one launch over all
-// n lattices' bricks (batch.cu), in the order the single-lattice cycle runs them, so every
-// lattice's result is bitwise its own V-cycle's. The caller has checked that the lattices
-// share the material, the options, the level count and the stream.
+// The FP32 damped-Jacobi V-cycle of vcycle() on several hierarchies at once: each phase
+// (first sweep from zero, sweep, residual, restriction, coarsest solve, prolongation) is
+// one launch over the bricks of all of them (batch.cu), in the order the single-lattice
+// cycle runs them, so every lattice's result is bitwise its own V-cycle's. Lattices may
+// have different level counts: at level l those whose coarsest level is l take their
+// coarsest solve, the others the smoothing part of the cycle.
 using PtrVec = std::vector<void*>;
 
-static void bsmooth(gmt_hierarchy* const* hs, int n, int l, const PtrVec& f, PtrVec& u,
-                    PtrVec& o, int sweeps, bool zero) {
+struct BMember {
+  gmt_hierarchy* h;
+  Workspace* w;
+};
+
+static void bsmooth(std::vector<gmt_hierarchy*>& hs, cudaStream_t s, int l, const PtrVec& f,
+                    PtrVec& u, PtrVec& o, int sweeps, bool zero,
+                    const std::vector<double*>* part, const PtrVec* aux) {
+  const int n = (int)hs.size();
   if (sweeps <= 0) {
-    if (zero)
-      for (int i = 0; i < n; ++i) vec_zero(hs[i], l, P32, u[i]);
+    if (zero) batch_zero(hs.data(), n, s, l, u.data());
     return;
   }
   int s0 = 0;
   if (zero) {
-    batch_diag(hs, n, l, f.data(), u.data(), hs[0]->opts.omega);
+    batch_diag(hs.data(), n, s, l, f.data(), u.data(), hs[0]->opts.omega);
     s0 = 1;
   }
-  for (int s = s0; s < sweeps; ++s) {
-    batch_stencil(hs, n, l, ST_JACOBI, u.data(), f.data(), o.data());
+  for (int k = s0; k < sweeps; ++k) {
+    const bool last = k + 1 == sweeps;
+    batch_stencil(hs.data(), n, s, l, ST_JACOBI, u.data(), f.data(), o.data(),
+                  last && part ? part->data() : nullptr, last && aux ? aux->data() : nullptr);
     std::swap(u, o);
   }
 }
 
-static PtrVec bvcycle(gmt_hierarchy* const* hs, Workspace* const* ws, int n, int l,
-                      const PtrVec& f, const PtrVec* init) {
-  PtrVec u(n), o(n);
-  if (l == hs[0]->L - 1) {
-    for (int i = 0; i < n; ++i) u[i] = ws[i]->ua[l];
-    batch_coarse_solve(hs, n, f.data(), u.data());
-    return u;
-  }
+// m[i] at level l (l <= its coarsest level) for K_l u = f[i], from init[i] (or zero);
+// part/aux (level 0): the last post-smoothing sweep also writes the fused Krylov partials
+static PtrVec bvcycle(const std::vector<BMember>& m, int l, const PtrVec& f, const PtrVec* init,
+                      const std::vector<double*>* part, const PtrVec* aux, cudaStream_t s) {
+  const int n = (int)m.size();
+  PtrVec u(n, nullptr);
+  std::vector<gmt_hierarchy*> hc;
+  PtrVec fc, uc;
+  std::vector<int> sm;
   for (int i = 0; i < n; ++i) {
-    u[i] = init ? (*init)[i] : ws[i]->ua[l];
-    o[i] = u[i] == ws[i]->ua[l] ? ws[i]->ub[l] : ws[i]->ua[l];
+    if (m[i].h->L - 1 == l) {
+      hc.push_back(m[i].h);
+      fc.push_back(f[i]);
+      uc.push_back(m[i].w->ua[l]);
+      u[i] = m[i].w->ua[l];
+    } else {
+      sm.push_back(i);
+    }
+  }
+  if (!hc.empty()) batch_coarse_solve(hc.data(), (int)hc.size(), s, fc.data(), uc.data());
+  if (sm.empty()) return u;
+  const int k = (int)sm.size();
+  std::vector<BMember> mm;
+  std::vector<gmt_hierarchy*> hs;
+  PtrVec fs(k), us(k), os(k), r(k), fn(k), ax(k, nullptr);
+  std::vector<double*> pt(k, nullptr);
+  for (int j = 0; j < k; ++j) {
+    const int i = sm[j];
+    Workspace* w = m[i].w;
+    mm.push_back(m[i]);
+    hs.push_back(m[i].h);
+    fs[j] = f[i];
+    us[j] = init ? (*init)[i] : w->ua[l];
+    os[j] = us[j] == w->ua[l] ? w->ub[l] : w->ua[l];
+    r[j] = w->r[l];
+    fn[j] = w->f[l + 1];
+    if (part) {
+      pt[j] = (*part)[i];
+      ax[j] = (*aux)[i];
+    }
   }
   const gmt_options& op = hs[0]->opts;
   const int nu1 = (l > 0 && op.nu_coarse > 0) ? op.nu_coarse : op.nu_pre;
   const int nu2 = (l > 0 && op.nu_coarse > 0) ? op.nu_coarse : op.nu_post;
-  bsmooth(hs, n, l, f, u, o, nu1, init == nullptr);
-  PtrVec r(n), fc(n);
-  for (int i = 0; i < n; ++i) {
-    r[i] = ws[i]->r[l];
-    fc[i] = ws[i]->f[l + 1];
-  }
-  batch_stencil(hs, n, l, ST_RESID, u.data(), f.data(), r.data());
-  batch_restrict(hs, n, l, r.data(), fc.data());
-  const PtrVec uc = bvcycle(hs, ws, n, l + 1, fc, nullptr);
-  batch_prolong(hs, n, l, uc.data(), u.data());
-  bsmooth(hs, n, l, f, u, o, nu2, false);
+  bsmooth(hs, s, l, fs, us, os, nu1, init == nullptr, nullptr, nullptr);
+  batch_stencil(hs.data(), k, s, l, ST_RESID, us.data(), fs.data(), r.data());
+  batch_restrict(hs.data(), k, s, l, r.data(), fn.data());
+  const PtrVec ucn = bvcycle(mm, l + 1, fn, nullptr, nullptr, nullptr, s);
+  batch_prolong(hs.data(), k, s, l, ucn.data(), us.data());
+  bsmooth(hs, s, l, fs, us, os, nu2, false, part ? &pt : nullptr, part ? &ax : nullptr);
+  for (int j = 0; j < k; ++j) u[sm[j]] = us[j];
   return u;
 }
 
 void step_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
                        double* const* u, bool zero) {
-  std::vector<Workspace*> ws(n);
+  std::vector<BMember> m(n);
   PtrVec fs(n), init(n);
   for (int i = 0; i < n; ++i) {
-    ws[i] = workspace(hs[i], P32);
-    canon_to_slots(hs[i], 0, P32, f[i], ws[i]->f[0]);
-    fs[i] = ws[i]->f[0];
+    m[i] = BMember{hs[i], workspace(hs[i], P32)};
+    prepare_batched_levels(hs[i]);
+    canon_to_slots(hs[i], 0, P32, f[i], m[i].w->f[0]);
+    fs[i] = m[i].w->f[0];
     if (!zero) {
-      canon_to_slots(hs[i], 0, P32, u[i], ws[i]->ua[0]);
-      init[i] = ws[i]->ua[0];
+      canon_to_slots(hs[i], 0, P32, u[i], m[i].w->ua[0]);
+      init[i] = m[i].w->ua[0];
     }
   }
-  const PtrVec res = bvcycle(hs, ws.data(), n, 0, fs, zero ? nullptr : &init);
+  const PtrVec res = bvcycle(m, 0, fs, zero ? nullptr : &init, nullptr, nullptr, hs[0]->stream);
   for (int i = 0; i < n; ++i) slots_to_canon(hs[i], 0, P32, res[i], u[i]);
   GMT_CUDA(cudaStreamSynchronize(hs[0]->stream));
+}
+
+// ------------------------------------------------------------------ batched solves
+// Lattices solved together (gmt_solve_batch): one host thread per lattice runs the
+// single-lattice solve on the lattice's own stream; its mixed-precision V-cycles meet here.
+// Once every lattice still in its mixed-precision iteration has asked for a V-cycle, the
+// last to arrive launches one batched V-cycle for all of them on the group's stream
+// (ordered after each lattice's work by an event, and each lattice's stream after it by
+// another). Every lattice's arithmetic is that of its own solve, so its results are
+// bitwise gmt_solve's; the small coarse levels of all lattices share each launch.
+// The wait for the other lattices is a host wait with a time limit.
+constexpr int kRendezvousLimitS = 900;
+
+struct BatchGroup {
+  struct Req {
+    gmt_hierarchy* h;
+    Workspace* w;
+    int form;
+    void* out = nullptr;
+    bool done = false;
+    gmt_status st = GMT_OK;
+    std::string err;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  int members = 0;               // lattices still in their mixed-precision iteration
+  std::vector<Req*> pending;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t finished = nullptr;   // recorded after each batched V-cycle
+  std::vector<cudaEvent_t> ready;   // per lattice: its work before the V-cycle
+
+  // with mu held: one batched V-cycle for every pending request (each form its own)
+  void launch_locked() {
+    std::vector<Req*> batch;
+    batch.swap(pending);
+    gmt_status st = GMT_OK;
+    std::string err;
+    try {
+      for (int form = 0; form < 2; ++form) {
+        std::vector<BMember> m;
+        std::vector<Req*> rs;
+        PtrVec f, ax;
+        std::vector<double*> part;
+        for (Req* r : batch) {
+          if (r->form != form) continue;
+          m.push_back(BMember{r->h, r->w});
+          rs.push_back(r);
+          f.push_back(r->w->rr);
+          part.push_back(form ? r->w->part : nullptr);
+          ax.push_back(form ? r->w->q : nullptr);
+        }
+        if (m.empty()) continue;
+        const PtrVec out = bvcycle(m, 0, f, nullptr, form ? &part : nullptr,
+                                   form ? &ax : nullptr, stream);
+        for (size_t k = 0; k < rs.size(); ++k) rs[k]->out = out[k];
+      }
+      GMT_CUDA(cudaEventRecord(finished, stream));
+    } catch (const Fail& e) {
+      st = e.status;
+      err = last_error();
+    } catch (...) {
+      st = GMT_ERR_ARG;
+      err = "unexpected host exception in a batched V-cycle";
+    }
+    for (Req* r : batch) {
+      r->st = st;
+      r->err = err;
+      r->done = true;
+    }
+    cv.notify_all();
+  }
+
+  void* vcycle(gmt_hierarchy* h, Workspace* w, int form, cudaEvent_t ev) {
+    GMT_CUDA(cudaEventRecord(ev, h->stream));
+    Req r{h, w, form};
+    std::unique_lock<std::mutex> lk(mu);
+    GMT_CUDA(cudaStreamWaitEvent(stream, ev, 0));
+    pending.push_back(&r);
+    if ((int)pending.size() == members) launch_locked();
+    const auto t0 = std::chrono::steady_clock::now();
+    while (!r.done) {
+      cv.wait_for(lk, std::chrono::seconds(1));
+      if (!r.done && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(kRendezvousLimitS)) {
+        pending.erase(std::find(pending.begin(), pending.end(), &r));
+        GMT_REQUIRE(false, GMT_ERR_STATE,
+                    "batched solve: waited %d s for the other lattices' V-cycles",
+                    kRendezvousLimitS);
+      }
+    }
+    lk.unlock();
+    GMT_REQUIRE(r.st == GMT_OK, r.st, "%s", r.err.c_str());
+    GMT_CUDA(cudaStreamWaitEvent(h->stream, finished, 0));
+    return r.out;
+  }
+
+  void leave() {
+    std::lock_guard<std::mutex> lk(mu);
+    --members;
+    if (members > 0 && (int)pending.size() == members) launch_locked();
+  }
+};
+
+namespace {
+thread_local BatchGroup* t_group = nullptr;    // the group of this solve thread
+thread_local cudaEvent_t t_ready = nullptr;    // its event before each V-cycle
+thread_local bool t_batch_thread = false;      // a solve thread of gmt_solve_batch
+}  // namespace
+
+void leave_batch_group() {
+  if (t_group) {
+    BatchGroup* g = t_group;
+    t_group = nullptr;
+    g->leave();
+  }
+}
+
+static void* group_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
+  return t_group->vcycle(h, w, form, t_ready);
+}
+
+bool in_batch_group(const Workspace* w) { return t_group != nullptr && w->prec == P32; }
+bool batch_thread() { return t_batch_thread; }
+
+void run_batched(gmt_hierarchy* const* hs, int n, const std::function<void(int)>& body) {
+  BatchGroup g;
+  g.members = n;
+  GMT_CUDA(cudaSetDevice(hs[0]->device));
+  GMT_CUDA(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+  cudaError_t ce = cudaEventCreateWithFlags(&g.finished, cudaEventDisableTiming);
+  g.ready.assign(n, nullptr);
+  for (int i = 0; i < n && ce == cudaSuccess; ++i)
+    ce = cudaEventCreateWithFlags(&g.ready[i], cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : g.ready)
+      if (e) cudaEventDestroy(e);
+    if (g.finished) cudaEventDestroy(g.finished);
+    cudaStreamSynchronize(g.stream);
+    cudaStreamDestroy(g.stream);
+  };
+  if (ce != cudaSuccess) {
+    cleanup();
+    GMT_CUDA(ce);
+  }
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      t_group = &g;
+      t_ready = g.ready[i];
+      t_batch_thread = true;
+      body(i);               // catches its own failures and calls leave_batch_group()
+      leave_batch_group();   // (a no-op when body has left)
+      t_batch_thread = false;
+    });
+  for (std::thread& t : th) t.join();
+  cleanup();
 }
 
 }  // namespace gmt

@@ -130,22 +130,34 @@ void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst);
 
 inline int64_t blocks_of(const Level& lv) { return lv.nb; }
 
-// ---- batched V-cycle phases (batch.cu): one launch over level `level` of n <= kBatchMax
-// lattices (FP32 vectors; the same material prepared on each; the stream of hs[0]).
-// Per-lattice arguments are arrays of n pointers, as for the single-lattice launchers.
+// ---- batched V-cycle phases (batch.cu): one launch on stream s over level `level` of n <=
+// kBatchMax lattices (FP32 vectors; the same physics and material prepared on each; levels
+// 1..L-2 prepared by prepare_batched_levels). Per-lattice arguments are arrays of n
+// pointers, as for the single-lattice launchers. Callers pass only lattices that have the
+// operation at that level (a sweep or transfer below their coarsest level).
 constexpr int kBatchMax = GMT_BATCH_MAX;
+// builds the stored FP32 stencils of levels 1..L-2 that the batched sweeps read
+void prepare_batched_levels(gmt_hierarchy* h);
 // damped-Jacobi sweep (mode ST_JACOBI: out = u + omega D^-1 (f - K u)) or residual
-// (ST_RESID: out = f - K u)
-void batch_stencil(gmt_hierarchy* const* hs, int n, int level, StencilMode mode,
-                   const void* const* u, const void* const* f, void* const* out);
+// (ST_RESID: out = f - K u). part (level-0 Jacobi only, nullable, entries nullable): the
+// lattices with part[i] set also write the fused Krylov partials of the last sweep of a
+// V-cycle, dotted with aux[i] (k_stencil's SUMS form).
+void batch_stencil(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                   StencilMode mode, const void* const* u, const void* const* f,
+                   void* const* out, double* const* part = nullptr,
+                   const void* const* aux = nullptr);
 // first smoothing step from zero: out = scale D^-1 f
-void batch_diag(gmt_hierarchy* const* hs, int n, int level, const void* const* f,
-                void* const* out, double scale);
-void batch_restrict(gmt_hierarchy* const* hs, int n, int level, const void* const* rf,
-                    void* const* fc);
-void batch_prolong(gmt_hierarchy* const* hs, int n, int level, const void* const* uc,
-                   void* const* uf);
-void batch_coarse_solve(gmt_hierarchy* const* hs, int n, const void* const* f, void* const* u);
+void batch_diag(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                const void* const* f, void* const* out, double scale);
+void batch_restrict(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                    const void* const* rf, void* const* fc);
+void batch_prolong(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,
+                   const void* const* uc, void* const* uf);
+// the coarsest solve of each lattice (its own coarsest level)
+void batch_coarse_solve(gmt_hierarchy* const* hs, int n, cudaStream_t s, const void* const* f,
+                        void* const* u);
+// x[i] = 0 over level `level` of lattice i
+void batch_zero(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level, void* const* x);
 inline size_t prec_bytes(Prec p) { return p == P64 ? 8 : (p == P32 ? 4 : 2); }
 
 }  // namespace gmt

@@ -110,6 +110,7 @@ _SIGS = {
     "gmt_coarse_solve": (_I, [_P, _P, _P]),
     "gmt_vcycle": (_I, [_P, _I, _P, _P, _I]),
     "gmt_vcycle_batch": (_I, [_P, _I, _P, _P, _I]),
+    "gmt_solve_batch": (_I, [_P, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P]),
     "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
@@ -452,6 +453,32 @@ def vcycle_batch(hierarchies, fs, us=None):
     up = (_P * n)(*[_ptr(x) for x in u])
     _check(lib().gmt_vcycle_batch(hp, n, fp, up, int(us is None)), "gmt_vcycle_batch")
     return u
+
+
+def solve_batch(hierarchies, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, tol=1e-5, u0s=None,
+                want_fields=True, allow_not_converged=False):
+    """Solve the cells of several hierarchies together (gmt_solve_batch): every result is
+    bitwise Hierarchy.solve's for that cell, while the V-cycles of all cells share their
+    launches. Returns a list of (status, field or None, Info) per hierarchy."""
+    torch = _torch()
+    n = len(hierarchies)
+    if not 1 <= n <= BATCH_MAX or (u0s is not None and len(u0s) != n):
+        raise ValueError(f"batch of {n} hierarchies (1..{BATCH_MAX})")
+    for h in hierarchies:
+        h.physics = physics
+    u0t = [None if (u0s is None or x is None) else h._field(0, x)
+           for h, x in zip(hierarchies, u0s if u0s is not None else [None] * n)]
+    outs = [h._field(0, None) if want_fields else None for h in hierarchies]
+    infos = (Info * n)()
+    stats = (ctypes.c_int * n)()
+    hp = (_P * n)(*[h._h for h in hierarchies])
+    u0p = (_P * n)(*[_ptr(x) for x in u0t]) if u0s is not None else None
+    outp = (_P * n)(*[_ptr(x) for x in outs]) if want_fields else None
+    st = lib().gmt_solve_batch(hp, n, physics, E, nu, k, tol, u0p, outp, infos, stats)
+    allow = (OK, NOT_CONVERGED, DIVERGED) if allow_not_converged else (OK,)
+    _check(st, "gmt_solve_batch", allow)
+    torch.cuda.synchronize()
+    return [(int(stats[i]), outs[i], infos[i]) for i in range(n)]
 
 
 def unet_layers(out_channels: int, widths=UNET_WIDTHS):

@@ -1,8 +1,8 @@
 """Batched V-cycle (gmt_vcycle_batch): one launch per phase over the bricks of many
 lattices gives every lattice bitwise the FP32 V-cycle that gmt_vcycle runs for it alone,
-with bricked and dense coarsest levels mixed in one batch, from zero and from a given
-field, for elasticity and heat conduction, up to the largest batch; the first lattice's
-result also matches the oracle's V-cycle (Alg. 1) to FP32 accuracy."""
+with bricked and dense coarsest levels and different level counts mixed in one batch, from
+zero and from a given field, for elasticity and heat conduction, up to the largest batch;
+the first lattice's result also matches the oracle's V-cycle (Alg. 1) to FP32 accuracy."""
 import numpy as np
 import pytest
 
@@ -40,7 +40,6 @@ def test_batch_bitwise_equal_to_single(gmt_lib, physics):
     gmt = gmt_lib
     ph = gmt.ELASTIC if physics == "elastic" else gmt.HEAT
     hs = [gmt.Hierarchy(v) for v in _cells()]
-    assert len({h.levels for h in hs}) == 1
     for h in hs:
         h.prepare(ph)
     F = _loads(gmt, hs, 5)
@@ -95,7 +94,6 @@ def test_largest_batch(gmt_lib):
         if not v.any():
             v[0, 0, 0] = 1
         hs.append(gmt.Hierarchy(v))
-    assert len({h.levels for h in hs}) == 1
     for h in hs:
         h.prepare(gmt.ELASTIC)
     F = _loads(gmt, hs, 9)
@@ -128,10 +126,29 @@ def test_batch_rejects_mismatched_hierarchies(gmt_lib):
     with pytest.raises(gmt.GmtError) as e:
         gmt.vcycle_batch([a, c], [F[0], F[0]])
     assert e.value.status == gmt.ERR_ARG
-    d = gmt.Hierarchy(L.tpms_network("gyroid", 64, 0.3))       # four levels, not three
-    d.prepare(gmt.ELASTIC)
+    d = gmt.Hierarchy(cells[0])
+    d.prepare(gmt.HEAT)
     with pytest.raises(gmt.GmtError) as e:
         gmt.vcycle_batch([a, d], [F[0], _loads(gmt, [d], 2)[0]])
     assert e.value.status == gmt.ERR_ARG
     for h in (a, b, c, d):
+        h.free()
+
+
+def test_batch_with_different_level_counts(gmt_lib):
+    """Lattices of 2, 3 and 4 levels in one batch: each takes its coarsest solve at its own
+    coarsest level, bitwise as alone."""
+    import torch
+    gmt = gmt_lib
+    cells = [L.tpms_network("gyroid", 16, 0.3), _cells()[0], L.tpms_plate("schwarz_p", 24, 0.35),
+             L.tpms_network("diamond", 48, 0.3), L.spinodal(64, 0.35, 4, np.random.default_rng(8))]
+    hs = [gmt.Hierarchy(v) for v in cells]
+    assert sorted({h.levels for h in hs}) == [2, 3, 4]
+    for h in hs:
+        h.prepare(gmt.ELASTIC)
+    F = _loads(gmt, hs, 12)
+    batch = gmt.vcycle_batch(hs, F)
+    for h, f, b in zip(hs, F, batch):
+        assert torch.equal(h.vcycle(f, None, gmt.FP32), b)
+    for h in hs:
         h.free()
