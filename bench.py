@@ -315,6 +315,8 @@ def run_gmt(args, rank: int, world: int):
                          "gs8": gmt.GS8}[args.smoother]
     if args.cycle:
         opts.cycle = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[args.cycle]
+    if args.coarse_fp16:
+        opts.coarse_fp16 = 1
     if args.cells:
         cells = cells[:args.cells]
     vals = 18 if ph == gmt.ELASTIC else 3        # values per node (components x cases)
@@ -560,7 +562,8 @@ def run_gmt(args, rank: int, world: int):
               default=None)
     dom_n, dom_ms, dom_b = totals.get(dom, [0, 0.0, 0.0]) if dom else (0, 0.0, 0.0)
     dom_gbs = (dom_b / (dom_ms / 1000.0) / 1e9) if dom_ms > 0 else None
-    ncu = NCU_DRAM_BYTES_PER_NODE.get(dom) if (ph == gmt.ELASTIC and prec == gmt.FP32) else None
+    ncu = NCU_DRAM_BYTES_PER_NODE.get(dom) if (ph == gmt.ELASTIC and prec == gmt.FP32 and
+                                               not opts.coarse_fp16) else None
     dom_nodes = avg_nodes if dom in ("smooth_l0", "resid_l0", "diag_l0") else \
         level_nodes.get(1) if dom == "stencil_l1" else None
     traffic = ncu * dom_nodes if (ncu is not None and dom_nodes) else None
@@ -603,7 +606,7 @@ def run_gmt(args, rank: int, world: int):
                        [opts.smoother], opts.nu_pre, opts.nu_post),
                    "cycle": "VWF"[opts.cycle],
                    "inner_tol": opts.inner_tol, "nu_coarse": opts.nu_coarse,
-                   "omega": opts.omega,
+                   "omega": opts.omega, "coarse_fp16": opts.coarse_fp16,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
                    "concurrent_cells": nstreams,
@@ -759,6 +762,8 @@ def main():
                     help="smoothing sweeps on levels >= 1 (0: as on level 0)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="mixed precision: true-residual replacement factor (0: default)")
+    ap.add_argument("--coarse-fp16", action="store_true",
+                    help="FP16 copies of the coarse levels' stored stencils")
     ap.add_argument("--batched", action="store_true",
                     help="solve the cells of a step together (gmt_solve_batch)")
     ap.add_argument("--streams", type=int, default=4,

@@ -103,6 +103,10 @@ typedef struct {
                           operations concurrent with other threads' kernel launches
                           crashed the driver). Kernels that the caller launches from other
                           threads itself are not covered: such a caller sets 0. */
+  int coarse_fp16;     /* [0] mixed precision: the stored per-node stencils of levels >= 1
+                          in FP16 (scaled per level, FP32 arithmetic), half the bytes the
+                          coarse sweeps read; the V-cycle becomes a slightly different
+                          preconditioner (the solve's accuracy is unchanged) */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,

@@ -56,7 +56,8 @@ static bool opts_valid(const gmt_options& o) {
          o.cycle >= 0 && o.cycle <= 2 && o.nu_coarse >= 0 &&
          o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post > 0 && o.omega > 0 &&
          o.cheb_ratio > 1 && o.cheb_upper >= 1 && o.precision >= 0 && o.precision <= 2 &&
-         o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0;
+         o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0 &&
+         (o.coarse_fp16 == 0 || o.coarse_fp16 == 1);
 }
 
 static void ensure_device(gmt_hierarchy* h) { GMT_CUDA(cudaSetDevice(h->device)); }
@@ -111,6 +112,7 @@ void gmt_default_options(gmt_options* o) {
   o->fp64_fallback = 1;
   o->nu_coarse = 2;
   o->graphs = 1;
+  o->coarse_fp16 = 0;
 }
 
 const char* gmt_status_string(gmt_status s) {
@@ -379,7 +381,8 @@ gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const
     GMT_REQUIRE(h->device == a->device && h->stream == a->stream, GMT_ERR_ARG,
                 "batched V-cycle: hierarchy %d is on another device or stream", i);
     GMT_REQUIRE(o.omega == a->opts.omega && o.nu_pre == a->opts.nu_pre &&
-                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse,
+                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse &&
+                    o.coarse_fp16 == a->opts.coarse_fp16,
                 GMT_ERR_ARG, "batched V-cycle: hierarchy %d has other smoothing options", i);
     GMT_REQUIRE(h->mat.physics == a->mat.physics && h->mat.E == a->mat.E &&
                     h->mat.nu == a->mat.nu && h->mat.k == a->mat.k,
@@ -473,7 +476,8 @@ gmt_status gmt_solve_batch(gmt_hierarchy* const* hs, int n, gmt_physics physics,
     GMT_REQUIRE(h->device == a->device, GMT_ERR_ARG,
                 "batched solve: hierarchy %d is on another device", i);
     GMT_REQUIRE(o.omega == a->opts.omega && o.nu_pre == a->opts.nu_pre &&
-                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse,
+                    o.nu_post == a->opts.nu_post && o.nu_coarse == a->opts.nu_coarse &&
+                    o.coarse_fp16 == a->opts.coarse_fp16,
                 GMT_ERR_ARG, "batched solve: hierarchy %d has other smoothing options", i);
   }
   std::vector<gmt_status> st(n, GMT_OK);

@@ -40,6 +40,7 @@ struct LatView {
   double* part;
   A omega, c1, c2;
   int colour;
+  A kscale;
   const FineC<A, D, M>& fc;
 };
 
@@ -55,6 +56,7 @@ struct StPtrs {
   int64_t nslots;
   double* part;    // SUMS: the sweep's per-brick partials (see stencil_brick)
   const TS* aux;   // SUMS: the vector dotted with the result per case (or nullptr)
+  A kscale;        // KIND 2: the scale of the FP16 stencils
 };
 
 template <typename TS, typename A, int D, int M>
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(64) k_stencil_multi(const __grid_constant__ Mu
   stage_tile<TS, A, C>(lp.u, b, t, nb, tile, self);
   __syncthreads();
   const LatView<TS, A, D, M> v{lp.mask, lp.kmat, lp.dinv, lp.f, nullptr, lp.aux, lp.out,
-                               nullptr, lp.part, mp.omega, A(0), A(0), -1, mp.fc};
+                               nullptr, lp.part, mp.omega, A(0), A(0), -1, lp.kscale, mp.fc};
   stencil_brick<TS, A, D, M, KIND, MODE, SUMS, PREF>(v, b, tile, fpre, self);
 }
 
@@ -103,7 +105,7 @@ __global__ void k_diag_multi(const __grid_constant__ MultiSt<TS, A, D, M> mp) {
   const int64_t slot = ((int64_t)blockIdx.x - mp.start[l]) * 128 + threadIdx.x;
   if (slot >= lp.nslots) return;
   const LatView<TS, A, D, M> v{lp.mask, lp.kmat, lp.dinv, lp.f, nullptr, nullptr, lp.out,
-                               nullptr, nullptr, mp.omega, A(0), A(0), -1, mp.fc};
+                               nullptr, nullptr, mp.omega, A(0), A(0), -1, lp.kscale, mp.fc};
   diag_slot<TS, A, D, M, KIND>(v, slot);
 }
 
@@ -221,19 +223,21 @@ static void stencil_multi_t(gmt_hierarchy* const* hs, const std::vector<int>& se
   mp->omega = (A)omega;
   mp->n = (int)sel.size();
   const bool fine = level == 0;
+  const bool half = !fine && hs[0]->opts.coarse_fp16 != 0;   // KIND 2 (as stencil_t)
   const bool sums = part != nullptr && part[sel[0]] != nullptr;
   int64_t tot = 0;
   for (int k = 0; k < mp->n; ++k) {
     const int i = sel[k];
     Level& lv = hs[i]->lv[level];
-    GMT_REQUIRE(fine || lv.S32 != nullptr, GMT_ERR_STATE,
+    GMT_REQUIRE(fine || (half ? lv.S16 != nullptr : lv.S32 != nullptr), GMT_ERR_STATE,
                 "batched sweep: level %d stencils of lattice %d are not built", level, i);
     mp->start[k] = tot;
     tot += diag ? (int64_t)nblocks(lv.nslots, 128) : lv.nb;
-    mp->lp[k] = StPtrs<TS, A>{lv.brick_nbr, lv.mask, (const A*)lv.S32, (const A*)lv.dinv32,
+    mp->lp[k] = StPtrs<TS, A>{lv.brick_nbr, lv.mask,
+                              half ? (const A*)lv.S16 : (const A*)lv.S32, (const A*)lv.dinv32,
                               (const TS*)u[i], (const TS*)f[i], (TS*)out[i], lv.nslots,
                               sums ? part[i] : nullptr,
-                              sums && aux ? (const TS*)aux[i] : nullptr};
+                              sums && aux ? (const TS*)aux[i] : nullptr, (A)lv.s16_scale};
   }
   mp->start[mp->n] = tot;
   if (tot == 0) return;
@@ -245,9 +249,11 @@ static void stencil_multi_t(gmt_hierarchy* const* hs, const std::vector<int>& se
     k_stencil_multi<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(*mp);
   } else if (mode == ST_JACOBI) {
     if (fine) k_stencil_multi<TS, A, D, M, 0, ST_JACOBI><<<g, 64, 0, s>>>(*mp);
+    else if (half) k_stencil_multi<TS, A, D, M, 2, ST_JACOBI><<<g, 64, 0, s>>>(*mp);
     else k_stencil_multi<TS, A, D, M, 1, ST_JACOBI><<<g, 64, 0, s>>>(*mp);
   } else {
     if (fine) k_stencil_multi<TS, A, D, M, 0, ST_RESID><<<g, 64, 0, s>>>(*mp);
+    else if (half) k_stencil_multi<TS, A, D, M, 2, ST_RESID><<<g, 64, 0, s>>>(*mp);
     else k_stencil_multi<TS, A, D, M, 1, ST_RESID><<<g, 64, 0, s>>>(*mp);
   }
   GMT_LAUNCH_CHECK();
@@ -272,7 +278,10 @@ static void stencil_split_t(gmt_hierarchy* const* hs, int n, cudaStream_t s, int
 }
 
 void prepare_batched_levels(gmt_hierarchy* h) {
-  for (int l = 1; l + 1 < h->L; ++l) build_node_stencils(h, l, false);
+  for (int l = 1; l + 1 < h->L; ++l) {
+    build_node_stencils(h, l, false);
+    if (h->opts.coarse_fp16) build_node_stencils16(h, l);
+  }
 }
 
 void batch_stencil(gmt_hierarchy* const* hs, int n, cudaStream_t s, int level,

@@ -197,6 +197,8 @@ struct Level {
   float* K32 = nullptr;
   double* S64 = nullptr;        // levels >= 1: per-node stencils [brick][27 D D][64] (lazy)
   float* S32 = nullptr;
+  uint16_t* S16 = nullptr;      // levels >= 1 with coarse_fp16: FP16 copy of S32 / s16_scale
+  float s16_scale = 0.f;        //   [brick][27 D D / 8 groups][64][8] (lazy)
   double* dinv64 = nullptr;     // levels >= 1: nslots x D*D block-diagonal inverses
   float* dinv32 = nullptr;
   double lmax = 0.0;            // Chebyshev: estimate of lambda_max(D^-1 K)

@@ -720,6 +720,7 @@ void prepare_material(gmt_hierarchy* h, int physics, double E, double nu, double
   for (Level& l : h->lv) {
     l.K64 = l.S64 = l.dinv64 = nullptr;
     l.K32 = l.S32 = l.dinv32 = nullptr;
+    l.S16 = nullptr;
     l.kidx_el = nullptr;
     l.lmax = 0.0;
   }

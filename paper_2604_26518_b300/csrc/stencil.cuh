@@ -138,6 +138,8 @@ inline int64_t blocks_of(const Level& lv) { return lv.nb; }
 constexpr int kBatchMax = GMT_BATCH_MAX;
 // builds the stored FP32 stencils of levels 1..L-2 that the batched sweeps read
 void prepare_batched_levels(gmt_hierarchy* h);
+// the FP16 copy of level `level`'s FP32 node stencils (coarse_fp16), built once
+void build_node_stencils16(gmt_hierarchy* h, int level);
 // damped-Jacobi sweep (mode ST_JACOBI: out = u + omega D^-1 (f - K u)) or residual
 // (ST_RESID: out = f - K u). part (level-0 Jacobi only, nullable, entries nullable): the
 // lattices with part[i] set also write the fused Krylov partials of the last sweep of a

@@ -3,6 +3,8 @@
 // brick tile staging (4^3 brick plus a one-node halo in shared memory).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cstring>
 #include <type_traits>
 
@@ -64,6 +66,7 @@ struct StArgs {
   double* part;
   A omega, c1, c2;
   int colour;
+  A kscale;        // KIND 2: the scale of the FP16 stencils
   FineC<A, D, M> fc;
 };
 
@@ -172,6 +175,15 @@ template <> struct Vec16<double> { using type = double2; static constexpr int n 
 template <typename A>
 __host__ __device__ constexpr int node_stencil_groups(int DD) {
   return (27 * DD + Vec16<A>::n - 1) / Vec16<A>::n;
+}
+// the FP16 copy: 8 coefficients per 16-byte group, same brick-major layout
+__host__ __device__ constexpr int node_stencil_groups16(int DD) { return (27 * DD + 7) / 8; }
+
+// coefficient j (0..7) of a 16-byte group of FP16 values
+__device__ __forceinline__ float half_of(const uint4& g, int j) {
+  const uint32_t w = j < 2 ? g.x : (j < 4 ? g.y : (j < 6 ? g.z : g.w));
+  const unsigned short b = (unsigned short)((j & 1) ? (w >> 16) : (w & 0xffffu));
+  return __half2float(__ushort_as_half(b));
 }
 __host__ __device__ __forceinline__ int64_t node_stencil_index(int64_t slot, int c, int groups,
                                                              int W) {

@@ -1,5 +1,8 @@
 // Per-node stencils of stored operators (coarse levels; level 0 with element densities) and
 // the dispatch of the operator kernels (stencil_op.cuh) to their per-physics instances.
+#include <algorithm>
+#include <cmath>
+
 #include "stencil_op.cuh"
 
 namespace gmt {
@@ -101,6 +104,41 @@ void build_node_stencils(gmt_hierarchy* h, int level, bool fp64) {
                                                  lv.dense, lv.nslots, lv.mask, kidx, K, cf,
                                                  lv.S32);
   }
+  GMT_LAUNCH_CHECK();
+}
+
+// FP16 copy of the FP32 node stencils of one level, divided by `scale`
+__global__ void k_stencil_to_half(const float* __restrict__ S32, int64_t nslots, int DD,
+                                  float inv_scale, __half* __restrict__ S16) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 27 * DD;
+  if (i >= nslots * n) return;
+  const int64_t slot = i / n;
+  const int c = (int)(i % n);
+  const float v = S32[node_stencil_index(slot, c, node_stencil_groups<float>(DD), 4)];
+  S16[node_stencil_index(slot, c, node_stencil_groups16(DD), 8)] = __float2half_rn(v * inv_scale);
+}
+
+void build_node_stencils16(gmt_hierarchy* h, int level) {
+  Level& lv = h->lv[level];
+  if (lv.S16 != nullptr) return;
+  build_node_stencils(h, level, false);
+  TraceScope ts(&h->tracer, h->stream, TR_OPS, 0.0);
+  const int D = h->mat.D, DD = D * D;
+  // every stored coefficient is a sum of at most 8 incident elements' blocks, and a
+  // Galerkin level's element matrices are about twice the next finer level's: dividing by
+  // 2^level max|K_e| keeps the FP16 values below ~8 (the FP16 range ends at 65504)
+  double kmax = 0.0;
+  for (int i = 0; i < 64 * DD; ++i) kmax = std::max(kmax, std::fabs(h->mat.Ke[i]));
+  const double scale = kmax * std::ldexp(1.0, level);
+  lv.s16_scale = (float)scale;
+  const size_t cnt = (size_t)lv.nslots * node_stencil_groups16(DD) * 8;
+  lv.S16 = h->op.alloc<uint16_t>(cnt);
+  GMT_CUDA(cudaMemsetAsync(lv.S16, 0, cnt * sizeof(uint16_t), h->stream));
+  const int64_t n = lv.nslots * 27 * DD;
+  k_stencil_to_half<<<grid_for(n, 256), 256, 0, h->stream>>>(lv.S32, lv.nslots, DD,
+                                                             (float)(1.0 / scale),
+                                                             (__half*)lv.S16);
   GMT_LAUNCH_CHECK();
 }
 

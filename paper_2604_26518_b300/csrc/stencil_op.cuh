@@ -186,6 +186,24 @@ __device__ __forceinline__ void stencil_brick(const P& p, int64_t b,
           else contribute(d, S);
         }
       }
+    } else if constexpr (KIND == 2) {
+      // FP16 copy (8 coefficients per 16-byte group), scaled by kscale after the sum
+      constexpr int NG = node_stencil_groups16(DD);
+      const uint4* sten = reinterpret_cast<const uint4*>(p.kmat) + b * (NG * 64) + loc;
+      uint4 cur;
+#pragma unroll
+      for (int d = 0; d < 27; ++d) {
+        A S[DD];
+#pragma unroll
+        for (int k = 0; k < DD; ++k) {
+          const int c = d * DD + k;
+          if (c % 8 == 0) cur = sten[(c / 8) * 64];
+          S[k] = (A)half_of(cur, c % 8);
+        }
+        if (DIFF && d == 13) continue;
+        if constexpr (PK) contribute_s(d, S);
+        else contribute(d, S);
+      }
     } else {
       // coefficient c = d * DD + k of this node sits in 16-byte group c / W (see
       // node_stencil_index); each group is loaded once, when its first coefficient is needed
@@ -215,6 +233,12 @@ __device__ __forceinline__ void stencil_brick(const P& p, int64_t b,
       acc[2 * k] = (A)lo;
       acc[2 * k + 1] = (A)hi;
     }
+  }
+  if constexpr (KIND == 2) {
+    // a rounded product, never contracted into the epilogue's subtraction: every kernel
+    // that shares this function rounds the same way (the batched sweeps are bitwise equal)
+#pragma unroll
+    for (int v = 0; v < C; ++v) acc[v] = __fmul_rn(acc[v], p.kscale);
   }
   const int64_t base = b * (64 * C) + loc;
   if constexpr (MODE == ST_APPLY) {
@@ -554,13 +578,17 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
   // level 0 forms its stencil from the octant masks and K_e (KIND 0), unless element
   // densities are set: then it reads stored per-node stencils like a coarse level (KIND 1)
   const bool fine = level == 0 && !h->dens;
+  // levels >= 1 of the FP32 V-cycle with coarse_fp16: the FP16 stencil copy (KIND 2)
+  const bool half = sizeof(A) == 4 && level > 0 && h->opts.coarse_fp16 != 0;
   if (!fine) build_node_stencils(h, level, sizeof(A) == 8);
+  if (half) build_node_stencils16(h, level);
   if constexpr (sizeof(A) == 8) {
     p.kmat = (const A*)lv.S64;
     p.dinv = (const A*)lv.dinv64;
   } else {
-    p.kmat = (const A*)lv.S32;
+    p.kmat = half ? (const A*)lv.S16 : (const A*)lv.S32;
     p.dinv = (const A*)lv.dinv32;
+    p.kscale = (A)lv.s16_scale;
   }
   p.u = (const TS*)va.u;
   p.f = (const TS*)va.f;
@@ -589,19 +617,27 @@ static void stencil_t(gmt_hierarchy* h, int level, StencilMode mode, const VecAr
 #define GMT_ST(KIND, MODE) k_stencil<TS, A, D, M, KIND, MODE><<<g, 64, 0, s>>>(p)
   // smoother modes at level 0: fused r.z and sums of z
   const bool sums = level == 0 && va.part != nullptr;
+  // KIND 2 exists for FP32 only (the FP64 instances keep KIND 1 there: never launched)
+  constexpr int K2 = sizeof(A) == 4 ? 2 : 1;
   switch (mode) {
-    case ST_APPLY: if (fine) GMT_ST(0, ST_APPLY); else GMT_ST(1, ST_APPLY); break;
-    case ST_RESID: if (fine) GMT_ST(0, ST_RESID); else GMT_ST(1, ST_RESID); break;
+    case ST_APPLY:
+      if (fine) GMT_ST(0, ST_APPLY); else if (half) GMT_ST(K2, ST_APPLY); else GMT_ST(1, ST_APPLY);
+      break;
+    case ST_RESID:
+      if (fine) GMT_ST(0, ST_RESID); else if (half) GMT_ST(K2, ST_RESID); else GMT_ST(1, ST_RESID);
+      break;
     case ST_JACOBI:
       if (sums && fine) k_stencil<TS, A, D, M, 0, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
       else if (sums) k_stencil<TS, A, D, M, 1, ST_JACOBI, true><<<g, 64, 0, s>>>(p);
       else if (fine) GMT_ST(0, ST_JACOBI);
+      else if (half) GMT_ST(K2, ST_JACOBI);
       else GMT_ST(1, ST_JACOBI);
       break;
     case ST_CHEB:
       if (sums && fine) k_stencil<TS, A, D, M, 0, ST_CHEB, true><<<g, 64, 0, s>>>(p);
       else if (sums) k_stencil<TS, A, D, M, 1, ST_CHEB, true><<<g, 64, 0, s>>>(p);
       else if (fine) GMT_ST(0, ST_CHEB);
+      else if (half) GMT_ST(K2, ST_CHEB);
       else GMT_ST(1, ST_CHEB);
       break;
   }

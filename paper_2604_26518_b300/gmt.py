@@ -46,6 +46,7 @@ class Options(ctypes.Structure):
         ("fp64_fallback", ctypes.c_int),
         ("nu_coarse", ctypes.c_int),
         ("graphs", ctypes.c_int),
+        ("coarse_fp16", ctypes.c_int),
     ]
 
 
