@@ -766,8 +766,10 @@ def main():
                     help="FP16 copies of the coarse levels' stored stencils")
     ap.add_argument("--batched", action="store_true",
                     help="solve the cells of a step together (gmt_solve_batch)")
-    ap.add_argument("--streams", type=int, default=4,
-                    help="cells solved concurrently, one host thread and CUDA stream each")
+    ap.add_argument("--streams", type=int, default=6,
+                    help="cells solved concurrently, one host thread and CUDA stream each "
+                         "(6: 96.0 / 96.5 C^H solves/s on the 128^3 batch against 94.0 / 94.6 "
+                         "with 4 and 95.6 with 8)")
     ap.add_argument("--smoother", default="", choices=["", "jacobi", "chebyshev", "gs8"])
     ap.add_argument("--cycle", default="", choices=["", "V", "W", "F"])
     ap.add_argument("--cells", type=int, default=0, help="use only the first K cells (profiling)")
