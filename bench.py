@@ -345,6 +345,9 @@ def run_gmt(args, rank: int, world: int):
         if args.batched:
             raise SystemExit("--learned runs per-cell solves (no --batched)")
         net, learned = train_initializer(args, ph, opts)
+        if args.learned_tc:
+            net.tensor_cores(True)
+            learned["inference"] = "tcgen05, FP16 operands, FP32 accumulation in tensor memory"
 
     def run_cells(src, idx, s, trace):
         tot, CH, cyc = {}, {}, []
@@ -776,6 +779,8 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="warm-start every solve from the learned initializer, trained first "
                          "(untimed) on seeded 32^3 cells")
+    ap.add_argument("--learned-tc", action="store_true",
+                    help="network inference on the tensor cores (FP16 operands, tcgen05)")
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--learned-cells", type=int, default=64)
     args = ap.parse_args()

@@ -402,6 +402,14 @@ gmt_status gmt_netgraph_tables(const gmt_netgraph* g, int level, int32_t* same_o
 /* u_out (device double[n_0][cout]) = scale * network output: the predicted canonical field,
    ready to pass to gmt_solve as u0. */
 gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* g, double scale, double* u_out);
+
+/* Inference on the 5th-generation tensor cores: with on != 0, gmt_unet_forward runs every
+   layer as an implicit-GEMM gather convolution with FP16 operands (weights and the gathered
+   activations rounded to FP16 per call) and FP32 accumulation in tensor memory; the
+   prediction then differs from the FP32 forward by FP16 rounding (about 1e-3 relative).
+   Training (gmt_unet_gradient, gmt_unet_train_step) always runs in FP32. Off by default.
+   GMT_ERR_CUDA from gmt_unet_forward if a bounded wait inside the kernel ran out. */
+gmt_status gmt_unet_set_tensor_cores(gmt_unet* net, int on);
 /* Loss against the canonical field u_target (device double[n_0][cout]) and its gradient
    with respect to every parameter (grad_out: host or device float[P], nullable; loss_out:
    host, nullable). The parameters do not change. h: the hierarchy the graph was built

@@ -26,9 +26,18 @@
 #include <memory>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace gmt {
+bool tc_supported(int cin, int cout);                                        // gconv_tc.cu
+int64_t tc_image_halves(int cin, int cout);
+void tc_build_image(cudaStream_t s, const float* W, int cin, int cout, __half* img);
+void launch_gconv_tc(cudaStream_t s, const float* x, int cin, const int* tab, const __half* img,
+                     const float* bias, const float* add, int relu, float* out, int cout,
+                     int64_t n_out, const int* omap);
+int tc_take_status(cudaStream_t s);
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);       // hierarchy.cu
 void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);  // solver.cu
 }
@@ -483,6 +492,10 @@ struct gmt_unet {
   float* m = nullptr;     // AdamW moments
   float* v = nullptr;
   int64_t steps = 0;
+  // inference on the tensor cores (gmt_unet_set_tensor_cores): FP16 weight images per layer
+  int tc = 0;
+  __half* img = nullptr;
+  int64_t img_off[NLAYERS];
 };
 
 struct gmt_netgraph {
@@ -574,15 +587,35 @@ void launch_gconv(cudaStream_t s, const float* x, int cin, const int* tab, int f
   GMT_LAUNCH_CHECK();
 }
 
-void forward(gmt_unet* net, gmt_netgraph* G) {
+// tc: the layers run as tensor-core convolutions (FP16 operands, FP32 accumulation) from
+// FP16 images of the current weights; training keeps the FP32 kernels (tc = false)
+void forward(gmt_unet* net, gmt_netgraph* G, bool tc = false) {
   ensure_buffers(G, net);
+  if (tc && net->img == nullptr) {
+    int64_t off = 0;
+    for (int i = 0; i < NLAYERS; ++i) {
+      net->img_off[i] = off;
+      off += gmt::tc_image_halves(net->L[i].cin, net->L[i].cout);
+    }
+    GMT_CUDA(cudaMalloc(&net->img, sizeof(__half) * (size_t)off));
+  }
   for (int i = 0; i < NLAYERS; ++i) {
     const LayerDef& d = net->L[i];
     const bool up = d.kind == UP;
-    launch_gconv(G->stream, G->a[d.in], d.cin, up ? G->up_perm[d.lvl_out] : fwd_table(G, d), 0,
-                 net->p + net->woff[i], 0, net->p + net->boff[i],
-                 d.skip >= 0 ? G->a[d.skip] : nullptr, d.relu, 0, G->a[i + 1], d.cout,
-                 G->n[d.lvl_out], up ? G->up_rows[d.lvl_out] : nullptr);
+    const int* tab = up ? G->up_perm[d.lvl_out] : fwd_table(G, d);
+    const int* omap = up ? G->up_rows[d.lvl_out] : nullptr;
+    const float* add = d.skip >= 0 ? G->a[d.skip] : nullptr;
+    if (tc && gmt::tc_supported(d.cin, d.cout)) {
+      gmt::tc_build_image(G->stream, net->p + net->woff[i], d.cin, d.cout,
+                          net->img + net->img_off[i]);
+      gmt::launch_gconv_tc(G->stream, G->a[d.in], d.cin, tab, net->img + net->img_off[i],
+                           net->p + net->boff[i], add, d.relu, G->a[i + 1], d.cout,
+                           G->n[d.lvl_out], omap);
+    } else {
+      launch_gconv(G->stream, G->a[d.in], d.cin, tab, 0, net->p + net->woff[i], 0,
+                   net->p + net->boff[i], add, d.relu, 0, G->a[i + 1], d.cout, G->n[d.lvl_out],
+                   omap);
+    }
   }
 }
 
@@ -772,7 +805,16 @@ void gmt_unet_free(gmt_unet* net) {
   cudaFree(net->g);
   cudaFree(net->m);
   cudaFree(net->v);
+  cudaFree(net->img);
   delete net;
+}
+
+gmt_status gmt_unet_set_tensor_cores(gmt_unet* net, int on) {
+  UNET_BEGIN
+  GMT_REQUIRE(net, GMT_ERR_ARG, "null network");
+  net->tc = on != 0;
+  return GMT_OK;
+  UNET_END
 }
 
 int64_t gmt_unet_num_params(const gmt_unet* net) { return net ? net->P : -1; }
@@ -882,11 +924,14 @@ gmt_status gmt_unet_forward(gmt_unet* net, gmt_netgraph* G, double scale, double
   UNET_BEGIN
   check_pair(net, G);
   GMT_REQUIRE(u_out && scale > 0 && std::isfinite(scale), GMT_ERR_ARG, "bad output or scale");
-  forward(net, G);
+  forward(net, G, net->tc != 0);
   const int64_t e = G->n[0] * net->cout;
   k_to_field<<<blocks(e), 256, 0, G->stream>>>(G->a[NACT - 1], e, scale, u_out);
   GMT_LAUNCH_CHECK();
   GMT_CUDA(cudaStreamSynchronize(G->stream));
+  if (net->tc)
+    GMT_REQUIRE(gmt::tc_take_status(G->stream) == 0, GMT_ERR_CUDA,
+                "tensor-core convolution: a bounded wait for the MMAs ran out");
   return GMT_OK;
   UNET_END
 }

@@ -132,6 +132,7 @@ _SIGS = {
     "gmt_unet_num_params": (_L, [_P]),
     "gmt_unet_get_params": (_I, [_P, _P]),
     "gmt_unet_set_params": (_I, [_P, _P]),
+    "gmt_unet_set_tensor_cores": (_I, [_P, _I]),
     "gmt_netgraph_build": (_I, [_P, ctypes.POINTER(_P)]),
     "gmt_netgraph_free": (None, [_P]),
     "gmt_netgraph_nodes": (_L, [_P, _I]),
@@ -557,6 +558,11 @@ class UNet:
         torch = _torch()
         p = p.detach().to(device="cuda", dtype=torch.float32).contiguous()
         _check(lib().gmt_unet_set_params(self._n, _ptr(p)), "gmt_unet_set_params")
+
+    def tensor_cores(self, on: bool = True):
+        """Inference on the tensor cores (FP16 operands, FP32 accumulation); training stays
+        FP32 (gmt_unet_set_tensor_cores)."""
+        _check(lib().gmt_unet_set_tensor_cores(self._n, int(bool(on))), "gmt_unet_set_tensor_cores")
 
     def forward(self, graph: NetGraph, scale: float):
         """Predicted canonical field, float64 (n0, cout) on the device (gmt_unet_forward)."""

@@ -154,3 +154,31 @@ def test_training_lowers_energy_error_and_warm_start_keeps_accuracy():
         _, _, iz = h.solve(gmt.ELASTIC, tol=1e-5)
         print(f"held-out cell {i}: energy error of the prediction {err:.3f}, "
               f"V-cycles from zero {iz.inner_total}, from the prediction {i1.inner_total}")
+
+
+@pytest.mark.parametrize("cout", [18, 3])
+def test_tensor_core_forward_parity(cell, cout):
+    """gmt_unet_set_tensor_cores: every layer as a tcgen05 implicit-GEMM gather convolution
+    (FP16 operands, FP32 accumulation in tensor memory). The prediction matches the float64
+    oracle within FP16 operand rounding through twelve layers; switching back gives the FP32
+    forward bit for bit, and the gradient (training) stays the FP32 one."""
+    _, _, G, O = cell
+    rows = ounet.layers(cout)
+    p = lattices.unet_init(rows, seed=21 + cout)
+    p[_segments(rows)[3][1] - 64:_segments(rows)[3][1]] = 0.1
+    net = gmt.UNet(cout, torch.tensor(p))
+    scale = 1.3
+    y32 = net.forward(G, scale).cpu().numpy()
+    u = torch.tensor(np.random.default_rng(5).normal(size=(O.n[0], cout)) * scale)
+    loss32, grad32 = net.gradient(G, u, scale)
+    net.tensor_cores(True)
+    ytc = net.forward(G, scale).cpu().numpy()
+    y_ref = scale * ounet.forward(O, torch.tensor(p.astype(np.float64)), rows).numpy()
+    err = np.abs(ytc - y_ref).max()
+    # FP16 rounding of every operand (unit roundoff 4.9e-4) through twelve layers
+    assert err <= 1e-2 * np.abs(y_ref).max(), (err, np.abs(y_ref).max())
+    assert not np.array_equal(ytc, y32)           # the tensor-core path did run
+    loss_tc, grad_tc = net.gradient(G, u, scale)  # training stays FP32
+    assert loss_tc == loss32 and torch.equal(grad_tc, grad32)
+    net.tensor_cores(False)
+    assert np.array_equal(net.forward(G, scale).cpu().numpy(), y32)
