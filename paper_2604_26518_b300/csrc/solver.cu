@@ -1123,7 +1123,10 @@ struct BatchGroup {
     while (!r.done) {
       cv.wait_for(lk, std::chrono::seconds(1));
       if (!r.done && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(kRendezvousLimitS)) {
-        pending.erase(std::find(pending.begin(), pending.end(), &r));
+        // (a leader completes every request it takes under the lock, so an undone request
+        // is still pending here)
+        const auto it = std::find(pending.begin(), pending.end(), &r);
+        if (it != pending.end()) pending.erase(it);
         GMT_REQUIRE(false, GMT_ERR_STATE,
                     "batched solve: waited %d s for the other lattices' V-cycles",
                     kRendezvousLimitS);
