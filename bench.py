@@ -12,6 +12,11 @@ timed region) and reads each C^H back to the host.
                     [--workload c128|c32|c256|c512|batch64] [--physics elastic|heat]
                     [--precision fp32|fp64] [--smoother jacobi|chebyshev|gs8] [--cycle V|W|F]
 
+Before the warm-up the smoothing schedule (nu_pre = nu_post, nu_coarse, coarse_fp16) is
+tuned on the workload itself (--no-autotune keeps the fixed one): one timed step per
+candidate for a batch of cells, gmt_autotune (one solve per candidate) for a single cell;
+the choice and every candidate's time are in config.autotune.
+
 The default (c128) line also carries the 512^3 gyroid as a keyed sub-result (value_512,
 ms_per_solve_512, vcycles_512), the V-cycle roofline (roofline.vcycle: algorithmic bytes of
 every V-cycle over the traced V-cycle kernel time) and per-kernel rooflines.
@@ -317,6 +322,17 @@ def run_gmt(args, rank: int, world: int):
         opts.cycle = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[args.cycle]
     if args.coarse_fp16:
         opts.coarse_fp16 = 1
+    tuned = None
+    if args.autotune and len(cells) == 1:
+        # one cell fills the GPU alone: gmt_autotune's solve time is the throughput (untimed)
+        h = gmt.Hierarchy(cells[0][0], opts)
+        best, times = h.autotune(ph, tol=TOL)
+        h.free()
+        for f in TUNED:
+            setattr(opts, f, getattr(best, f))
+        tuned = {"by": "gmt_autotune on the cell (one solve per candidate)",
+                 "times_ms": [round(float(t), 3) for t in times],
+                 "chosen": {f: getattr(best, f) for f in TUNED}}
     if args.cells:
         cells = cells[:args.cells]
     vals = 18 if ph == gmt.ELASTIC else 3        # values per node (components x cases)
@@ -477,6 +493,33 @@ def run_gmt(args, rank: int, world: int):
         cycles_seen.extend(c for _, c in sorted(cyc))
         return tot, [CH[i] for i in range(len(src))]
 
+    if args.autotune and len(cells) > 1:
+        # several cells in flight: a schedule's solve time alone is not the batch's
+        # throughput (a second sweep that saves V-cycles on one cell can cost the batch),
+        # so every candidate times one whole step (after an untimed one); untimed region
+        cands = [(a, b, c) for a in (1, 2) for b in (1, 2, 3) for c in (0, 1)]
+        times = []
+        for a, b, c in cands:
+            opts.nu_pre = opts.nu_post = a
+            opts.nu_coarse = b
+            opts.coarse_fp16 = c
+            one_step(vox_dev, False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one_step(vox_dev, False)
+            torch.cuda.synchronize()
+            times.append(1000.0 * (time.perf_counter() - t0))
+        a, b, c = cands[min(range(len(cands)), key=lambda i: times[i])]
+        opts.nu_pre = opts.nu_post = a
+        opts.nu_coarse = b
+        opts.coarse_fp16 = c
+        tuned = {"by": "one timed step of the workload per candidate (nu_pre = nu_post in "
+                       "{1, 2} x nu_coarse in {1, 2, 3} x coarse_fp16 in {0, 1})",
+                 "times_ms": [round(t, 2) for t in times],
+                 "chosen": {f: getattr(opts, f) for f in TUNED}}
+        cycles_seen.clear()
+        unconverged.clear()
+        fallbacks.clear()
     for _ in range(args.warmup):
         one_step(vox_dev, False)
     # ---- device-resident timed region
@@ -610,6 +653,7 @@ def run_gmt(args, rank: int, world: int):
                    "cycle": "VWF"[opts.cycle],
                    "inner_tol": opts.inner_tol, "nu_coarse": opts.nu_coarse,
                    "omega": opts.omega, "coarse_fp16": opts.coarse_fp16,
+                   "autotune": tuned,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
                    "concurrent_cells": nstreams,
@@ -664,9 +708,19 @@ def run_512(args, gmt, ph, prec):
     import torch
     vox = torch.from_numpy(lattices.tpms_network("gyroid", 512, 0.20)).cuda()
     opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
-    opts.nu_pre = opts.nu_post = 2       # two level-0 sweeps win at 512^3 (7 vs 9 cycles)
+    opts.nu_pre = opts.nu_post = 2       # the fixed schedule (--no-autotune)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:   # untimed: one solve of the cell per candidate schedule
+        h = gmt.Hierarchy(vox, opts, stream)
+        best, times = h.autotune(ph, tol=TOL)
+        h.free()
+        for f in TUNED:
+            setattr(opts, f, getattr(best, f))
+        tuned = {"by": "gmt_autotune on the cell (one solve per candidate)",
+                 "times_ms": [round(float(t), 3) for t in times],
+                 "chosen": {f: getattr(best, f) for f in TUNED}}
 
     def once():
         h = gmt.Hierarchy(vox, opts, stream)
@@ -697,11 +751,13 @@ def run_512(args, gmt, ph, prec):
     return {"value_512": 1000.0 / mean, "ms_per_solve_512": mean, "vcycles_512": cyc[-1],
             "config_512": {"workload": "gyroid 512^3, phi 0.20, elasticity" if ph == gmt.ELASTIC
                            else "gyroid 512^3, phi 0.20, heat conduction",
-                           "solves": len(ms), "nu_pre": 2, "nu_post": 2,
-                           "status": sts, "ms_each": ms,
+                           "solves": len(ms), "nu_pre": opts.nu_pre, "nu_post": opts.nu_post,
+                           "nu_coarse": opts.nu_coarse, "coarse_fp16": opts.coarse_fp16,
+                           "autotune": tuned, "status": sts, "ms_each": ms,
                            "step": "hierarchy + operators + solve + C^H"}}
 
 
+TUNED = ("nu_pre", "nu_post", "nu_coarse", "coarse_fp16")   # the options --autotune picks
 LEARNED_SCALE = 0.04   # network output x 0.04 N = field (u / N has a spread of about 0.04)
 
 
@@ -765,6 +821,10 @@ def main():
                     help="smoothing sweeps on levels >= 1 (0: as on level 0)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="mixed precision: true-residual replacement factor (0: default)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the fixed smoothing schedule (by default it is tuned on the "
+                         "workload before the warm-up: one timed step per candidate for a "
+                         "batch, gmt_autotune for a single cell and for the 512^3 sub-result)")
     ap.add_argument("--coarse-fp16", action="store_true",
                     help="FP16 copies of the coarse levels' stored stencils")
     ap.add_argument("--batched", action="store_true",

@@ -232,6 +232,23 @@ gmt_status gmt_lambda_max(gmt_hierarchy* h, int level, double* out);
 gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
                      double tol, const double* u0, double* u_out, gmt_info* info);
 
+/* Number of option sets gmt_autotune tries. */
+#define GMT_AUTOTUNE_CANDIDATES 12
+
+/* Solver-schedule autotuner: solves this hierarchy's cell problems to tol once per
+   candidate and keeps the fastest. Candidate i (0..GMT_AUTOTUNE_CANDIDATES-1) sets
+   nu_pre = nu_post = 1 + i / 6, nu_coarse = 1 + (i / 2) % 3, coarse_fp16 = i % 2 (with
+   GMT_PREC_FP64 the FP16 candidates are skipped); the other options stay the hierarchy's.
+   Each solve starts from zero and is timed with CUDA events on the hierarchy's stream,
+   after one untimed solve and after the lazily built operators of every candidate exist.
+   The fastest candidate that returned GMT_OK is set on the hierarchy and written to best
+   (nullable); times_ms (nullable, GMT_AUTOTUNE_CANDIDATES entries) receives each
+   candidate's time in ms, infinity for a skipped or unconverged one. The 4^3 brick and
+   the kernels' tile shapes are fixed by the data layout and are not tuned.
+   GMT_NOT_CONVERGED if no candidate converged (the options are then unchanged). */
+gmt_status gmt_autotune(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                        double tol, gmt_options* best, double* times_ms);
+
 /* Solves the cell problems of n (1..GMT_BATCH_MAX) distinct hierarchies together, each
    exactly as gmt_solve(hs[i], physics, E, nu, k, tol, u0[i], u_out[i], &info[i]) would:
    every field, gmt_info and stored solution is bitwise what that call returns, including

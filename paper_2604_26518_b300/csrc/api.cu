@@ -29,6 +29,8 @@ void run_batched(gmt_hierarchy* const* hs, int n, const std::function<void(int)>
 void leave_batch_group();
 void prepare_batched_levels(gmt_hierarchy* h);
 bool batch_thread();
+void build_node_stencils(gmt_hierarchy* h, int level, bool fp64);
+void build_node_stencils16(gmt_hierarchy* h, int level);
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);
 void export_elems(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* c);
 void export_stencil(gmt_hierarchy* h, int l, int32_t* idx, double* w);
@@ -505,6 +507,78 @@ gmt_status gmt_solve_batch(gmt_hierarchy* const* hs, int n, gmt_physics physics,
     }
   }
   return worst;
+  GMT_API_END
+}
+
+gmt_status gmt_autotune(gmt_hierarchy* h, gmt_physics physics, double E, double nu, double k,
+                        double tol, gmt_options* best, double* times_ms) {
+  GMT_API_BEGIN
+  GMT_REQUIRE(h, GMT_ERR_ARG, "null hierarchy");
+  GMT_REQUIRE(tol > 0 && tol < 1, GMT_ERR_ARG, "tol must be in (0, 1)");
+  ensure_device(h);
+  ensure_material(h, physics, E, nu, k, nullptr);
+  const gmt_options base = h->opts;
+  const bool mixed = base.precision != GMT_PREC_FP64;
+  // build what the candidates create lazily, so that no candidate's time includes it
+  for (int l = 1; l + 1 < h->L; ++l) {
+    gmt::build_node_stencils(h, l, !mixed);
+    if (mixed) gmt::build_node_stencils16(h, l);
+  }
+  struct Cand {
+    int nu, nc, fp16;
+  };
+  std::vector<Cand> cands;
+  for (int nu_ = 1; nu_ <= 2; ++nu_)
+    for (int nc = 1; nc <= 3; ++nc)
+      for (int f = 0; f <= 1; ++f) cands.push_back(Cand{nu_, nc, f});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GMT_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) cudaEventDestroy(e0);
+  GMT_CUDA(ce);
+  double best_ms = INFINITY;
+  int best_i = -1;
+  try {
+    // one untimed solve: the workspace of this precision is allocated on first use
+    (void)solve_one(h, physics, E, nu, k, tol, nullptr, nullptr, nullptr);
+    for (size_t i = 0; i < cands.size(); ++i) {
+      double ms = INFINITY;
+      if (mixed || cands[i].fp16 == 0) {
+        gmt_options o = base;
+        o.nu_pre = o.nu_post = cands[i].nu;
+        o.nu_coarse = cands[i].nc;
+        o.coarse_fp16 = cands[i].fp16;
+        h->opts = o;
+        gmt_info info;
+        GMT_CUDA(cudaEventRecord(e0, h->stream));
+        const gmt_status st = solve_one(h, physics, E, nu, k, tol, nullptr, nullptr, &info);
+        GMT_CUDA(cudaEventRecord(e1, h->stream));
+        GMT_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        GMT_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (st == GMT_OK) ms = t;
+      }
+      if (times_ms) times_ms[i] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_i = (int)i;
+      }
+    }
+  } catch (...) {
+    h->opts = base;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->opts = base;
+  GMT_REQUIRE(best_i >= 0, GMT_NOT_CONVERGED, "autotune: no candidate reached tol %g", tol);
+  h->opts.nu_pre = h->opts.nu_post = cands[best_i].nu;
+  h->opts.nu_coarse = cands[best_i].nc;
+  h->opts.coarse_fp16 = cands[best_i].fp16;
+  if (best) *best = h->opts;
+  return GMT_OK;
   GMT_API_END
 }
 

@@ -112,6 +112,7 @@ _SIGS = {
     "gmt_vcycle": (_I, [_P, _I, _P, _P, _I]),
     "gmt_vcycle_batch": (_I, [_P, _I, _P, _P, _I]),
     "gmt_solve_batch": (_I, [_P, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P]),
+    "gmt_autotune": (_I, [_P, _I, _D, _D, _D, _D, ctypes.POINTER(Options), _P]),
     "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "gmt_solve": (_I, [_P, _I, _D, _D, _D, _D, _P, _P, ctypes.POINTER(Info)]),
     "gmt_homogenize": (_I, [_P, _I, _D, _D, _D, _P, _P]),
@@ -144,6 +145,7 @@ _SIGS = {
 }
 
 TRACE_CATEGORIES = 16
+AUTOTUNE_CANDIDATES = 12
 
 
 def release_cached_memory():
@@ -364,6 +366,16 @@ class Hierarchy:
                              ctypes.byref(info))
         _check(st, "gmt_solve", allow)
         return st, out, info
+
+    def autotune(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, tol=1e-5):
+        """gmt_autotune: solve once per candidate schedule and keep the fastest. Returns the
+        chosen Options (also set on the hierarchy) and each candidate's time in ms."""
+        self.physics = physics
+        best = Options()
+        times = np.zeros(AUTOTUNE_CANDIDATES, dtype=np.float64)
+        _check(lib().gmt_autotune(self._h, physics, E, nu, k, tol, ctypes.byref(best),
+                                  times.ctypes.data_as(ctypes.c_void_p)), "gmt_autotune")
+        return best, times
 
     def homogenize(self, physics=ELASTIC, E=1.0, nu=0.3, k=1.0, u=None):
         self.physics = physics
