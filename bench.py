@@ -50,13 +50,15 @@ C2_FAMILIES = ("gyroid", "schwarz_p", "diamond", "plate_gyroid", "plate_schwarz_
 METRIC = "C^H solves/s at rel. residual 1e-5 (128^3, 512^3); V-cycle HBM GB/s vs peak"
 TOL = 1e-5
 # ncu DRAM bytes (read + write) per active node and launch, from one capture of each
-# kernel on the first 128^3 bench cell (FP32 elasticity), keyed by trace category. A
+# kernel on the first 128^3 bench cell (FP32 elasticity). A
 # kernel whose source changed after its capture has no entry (its traffic is reported as
 # null until it is captured again).
 NCU_DRAM_BYTES_PER_NODE = {
-    # level-1 damped-Jacobi sweep (k_stencil KIND 1): 116.9 MB read + 3.1 MB written over
-    # the 88,670 level-1 nodes of the first bench cell (stored per-node stencils + vectors)
-    "stencil_l1": (116.924672e6 + 3.106304e6) / 88670,
+    # level-1 damped-Jacobi sweep over the 88,670 level-1 nodes of the first bench cell,
+    # keyed by (category, coarse_fp16): stored FP32 per-node stencils (k_stencil KIND 1):
+    # 116.9 MB read + 3.1 MB written; their FP16 copy (KIND 2): 69.0 MB + 1.6 MB
+    ("stencil_l1", 0): (116.924672e6 + 3.106304e6) / 88670,
+    ("stencil_l1", 1): (68.956672e6 + 1.588480e6) / 88670,
 }
 
 
@@ -608,8 +610,8 @@ def run_gmt(args, rank: int, world: int):
               default=None)
     dom_n, dom_ms, dom_b = totals.get(dom, [0, 0.0, 0.0]) if dom else (0, 0.0, 0.0)
     dom_gbs = (dom_b / (dom_ms / 1000.0) / 1e9) if dom_ms > 0 else None
-    ncu = NCU_DRAM_BYTES_PER_NODE.get(dom) if (ph == gmt.ELASTIC and prec == gmt.FP32 and
-                                               not opts.coarse_fp16) else None
+    ncu = NCU_DRAM_BYTES_PER_NODE.get((dom, opts.coarse_fp16)) \
+        if (ph == gmt.ELASTIC and prec == gmt.FP32) else None
     dom_nodes = avg_nodes if dom in ("smooth_l0", "resid_l0", "diag_l0") else \
         level_nodes.get(1) if dom == "stencil_l1" else None
     traffic = ncu * dom_nodes if (ncu is not None and dom_nodes) else None

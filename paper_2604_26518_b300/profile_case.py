@@ -1,6 +1,7 @@
 """Small, fixed launch sequences for profiling the library under ncu.
 
     python -m paper_2604_26518_b300.profile_case smoother   # k_stencil on one 128^3 cell
+    python -m paper_2604_26518_b300.profile_case smoother16 # the same, FP16 coarse stencils
     python -m paper_2604_26518_b300.profile_case setup      # hierarchy + operators, twice
     python -m paper_2604_26518_b300.profile_case solve      # one solve + C^H of one cell
 
@@ -29,8 +30,8 @@ def main(argv):
     import torch
     case = argv[1] if len(argv) > 1 else "smoother"
     vox = cell()
-    if case == "smoother":
-        h = gmt.Hierarchy(vox)
+    if case in ("smoother", "smoother16"):
+        h = gmt.Hierarchy(vox, gmt.default_options(coarse_fp16=int(case == "smoother16")))
         h.prepare(gmt.ELASTIC)
         rng = np.random.default_rng(0)
         for level in (0, 1):
