@@ -30,9 +30,9 @@ __global__ void k_tc_image(const float* __restrict__ W, int cin, int cout, int n
   img[i] = __float2half_rn(w);
 }
 
-__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
-  const __half2 h = __floats2half2_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
+__global__ void k_to_half(const float* __restrict__ x, int64_t n, __half* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2half_rn(x[i]);
 }
 
 // shared memory: A tiles [2][8 KB], B tiles [2][8 KB] (npad * 64 bytes used), the CTA's
@@ -46,13 +46,17 @@ constexpr int TC_SMEM = 47 * 1024;
 static_assert(TC_SMEM_USED <= TC_SMEM && 5 * TC_SMEM > 228 * 1024, "TMEM residency bound");
 constexpr int TC_BQ = TC_TILE / 16 / TC_ROWS;   // 16-byte B chunks per thread at npad = 128
 
-__global__ void __launch_bounds__(128) k_gconv_tc(const float* __restrict__ x, int cin,
+// x: FP16 input activations [rows of the input level][cin]; out32 / out16: the output
+// activations in FP32 (the last layer) or FP16 (one of them is null); add: FP16 skip input
+__global__ void __launch_bounds__(128) k_gconv_tc(const __half* __restrict__ x, int cin,
                                                   const int* __restrict__ tab,
                                                   const __half* __restrict__ img,
                                                   const float* __restrict__ bias,
-                                                  const float* __restrict__ add, int relu,
-                                                  float* __restrict__ out, int cout, int npad,
-                                                  int64_t n_out, const int* __restrict__ omap) {
+                                                  const __half* __restrict__ add, int relu,
+                                                  float* __restrict__ out32,
+                                                  __half* __restrict__ out16, int cout,
+                                                  int npad, int64_t n_out,
+                                                  const int* __restrict__ omap) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* sA = tc_smem;
   unsigned char* sB = tc_smem + TC_OFF_B;
@@ -102,18 +106,18 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const float* __restrict__ x, i
   const int nq = npad * 4;   // 16-byte chunks of a B tile
   const uint32_t idesc = tc_idesc(TC_ROWS, npad);
   // stage k's operands, loaded into registers one stage ahead
-  float4 an[TC_KC / 4];
+  uint4 an[TC_KC / 8];
   uint4 bn[TC_BQ];
   auto prefetch = [&](int k) {
     const int t = sTaps[1 + k / nch];
     const int ci0 = (k % nch) * TC_KC;
     const int src = sSrc[t * TC_ROWS + tid];
 #pragma unroll
-    for (int q = 0; q < TC_KC / 4; ++q) {
-      const int ch = ci0 + 4 * q;
+    for (int q = 0; q < TC_KC / 8; ++q) {
+      const int ch = ci0 + 8 * q;
       an[q] = (src >= 0 && ch < cin)
-                  ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)src * cin + ch))
-                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                  ? __ldg(reinterpret_cast<const uint4*>(x + (int64_t)src * cin + ch))
+                  : make_uint4(0u, 0u, 0u, 0u);
     }
     const uint4* bsrc =
         reinterpret_cast<const uint4*>(img + ((int64_t)t * nch + k % nch) * (npad * TC_KC));
@@ -128,10 +132,10 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const float* __restrict__ x, i
   int issued = 0;
   for (int k = 0; k < S; ++k) {
     const int buf = k & 1;
-    float4 ac[TC_KC / 4];
+    uint4 ac[TC_KC / 8];
     uint4 bc[TC_BQ];
 #pragma unroll
-    for (int q = 0; q < TC_KC / 4; ++q) ac[q] = an[q];
+    for (int q = 0; q < TC_KC / 8; ++q) ac[q] = an[q];
 #pragma unroll
     for (int j = 0; j < TC_BQ; ++j) bc[j] = bn[j];
     if (k + 1 < S) prefetch(k + 1);   // in flight while this stage is written and issued
@@ -143,12 +147,7 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const float* __restrict__ x, i
     }
     unsigned char* a = sA + buf * TC_TILE;
 #pragma unroll
-    for (int q = 0; q < TC_KC / 8; ++q) {
-      const float4 u = ac[2 * q], w = ac[2 * q + 1];
-      *reinterpret_cast<uint4*>(a + tc_offset(tid, 8 * q)) =
-          make_uint4(pack_half2(u.x, u.y), pack_half2(u.z, u.w), pack_half2(w.x, w.y),
-                     pack_half2(w.z, w.w));
-    }
+    for (int q = 0; q < TC_KC / 8; ++q) *reinterpret_cast<uint4*>(a + tc_offset(tid, 8 * q)) = ac[q];
     uint4* bdst = reinterpret_cast<uint4*>(sB + buf * TC_TILE);
 #pragma unroll
     for (int j = 0; j < TC_BQ; ++j) {
@@ -196,9 +195,10 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const float* __restrict__ x, i
           const int co = c0 + i;
           if (co < cout) {
             const int64_t o = node * cout + co;
-            float r = v[i] + (bias ? bias[co] : 0.f) + (add ? add[o] : 0.f);
+            float r = v[i] + (bias ? bias[co] : 0.f) + (add ? __half2float(add[o]) : 0.f);
             if (relu) r = fmaxf(r, 0.f);
-            out[o] = r;
+            if (out32) out32[o] = r;
+            else out16[o] = __float2half_rn(r);
           }
         }
       }
@@ -224,16 +224,24 @@ void tc_build_image(cudaStream_t s, const float* W, int cin, int cout, __half* i
   GMT_LAUNCH_CHECK();
 }
 
-void launch_gconv_tc(cudaStream_t s, const float* x, int cin, const int* tab, const __half* img,
-                     const float* bias, const float* add, int relu, float* out, int cout,
-                     int64_t n_out, const int* omap) {
+void tc_to_half(cudaStream_t s, const float* x, int64_t n, __half* y) {
+  if (n <= 0) return;
+  k_to_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, y);
+  GMT_LAUNCH_CHECK();
+}
+
+void launch_gconv_tc(cudaStream_t s, const __half* x, int cin, const int* tab, const __half* img,
+                     const float* bias, const __half* add, int relu, float* out32,
+                     __half* out16, int cout, int64_t n_out, const int* omap) {
+  GMT_REQUIRE((out32 == nullptr) != (out16 == nullptr), GMT_ERR_ARG,
+              "tensor-core convolution: exactly one output");
   GMT_REQUIRE(tc_supported(cin, cout), GMT_ERR_ARG, "tensor-core convolution: %d -> %d channels",
               cin, cout);
   if (n_out <= 0) return;
   ensure_smem_attr((const void*)k_gconv_tc, TC_SMEM);
   const unsigned grid = (unsigned)((n_out + TC_ROWS - 1) / TC_ROWS);
-  k_gconv_tc<<<grid, TC_ROWS, TC_SMEM, s>>>(x, cin, tab, img, bias, add, relu, out, cout,
-                                            tc_npad(cout), n_out, omap);
+  k_gconv_tc<<<grid, TC_ROWS, TC_SMEM, s>>>(x, cin, tab, img, bias, add, relu, out32, out16,
+                                            cout, tc_npad(cout), n_out, omap);
   GMT_LAUNCH_CHECK();
 }
 

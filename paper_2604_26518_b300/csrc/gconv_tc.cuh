@@ -5,8 +5,9 @@
 //
 // One CTA of 128 threads owns 128 output rows (one TMEM lane each, the MMA's M = 128) and
 // all N <= 128 output channels. It walks the (tap, 32-channel chunk) stages that any of its
-// rows uses; per stage every thread gathers its row's 32 input channels (FP32 -> FP16) into
-// the A tile, the CTA copies the stage's prepared FP16 weight image into the B tile, and
+// rows uses; per stage every thread gathers its row's 32 input channels (FP16 activations,
+// 64 bytes) into the A tile, the CTA copies the stage's prepared FP16 weight image into the
+// B tile, and
 // one thread issues two K = 16 MMAs and commits them to the stage buffer's mbarrier. Two
 // buffers: the gather of stage k overlaps the MMAs of stage k - 1, and buffer k & 1 is
 // refilled only after the MMAs of stage k - 2 have completed. Every wait is bounded; a wait

@@ -34,9 +34,10 @@ namespace gmt {
 bool tc_supported(int cin, int cout);                                        // gconv_tc.cu
 int64_t tc_image_halves(int cin, int cout);
 void tc_build_image(cudaStream_t s, const float* W, int cin, int cout, __half* img);
-void launch_gconv_tc(cudaStream_t s, const float* x, int cin, const int* tab, const __half* img,
-                     const float* bias, const float* add, int relu, float* out, int cout,
-                     int64_t n_out, const int* omap);
+void launch_gconv_tc(cudaStream_t s, const __half* x, int cin, const int* tab, const __half* img,
+                     const float* bias, const __half* add, int relu, float* out32,
+                     __half* out16, int cout, int64_t n_out, const int* omap);
+void tc_to_half(cudaStream_t s, const float* x, int64_t n, __half* y);
 int tc_take_status(cudaStream_t s);
 void export_nodes(gmt_hierarchy* h, int l, int32_t* xyz, uint8_t* m);       // hierarchy.cu
 void step_apply(gmt_hierarchy* h, int level, int precision, const double* u, double* y);  // solver.cu
@@ -515,6 +516,7 @@ struct gmt_netgraph {
   int key[4] = {0, 0, 0, 0};
   float* a[NACT] = {};
   float* g[NACT] = {};
+  __half* h[NACT] = {};   // tensor-core inference: FP16 copies of the activations 0..NACT-2
   float* dz = nullptr;
   float* part = nullptr;
   float* bpart = nullptr;
@@ -535,6 +537,7 @@ void ensure_buffers(gmt_netgraph* G, const gmt_unet* net) {
     return;
   G->buf.release();
   G->buf.bind(G->stream);
+  for (int a = 0; a < NACT; ++a) G->h[a] = nullptr;
   int64_t maxe = 0, maxpart = 0, maxb = 0;
   for (int a = 1; a < NACT; ++a) {
     const int64_t e = G->n[act_level(net->L, a)] * act_ch(net->L, a);
@@ -599,17 +602,29 @@ void forward(gmt_unet* net, gmt_netgraph* G, bool tc = false) {
     }
     GMT_CUDA(cudaMalloc(&net->img, sizeof(__half) * (size_t)off));
   }
+  bool all_tc = tc;
+  for (int i = 0; i < NLAYERS; ++i) all_tc = all_tc && gmt::tc_supported(net->L[i].cin, net->L[i].cout);
+  if (all_tc) {
+    // every layer on the tensor cores: the activations stay in FP16 between layers (the
+    // gathers move half the bytes); the last layer writes FP32
+    if (G->h[0] == nullptr)
+      for (int a = 0; a + 1 < NACT; ++a)
+        G->h[a] = G->buf.alloc<__half>(G->n[act_level(net->L, a)] * act_ch(net->L, a));
+    gmt::tc_to_half(G->stream, G->a[0], G->n[0] * IN_CH, G->h[0]);
+  }
   for (int i = 0; i < NLAYERS; ++i) {
     const LayerDef& d = net->L[i];
     const bool up = d.kind == UP;
     const int* tab = up ? G->up_perm[d.lvl_out] : fwd_table(G, d);
     const int* omap = up ? G->up_rows[d.lvl_out] : nullptr;
     const float* add = d.skip >= 0 ? G->a[d.skip] : nullptr;
-    if (tc && gmt::tc_supported(d.cin, d.cout)) {
+    if (all_tc) {
       gmt::tc_build_image(G->stream, net->p + net->woff[i], d.cin, d.cout,
                           net->img + net->img_off[i]);
-      gmt::launch_gconv_tc(G->stream, G->a[d.in], d.cin, tab, net->img + net->img_off[i],
-                           net->p + net->boff[i], add, d.relu, G->a[i + 1], d.cout,
+      const bool last = i + 1 == NLAYERS;
+      gmt::launch_gconv_tc(G->stream, G->h[d.in], d.cin, tab, net->img + net->img_off[i],
+                           net->p + net->boff[i], d.skip >= 0 ? G->h[d.skip] : nullptr, d.relu,
+                           last ? G->a[i + 1] : nullptr, last ? nullptr : G->h[i + 1], d.cout,
                            G->n[d.lvl_out], omap);
     } else {
       launch_gconv(G->stream, G->a[d.in], d.cin, tab, 0, net->p + net->woff[i], 0,
