@@ -9,7 +9,7 @@ solved directly:
     coarsest solve
     for l = L-1..1: u^l += P u^{l+1}; post-smooth
 
-The smoother is this build's choice: damped block-Jacobi, u <- u + omega D^-1 (f - K u)
+The smoother is selectable: damped block-Jacobi, u <- u + omega D^-1 (f - K u)
 applied to all nodes at once (the update form of Sec. 4.6), or Chebyshev, or the 8-colour
 Gauss-Seidel form of Sec. 4.6. D^l is the block diagonal of K^l (D x D node blocks). The
 coarsest solve (an exact solve in place of Alg. 1's inexact coarsest smoothing) is the
