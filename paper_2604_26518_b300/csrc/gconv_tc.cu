@@ -35,15 +35,22 @@ __global__ void k_to_half(const float* __restrict__ x, int64_t n, __half* __rest
   if (i < n) y[i] = __float2half_rn(x[i]);
 }
 
-// shared memory: A tiles [2][8 KB], B tiles [2][8 KB] (npad * 64 bytes used), the CTA's
-// table rows [27][128], mbarriers, TMEM slot, tap flags and list
-constexpr int TC_OFF_B = 2 * TC_TILE;
-constexpr int TC_OFF_SRC = 4 * TC_TILE;
-constexpr int TC_OFF_BAR = TC_OFF_SRC + 27 * TC_ROWS * 4;
-constexpr int TC_SMEM_USED = TC_OFF_BAR + 32 + 27 * 4 + 28 * 4;
-// 47 KB per CTA: at most four CTAs per SM, so their TMEM (at most 4 x 128 columns) fits
-constexpr int TC_SMEM = 47 * 1024;
-static_assert(TC_SMEM_USED <= TC_SMEM && 5 * TC_SMEM > 228 * 1024, "TMEM residency bound");
+// shared memory: A tiles [2][8 KB], B tiles [2][npad * 64 bytes], the CTA's table rows
+// [27][128], mbarriers, TMEM slot, tap flags and list
+__host__ __device__ constexpr int tc_off_src(int npad) { return 2 * TC_TILE + 2 * npad * 64; }
+__host__ __device__ constexpr int tc_off_bar(int npad) { return tc_off_src(npad) + 27 * TC_ROWS * 4; }
+__host__ __device__ constexpr int tc_smem_used(int npad) { return tc_off_bar(npad) + 32 + 55 * 4; }
+// dynamic shared memory per CTA, chosen so that the CTAs an SM can hold never ask for more
+// than its 512 TMEM columns: N = 128 (128 columns) -> 47 KB, at most 4 CTAs (each CTA also
+// holds 1 KB of reserved shared memory); N <= 64 -> what the tiles need, at most 38 KB (the
+// registers allow 6 CTAs: 6 x 64 columns fit)
+constexpr int TC_SMEM_MAX = 47 * 1024;
+__host__ __device__ constexpr int tc_smem_bytes(int npad) {
+  return npad > 64 ? TC_SMEM_MAX : (tc_smem_used(npad) + 1023) / 1024 * 1024;
+}
+static_assert(tc_smem_used(128) <= TC_SMEM_MAX && 5 * (TC_SMEM_MAX + 1024) > 228 * 1024,
+              "at most four 128-column CTAs per SM");
+static_assert(8 * 64 <= 512, "any number of 64-column CTAs the registers allow fits");
 constexpr int TC_BQ = TC_TILE / 16 / TC_ROWS;   // 16-byte B chunks per thread at npad = 128
 
 // x: FP16 input activations [rows of the input level][cin]; out32 / out16: the output
@@ -58,12 +65,13 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const __half* __restrict__ x, 
                                                   int npad, int64_t n_out,
                                                   const int* __restrict__ omap) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
+  const int btile = npad * 64;                    // bytes of one B tile
   unsigned char* sA = tc_smem;
-  unsigned char* sB = tc_smem + TC_OFF_B;
-  int* sSrc = reinterpret_cast<int*>(tc_smem + TC_OFF_SRC);               // [27][128]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + TC_OFF_BAR);     // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + TC_OFF_BAR + 16);
-  int* sAny = reinterpret_cast<int*>(tc_smem + TC_OFF_BAR + 32);          // [27]
+  unsigned char* sB = tc_smem + 2 * TC_TILE;
+  int* sSrc = reinterpret_cast<int*>(tc_smem + tc_off_src(npad));           // [27][128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + tc_off_bar(npad)); // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + tc_off_bar(npad) + 16);
+  int* sAny = reinterpret_cast<int*>(tc_smem + tc_off_bar(npad) + 32);      // [27]
   int* sTaps = sAny + 27;                                                 // [28]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t n0 = (int64_t)blockIdx.x * TC_ROWS;
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const __half* __restrict__ x, 
     unsigned char* a = sA + buf * TC_TILE;
 #pragma unroll
     for (int q = 0; q < TC_KC / 8; ++q) *reinterpret_cast<uint4*>(a + tc_offset(tid, 8 * q)) = ac[q];
-    uint4* bdst = reinterpret_cast<uint4*>(sB + buf * TC_TILE);
+    uint4* bdst = reinterpret_cast<uint4*>(sB + buf * btile);
 #pragma unroll
     for (int j = 0; j < TC_BQ; ++j) {
       const int i = tid + j * TC_ROWS;
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(128) k_gconv_tc(const __half* __restrict__ x, 
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_u32(a), b0 = smem_u32(sB + buf * TC_TILE);
+      const uint32_t a0 = smem_u32(a), b0 = smem_u32(sB + buf * btile);
 #pragma unroll
       for (int kk = 0; kk < 2; ++kk)
         tc_mma(tmem, tc_smem_desc(a0 + kk * 4096, 128, 256),
@@ -238,10 +246,11 @@ void launch_gconv_tc(cudaStream_t s, const __half* x, int cin, const int* tab, c
   GMT_REQUIRE(tc_supported(cin, cout), GMT_ERR_ARG, "tensor-core convolution: %d -> %d channels",
               cin, cout);
   if (n_out <= 0) return;
-  ensure_smem_attr((const void*)k_gconv_tc, TC_SMEM);
+  ensure_smem_attr((const void*)k_gconv_tc, TC_SMEM_MAX);
+  const int npad = tc_npad(cout);
   const unsigned grid = (unsigned)((n_out + TC_ROWS - 1) / TC_ROWS);
-  k_gconv_tc<<<grid, TC_ROWS, TC_SMEM, s>>>(x, cin, tab, img, bias, add, relu, out32, out16,
-                                            cout, tc_npad(cout), n_out, omap);
+  k_gconv_tc<<<grid, TC_ROWS, tc_smem_bytes(npad), s>>>(x, cin, tab, img, bias, add, relu, out32,
+                                                        out16, cout, npad, n_out, omap);
   GMT_LAUNCH_CHECK();
 }
 
