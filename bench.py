@@ -330,8 +330,11 @@ def run_gmt(args, rank: int, world: int):
         h = gmt.Hierarchy(cells[0][0], opts)
         best, times = h.autotune(ph, tol=TOL)
         h.free()
+        choice = [{f: getattr(best, f) for f in TUNED}]
+        if world > 1:   # every rank runs rank 0's choice
+            dist.broadcast_object_list(choice, src=0)
         for f in TUNED:
-            setattr(opts, f, getattr(best, f))
+            setattr(opts, f, choice[0][f])
         tuned = {"by": "gmt_autotune on the cell (one solve per candidate)",
                  "times_ms": [round(float(t), 3) for t in times],
                  "chosen": {f: getattr(best, f) for f in TUNED}}
@@ -512,6 +515,10 @@ def run_gmt(args, rank: int, world: int):
             torch.cuda.synchronize()
             times.append(1000.0 * (time.perf_counter() - t0))
         a, b, c = cands[min(range(len(cands)), key=lambda i: times[i])]
+        if world > 1:   # every rank runs rank 0's choice
+            choice = [(a, b, c)]
+            dist.broadcast_object_list(choice, src=0)
+            a, b, c = choice[0]
         opts.nu_pre = opts.nu_post = a
         opts.nu_coarse = b
         opts.coarse_fp16 = c
