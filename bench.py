@@ -324,6 +324,7 @@ def run_gmt(args, rank: int, world: int):
         opts.cycle = {"V": gmt.CYCLE_V, "W": gmt.CYCLE_W, "F": gmt.CYCLE_F}[args.cycle]
     if args.coarse_fp16:
         opts.coarse_fp16 = 1
+    opts.warm_sweeps = args.warm_sweeps
     tuned = None
     if args.autotune and len(cells) == 1:
         # one cell fills the GPU alone: gmt_autotune's solve time is the throughput (untimed)
@@ -662,6 +663,7 @@ def run_gmt(args, rank: int, world: int):
                    "cycle": "VWF"[opts.cycle],
                    "inner_tol": opts.inner_tol, "nu_coarse": opts.nu_coarse,
                    "omega": opts.omega, "coarse_fp16": opts.coarse_fp16,
+                   "warm_sweeps": opts.warm_sweeps,
                    "autotune": tuned,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
@@ -848,6 +850,8 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="warm-start every solve from the learned initializer, trained first "
                          "(untimed) on seeded 32^3 cells")
+    ap.add_argument("--warm-sweeps", type=int, default=0,
+                    help="damped-Jacobi sweeps on a warm start before the iteration")
     ap.add_argument("--learned-tc", action="store_true",
                     help="network inference on the tensor cores (FP16 operands, tcgen05)")
     ap.add_argument("--learned-epochs", type=int, default=20)

@@ -107,6 +107,10 @@ typedef struct {
                           in FP16 (scaled per level, FP32 arithmetic), half the bytes the
                           coarse sweeps read; the V-cycle becomes a slightly different
                           preconditioner (the solve's accuracy is unchanged) */
+  int warm_sweeps;     /* [0] with a given initial field u0: this many damped-Jacobi sweeps
+                          on level 0 (omega) smooth it before the iteration starts, removing
+                          the rough part of a predicted field's error that the V-cycle
+                          preconditioned iteration would otherwise carry (0..16) */
 } gmt_options;
 
 /* Per-solve report. rel_residual[m] = ||f_m - K u_m|| / ||f_m|| of the returned field,

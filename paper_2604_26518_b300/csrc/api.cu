@@ -59,7 +59,8 @@ static bool opts_valid(const gmt_options& o) {
          o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post > 0 && o.omega > 0 &&
          o.cheb_ratio > 1 && o.cheb_upper >= 1 && o.precision >= 0 && o.precision <= 2 &&
          o.inner_tol > 0 && o.inner_tol < 1 && o.max_inner > 0 && o.max_outer >= 0 &&
-         (o.coarse_fp16 == 0 || o.coarse_fp16 == 1);
+         (o.coarse_fp16 == 0 || o.coarse_fp16 == 1) && o.warm_sweeps >= 0 &&
+         o.warm_sweeps <= 16;
 }
 
 static void ensure_device(gmt_hierarchy* h) { GMT_CUDA(cudaSetDevice(h->device)); }
@@ -115,6 +116,7 @@ void gmt_default_options(gmt_options* o) {
   o->nu_coarse = 2;
   o->graphs = 1;
   o->coarse_fp16 = 0;
+  o->warm_sweeps = 0;
 }
 
 const char* gmt_status_string(gmt_status s) {

@@ -471,6 +471,37 @@ static Prec prec_of(int p) { return p == GMT_PREC_FP64 ? P64 : (p == GMT_PREC_BF
 //   float-float difference-form kernel and replaces the iterated one. The Krylov recurrence
 //   (p, r.z) continues across these replacements instead of restarting, so the iteration
 //   count stays that of FP64 CG while every vector operation runs in FP32.
+// warm_sweeps damped-Jacobi sweeps on level 0 applied to the given initial field (the
+// solution buffers of the solve: u64, or hi with lo cleared) against the level-0 load
+static void smooth_start(gmt_hierarchy* h, Workspace* w, bool mixed) {
+  const gmt_options& o = h->opts;
+  const Prec pr = mixed ? P32 : P64;
+  void* f = w->f[0];
+  if (mixed) {
+    launch_resid_ff(h, nullptr, nullptr, (float*)f, nullptr);   // the load (zero start)
+  } else {
+    vec_zero(h, 0, P64, w->ub[0]);
+    VecArgs r;   // f - K 0 with the load formed by the kernel
+    r.u = w->ub[0];
+    r.out = f;
+    launch_stencil(h, 0, P64, ST_RESID, r);
+  }
+  void* cur = mixed ? (void*)w->hi : (void*)w->u64;
+  void* oth = w->ua[0];
+  for (int k = 0; k < o.warm_sweeps; ++k) {
+    VecArgs a;
+    a.u = cur;
+    a.f = f;
+    a.out = oth;
+    a.omega = o.omega;
+    launch_stencil(h, 0, pr, ST_JACOBI, a);
+    std::swap(cur, oth);
+  }
+  void* sol = mixed ? (void*)w->hi : (void*)w->u64;
+  if (cur != sol) vec_copy(h, 0, pr, cur, sol);
+  if (mixed) vec_zero(h, 0, P32, w->lo);
+}
+
 gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, gmt_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   const gmt_options& o = h->opts;
@@ -535,6 +566,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       vec_zero(h, 0, P32, w->lo);
     }
   }
+  if (u0 && o.warm_sweeps > 0) smooth_start(h, w, mixed);
   const Prec ar = w->arith;
   // Mixed precision: the difference-form FP32 operator annihilates translations exactly,
   // while FP32 rounding leaves the iterated residual, and the V-cycle output, with small

@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("nu_coarse", ctypes.c_int),
         ("graphs", ctypes.c_int),
         ("coarse_fp16", ctypes.c_int),
+        ("warm_sweeps", ctypes.c_int),
     ]
 
 
