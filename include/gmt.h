@@ -216,9 +216,10 @@ gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* 
    over the bricks of all n lattices, so the small coarse levels of many cells fill the GPU
    together and the launch count does not grow with n. The hierarchies must share the
    material (physics and parameters of gmt_prepare), have no element densities, use the
-   damped-Jacobi smoother and the V-cycle with the same omega, nu_pre, nu_post, nu_coarse,
-   and run on the same device and stream; otherwise GMT_ERR_ARG (GMT_ERR_STATE if one is
-   not prepared). Sizes and level counts may differ: at each level the lattices whose
+   damped-Jacobi smoother and the V-cycle with the same omega, nu_pre, nu_post, nu_coarse
+   and coarse_fp16, and run on the same device and stream; otherwise GMT_ERR_ARG
+   (GMT_ERR_STATE if one is not prepared). Sizes and level counts may differ: at each
+   level the lattices whose
    coarsest level it is take their coarsest solve in one launch, the others go on down.
    The launches go to that stream and the call returns after it has finished them. */
 gmt_status gmt_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
@@ -261,7 +262,8 @@ gmt_status gmt_autotune(gmt_hierarchy* h, gmt_physics physics, double E, double 
    run as one batched V-cycle (as gmt_vcycle_batch) on a stream of the call's own, so the
    small coarse levels of all cells share each launch. The hierarchies must be on one
    device and use mixed precision (GMT_PREC_FP32), the damped-Jacobi smoother and the
-   V-cycle with the same omega, nu_pre, nu_post and nu_coarse, without element densities;
+   V-cycle with the same omega, nu_pre, nu_post, nu_coarse and coarse_fp16, without
+   element densities;
    their sizes and level counts may differ. u0 and u_out are arrays of n device pointers,
    or NULL (entries may be NULL: zero start / no copy out, as for gmt_solve); info and
    status, if not NULL, receive n entries. Returns GMT_OK when every lattice returned
