@@ -203,6 +203,27 @@ def cpu_sample(seeds, n: int = 32, procs: int = 1, timeout: float = 900.0):
 
 
 # ---------------------------------------------------------------- reference arm
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def from_rank0(obj, world: int):
+    """Rank 0's obj on every rank (a choice all ranks must share)."""
+    if world <= 1:
+        return obj
+    import torch.distributed as dist
+    box = [obj]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
 def run_reference(args, rank: int, world: int):
     """The CPU FP64 oracle on the bench's 16 cells, regenerated at 32^3 (the 128^3 cells
     need an assembled matrix of ~8 GB and hours of Jacobi-PCG per cell), spread over the
@@ -331,11 +352,9 @@ def run_gmt(args, rank: int, world: int):
         h = gmt.Hierarchy(cells[0][0], opts)
         best, times = h.autotune(ph, tol=TOL)
         h.free()
-        choice = [{f: getattr(best, f) for f in TUNED}]
-        if world > 1:   # every rank runs rank 0's choice
-            dist.broadcast_object_list(choice, src=0)
+        choice = from_rank0({f: getattr(best, f) for f in TUNED}, world)   # rank 0's choice
         for f in TUNED:
-            setattr(opts, f, choice[0][f])
+            setattr(opts, f, choice[f])
         tuned = {"by": "gmt_autotune on the cell (one solve per candidate)",
                  "times_ms": [round(float(t), 3) for t in times],
                  "chosen": {f: getattr(best, f) for f in TUNED}}
@@ -516,10 +535,7 @@ def run_gmt(args, rank: int, world: int):
             torch.cuda.synchronize()
             times.append(1000.0 * (time.perf_counter() - t0))
         a, b, c = cands[min(range(len(cands)), key=lambda i: times[i])]
-        if world > 1:   # every rank runs rank 0's choice
-            choice = [(a, b, c)]
-            dist.broadcast_object_list(choice, src=0)
-            a, b, c = choice[0]
+        a, b, c = from_rank0((a, b, c), world)   # every rank runs rank 0's choice
         opts.nu_pre = opts.nu_post = a
         opts.nu_coarse = b
         opts.coarse_fp16 = c
@@ -570,11 +586,7 @@ def run_gmt(args, rank: int, world: int):
     brk, _ = one_step(vox_dev, 2, serial=True)
     torch.cuda.synchronize()
     barrier()
-    elapsed_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(sum(step_ms), world, dev)
     cells_total = len(cells) * world * args.steps
     value = cells_total / (elapsed_ms / 1000.0)
     # ---- e2e through the public API from pinned host voxels
@@ -584,11 +596,7 @@ def run_gmt(args, rank: int, world: int):
     for s in range(args.steps):
         one_step(vox_host, False)
     torch.cuda.synchronize()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0), world, dev)
     e2e_value = cells_total / (e2e_ms / 1000.0)
     if rank != 0:
         return
