@@ -91,3 +91,19 @@ def test_batch_solve_rejects_unsupported_options(gmt_lib):
         gmt.solve_batch([a, a], gmt.ELASTIC)
     assert e.value.status == gmt.ERR_ARG
     a.free()
+
+
+def test_batch_of_one_without_fields(gmt_lib):
+    """A batch of one cell, with no field copied out: the stored solution's C^H and the
+    V-cycle count are gmt_solve's."""
+    gmt = gmt_lib
+    vox = L.tpms_plate("diamond", 48, 0.3)
+    h1 = gmt.Hierarchy(vox)
+    st, _, info = h1.solve(gmt.ELASTIC, tol=1e-5, want_field=False)
+    CH = h1.homogenize(gmt.ELASTIC)
+    h2 = gmt.Hierarchy(vox)
+    (bst, bu, binfo), = gmt.solve_batch([h2], gmt.ELASTIC, tol=1e-5, want_fields=False)
+    assert bst == st == gmt.OK and bu is None and binfo.inner_total == info.inner_total
+    assert np.array_equal(h2.homogenize(gmt.ELASTIC), CH)
+    h1.free()
+    h2.free()
