@@ -132,7 +132,16 @@ void free_workspace(gmt_hierarchy* h) {
 
 static Workspace* workspace(gmt_hierarchy* h, Prec prec) {
   if (h->ws && h->ws_for_prec == (int64_t)prec) return h->ws;
-  free_workspace(h);
+  // a stored solution outlives the switch to another precision's workspace: it waits as a
+  // canonical FP64 field (exact for a float-float pair) and moves into the new workspace's
+  // form below
+  double* keep = nullptr;
+  if (h->ws && h->have_solution) {
+    keep = (double*)pool_alloc((size_t)h->lv[0].n_nodes * h->mat.C * sizeof(double));
+    if (h->ws->prec == P64) slots_to_canon(h, 0, P64, h->ws->u64, keep);
+    else ff_to_canon(h, h->ws->hi, h->ws->lo, keep);
+  }
+  free_workspace(h);   // waits for the hierarchy's stream
   Workspace* w = new Workspace();
   h->ws = w;
   h->ws_for_prec = prec;
@@ -168,7 +177,12 @@ static Workspace* workspace(gmt_hierarchy* h, Prec prec) {
   w->ones = h->work.alloc<double>(8);
   double ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
   GMT_CUDA(cudaMemcpyAsync(w->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream));
+  if (keep) {
+    if (prec == P64) canon_to_slots(h, 0, P64, keep, w->u64);
+    else canon_to_ff(h, keep, w->hi, w->lo);
+  }
   GMT_CUDA(cudaStreamSynchronize(h->stream));
+  if (keep) pool_free(keep);
   return w;
 }
 
@@ -813,6 +827,22 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   return st;
 }
 
+// A caller's canonical field in the workspace's form, in scratch buffers (the stored
+// solution stays): FP64 slots on an FP64 workspace, else a float-float pair in the
+// conversion scratch (cvt and rout hold n0 floats there)
+static void external_field(gmt_hierarchy* h, Workspace* w, const double* u, const void** u64,
+                           const float** hi, const float** lo) {
+  if (w->prec == P64) {
+    canon_to_slots(h, 0, P64, u, w->f64);
+    *u64 = w->f64;
+  } else {
+    float* shi = (float*)w->cvt;
+    canon_to_ff(h, u, shi, w->rout);
+    *hi = shi;
+    *lo = w->rout;
+  }
+}
+
 // C^H from the stored solution (u == nullptr) or a canonical field
 void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
   const Material& mt = h->mat;
@@ -821,18 +851,10 @@ void homogenize(gmt_hierarchy* h, const double* u, double* CH) {
   Prec pr = w ? w->prec : P32;
   if (!w) w = workspace(h, P32);
   const void* u64 = w->u64;
-  if (u) {
-    // external field: FP64 on an FP64 workspace (scratch copy, the stored solution stays),
-    // else the float-float split of the FP64 input
-    if (pr == P64) {
-      canon_to_slots(h, 0, P64, u, w->f64);
-      u64 = w->f64;
-    } else {
-      canon_to_ff(h, u, w->hi, w->lo);
-    }
-  }
+  const float *hi = w->hi, *lo = w->lo;
+  if (u) external_field(h, w, u, &u64, &hi, &lo);
   if (pr == P64) launch_energy(h, P64, u64, nullptr, w->part);
-  else launch_energy(h, P32, w->hi, w->lo, w->part);
+  else launch_energy(h, P32, hi, lo, w->part);
   double e[21];
   fetch(h, reduce_to(h, w, 0, K, 0), e, K);
   const double vol = (double)h->N * h->N * h->N;
@@ -853,19 +875,13 @@ void sensitivities(gmt_hierarchy* h, const double* u, double simp_p, double* out
   Prec pr = w ? w->prec : P32;
   if (!w) w = workspace(h, P32);
   const void* u64 = w->u64;
-  if (u) {
-    if (pr == P64) {
-      canon_to_slots(h, 0, P64, u, w->f64);
-      u64 = w->f64;
-    } else {
-      canon_to_ff(h, u, w->hi, w->lo);
-    }
-  }
+  const float *hi = w->hi, *lo = w->lo;
+  if (u) external_field(h, w, u, &u64, &hi, &lo);
   // with densities the factor p rho_e^(p-1) is applied per element by the kernel
   const double vol = (double)h->N * h->N * h->N;
   const double scale = h->dens ? 1.0 / vol : simp_p / vol;
   if (pr == P64) launch_energy_per(h, P64, u64, nullptr, out, scale);
-  else launch_energy_per(h, P32, w->hi, w->lo, out, scale);
+  else launch_energy_per(h, P32, hi, lo, out, scale);
   GMT_CUDA(cudaStreamSynchronize(h->stream));
 }
 
@@ -877,9 +893,12 @@ void residual_of(gmt_hierarchy* h, int precision, const double* u, double* out) 
   double fn[8], rn[8];
   load_norms2(h, fn);
   if (precision == GMT_PREC_FP64) {
-    canon_to_slots(h, 0, P64, u, w->u64);
+    // scratch for the FP64 copy: u64 holds the stored solution on an FP64 workspace, where
+    // the correction x has n0 doubles; on the others u64 is scratch
+    void* ucp = w->prec == P64 ? w->x : w->u64;
+    canon_to_slots(h, 0, P64, u, ucp);
     VecArgs a;
-    a.u = w->u64;
+    a.u = ucp;
     a.out = w->f64;
     a.part = w->part;
     launch_stencil(h, 0, P64, ST_RESID, a);

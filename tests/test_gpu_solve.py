@@ -124,6 +124,37 @@ def test_repeat_runs_bitwise_identical(gmt_lib):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+def test_stored_solution_survives_other_calls(gmt_lib, kind):
+    """Calls between gmt_solve and C^H of the stored solution leave that solution as it was:
+    per-step applies that switch the workspace to the other precision and back, an FP64
+    residual, and C^H or sensitivities of another field."""
+    gmt = gmt_lib
+    ph = gmt.ELASTIC if kind == "elastic" else gmt.HEAT
+    vox = L.tpms_network("gyroid", 32, 0.30)
+    h = gmt.Hierarchy(vox)
+    st, u, info = h.solve(ph, tol=TOL)
+    assert st == gmt.OK
+    CH = h.homogenize(ph)
+    other = u * 0.5
+    h.apply(0, u, gmt.FP64)              # the FP64 workspace takes the solution over
+    CH64 = h.homogenize(ph)
+    assert np.abs(CH64 - CH).max() <= 1e-6 * np.abs(CH).max()
+    h.residual(u, gmt.FP64)
+    h.homogenize(ph, u=other)
+    h.sensitivities(ph, u=other)
+    assert np.array_equal(h.homogenize(ph), CH64)
+    h.apply(0, u, gmt.FP32)              # and back: the float-float pair round-trips exactly
+    assert np.array_equal(h.homogenize(ph), CH)
+    h.homogenize(ph, u=other)
+    h.sensitivities(ph, u=other)
+    h.residual(other, gmt.FP64)
+    h.residual(other, gmt.FP32)
+    assert np.array_equal(h.homogenize(ph), CH)
+    assert not np.allclose(h.homogenize(ph, u=other), CH)
+    h.free()
+
+
 def test_warm_start_resumes(gmt_lib):
     gmt = gmt_lib
     vox = L.largest_component(L.truss("bcc", 32, 0.09))
