@@ -274,7 +274,10 @@ gmt_status gmt_solve_batch(gmt_hierarchy* const* hs, int n, gmt_physics physics,
 
 /* Homogenized tensor (App. F.1 C^H, App. F.2 kappa^H): CH_out host double[M][M]
    row-major = 1/N^3 sum_e (x0^I - u_e^I)^T K_e (x0^J - u_e^J). u: device canonical field,
-   or NULL for the field of the last gmt_solve on this hierarchy. */
+   or NULL for the field of the last gmt_solve on this hierarchy. That stored field stays
+   as the solve left it through later calls on the hierarchy (per-level steps in either
+   precision, residuals, C^H or sensitivities of other fields); a new material, new
+   densities or another solve replace or discard it. */
 gmt_status gmt_homogenize(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                           double k, const double* u, double* CH_out);
 
