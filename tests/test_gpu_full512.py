@@ -1,7 +1,7 @@
-"""Full-size 512^3 gyroid (phi 0.20, elasticity): the benchmark's 512^3 cell, solved with the
-schedule its autotuner picks there (nu 1, coarse nu 2, FP16 coarse stencils), checked where
-the FP64 oracle can follow at 30 M nodes (an assembled solve of 2e8 unknowns is out of its
-reach; the 128^3 test checks the whole-field identities):
+"""Full-size 512^3 gyroid (phi 0.20), elasticity and heat conduction: the benchmark's 512^3
+cell, solved with the schedule its autotuner picks there (nu 1, coarse nu 2, FP16 coarse
+stencils), checked where the FP64 oracle can follow at 30 M nodes (an assembled solve of
+2e8 unknowns is out of its reach; the 128^3 test checks the whole-field identities):
 - canonical numbering (Sec. 4.1): the library's node list is the oracle's, node for node;
 - the matrix-free operator (Sec. 4.6): the library's FP64 and FP32 K u at sampled nodes,
   interior and surface, against the oracle's sum over each node's active incident elements
@@ -58,22 +58,24 @@ def _oracle_Ku(Ke, D, masks, U27):
 
 @pytest.fixture(scope="module")
 def cell512():
-    return L.tpms_network("gyroid", N, 0.20)
+    vox = L.tpms_network("gyroid", N, 0.20)
+    return vox, grid.Level(vox)
 
 
-def test_full_size_512_sampled_parity(gmt_lib, cell512):
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+def test_full_size_512_sampled_parity(gmt_lib, cell512, kind):
     import torch
     gmt = gmt_lib
-    vox = cell512
-    Ke, x0, D, M, C0 = fe.physics("elastic")
+    vox, lev = cell512
+    ph = gmt.ELASTIC if kind == "elastic" else gmt.HEAT
+    Ke, x0, D, M, C0 = fe.physics(kind)
     opts = gmt.default_options(nu_coarse=2, coarse_fp16=1)
     opts.nu_pre = opts.nu_post = 1
     h = gmt.Hierarchy(torch.from_numpy(vox).cuda(), opts)
-    st, u, info = h.solve(gmt.ELASTIC, tol=TOL)
-    assert st == gmt.OK and max(info.as_dict()["rel_residual"]) <= TOL
+    st, u, info = h.solve(ph, tol=TOL)
+    assert st == gmt.OK and max(info.as_dict()["rel_residual"][:M]) <= TOL
 
     # canonical numbering, node for node
-    lev = grid.Level(vox)
     n = h.num_nodes(0)
     assert n == lev.num_nodes
     xyz, mk = h.node_coords(0)
@@ -122,7 +124,7 @@ def test_full_size_512_sampled_parity(gmt_lib, cell512):
     # the load itself is large at the surface: the bound is not met trivially
     assert (np.sqrt((Ftab[masks] ** 2).sum(axis=1)) > TOL * fnorm).any()
 
-    CH = h.homogenize(gmt.ELASTIC)
+    CH = h.homogenize(ph)
     phi = vox.mean()
     assert np.abs(CH - CH.T).max() < 1e-12 * np.abs(CH).max()
     assert np.linalg.eigvalsh(CH).min() > 0
