@@ -781,16 +781,16 @@ LEARNED_SCALE = 0.04   # network output x 0.04 N = field (u / N has a spread of 
 
 
 def train_initializer(args, ph, opts):
-    """Train the initializer network (untimed): solve seeded 32^3 cells to r <= 1e-6 with
-    this library, then AdamW on the relative energy-norm loss, one cell per step, cosine
-    learning rate from 1e-3."""
+    """Train the initializer network (untimed): solve seeded cells of side --learned-n
+    (32^3 by default) to r <= 1e-6 with this library, then AdamW on the relative energy-norm
+    loss, one cell per step, cosine learning rate from 1e-3."""
     import torch
 
     from paper_2604_26518_b300 import gmt
     t0 = time.perf_counter()
     data = []
     for i in range(args.learned_cells):
-        vox, _ = lattices.mixed_cell(100 + i, 32, families=C2_FAMILIES)
+        vox, _ = lattices.mixed_cell(100 + i, args.learned_n, families=C2_FAMILIES)
         h = gmt.Hierarchy(vox, opts)
         _, u, _ = h.solve(ph, E=1.0, nu=0.3, k=1.0, tol=1e-6)
         data.append((h, gmt.NetGraph(h), u.reshape(h.num_nodes(0), -1).contiguous()))
@@ -803,7 +803,8 @@ def train_initializer(args, ph, opts):
         for i in np.random.default_rng(ep).permutation(len(data)):
             h, g, u = data[i]
             lr = 1e-3 * 0.5 * (1.0 + np.cos(np.pi * k / steps))
-            losses.append(net.train_step(g, u, LEARNED_SCALE * 32, lr=lr, weight_decay=1e-4,
+            losses.append(net.train_step(g, u, LEARNED_SCALE * args.learned_n, lr=lr,
+                                         weight_decay=1e-4,
                                          loss=gmt.LOSS_ENERGY, hier=h))
             k += 1
     torch.cuda.synchronize()
@@ -812,7 +813,7 @@ def train_initializer(args, ph, opts):
         g.free()
         h.free()
     last = losses[-len(data):]
-    return net, {"params": net.num_params, "train_cells": len(data), "train_n": 32,
+    return net, {"params": net.num_params, "train_cells": len(data), "train_n": args.learned_n,
                  "steps": steps, "loss": "relative energy norm of the error, (e^T K e)/(u^T K u)",
                  "first_epoch_loss": float(np.mean(losses[:len(data)])),
                  "last_epoch_loss": float(np.mean(last)),
@@ -864,6 +865,8 @@ def main():
                     help="network inference on the tensor cores (FP16 operands, tcgen05)")
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--learned-cells", type=int, default=64)
+    ap.add_argument("--learned-n", type=int, default=32, choices=[32, 64],
+                    help="side of the training cells")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
