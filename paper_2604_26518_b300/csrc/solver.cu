@@ -134,55 +134,73 @@ static Workspace* workspace(gmt_hierarchy* h, Prec prec) {
   if (h->ws && h->ws_for_prec == (int64_t)prec) return h->ws;
   // a stored solution outlives the switch to another precision's workspace: it waits as a
   // canonical FP64 field (exact for a float-float pair) and moves into the new workspace's
-  // form below
-  double* keep = nullptr;
+  // form below; the block goes back to the pool once the stream has finished with it
+  struct Keep {
+    double* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Keep() {
+      if (p) {
+        cudaStreamSynchronize(s);
+        pool_free(p);
+      }
+    }
+  } keep;
+  keep.s = h->stream;
   if (h->ws && h->have_solution) {
-    keep = (double*)pool_alloc((size_t)h->lv[0].n_nodes * h->mat.C * sizeof(double));
-    if (h->ws->prec == P64) slots_to_canon(h, 0, P64, h->ws->u64, keep);
-    else ff_to_canon(h, h->ws->hi, h->ws->lo, keep);
+    keep.p = (double*)pool_alloc((size_t)h->lv[0].n_nodes * h->mat.C * sizeof(double));
+    if (h->ws->prec == P64) slots_to_canon(h, 0, P64, h->ws->u64, keep.p);
+    else ff_to_canon(h, h->ws->hi, h->ws->lo, keep.p);
   }
   free_workspace(h);   // waits for the hierarchy's stream
+  // built aside and published only when complete: a failed allocation leaves no
+  // half-built workspace behind for a later call to use
   Workspace* w = new Workspace();
+  try {
+    w->prec = prec;
+    w->arith = prec == P64 ? P64 : P32;
+    const int C = h->mat.C;
+    const size_t sb = prec_bytes(prec), ab = prec_bytes(w->arith);
+    for (int l = 0; l < h->L; ++l) {
+      const int64_t nv = h->lv[l].nslots * C;
+      w->ua.push_back(h->work.raw(nv * sb));
+      w->ub.push_back(h->work.raw(nv * sb));
+      w->f.push_back(h->work.raw(nv * sb));
+      w->r.push_back(h->work.raw(nv * sb));
+      w->dc.push_back(h->work.raw(nv * sb));
+    }
+    const int64_t n0 = h->lv[0].nslots * C;
+    w->x = h->work.raw(n0 * ab);
+    w->rr = h->work.raw(n0 * ab);
+    w->p = h->work.raw(n0 * ab);
+    w->q = h->work.raw(n0 * ab);
+    w->cvt = h->work.raw(n0 * ab);
+    w->hi = h->work.alloc<float>(n0);
+    w->lo = h->work.alloc<float>(n0);
+    w->rout = h->work.alloc<float>(n0);
+    w->u64 = h->work.alloc<double>(n0);
+    w->f64 = h->work.alloc<double>(n0);
+    int64_t rows = 1;
+    for (int l = 0; l < h->L; ++l) rows = std::max<int64_t>(rows, h->lv[l].nb);
+    w->part_rows = rows;
+    w->part = h->work.alloc<double>(rows * 32);
+    w->red = h->work.alloc<double>(12 * 32);
+    w->active = h->work.alloc<int>(8);
+    w->ones = h->work.alloc<double>(8);
+    double ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    GMT_CUDA(cudaMemcpyAsync(w->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream));
+    if (keep.p) {
+      if (prec == P64) canon_to_slots(h, 0, P64, keep.p, w->u64);
+      else canon_to_ff(h, keep.p, w->hi, w->lo);
+    }
+    GMT_CUDA(cudaStreamSynchronize(h->stream));
+  } catch (...) {
+    h->work.release();
+    delete w;
+    h->have_solution = false;   // it lived in the workspace just freed
+    throw;
+  }
   h->ws = w;
   h->ws_for_prec = prec;
-  w->prec = prec;
-  w->arith = prec == P64 ? P64 : P32;
-  const int C = h->mat.C;
-  const size_t sb = prec_bytes(prec), ab = prec_bytes(w->arith);
-  for (int l = 0; l < h->L; ++l) {
-    const int64_t nv = h->lv[l].nslots * C;
-    w->ua.push_back(h->work.raw(nv * sb));
-    w->ub.push_back(h->work.raw(nv * sb));
-    w->f.push_back(h->work.raw(nv * sb));
-    w->r.push_back(h->work.raw(nv * sb));
-    w->dc.push_back(h->work.raw(nv * sb));
-  }
-  const int64_t n0 = h->lv[0].nslots * C;
-  w->x = h->work.raw(n0 * ab);
-  w->rr = h->work.raw(n0 * ab);
-  w->p = h->work.raw(n0 * ab);
-  w->q = h->work.raw(n0 * ab);
-  w->cvt = h->work.raw(n0 * ab);
-  w->hi = h->work.alloc<float>(n0);
-  w->lo = h->work.alloc<float>(n0);
-  w->rout = h->work.alloc<float>(n0);
-  w->u64 = h->work.alloc<double>(n0);
-  w->f64 = h->work.alloc<double>(n0);
-  int64_t rows = 1;
-  for (int l = 0; l < h->L; ++l) rows = std::max<int64_t>(rows, h->lv[l].nb);
-  w->part_rows = rows;
-  w->part = h->work.alloc<double>(rows * 32);
-  w->red = h->work.alloc<double>(12 * 32);
-  w->active = h->work.alloc<int>(8);
-  w->ones = h->work.alloc<double>(8);
-  double ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-  GMT_CUDA(cudaMemcpyAsync(w->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream));
-  if (keep) {
-    if (prec == P64) canon_to_slots(h, 0, P64, keep, w->u64);
-    else canon_to_ff(h, keep, w->hi, w->lo);
-  }
-  GMT_CUDA(cudaStreamSynchronize(h->stream));
-  if (keep) pool_free(keep);
   return w;
 }
 
