@@ -205,6 +205,16 @@ gmt_status gmt_coarse_solve(gmt_hierarchy* h, const double* f, double* u);
 gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u,
                       int zero_init);
 
+/* One V-cycle with injected coarse corrections (Alg. 2): as gmt_vcycle, except that on the
+   way down the coarse unknown of each level l >= 1 starts from the correction e[l] instead
+   of zero and is pre-smoothed from there. e: n_e = gmt_num_levels(h) pointers, e[l] a
+   device canonical field of level l ([node][comp][case] doubles, gmt_num_nodes(h, l)
+   nodes) or NULL for that level's zero start; e[0] is not read (u is the fine level's
+   start), nor is the coarsest level's entry (that level is solved exactly). Read during
+   the call. GMT_ERR_ARG for a W- or F-cycle schedule. */
+gmt_status gmt_vcycle_inject(gmt_hierarchy* h, int precision, const double* f, double* u,
+                             int zero_init, const double* const* e, int n_e);
+
 /* Largest number of hierarchies one gmt_vcycle_batch call takes. */
 #define GMT_BATCH_MAX 64
 

@@ -22,6 +22,11 @@ coordinates, c = (x&1) + 2(y&1) + 4(z&1); nodes of one colour share no stencil e
 each colour is updated at once with the damped block-Jacobi step
 u_c <- u_c + omega (D^{-1} (f - K u))_c on the latest u, colours 0..7 in turn, per sweep.
 
+Injected corrections (Alg. 2): the only change to the recursion is the starting value of
+each coarse unknown on the first descent, a given field e^l instead of zero, from which it
+is pre-smoothed as usual; the fine level starts from the given u. With the coarsest level
+solved exactly, its entry has no effect.
+
 Cycle schedules (Sec. 5 compares V-, W- and F-cycles; it prints no pseudocode): the coarse
 problem of level l is solved by one cycle of the same kind (V), by two W-cycles (the second
 starting from the first's result), or by an F-cycle followed by a V-cycle; the coarsest
@@ -122,7 +127,11 @@ class VCycle:
             rho = rho_new
         return u
 
-    def cycle(self, f, u=None, level: int = 0, kind=None):
+    def cycle(self, f, u=None, level: int = 0, kind=None, e=None):
+        """One cycle on K_level u = f from u (zero if None). e: the injected corrections of
+        Alg. 2, one entry per level (None, or the starting value of that level's coarse
+        unknown on the first descent instead of zero); the coarsest level is solved
+        exactly, so its entry changes nothing."""
         L = len(self.Ks)
         kind = self.kind if kind is None else kind
         if level == L - 1:
@@ -135,7 +144,8 @@ class VCycle:
         u = self.smooth(level, u, f, pre)
         r = f - self.Ks[level] @ u
         fc = self.Ps[level].T @ r
-        uc = self.cycle(fc, None, level + 1, kind)
+        start = None if e is None or e[level + 1] is None else np.array(e[level + 1], dtype=float)
+        uc = self.cycle(fc, start, level + 1, kind, e)
         if level + 2 < L and kind != "V":
             uc = self.cycle(fc, uc, level + 1, "W" if kind == "W" else "V")
         u = u + self.Ps[level] @ uc

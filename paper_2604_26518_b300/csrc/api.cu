@@ -23,6 +23,8 @@ void step_restrict(gmt_hierarchy* h, int level, int precision, const double* rf,
 void step_prolong(gmt_hierarchy* h, int level, int precision, const double* uc, double* uf);
 void step_coarse(gmt_hierarchy* h, const double* f, double* u);
 void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero);
+void step_vcycle_inject(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero,
+                        const double* const* e);
 void step_vcycle_batch(gmt_hierarchy* const* hs, int n, const double* const* f,
                        double* const* u, bool zero);
 void run_batched(gmt_hierarchy* const* hs, int n, const std::function<void(int)>& body);
@@ -359,6 +361,21 @@ gmt_status gmt_vcycle(gmt_hierarchy* h, int precision, const double* f, double* 
   GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
   ensure_device(h);
   gmt::step_vcycle(h, precision, f, u, zero_init != 0);
+  return GMT_OK;
+  GMT_API_END
+}
+
+gmt_status gmt_vcycle_inject(gmt_hierarchy* h, int precision, const double* f, double* u,
+                             int zero_init, const double* const* e, int n_e) {
+  GMT_API_BEGIN
+  need_prepared(h);
+  GMT_REQUIRE(f && u && e, GMT_ERR_ARG, "null argument");
+  GMT_REQUIRE(precision == GMT_PREC_FP64 || precision == GMT_PREC_FP32, GMT_ERR_ARG, "precision");
+  GMT_REQUIRE(n_e == h->L, GMT_ERR_ARG, "n_e = %d, the hierarchy has %d levels", n_e, h->L);
+  GMT_REQUIRE(h->opts.cycle == GMT_CYCLE_V, GMT_ERR_ARG,
+              "corrections are injected into V-cycles only (the options select a W- or F-cycle)");
+  ensure_device(h);
+  gmt::step_vcycle_inject(h, precision, f, u, zero_init != 0, e);
   return GMT_OK;
   GMT_API_END
 }

@@ -118,6 +118,9 @@ struct Workspace {
     gmt_options opts;
     int direct = 0;
   } vg[2];
+  // levels l >= 1 whose coarse unknown starts from the field already in ua[l] instead of
+  // zero on the way down (bit l; set only for the duration of one step_vcycle_inject)
+  unsigned inject = 0;
   ~Workspace() {
     for (Captured& c : vg) retire_graph(c.exec);   // destroyed once no other call is in flight
   }
@@ -352,7 +355,10 @@ static void* vcycle(gmt_hierarchy* h, Workspace* w, int l, const void* f, void* 
   a.out = w->r[l];
   launch_stencil(h, l, pr, ST_RESID, a);
   launch_restrict(h, l, pr, w->r[l], w->f[l + 1]);
-  void* uc = vcycle(h, w, l + 1, w->f[l + 1], nullptr, true, nullptr, cycle);
+  // Alg. 2: the coarse unknown starts from an injected correction where one is given
+  void* uc = ((w->inject >> (l + 1)) & 1u)
+                 ? vcycle(h, w, l + 1, w->f[l + 1], w->ua[l + 1], false, nullptr, cycle)
+                 : vcycle(h, w, l + 1, w->f[l + 1], nullptr, true, nullptr, cycle);
   if (l + 2 < h->L && cycle != GMT_CYCLE_V)
     uc = vcycle(h, w, l + 1, w->f[l + 1], uc, false, nullptr,
                 cycle == GMT_CYCLE_W ? GMT_CYCLE_W : GMT_CYCLE_V);
@@ -999,6 +1005,39 @@ void step_vcycle(gmt_hierarchy* h, int precision, const double* f, double* u, bo
     init = w->ua[0];
   }
   void* res = vcycle(h, w, 0, w->f[0], init, zero);
+  slots_to_canon(h, 0, pr, res, u);
+  GMT_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// One V-cycle in which the coarse unknown of each level l with e[l] != nullptr
+// (1 <= l < L - 1) starts from that canonical field instead of zero (Alg. 2's injected
+// corrections); the coarsest level is solved exactly, so its entry is not read
+void step_vcycle_inject(gmt_hierarchy* h, int precision, const double* f, double* u, bool zero,
+                        const double* const* e) {
+  const Prec pr = precision == GMT_PREC_FP64 ? P64 : P32;
+  if (h->opts.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1 && h->lv[0].lmax == 0.0) estimate_lmax(h);
+  Workspace* w = workspace(h, pr);
+  canon_to_slots(h, 0, pr, f, w->f[0]);
+  void* init = nullptr;
+  if (!zero) {
+    canon_to_slots(h, 0, pr, u, w->ua[0]);
+    init = w->ua[0];
+  }
+  unsigned mask = 0;
+  for (int l = 1; l + 1 < h->L; ++l)
+    if (e[l]) {
+      canon_to_slots(h, l, pr, e[l], w->ua[l]);
+      mask |= 1u << l;
+    }
+  w->inject = mask;
+  void* res = nullptr;
+  try {
+    res = vcycle(h, w, 0, w->f[0], init, zero);
+  } catch (...) {
+    w->inject = 0;
+    throw;
+  }
+  w->inject = 0;
   slots_to_canon(h, 0, pr, res, u);
   GMT_CUDA(cudaStreamSynchronize(h->stream));
 }

@@ -112,6 +112,7 @@ _SIGS = {
     "gmt_coarse_solve": (_I, [_P, _P, _P]),
     "gmt_vcycle": (_I, [_P, _I, _P, _P, _I]),
     "gmt_vcycle_batch": (_I, [_P, _I, _P, _P, _I]),
+    "gmt_vcycle_inject": (_I, [_P, _I, _P, _P, _I, _P, _I]),
     "gmt_solve_batch": (_I, [_P, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P]),
     "gmt_autotune": (_I, [_P, _I, _D, _D, _D, _D, ctypes.POINTER(Options), _P]),
     "gmt_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
@@ -343,11 +344,24 @@ class Hierarchy:
         _check(lib().gmt_coarse_solve(self._h, _ptr(f), _ptr(u)), "gmt_coarse_solve")
         return u
 
-    def vcycle(self, f, u=None, precision=FP64):
+    def vcycle(self, f, u=None, precision=FP64, corrections=None):
+        """One V-cycle on K_0 u = f (gmt_vcycle). corrections: per-level starting fields
+        of the coarse unknowns (Alg. 2's injected corrections, gmt_vcycle_inject), a list
+        of `levels` entries, each None or a level-l field; entry 0 is not used."""
         f = self._field(0, f)
         zero = u is None
         u = self._field(0, u).clone()
-        _check(lib().gmt_vcycle(self._h, precision, _ptr(f), _ptr(u), int(zero)), "gmt_vcycle")
+        if corrections is None:
+            _check(lib().gmt_vcycle(self._h, precision, _ptr(f), _ptr(u), int(zero)),
+                   "gmt_vcycle")
+            return u
+        if len(corrections) != self.levels:
+            raise ValueError(f"{len(corrections)} corrections for {self.levels} levels")
+        es = [None if (l == 0 or c is None) else self._field(l, c)
+              for l, c in enumerate(corrections)]
+        ep = (_P * self.levels)(*[_ptr(x) for x in es])
+        _check(lib().gmt_vcycle_inject(self._h, precision, _ptr(f), _ptr(u), int(zero), ep,
+                                       self.levels), "gmt_vcycle_inject")
         return u
 
     def lambda_max(self, level):

@@ -221,3 +221,33 @@ def test_chebyshev_smoother_matches_closed_form_damping(D, k):
     inside = (w >= a) & (w <= b)
     assert inside.sum() >= n // 2 and (w < a).sum() >= 1
     assert np.all(np.abs(damp[inside]) <= 1.0 / _cheb_T(k, np.array([theta / delta]))[0] + 1e-12)
+
+
+@pytest.mark.parametrize("kind", ["elastic", "heat"])
+def test_injected_corrections_follow_the_error_propagation_form(kind):
+    """Alg. 2's injected coarse start, pinned by the textbook error propagation of the cycle:
+    on three levels, starting level 1's coarse unknown from x instead of zero changes the
+    cycle's output by S0_post P0 S1_post (I - P1 A2 P1^T K1) S1_pre x, S = (I - w D^-1 K)^nu
+    the damped-Jacobi error propagators and A2 the exact coarsest solve; an entry at the
+    coarsest level changes nothing, and corrections that are all None give Alg. 1 exactly."""
+    vox = L.tpms_network("gyroid", 16, 0.3)
+    lv, Ke, x0, D, K1, F, Ks, Ps = _setup(vox, kind, levels=3)
+    vc = vcycle.VCycle(Ks, Ps, D, nu_pre=1, nu_post=1, nu_coarse=2)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((Ks[1].shape[0], F.shape[1]))
+    base = vc.cycle(F)
+    assert np.array_equal(vc.cycle(F, e=[None, None, None]), base)
+    assert np.array_equal(vc.cycle(F, e=[None, None, rng.standard_normal((Ks[2].shape[0], F.shape[1]))]), base)
+
+    def S(l, v, nu):
+        Di = vcycle.block_diag_inverse(Ks[l], D)
+        for _ in range(nu):
+            v = v - 0.6 * (Di @ (Ks[l] @ v))
+        return v
+    d = S(1, x, 2)
+    d = d - Ps[1] @ (vc.Ainv @ (Ps[1].T @ (Ks[1] @ d)))
+    d = S(1, d, 2)
+    d = S(0, Ps[0] @ d, 1)
+    got = vc.cycle(F, e=[None, x, None]) - base
+    assert np.abs(got - d).max() <= 1e-9 * np.abs(d).max(), np.abs(got - d).max() / np.abs(d).max()
+    assert np.abs(d).max() > 1e-3 * np.abs(base).max()     # the injection is not negligible
