@@ -319,7 +319,7 @@ def run_gmt(args, rank: int, world: int):
     gmt.lib()
     cells, desc = workload(args.workload, rank)
     ph = gmt.ELASTIC if args.physics == "elastic" else gmt.HEAT
-    prec = gmt.FP32 if args.precision == "fp32" else gmt.FP64
+    prec = {"fp32": gmt.FP32, "fp64": gmt.FP64, "bf16": gmt.BF16}[args.precision]
     opts = gmt.default_options(precision=prec, coarsest_max=args.coarsest)
     if args.nu:
         opts.nu_pre = opts.nu_post = args.nu
@@ -361,7 +361,7 @@ def run_gmt(args, rank: int, world: int):
     if args.cells:
         cells = cells[:args.cells]
     vals = 18 if ph == gmt.ELASTIC else 3        # values per node (components x cases)
-    esz = 4 if prec == gmt.FP32 else 8           # bytes per value of the V-cycle vectors
+    esz = {gmt.FP32: 4, gmt.FP64: 8, gmt.BF16: 2}[prec]   # bytes per V-cycle vector value
     vox_dev = [torch.from_numpy(v).to(dev) for v, _ in cells]
     vox_host = [torch.from_numpy(v).pin_memory() for v, _ in cells]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -655,14 +655,18 @@ def run_gmt(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": "C^H solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == gmt.FP32 else "f64",
+        "dtype": "f64" if prec == gmt.FP64 else "f32",     # arithmetic (BF16 is storage)
         "data": "synthetic",
         "config": {"workload": desc, "cells_per_step_per_gpu": len(cells),
                    "n": (cells[0][1]["n"] if len({c[1]["n"] for c in cells}) == 1
                          else sorted({c[1]["n"] for c in cells})),
                    "physics": args.physics, "tol": TOL,
-                   "precision": ("fp32 V-cycle CG, float-float outer residual, fp64 coarsest "
-                                 "solve and C^H accumulation") if prec == gmt.FP32 else "fp64",
+                   "precision": {gmt.FP32: "fp32 V-cycle CG, float-float outer residual, fp64 "
+                                           "coarsest solve and C^H accumulation",
+                                 gmt.BF16: "bf16 V-cycle vectors (fp32 arithmetic), fp32 CG, "
+                                           "float-float outer residual, fp64 coarsest solve "
+                                           "and C^H accumulation",
+                                 gmt.FP64: "fp64"}[prec],
                    "step": "hierarchy + operators + solve + C^H per cell",
                    "coarsest_max": args.coarsest,
                    "smoother": "%s, nu_pre %d, nu_post %d" % (
@@ -828,7 +832,8 @@ def main():
     ap.add_argument("--impl", default="gmt", choices=["gmt", "reference"])
     ap.add_argument("--workload", default="c128", choices=["c128", "c32", "c256", "c512", "batch64"])
     ap.add_argument("--physics", default="elastic", choices=["elastic", "heat"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"],
+                    help="inner V-cycle precision (bf16: BF16 vectors, FP32 arithmetic)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-512", dest="with_512", action="store_false",
                     help="skip the 512^3 gyroid sub-result of the c128 line")

@@ -56,8 +56,11 @@ typedef enum {
   GMT_ERR_STATE = 8         /* call needs gmt_prepare / gmt_solve to have run first */
 } gmt_status;
 
-/* GMT_PREC_BF16 (BF16 storage of the V-cycle vectors) is reserved: gmt_solve returns
-   GMT_ERR_ARG for it in this build. */
+/* Precision of a solve's inner V-cycle. GMT_PREC_FP32: FP32 vectors and arithmetic;
+   GMT_PREC_BF16: the V-cycle's vectors stored in BF16 on every level (its input rounded
+   from the FP32 Krylov residual, its result widened back), arithmetic in FP32; both with
+   FP32 Krylov vectors and a float-float solution. GMT_PREC_FP64: everything in FP64. The
+   per-step calls (gmt_apply ... gmt_vcycle) take FP64 or FP32. */
 typedef enum { GMT_PREC_FP64 = 0, GMT_PREC_FP32 = 1, GMT_PREC_BF16 = 2 } gmt_precision;
 typedef enum { GMT_SMOOTH_JACOBI = 0, GMT_SMOOTH_CHEBYSHEV = 1, GMT_SMOOTH_GS8 = 2 } gmt_smoother;
 /* Multigrid cycle of Sec. 5's schedules: V (one coarse correction per level), W (two),
@@ -77,8 +80,8 @@ typedef struct {
   double omega;        /* [0.6] Jacobi damping */
   double cheb_ratio;   /* [30] Chebyshev interval [lmax/cheb_ratio, cheb_upper*lmax] */
   double cheb_upper;   /* [1.1] */
-  int precision;       /* [GMT_PREC_FP32] arithmetic of the inner V-cycle / Krylov loop;
-                          GMT_PREC_FP64 = plain all-FP64 solve */
+  int precision;       /* [GMT_PREC_FP32] precision of the inner V-cycle / Krylov loop
+                          (gmt_precision); GMT_PREC_FP64 = plain all-FP64 solve */
   int krylov;          /* [1] 1: conjugate gradients preconditioned by the V-cycle;
                           0: stationary V-cycle iteration (the paper's GMG loop) */
   double inner_tol;    /* [0.03] mixed precision: the true residual is recomputed (and replaces the

@@ -390,9 +390,19 @@ static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
   double* part = form ? w->part : nullptr;
   const void* aux = form ? w->q : nullptr;
   Workspace::Captured& c = w->vg[form];
+  // the cycle on the FP32 residual rr; the BF16 V-cycle rounds rr to BF16 on entry and
+  // returns its result widened to FP32 in cvt (form 0 only: the fused partials need the
+  // FP32 vectors inside the last sweep)
+  auto body = [&]() -> void* {
+    if (w->prec != PBF) return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+    f32_to_bf16(h, (const float*)w->rr, w->f[0]);
+    void* res = vcycle(h, w, 0, w->f[0], nullptr, true, nullptr, -1, nullptr);
+    bf16_to_f32(h, res, (float*)w->cvt);
+    return w->cvt;
+  };
   auto direct = [&]() {
     TraceScope tv(&h->tracer, h->stream, TR_VCYCLE, 0.0);
-    return vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+    return body();
   };
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   const bool can = h->opts.graphs != 0 && !h->tracer.on && h->stream != nullptr && !batch_thread() &&
@@ -436,7 +446,7 @@ static void* run_vcycle(gmt_hierarchy* h, Workspace* w, int form) {
   GMT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   void* out = nullptr;
   try {
-    out = vcycle(h, w, 0, w->rr, nullptr, true, part, -1, aux);
+    out = body();
   } catch (...) {
     cudaStreamEndCapture(h->stream, &g);
     if (g) cudaGraphDestroy(g);
@@ -514,7 +524,10 @@ static Prec prec_of(int p) { return p == GMT_PREC_FP64 ? P64 : (p == GMT_PREC_BF
 static void smooth_start(gmt_hierarchy* h, Workspace* w, bool mixed) {
   const gmt_options& o = h->opts;
   const Prec pr = mixed ? P32 : P64;
-  void* f = w->f[0];
+  // FP32 sweeps: on a BF16 workspace the level-0 buffers hold BF16, so the load and the
+  // ping-pong partner go to the FP32 scratch cvt and x (x is cleared before the iteration)
+  const bool bf = w->prec == PBF;
+  void* f = bf ? w->cvt : w->f[0];
   if (mixed) {
     launch_resid_ff(h, nullptr, nullptr, (float*)f, nullptr);   // the load (zero start)
   } else {
@@ -525,7 +538,7 @@ static void smooth_start(gmt_hierarchy* h, Workspace* w, bool mixed) {
     launch_stencil(h, 0, P64, ST_RESID, r);
   }
   void* cur = mixed ? (void*)w->hi : (void*)w->u64;
-  void* oth = w->ua[0];
+  void* oth = bf ? w->x : w->ua[0];
   for (int k = 0; k < o.warm_sweeps; ++k) {
     VecArgs a;
     a.u = cur;
@@ -544,7 +557,6 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
   auto t0 = std::chrono::steady_clock::now();
   const gmt_options& o = h->opts;
   const Prec pr = prec_of(o.precision);
-  GMT_REQUIRE(pr != PBF, GMT_ERR_ARG, "BF16 inner precision is not available in this build");
   if (o.smoother == GMT_SMOOTH_CHEBYSHEV && h->L > 1 && h->lv[0].lmax == 0.0) estimate_lmax(h);
   Workspace* w = workspace(h, pr);
   const int M = h->mat.M, C = h->mat.C;
@@ -763,7 +775,7 @@ gmt_status solve(gmt_hierarchy* h, double tol, const double* u0, double* u_out, 
       }
       // the last post-smoothing sweep writes the partials of r.z, q.z (q = K p of the last
       // direction) and of the sums of z
-      const bool fused = krylov && h->L > 1 && o.nu_post >= 1;
+      const bool fused = krylov && h->L > 1 && o.nu_post >= 1 && w->prec != PBF;
       z = run_vcycle(h, w, fused ? 1 : 0);
       ++cycles;
       if (krylov) {

@@ -710,6 +710,18 @@ __global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__
   if (i < n) dst[i] = (float)src[i];
 }
 
+__global__ void k_f32_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                              int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__global__ void k_bf16_to_f32(const __nv_bfloat16* __restrict__ src, float* __restrict__ dst,
+                              int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __bfloat162float(src[i]);
+}
+
 template <typename TS, typename A, int D, int M>
 static void restrict_t(gmt_hierarchy* h, int level, const void* rf, void* fc) {
   const Level& c = h->lv[level + 1];
@@ -1137,6 +1149,18 @@ void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst) 
 void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst) {
   const int64_t n = nvals(h, 0);
   k_f64_to_f32<<<grid_for(n, 256), 256, 0, h->stream>>>(src, dst, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void f32_to_bf16(gmt_hierarchy* h, const float* src, void* dst) {
+  const int64_t n = nvals(h, 0);
+  k_f32_to_bf16<<<grid_for(n, 256), 256, 0, h->stream>>>(src, (__nv_bfloat16*)dst, n);
+  GMT_LAUNCH_CHECK();
+}
+
+void bf16_to_f32(gmt_hierarchy* h, const void* src, float* dst) {
+  const int64_t n = nvals(h, 0);
+  k_bf16_to_f32<<<grid_for(n, 256), 256, 0, h->stream>>>((const __nv_bfloat16*)src, dst, n);
   GMT_LAUNCH_CHECK();
 }
 

@@ -125,8 +125,10 @@ void slots_to_canon(gmt_hierarchy* h, int level, Prec prec, const void* src, dou
 void canon_to_ff(gmt_hierarchy* h, const double* src, float* hi, float* lo);
 void ff_to_canon(gmt_hierarchy* h, const float* hi, const float* lo, double* dst);
 void ff_to_f64(gmt_hierarchy* h, const float* hi, const float* lo, double* dst);
-// level-0 slot field FP64 -> FP32
+// level-0 slot field FP64 -> FP32, FP32 -> BF16 (round to nearest even), BF16 -> FP32
 void f64_to_f32(gmt_hierarchy* h, const double* src, float* dst);
+void f32_to_bf16(gmt_hierarchy* h, const float* src, void* dst);
+void bf16_to_f32(gmt_hierarchy* h, const void* src, float* dst);
 
 inline int64_t blocks_of(const Level& lv) { return lv.nb; }
 

@@ -143,27 +143,28 @@ void build_node_stencils16(gmt_hierarchy* h, int level) {
 }
 
 // ------------------------------------------------------------------ dispatch
-// The V-cycle stores its vectors in FP32 or FP64; BF16 storage is reserved (gmt_solve
-// rejects it), so the operator kernels are built for the two.
+// The V-cycle stores its vectors in FP64, FP32 or BF16 (FP32 arithmetic for the last two).
 void launch_stencil(gmt_hierarchy* h, int level, Prec prec, StencilMode mode, const VecArgs& a) {
-  GMT_REQUIRE(prec != PBF, GMT_ERR_ARG, "BF16 vectors are not available in this build");
   if (h->mat.D == 3) {
     if (prec == P64) stencil_el64(h, level, mode, a);
+    else if (prec == PBF) stencil_elbf(h, level, mode, a);
     else stencil_el32(h, level, mode, a);
   } else {
     if (prec == P64) stencil_heat64(h, level, mode, a);
+    else if (prec == PBF) stencil_heatbf(h, level, mode, a);
     else stencil_heat32(h, level, mode, a);
   }
 }
 
 void launch_diag(gmt_hierarchy* h, int level, Prec prec, const void* f, void* out, void* dout,
                  double scale) {
-  GMT_REQUIRE(prec != PBF, GMT_ERR_ARG, "BF16 vectors are not available in this build");
   if (h->mat.D == 3) {
     if (prec == P64) diag_el64(h, level, f, out, dout, scale);
+    else if (prec == PBF) diag_elbf(h, level, f, out, dout, scale);
     else diag_el32(h, level, f, out, dout, scale);
   } else {
     if (prec == P64) diag_heat64(h, level, f, out, dout, scale);
+    else if (prec == PBF) diag_heatbf(h, level, f, out, dout, scale);
     else diag_heat32(h, level, f, out, dout, scale);
   }
 }

@@ -699,8 +699,13 @@ static void resid_ff_t(gmt_hierarchy* h, const float* hi, const float* lo, float
   GMT_LAUNCH_CHECK();
 }
 
-// per physics / precision instances (stencil_el32.cu, stencil_el64.cu, stencil_heat.cu)
+// per physics / precision instances (stencil_el32.cu, stencil_el64.cu, stencil_heat.cu,
+// stencil_bf16.cu)
 void stencil_el32(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
+void stencil_elbf(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
+void stencil_heatbf(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
+void diag_elbf(gmt_hierarchy* h, int level, const void* f, void* out, void* dout, double s);
+void diag_heatbf(gmt_hierarchy* h, int level, const void* f, void* out, void* dout, double s);
 void stencil_el64(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
 void stencil_heat32(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
 void stencil_heat64(gmt_hierarchy* h, int level, StencilMode mode, const VecArgs& a);
