@@ -218,11 +218,13 @@ class Hierarchy:
         if isinstance(voxels, np.ndarray):
             vox = np.ascontiguousarray(voxels, dtype=np.uint8)
             n = vox.shape[0]
-            assert vox.shape == (n, n, n)
+            if vox.shape != (n, n, n):
+                raise ValueError(f"voxels must be a cube, got shape {vox.shape}")
             src, on_dev, self._keep = vox.ctypes.data, 0, vox
         else:
             vox = voxels.contiguous()
-            assert vox.dtype == torch.uint8 and vox.dim() == 3
+            if vox.dtype != torch.uint8 or vox.dim() != 3 or len(set(vox.shape)) != 1:
+                raise ValueError(f"voxels must be a uint8 cube, got {vox.dtype} {tuple(vox.shape)}")
             n = vox.shape[0]
             src, on_dev, self._keep = vox.data_ptr(), int(vox.is_cuda), vox
         self.n = int(n)
@@ -309,7 +311,8 @@ class Hierarchy:
         if x is None:
             return torch.zeros((n, D, M), dtype=torch.float64, device="cuda")
         x = torch.as_tensor(x, dtype=torch.float64, device="cuda").contiguous()
-        assert x.numel() == n * D * M, (x.shape, n, D, M)
+        if x.numel() != n * D * M:   # the library reads exactly n * D * M values
+            raise ValueError(f"level-{l} field has {x.numel()} values, expected {n * D * M}")
         return x.view(n, D, M)
 
     def apply(self, level, u, precision=FP64):
@@ -411,12 +414,14 @@ class Hierarchy:
         ne = self.num_elements(0)
         if isinstance(rho, np.ndarray):
             r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
-            assert r.size == ne, (r.size, ne)
+            if r.size != ne:
+                raise ValueError(f"{r.size} densities for {ne} elements")
             ptr, dev, keep = r.ctypes.data, 0, r
         else:
             torch = _torch()
             r = rho.to(torch.float64).contiguous().reshape(-1)
-            assert r.numel() == ne, (r.numel(), ne)
+            if r.numel() != ne:
+                raise ValueError(f"{r.numel()} densities for {ne} elements")
             ptr, dev, keep = r.data_ptr(), int(r.is_cuda), r
         _check(lib().gmt_set_densities(self._h, ptr, dev, float(rho_min), float(p)),
                "gmt_set_densities")

@@ -124,6 +124,29 @@ def test_repeat_runs_bitwise_identical(gmt_lib):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+def test_binding_rejects_mis_sized_inputs(gmt_lib):
+    """A field, density vector or voxel array of the wrong size never reaches the library:
+    the binding raises ValueError (the library reads exactly the sizes it expects)."""
+    import torch
+    gmt = gmt_lib
+    h = gmt.Hierarchy(L.tpms_network("gyroid", 16, 0.3))
+    h.prepare(gmt.ELASTIC)
+    n = h.num_nodes(0)
+    for bad in (np.zeros((n - 1) * 18), torch.zeros(n * 18 + 6, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            h.apply(0, bad, gmt.FP64)
+    with pytest.raises(ValueError):
+        h.vcycle(np.zeros(n * 18), None, gmt.FP64,
+                 corrections=[None, np.zeros(5)] + [None] * (h.levels - 2))
+    with pytest.raises(ValueError):
+        h.set_densities(np.ones(h.num_elements(0) + 1))
+    with pytest.raises(ValueError):
+        gmt.Hierarchy(np.zeros((8, 8, 4), dtype=np.uint8))
+    with pytest.raises(ValueError):
+        gmt.Hierarchy(torch.zeros((8, 8, 4), dtype=torch.uint8))
+    h.free()
+
+
 @pytest.mark.parametrize("kind", ["elastic", "heat"])
 def test_stored_solution_survives_other_calls(gmt_lib, kind):
     """Calls between gmt_solve and C^H of the stored solution leave that solution as it was:
