@@ -69,3 +69,18 @@ def test_bf16_warm_sweeps_and_full_size_128(gmt_lib):
     CH32 = h.homogenize(gmt.ELASTIC)
     h.free()
     assert np.abs(CH16 - CH32).max() <= 1e-4 * np.abs(CH32).max()
+
+
+@pytest.mark.parametrize("smoother", ["chebyshev", "gs8"])
+def test_bf16_solve_other_smoothers(gmt_lib, smoother):
+    """The BF16 instances of the Chebyshev and 8-colour Gauss-Seidel sweeps: solves reach the
+    tolerance with C^H within 1e-4 of the converged oracle."""
+    gmt = gmt_lib
+    vox = CELLS["gyroid32"]()
+    ref = solve.solve_cell(vox, "elastic", tol=1e-10)["CH"]
+    sm = gmt.CHEBYSHEV if smoother == "chebyshev" else gmt.GS8
+    h = gmt.Hierarchy(vox, gmt.default_options(precision=gmt.BF16, smoother=sm))
+    st, _, info = h.solve(gmt.ELASTIC, tol=TOL, want_field=False)
+    assert st == gmt.OK and max(info.as_dict()["rel_residual"]) <= TOL
+    assert np.abs(h.homogenize(gmt.ELASTIC) - ref).max() <= 1e-4 * np.abs(ref).max()
+    h.free()

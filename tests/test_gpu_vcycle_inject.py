@@ -62,6 +62,35 @@ def test_injected_vcycle_matches_oracle(gmt_lib, name, kind):
     h.free()
 
 
+@pytest.mark.parametrize("smoother", ["chebyshev", "gs8"])
+def test_injected_vcycle_other_smoothers(gmt_lib, smoother):
+    """The injected start goes through the Chebyshev and 8-colour Gauss-Seidel smoothers'
+    nonzero-start paths: against the oracle's cycle with the same corrections."""
+    gmt = gmt_lib
+    vox = CELLS["gyroid32"]()
+    sm = gmt.CHEBYSHEV if smoother == "chebyshev" else gmt.GS8
+    h = gmt.Hierarchy(vox, gmt.default_options(smoother=sm))
+    h.prepare(gmt.ELASTIC)
+    O = oracle_setup(vox, "elastic", h.levels)
+    o = gmt.default_options()
+    kw = {}
+    if smoother == "chebyshev":
+        kw = {"cheb_lmax": [h.lambda_max(l) for l in range(h.levels - 1)]}
+    else:
+        kw = {"levels": O["levels"]}
+    vc = vcycle.VCycle(O["Ks"], O["Ps"], 3, smoother=smoother, nu_pre=o.nu_pre,
+                       nu_post=o.nu_post, nu_coarse=o.nu_coarse, **kw)
+    rng = np.random.default_rng(9)
+    F = O["F"]
+    scale = np.abs(vc.cycle(F)).max()
+    e = [None] + [0.3 * scale * rng.standard_normal((h.num_nodes(l) * 3, 6))
+                  for l in range(1, h.levels)]
+    ref = vc.cycle(F, e=e)
+    got = to_np(h.vcycle(F, None, gmt.FP64, corrections=e), 3, 6)
+    assert rel_err(got, ref) < 1e-10, rel_err(got, ref)
+    h.free()
+
+
 def test_injection_rejects_bad_calls(gmt_lib):
     gmt = gmt_lib
     vox = CELLS["gyroid32"]()
