@@ -251,12 +251,14 @@ gmt_status gmt_solve(gmt_hierarchy* h, gmt_physics physics, double E, double nu,
                      double tol, const double* u0, double* u_out, gmt_info* info);
 
 /* Number of option sets gmt_autotune tries. */
-#define GMT_AUTOTUNE_CANDIDATES 12
+#define GMT_AUTOTUNE_CANDIDATES 13
 
 /* Solver-schedule autotuner: solves this hierarchy's cell problems to tol once per
-   candidate and keeps the fastest. Candidate i (0..GMT_AUTOTUNE_CANDIDATES-1) sets
-   nu_pre = nu_post = 1 + i / 6, nu_coarse = 1 + (i / 2) % 3, coarse_fp16 = i % 2 (with
-   GMT_PREC_FP64 the FP16 candidates are skipped); the other options stay the hierarchy's.
+   candidate and keeps the fastest. Candidate i (0..11) sets nu_pre = nu_post = 1 + i / 6,
+   nu_coarse = 1 + (i / 2) % 3, coarse_fp16 = i % 2 (with GMT_PREC_FP64 the FP16 candidates
+   are skipped); candidate 12 is the fastest of those with inner_tol = 0.003 (mixed
+   precision, when the hierarchy's inner_tol is larger; else skipped); the other options
+   stay the hierarchy's.
    Each solve starts from zero and is timed with CUDA events on the hierarchy's stream,
    after one untimed solve and after the lazily built operators of every candidate exist.
    The fastest candidate that returned GMT_OK is set on the hierarchy and written to best

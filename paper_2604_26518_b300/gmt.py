@@ -147,7 +147,7 @@ _SIGS = {
 }
 
 TRACE_CATEGORIES = 16
-AUTOTUNE_CANDIDATES = 12
+AUTOTUNE_CANDIDATES = 13
 
 
 def release_cached_memory():
